@@ -1,0 +1,131 @@
+"""Oracle for the split-precision modes (Ozaki-style error-free slicing).
+
+TEST INFRASTRUCTURE ONLY: the library never imports this module.
+
+The paper multiplies in FP64 with a BLAS DGEMM per tile task (Sec. 4.1). The
+split modes compute the same tile tasks C_ij += A_ik B_kj (Sec. 2.1) with the
+bulk of the arithmetic on low-precision integers, following the error-free
+splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59, 2012), with one
+power-of-two scale per tile:
+
+  slicing of a tile X (beta = bits per slice, s = slices):
+    mu = max |x|;  e = the smallest integer with mu < 2^e  (mu == 0: e = 0, slices 0)
+    rho_0 = X * 2^-e                               (exact, |rho_0| < 1)
+    for t = 1..s:  N_t = rint(rho_{t-1} * 2^(beta*t))    (round half to even)
+                   rho_t = rho_{t-1} - N_t * 2^(-beta*t)  (exact)
+    so X = 2^e * sum_t N_t 2^(-beta*t) + 2^e * rho_s,  |rho_s| <= 2^(-beta*s - 1)
+    and |N_1| <= 2^beta, |N_t| <= 2^(beta-1) for t >= 2.
+
+  product of one tile pair (A tile: e_A, NA_p;  B tile: e_B, NB_q):
+    S_d = sum_{p+q=d} NA_p NB_q           (integer matrices, d = 2..s+1; pairs with
+                                           p+q > s+1 are dropped)
+    T   = sum_d S_d * 2^(beta*(s+1-d))    (an exact integer)
+    contribution = T * 2^(e_A + e_B - beta*(s+1))
+
+  accumulation over k in ascending order, one rounding each:
+    acc <- fl( acc + fl(T) * 2^(e_A + e_B - beta*(s+1)) )
+  and the epilogue C_ij = fl(alpha*acc) + fl(beta*C_ij), as in the FP64 oracle.
+
+fl(T) rounds the exact integer T to FP64 once (round to nearest even), and the
+multiplication by a power of two is exact, so every value here is determined
+independently of how the integer sums are formed.
+
+All integer matrix products below go through a float64 matmul: every entry is an
+integer of magnitude below 2^53, so the library routine returns it exactly in
+any summation order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BETA_BITS = 7
+
+
+def tile_exponent(x: np.ndarray) -> int:
+    """Smallest integer e with max|x| < 2^e (0 for an all-zero or empty tile)."""
+    if x.size == 0:
+        return 0
+    mu = float(np.max(np.abs(x)))
+    if mu == 0.0:
+        return 0
+    _, e = np.frexp(mu)
+    return int(e)
+
+
+def slice_tile(x: np.ndarray, s: int, beta: int = BETA_BITS):
+    """Error-free slicing of one tile. Returns (e, [N_1..N_s] as float64 integer
+    matrices, rho_s residual in units of 2^e)."""
+    e = tile_exponent(x)
+    rho = np.ldexp(np.asarray(x, np.float64), -e)
+    slices = []
+    for t in range(1, s + 1):
+        n_t = np.rint(np.ldexp(rho, beta * t))
+        rho = rho - np.ldexp(n_t, -beta * t)
+        slices.append(n_t)
+    return e, slices, rho
+
+
+def pair_integer(na, nb, s: int, beta: int = BETA_BITS) -> np.ndarray:
+    """T = sum_d S_d 2^(beta(s+1-d)) for one tile pair, as an int64 matrix."""
+    r = na[0].shape[0]
+    c = nb[0].shape[1]
+    T = np.zeros((r, c), np.int64)
+    if r == 0 or c == 0:
+        return T
+    for d in range(2, s + 2):
+        Sd = np.zeros((r, c), np.float64)
+        for p in range(1, d):
+            q = d - p
+            if p > s or q > s:
+                continue
+            Sd += na[p - 1] @ nb[q - 1]
+        T += Sd.astype(np.int64) << np.int64(beta * (s + 1 - d))
+    return T
+
+
+def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, tiles=None):
+    """Split-mode product in place on the C arena (numpy arrays). ``prob_like``
+    carries row_sizes, col_sizes, inner_sizes, a_mask, b_mask, a_off, b_off, A, B,
+    alpha, beta. ``tiles`` restricts the work to a list of (i, j) C tiles."""
+    r = np.asarray(prob_like.row_sizes, np.int64)
+    c = np.asarray(prob_like.col_sizes, np.int64)
+    q = np.asarray(prob_like.inner_sizes, np.int64)
+    M, N, K = len(r), len(c), len(q)
+    am, bm = prob_like.a_mask, prob_like.b_mask
+    cacheA, cacheB = {}, {}
+
+    def a_sl(i, k):
+        if (i, k) not in cacheA:
+            o = int(prob_like.a_off[i, k])
+            x = prob_like.A[o:o + r[i] * q[k]].reshape(r[i], q[k])
+            e, sl, _ = slice_tile(x, s, beta)
+            cacheA[(i, k)] = (e, sl)
+        return cacheA[(i, k)]
+
+    def b_sl(k, j):
+        if (k, j) not in cacheB:
+            o = int(prob_like.b_off[k, j])
+            x = prob_like.B[o:o + q[k] * c[j]].reshape(q[k], c[j])
+            e, sl, _ = slice_tile(x, s, beta)
+            cacheB[(k, j)] = (e, sl)
+        return cacheB[(k, j)]
+
+    todo = tiles if tiles is not None else [(i, j) for i in range(M) for j in range(N) if c_struct[i, j]]
+    alpha, bet = float(prob_like.alpha), float(prob_like.beta)
+    for (i, j) in todo:
+        acc = np.zeros((r[i], c[j]), np.float64)
+        for k in range(K):
+            if not (am[i, k] and bm[k, j]):
+                continue
+            eA, na = a_sl(i, k)
+            eB, nb = b_sl(k, j)
+            T = pair_integer(na, nb, s, beta)
+            acc = acc + np.ldexp(T.astype(np.float64), eA + eB - beta * (s + 1))
+        o = int(c_off[i, j])
+        ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
+        u = alpha * acc
+        if bet != 0.0:
+            ct[...] = u + bet * ct
+        else:
+            ct[...] = u
+    return C

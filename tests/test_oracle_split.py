@@ -1,0 +1,206 @@
+"""Pins of the split-precision oracle (Ozaki-style slicing) against facts fixed
+outside it: exact rational reconstruction, the slicing bounds, a pure-integer
+brute force of the pair sums, the analytic truncation bound, integer inputs,
+bfloat16/float16 representability, and the error against the FP64 oracle."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import bsmm_gen as G
+import oracle
+from oracle import split as S
+from helpers import c_arena, exact_tile_fraction, rel_fro, struct_elements
+
+
+def _wide_tile(rng, r, c, spread):
+    """Entries with random signs and magnitudes spread over ``spread`` binades."""
+    mag = np.ldexp(rng.uniform(0.5, 1.0, (r, c)), rng.integers(-spread, 1, (r, c)))
+    return mag * rng.choice([-1.0, 1.0], (r, c)) * 2.0 ** rng.integers(-30, 30)
+
+
+def test_tile_exponent_definition():
+    cases = [np.array([[1.0]]), np.array([[0.75, -0.5]]), np.array([[-2.0, 1.0]]),
+             np.array([[3.0e-310]]), np.array([[1.5e300, -1.0]]), np.array([[0.0, 0.0]]),
+             np.array([[2.0 ** -1074]]), np.array([[np.nextafter(1.0, 0.0)]])]
+    for x in cases:
+        e = S.tile_exponent(x)
+        mu = float(np.max(np.abs(x)))
+        if mu == 0.0:
+            assert e == 0
+            continue
+        # smallest integer e with mu < 2^e, checked with exact rationals
+        assert Fraction(mu) < Fraction(2) ** e
+        assert not (Fraction(mu) < Fraction(2) ** (e - 1))
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("seed", range(4))
+def test_slicing_exact_reconstruction_and_bounds(s, seed):
+    rng = np.random.default_rng(seed * 10 + s)
+    x = _wide_tile(rng, 5, 7, spread=60)
+    beta = S.BETA_BITS
+    e, sl, rho = S.slice_tile(x, s)
+    assert len(sl) == s
+    for t, n in enumerate(sl, start=1):
+        assert np.array_equal(n, np.rint(n))                 # integers
+        lim = 2 ** beta if t == 1 else 2 ** (beta - 1)
+        assert np.max(np.abs(n)) <= lim
+    assert np.max(np.abs(rho)) <= 2.0 ** (-beta * s - 1)
+    for ii in range(x.shape[0]):
+        for jj in range(x.shape[1]):
+            rec = sum(Fraction(float(sl[t - 1][ii, jj])) * Fraction(2) ** (-beta * t) for t in range(1, s + 1))
+            rec += Fraction(float(rho[ii, jj]))
+            assert rec * Fraction(2) ** e == Fraction(float(x[ii, jj]))
+
+
+@pytest.mark.parametrize("s", [6, 7, 8])
+def test_slicing_narrow_range_is_error_free(s):
+    """Elements within a few binades of the tile maximum: s*beta >= 53 + spread leaves
+    a zero residual, so the slices alone reproduce every element."""
+    rng = np.random.default_rng(s)
+    x = _wide_tile(rng, 6, 6, spread=2)
+    e, sl, rho = S.slice_tile(x, s)
+    if s * S.BETA_BITS >= 53 + 3:
+        assert np.all(rho == 0.0)
+        back = sum(np.ldexp(sl[t - 1], e - S.BETA_BITS * t) for t in range(1, s + 1))
+        assert np.array_equal(back, x)
+
+
+def test_slices_representable_in_bf16_and_fp16():
+    rng = np.random.default_rng(1)
+    x = _wide_tile(rng, 32, 32, spread=40)
+    _, sl, _ = S.slice_tile(x, 6)
+    for n in sl:
+        t = torch.from_numpy(n.astype(np.float32))
+        assert torch.equal(t.to(torch.bfloat16).to(torch.float32), t)
+        assert torch.equal(t.to(torch.float16).to(torch.float32), t)
+
+
+@pytest.mark.parametrize("s", [1, 3, 6])
+def test_pair_integer_brute_force(s):
+    """T = sum_{p+q<=s+1} N^A_p N^B_q 2^(beta(s+1-p-q)) by explicit Python-integer loops."""
+    rng = np.random.default_rng(s)
+    a = _wide_tile(rng, 4, 5, 20)
+    b = _wide_tile(rng, 5, 3, 20)
+    _, na, _ = S.slice_tile(a, s)
+    _, nb, _ = S.slice_tile(b, s)
+    T = S.pair_integer(na, nb, s)
+    beta = S.BETA_BITS
+    for i in range(4):
+        for j in range(3):
+            tot = 0
+            for p in range(1, s + 1):
+                for q in range(1, s + 1):
+                    if p + q > s + 1:
+                        continue
+                    dot = 0
+                    for k in range(5):
+                        dot += int(na[p - 1][i, k]) * int(nb[q - 1][k, j])
+                    tot += dot << (beta * (s + 1 - p - q))
+            assert int(T[i, j]) == tot
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 6])
+@pytest.mark.parametrize("seed", range(3))
+def test_split_within_truncation_bound(s, seed):
+    """|C_split - C_exact| <= sum_k q_k (s+3) 2^(-beta s) 2^(eA+eB) |alpha| + rounding, where the
+    first term bounds the dropped slice pairs (p+q > s+1) and the slicing residuals."""
+    prob = G.random_small(seed + 300, max_blocks=4, max_size=8)
+    prob.beta = 0.0
+    cs, _, _ = oracle.structure(prob)
+    off, C = c_arena(prob, cs, fill=0.0)
+    S.bsmm_split(prob, cs, C, off, s)
+    beta = S.BETA_BITS
+    u = 2.0 ** -53
+    for i in range(prob.M):
+        for j in range(prob.N):
+            if not cs[i, j]:
+                continue
+            ex = exact_tile_fraction(prob, i, j)
+            r, c = int(prob.row_sizes[i]), int(prob.col_sizes[j])
+            got = C[off[i, j]:off[i, j] + r * c].reshape(r, c)
+            bound = 0.0
+            mag = 0.0
+            nk = 0
+            for k in range(prob.K):
+                if prob.a_mask[i, k] and prob.b_mask[k, j]:
+                    At = G.tile_view(prob.A, prob.a_off, prob.row_sizes, prob.inner_sizes, i, k)
+                    Bt = G.tile_view(prob.B, prob.b_off, prob.inner_sizes, prob.col_sizes, k, j)
+                    eA, eB = S.tile_exponent(At), S.tile_exponent(Bt)
+                    bound += int(prob.inner_sizes[k]) * (s + 3) * 2.0 ** (-beta * s + eA + eB)
+                    mag += int(prob.inner_sizes[k]) * 2.0 ** (eA + eB)
+                    nk += 1
+            bound = abs(prob.alpha) * (bound + (nk + 2) * u * mag) + 1e-300
+            for ii in range(r):
+                for jj in range(c):
+                    assert abs(float(Fraction(float(got[ii, jj])) - ex[ii][jj])) <= bound
+
+
+def test_dropping_a_pair_diagonal_breaks_the_bound():
+    """Sanity of the bound above: keeping only p+q <= s (one diagonal short) exceeds it."""
+    rng = np.random.default_rng(0)
+    a = rng.uniform(-1, 1, (8, 16))
+    b = rng.uniform(-1, 1, (16, 8))
+    s = 4
+    eA, na, _ = S.slice_tile(a, s)
+    eB, nb, _ = S.slice_tile(b, s)
+    beta = S.BETA_BITS
+    T_short = S.pair_integer(na[:s - 1] + [np.zeros_like(na[0])], nb[:s - 1] + [np.zeros_like(nb[0])], s)
+    approx = np.ldexp(T_short.astype(np.float64), eA + eB - beta * (s + 1))
+    err = np.max(np.abs(approx - a @ b))
+    assert err > 16 * (s + 3) * 2.0 ** (-beta * s + eA + eB)
+
+
+@pytest.mark.parametrize("s", [1, 2, 6])
+def test_integer_inputs_split_equals_exact(s):
+    """Entries in [-8, 8]: each tile scaled by 2^-e has at most 4 significant bits, the
+    first slice holds it exactly, and the split product is the exact integer product."""
+    prob = G.random_small(77 + s, max_blocks=5, max_size=20, values="integers")
+    prob.alpha, prob.beta = 2.0, 0.0
+    cs, _, _ = oracle.structure(prob)
+    off, C64 = c_arena(prob, cs, fill=0.0)
+    oracle.bsmm(prob, cs, C64, off)
+    Cs = np.zeros_like(C64)
+    S.bsmm_split(prob, cs, Cs, off, s)
+    assert np.array_equal(struct_elements(prob, cs, off, Cs), struct_elements(prob, cs, off, C64))
+
+
+@pytest.mark.parametrize("s,tol", [(3, 1e-5), (4, 1e-7), (5, 1e-9), (6, 1e-11)])
+def test_split_error_vs_fp64_oracle(s, tol):
+    prob = G.make_problem("nonuniform_dense", 21, 300, lo=24, hi=80)
+    cs, _, _ = oracle.structure(prob)
+    off, C64 = c_arena(prob, cs, fill=0.0)
+    oracle.bsmm(prob, cs, C64, off)
+    Cs = np.zeros_like(C64)
+    S.bsmm_split(prob, cs, Cs, off, s)
+    err = rel_fro(struct_elements(prob, cs, off, Cs), struct_elements(prob, cs, off, C64))
+    assert err <= tol
+
+
+def test_split_decay_tiles_keep_relative_accuracy():
+    """Banded tiles with norms over ~6 orders: per-tile scales keep the error relative."""
+    prob = G.make_problem("banded_decay_wide", 4, 400, lo=16, hi=48, band=3)
+    cs, _, _ = oracle.structure(prob)
+    off, C64 = c_arena(prob, cs, fill=0.0)
+    oracle.bsmm(prob, cs, C64, off)
+    Cs = np.zeros_like(C64)
+    S.bsmm_split(prob, cs, Cs, off, 6)
+    assert rel_fro(struct_elements(prob, cs, off, Cs), struct_elements(prob, cs, off, C64)) <= 1e-11
+
+
+def test_split_alpha_beta_epilogue():
+    prob = G.random_small(5, max_blocks=4, max_size=10)
+    prob.alpha, prob.beta = -0.75, 2.0
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, rng=np.random.default_rng(3))
+    C1 = C0.copy()
+    S.bsmm_split(prob, cs, C1, off, 6)
+    prob2 = G.Problem(**{**prob.__dict__})
+    prob2.alpha, prob2.beta = 1.0, 0.0
+    Cp = np.zeros_like(C0)
+    S.bsmm_split(prob2, cs, Cp, off, 6)
+    want = -0.75 * struct_elements(prob, cs, off, Cp) + 2.0 * struct_elements(prob, cs, off, C0)
+    assert np.array_equal(struct_elements(prob, cs, off, C1), want)
