@@ -1,0 +1,186 @@
+/*
+ * bsmm.h - block-sparse, irregularly tiled matrix product C = alpha*A*B + beta*C
+ * on one GB300 (sm_103a).
+ *
+ * The operation (Calvin & Valeev, "Task-Based Algorithm for Matrix
+ * Multiplication", SC15, Sec. 2.1 and Algorithm 1): the matrices are cut by
+ * three tilings -- row blocks r[0..M), column blocks c[0..N), inner blocks
+ * q[0..K) -- of arbitrary, nonuniform sizes (Sec. 3.2, data overdecomposition
+ * into arbitrarily sized blocks; Sec. 4.1, nonuniform blocking). A and B store
+ * only the tiles their masks mark nonzero (block sparsity, Sec. 1). The product
+ * is the set of tile tasks
+ *
+ *     C_ij <- alpha * sum_{k ascending : a[i][k] and b[k][j]} A_ik B_kj + beta * C_ij
+ *
+ * over the nonzero triples (i,k,j) (the rank-k updates of Sec. 2.1, the alpha
+ * of Algorithm 1; beta*C is the usual GEMM input term). The C tile set S_C is
+ * the boolean product of the masks, united with an optional C mask.
+ *
+ * Storage conventions (all entry points):
+ *   - Every stored tile is row-major and contiguous; its leading dimension is its
+ *     column-block size. A tile of A is r_i x q_k, of B q_k x c_j, of C r_i x c_j.
+ *   - Tiles live in caller-owned arenas (one double array per matrix). Offset
+ *     tables are int64 element offsets into the arena, row-major over the tile
+ *     grid (a_off: M x K, b_off: K x N, c_off: M x N), -1 for an absent tile.
+ *     Offsets of present tiles must be even (every tile 16-byte aligned).
+ *   - Block sizes are >= 0; a zero-size block is allowed.
+ *   - beta == 0 never reads C (NaN already in C is ignored).
+ *
+ * Ownership: the caller owns A, B, C and the offset tables. A plan owns its
+ * device task tables and its work buffers (the split modes' slice arenas)
+ * until bsmm_destroy.
+ *
+ * Errors: every entry point returns a bsmm_status and never throws or aborts;
+ * bsmm_last_error() gives a message for the calling thread. Kernels never trap:
+ * bounded waits and checks set a device error word that bsmm_status_device
+ * reads.
+ *
+ * Streams: entry points taking `stream` accept a cudaStream_t passed as void*
+ * (NULL = the legacy default stream). They are asynchronous with respect to the
+ * host unless stated otherwise, and never synchronise the device.
+ */
+#ifndef BSMM_H
+#define BSMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsmm_plan_s* bsmm_plan_t;
+
+typedef enum {
+  BSMM_OK = 0,
+  BSMM_ERR_INVALID = 1,      /* bad argument, layout, size or mask */
+  BSMM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  BSMM_ERR_NOMEM = 3,        /* host or device allocation failed */
+  BSMM_ERR_TIMEOUT = 4,      /* a kernel's bounded wait ran out (device error word) */
+  BSMM_ERR_UNSUPPORTED = 5,  /* a mode or size this build does not handle */
+  BSMM_ERR_DEVICE = 6        /* a kernel check failed (device error word) */
+} bsmm_status;
+
+typedef enum {
+  BSMM_FP64 = 0,        /* plain FP64 tile tasks */
+  BSMM_SPLIT_BF16 = 1,  /* Ozaki-style slices stored as bfloat16, tcgen05 tensor cores */
+  BSMM_SPLIT_FP16 = 2   /* the same slices stored as float16 */
+} bsmm_mode;
+
+typedef enum {
+  BSMM_SCHED_FLOPS = 0,   /* order and pack work units by useful flop count */
+  BSMM_SCHED_COSTS = 1,   /* by costs given through bsmm_plan_set_costs (e.g. the MLP) */
+  BSMM_SCHED_NATURAL = 2  /* no reordering: units in row-major order, dealt round robin */
+} bsmm_schedule;
+
+typedef struct {
+  int32_t mode;            /* bsmm_mode (default BSMM_FP64) */
+  int32_t nslices;         /* split modes: slices per operand, 1..6 (default 6) */
+  int32_t schedule;        /* bsmm_schedule (default BSMM_SCHED_FLOPS) */
+  int32_t max_ctas;        /* persistent grid size cap; 0 = one per SM (times residency) */
+  int32_t debug_checks;    /* 1 = kernels validate offsets against the plan */
+  int32_t record_timings;  /* 1 = record per-unit start/end times (bsmm_plan_timings) */
+  int32_t reserved[6];     /* must be zero */
+} bsmm_options;
+
+/* Fill *opt with the defaults above. */
+void bsmm_options_default(bsmm_options* opt);
+
+/*
+ * Build a plan for one block-sparse product structure.
+ * Computes S_C (boolean product of a_mask and b_mask, united with c_mask when
+ * given), the C-tile-owned work units with their ascending k order, their costs
+ * and their packing onto persistent CTAs, and uploads the task tables to the
+ * current device. Host inputs only; they are copied, not retained.
+ *   M, N, K          number of row, column and inner blocks (>= 0)
+ *   row_sizes[M]     r_i >= 0;  col_sizes[N] c_j >= 0;  inner_sizes[K] q_k >= 0
+ *   a_mask[M*K]      row-major, nonzero = tile A_ik stored
+ *   b_mask[K*N]      row-major, nonzero = tile B_kj stored
+ *   c_mask[M*N]      NULL, or extra C tiles to keep in S_C
+ *   opt              NULL = defaults
+ * Allocates device memory (task tables; slice arenas for the split modes).
+ * Returns BSMM_ERR_INVALID for negative sizes or an unknown option value,
+ * BSMM_ERR_UNSUPPORTED for a split mode whose inner block exceeds the exact
+ * accumulation depth of the tensor-core path (see bsmm_plan_query).
+ */
+bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
+                      const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,
+                      const uint8_t* a_mask, const uint8_t* b_mask, const uint8_t* c_mask,
+                      const bsmm_options* opt);
+
+/*
+ * Structure of a plan (host outputs; any pointer may be NULL):
+ *   n_ctiles     |S_C|;  n_triples  number of nonzero (i,k,j) triples
+ *   useful_flops sum over the triples of 2*r_i*c_j*q_k (padding and slices not counted)
+ *   c_mask_out   M*N bytes: S_C
+ *   n_units      number of work units (each owned by one CTA, fixed k order)
+ */
+bsmm_status bsmm_plan_query(bsmm_plan_t plan, int64_t* n_ctiles, int64_t* n_triples,
+                            double* useful_flops, uint8_t* c_mask_out, int64_t* n_units);
+
+/*
+ * Per-unit cost features for the learned cost model (host output, row-major
+ * n_units x BSMM_NFEATURES floats, see bsmm_features in the source for the
+ * order) and the unit's flop-count cost. Either pointer may be NULL.
+ */
+#define BSMM_NFEATURES 12
+bsmm_status bsmm_plan_features(bsmm_plan_t plan, float* features, double* flop_costs);
+
+/*
+ * Replace the unit costs used by BSMM_SCHED_COSTS and re-pack the units onto the
+ * persistent CTAs (longest-processing-time order, greedy least-loaded CTA).
+ * costs[n_units] host, > 0. The result bits do not change: only the order.
+ */
+bsmm_status bsmm_plan_set_costs(bsmm_plan_t plan, const double* costs);
+
+/* Re-pack with an explicit persistent grid size (1..65535; 0 = default). */
+bsmm_status bsmm_plan_set_ctas(bsmm_plan_t plan, int32_t ctas);
+
+/*
+ * Run the product on `stream` (device pointers):
+ *   A, B       device arenas of FP64 tiles; a_off (M*K), b_off (K*N) device int64
+ *   C          device arena; c_off (M*N) device int64; every tile of S_C must be
+ *              present in c_off (checked on the device when debug_checks is set)
+ * Asynchronous; the plan's work buffers are reused, so two executes of the same
+ * plan must not overlap on different streams.
+ */
+bsmm_status bsmm_execute(bsmm_plan_t plan, double alpha, const double* A, const int64_t* a_off,
+                         const double* B, const int64_t* b_off, double beta, double* C,
+                         const int64_t* c_off, void* stream);
+
+/*
+ * Same as bsmm_execute with HOST buffers: copies A, B (and C when beta != 0) and
+ * the offset tables to device buffers the plan keeps, runs, copies C back and
+ * synchronises `stream` before returning. a_elems, b_elems, c_elems = arena
+ * lengths in elements. Pinned host memory makes the copies asynchronous.
+ */
+bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const double* A, int64_t a_elems,
+                              const int64_t* a_off, const double* B, int64_t b_elems,
+                              const int64_t* b_off, double beta, double* C, int64_t c_elems,
+                              const int64_t* c_off, void* stream);
+
+/*
+ * Synchronise `stream` and return the plan's device error word as a status
+ * (BSMM_OK, BSMM_ERR_TIMEOUT or BSMM_ERR_DEVICE), clearing it.
+ */
+bsmm_status bsmm_status_device(bsmm_plan_t plan, void* stream);
+
+/*
+ * Per-unit timing records of the last execute with record_timings set:
+ * start_ns[n_units], end_ns[n_units] (device %globaltimer, host outputs, either
+ * may be NULL) and the CTA each unit ran on (cta[n_units], may be NULL).
+ * Synchronises the device.
+ */
+bsmm_status bsmm_plan_timings(bsmm_plan_t plan, int64_t* start_ns, int64_t* end_ns, int32_t* cta);
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* bsmm_last_error(void);
+
+/* Release a plan and its device memory. NULL-safe. */
+void bsmm_destroy(bsmm_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSMM_H */

@@ -1,0 +1,226 @@
+"""Python binding of the bsmm C ABI (``include/bsmm.h``).
+
+Argument marshalling only: every step of the product (planning, slicing,
+contraction, epilogue) runs in the native library ``_build/libbsmm.so``; this
+module converts numpy arrays and torch tensors to pointers and status codes to
+exceptions. There is no Python or CPU fallback: if the library cannot be built
+or loaded, every call raises.
+
+Function names follow the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "BsmmError", "lib", "library_path", "BSMM_FP64", "BSMM_SPLIT_BF16", "BSMM_SPLIT_FP16",
+    "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
+    "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
+    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
+    "bsmm_last_error", "bsmm_destroy", "EXPORTED",
+]
+
+BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
+BSMM_SCHED_FLOPS, BSMM_SCHED_COSTS, BSMM_SCHED_NATURAL = 0, 1, 2
+BSMM_NFEATURES = 12
+STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_NOMEM",
+          4: "BSMM_ERR_TIMEOUT", 5: "BSMM_ERR_UNSUPPORTED", 6: "BSMM_ERR_DEVICE"}
+
+# every symbol include/bsmm.h declares
+EXPORTED = [
+    "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
+    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
+    "bsmm_last_error", "bsmm_destroy",
+]
+
+
+class BsmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("nslices", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("max_ctas", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
+                ("record_timings", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building from source first if needed) the native library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.bsmm_options_default.argtypes = [ctypes.POINTER(Options)]
+        L.bsmm_options_default.restype = None
+        L.bsmm_plan.argtypes = [ctypes.POINTER(P), i32, P, i32, P, i32, P, P, P, P, ctypes.POINTER(Options)]
+        L.bsmm_plan_query.argtypes = [P, P, P, P, P, P]
+        L.bsmm_plan_features.argtypes = [P, P, P]
+        L.bsmm_plan_set_costs.argtypes = [P, P]
+        L.bsmm_plan_set_ctas.argtypes = [P, i32]
+        L.bsmm_execute.argtypes = [P, f64, P, P, P, P, f64, P, P, P]
+        L.bsmm_execute_host.argtypes = [P, f64, P, i64, P, P, i64, P, f64, P, i64, P, P]
+        L.bsmm_status_device.argtypes = [P, P]
+        L.bsmm_plan_timings.argtypes = [P, P, P, P]
+        L.bsmm_last_error.argtypes = []
+        L.bsmm_last_error.restype = ctypes.c_char_p
+        L.bsmm_destroy.argtypes = [P]
+        L.bsmm_destroy.restype = None
+        for name in EXPORTED:
+            if name not in ("bsmm_options_default", "bsmm_last_error", "bsmm_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def bsmm_last_error() -> str:
+    return lib().bsmm_last_error().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise BsmmError(status, bsmm_last_error())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or a torch tensor (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data if a.size else None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr() if a.numel() else None
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def bsmm_options_default() -> Options:
+    o = Options()
+    lib().bsmm_options_default(ctypes.byref(o))
+    return o
+
+
+class Plan:
+    """Owns one bsmm_plan_t; destroyed with the object or by bsmm_destroy."""
+
+    def __init__(self, handle: int, M: int, N: int, K: int, mode: int):
+        self.handle = handle
+        self.M, self.N, self.K, self.mode = M, N, K, mode
+
+    def __del__(self):
+        try:
+            bsmm_destroy(self)
+        except Exception:
+            pass
+
+
+def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *, mode: int = BSMM_FP64,
+              nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
+              record_timings: int = 0) -> Plan:
+    r = _np(row_sizes, np.int32)
+    c = _np(col_sizes, np.int32)
+    q = _np(inner_sizes, np.int32)
+    am = _np(a_mask, np.uint8)
+    bm = _np(b_mask, np.uint8)
+    cm = None if c_mask is None else _np(c_mask, np.uint8)
+    o = bsmm_options_default()
+    o.mode, o.nslices, o.schedule, o.max_ctas = mode, nslices, schedule, max_ctas
+    o.debug_checks, o.record_timings = debug_checks, record_timings
+    h = ctypes.c_void_p()
+    _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
+                           _ptr(bm), _ptr(cm), ctypes.byref(o)))
+    return Plan(h.value, len(r), len(c), len(q), mode)
+
+
+def bsmm_plan_query(plan: Plan) -> dict:
+    nct, ntr, nun = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    fl = ctypes.c_double()
+    cs = np.zeros((plan.M, plan.N), np.uint8)
+    _check(lib().bsmm_plan_query(plan.handle, ctypes.addressof(nct), ctypes.addressof(ntr), ctypes.addressof(fl),
+                                 _ptr(cs), ctypes.addressof(nun)))
+    return {"n_ctiles": nct.value, "n_triples": ntr.value, "useful_flops": fl.value, "c_mask": cs,
+            "n_units": nun.value}
+
+
+def bsmm_plan_features(plan: Plan):
+    n = bsmm_plan_query(plan)["n_units"]
+    f = np.zeros((n, BSMM_NFEATURES), np.float32)
+    c = np.zeros(n, np.float64)
+    _check(lib().bsmm_plan_features(plan.handle, _ptr(f), _ptr(c)))
+    return f, c
+
+
+def bsmm_plan_set_costs(plan: Plan, costs):
+    c = _np(costs, np.float64)
+    _check(lib().bsmm_plan_set_costs(plan.handle, _ptr(c)))
+
+
+def bsmm_plan_set_ctas(plan: Plan, ctas: int):
+    _check(lib().bsmm_plan_set_ctas(plan.handle, int(ctas)))
+
+
+def bsmm_execute(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=None):
+    """Device tensors (torch, CUDA): A, B, C float64 arenas; a_off, b_off, c_off int64 tables."""
+    _check(lib().bsmm_execute(plan.handle, float(alpha), _ptr(A), _ptr(a_off), _ptr(B), _ptr(b_off), float(beta),
+                              _ptr(C), _ptr(c_off), _stream(stream)))
+
+
+def bsmm_execute_host(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=None):
+    """Host arrays (numpy or CPU tensors, pinned for asynchronous copies); C is updated in place."""
+    def n(x):
+        return int(x.size if isinstance(x, np.ndarray) else x.numel())
+    _check(lib().bsmm_execute_host(plan.handle, float(alpha), _ptr(A), n(A), _ptr(a_off), _ptr(B), n(B),
+                                   _ptr(b_off), float(beta), _ptr(C), n(C), _ptr(c_off), _stream(stream)))
+
+
+def bsmm_status_device(plan: Plan, stream=None):
+    _check(lib().bsmm_status_device(plan.handle, _stream(stream)))
+
+
+def bsmm_plan_timings(plan: Plan):
+    n = bsmm_plan_query(plan)["n_units"]
+    s = np.zeros(n, np.int64)
+    e = np.zeros(n, np.int64)
+    cta = np.zeros(n, np.int32)
+    _check(lib().bsmm_plan_timings(plan.handle, _ptr(s), _ptr(e), _ptr(cta)))
+    return s, e, cta
+
+
+def bsmm_destroy(plan: Plan):
+    if plan is not None and plan.handle:
+        lib().bsmm_destroy(plan.handle)
+        plan.handle = None

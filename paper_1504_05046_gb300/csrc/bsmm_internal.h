@@ -1,0 +1,168 @@
+// Internal declarations shared by the planner, the C ABI and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bsmm.h"
+
+namespace bsmm {
+
+// Device error word bits (set by kernels with atomicOr, read by bsmm_status_device).
+enum : int32_t {
+  kErrTimeout = 1,     // a bounded wait ran out
+  kErrBadOffset = 2,   // debug check: a C tile of S_C without a C offset, or a bad A/B offset
+  kErrNonFinite = 4,   // split modes: a non-finite input element
+};
+
+// Split-mode geometry.
+constexpr int kSplitBM = 128;      // rows of one work unit (tcgen05 M)
+constexpr int kSplitKC = 32;       // inner elements per staged chunk (64-byte swizzled rows)
+constexpr int kSplitBeta = 7;      // bits per slice
+constexpr int kSplitMaxS = 6;      // slices per operand
+constexpr int kSplitEpiWarps = 8;  // epilogue warps (2 per TMEM lane quadrant)
+
+// FP64-mode geometry.
+constexpr int kF64BM = 64, kF64BN = 64, kF64BK = 16, kF64Threads = 256;
+
+// Largest inner block for which every diagonal sum of slice products stays an
+// integer of magnitude <= 2^24 (exact in the FP32 tensor-core accumulator).
+int split_max_depth(int s);
+int split_tile_n(int s);          // work-unit width (32 or 64)
+int split_stages(int s, int tn);  // smem ring depth
+size_t split_smem_bytes(int s, int tn, int stages);
+
+// Device arrays owned by a plan.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Fp64Unit {  // one C sub-tile of one C tile
+  int32_t i, j, r0, c0;
+};
+
+struct SplitUnit {  // one (128-row block, TN-column block)
+  int32_t rb, cb;
+};
+
+// Arguments of the FP64 tile-task kernel.
+struct Fp64Args {
+  const int32_t* r;
+  const int32_t* c;
+  const int32_t* q;
+  int32_t M, N, K;
+  const int64_t* kptr;     // CSR over M*N tiles
+  const int32_t* klist;    // ascending k per tile
+  const uint8_t* cs;       // S_C, M*N
+  const Fp64Unit* units;
+  const int32_t* sched_ptr;
+  const int32_t* sched_units;
+  double alpha, beta;
+  const double* A;
+  const int64_t* a_off;
+  const double* B;
+  const int64_t* b_off;
+  double* C;
+  const int64_t* c_off;
+  int64_t* timings;        // 2 per unit or null
+  int32_t* unit_cta;       // per unit or null
+  int32_t* err;
+  int32_t debug;
+};
+
+// Arguments of the split-mode kernels.
+struct SplitArgs {
+  int32_t M, N, K, s, tn, stages, fp16;
+  int64_t Mtot, Ntot;
+  int32_t RB, CB, kwords;
+  const int32_t* r;
+  const int32_t* c;
+  const int32_t* q;
+  const int64_t* ro;        // row prefix offsets (M+1)
+  const int64_t* co;        // col prefix offsets (N+1)
+  const int32_t* row_tile;  // Mtot
+  const int32_t* col_tile;  // Ntot
+  const uint8_t* cs;        // S_C
+  const uint8_t* am;        // A tile mask (M x K)
+  const uint8_t* bm;        // B tile mask (K x N)
+  const uint64_t* presA;    // RB x kwords
+  const uint64_t* presB;    // CB x kwords
+  const int64_t* apk_off;   // RB x K byte offsets into apk (-1 absent)
+  const int64_t* bpk_off;   // K x CB byte offsets into bpk (-1 absent)
+  uint8_t* apk;
+  uint8_t* bpk;
+  int16_t* rowexp;          // K x Mtot
+  int16_t* colexp;          // K x Ntot
+  int32_t* eA;              // M x K
+  int32_t* eB;              // K x N
+  const int32_t* a_tiles;   // present A tiles (i*K+k), count n_a_tiles
+  const int32_t* b_tiles;   // present B tiles (k*N+j)
+  int32_t n_a_tiles, n_b_tiles;
+  const int32_t* a_blocks;  // present (rb*K+kt)
+  const int32_t* b_blocks;  // present (kt*CB+cb)
+  int32_t n_a_blocks, n_b_blocks;
+  const SplitUnit* units;
+  const int32_t* sched_ptr;
+  const int32_t* sched_units;
+  double alpha, beta;
+  const double* A;
+  const int64_t* a_off;
+  const double* B;
+  const int64_t* b_off;
+  double* C;
+  const int64_t* c_off;
+  int64_t* timings;
+  int32_t* unit_cta;
+  int32_t* err;
+  int32_t debug;
+};
+
+cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st);
+cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st);
+int fp64_ctas_per_sm();
+
+void set_error(const std::string& msg);
+
+}  // namespace bsmm
+
+// The plan object behind bsmm_plan_t.
+struct bsmm_plan_s {
+  int32_t M = 0, N = 0, K = 0;
+  std::vector<int32_t> r, c, q;
+  std::vector<int64_t> ro, co, qo;
+  std::vector<uint8_t> am, bm, cs;
+  int64_t n_ctiles = 0, n_triples = 0;
+  double useful_flops = 0.0;
+  bsmm_options opt{};
+  int device = 0, sms = 0;
+
+  // work units (one kind per mode)
+  std::vector<bsmm::Fp64Unit> f64_units;
+  std::vector<bsmm::SplitUnit> sp_units;
+  std::vector<int64_t> kptr;   // FP64: CSR over M*N tiles
+  std::vector<int32_t> klist;
+  int64_t n_units = 0;
+  std::vector<double> flop_cost, cost;
+  std::vector<float> features;  // n_units x BSMM_NFEATURES
+  int ctas = 0;
+  std::vector<int32_t> sched_ptr, sched_units;
+
+  // split geometry
+  int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0;
+  int64_t Mtot = 0, Ntot = 0;
+  int64_t apk_bytes = 0, bpk_bytes = 0;
+
+  // device memory
+  bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
+  bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_apk_off, d_bpk_off, d_apk, d_bpk;
+  bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_eA, d_eB, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
+  bsmm::DevBuf d_err, d_timings, d_unit_cta;
+  int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;
+
+  // host-buffer execute staging (grown on demand)
+  bsmm::DevBuf h_A, h_B, h_C, h_aoff, h_boff, h_coff;
+};

@@ -1,0 +1,227 @@
+// C ABI: execution entry points, device status, timing records.
+#include <cstring>
+
+#include "bsmm_internal.h"
+
+using namespace bsmm;
+
+namespace {
+
+bsmm_status fill_fp64(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
+                      const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
+  a.r = (const int32_t*)p->d_r.p;
+  a.c = (const int32_t*)p->d_c.p;
+  a.q = (const int32_t*)p->d_q.p;
+  a.M = p->M;
+  a.N = p->N;
+  a.K = p->K;
+  a.kptr = (const int64_t*)p->d_kptr.p;
+  a.klist = (const int32_t*)p->d_klist.p;
+  a.cs = (const uint8_t*)p->d_cs.p;
+  a.units = (const Fp64Unit*)p->d_units.p;
+  a.sched_ptr = (const int32_t*)p->d_sched_ptr.p;
+  a.sched_units = (const int32_t*)p->d_sched_units.p;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.A = A;
+  a.a_off = a_off;
+  a.B = B;
+  a.b_off = b_off;
+  a.C = C;
+  a.c_off = c_off;
+  a.timings = p->opt.record_timings ? (int64_t*)p->d_timings.p : nullptr;
+  a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
+  a.err = (int32_t*)p->d_err.p;
+  a.debug = p->opt.debug_checks;
+  return BSMM_OK;
+}
+
+bsmm_status fill_split(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
+                       const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
+  a.M = p->M;
+  a.N = p->N;
+  a.K = p->K;
+  a.s = p->s;
+  a.tn = p->tn;
+  a.stages = p->stages;
+  a.fp16 = p->opt.mode == BSMM_SPLIT_FP16;
+  a.Mtot = p->Mtot;
+  a.Ntot = p->Ntot;
+  a.RB = p->RB;
+  a.CB = p->CB;
+  a.kwords = p->kwords;
+  a.r = (const int32_t*)p->d_r.p;
+  a.c = (const int32_t*)p->d_c.p;
+  a.q = (const int32_t*)p->d_q.p;
+  a.ro = (const int64_t*)p->d_ro.p;
+  a.co = (const int64_t*)p->d_co.p;
+  a.row_tile = (const int32_t*)p->d_row_tile.p;
+  a.col_tile = (const int32_t*)p->d_col_tile.p;
+  a.cs = (const uint8_t*)p->d_cs.p;
+  a.am = (const uint8_t*)p->d_am.p;
+  a.bm = (const uint8_t*)p->d_bm.p;
+  a.presA = (const uint64_t*)p->d_presA.p;
+  a.presB = (const uint64_t*)p->d_presB.p;
+  a.apk_off = (const int64_t*)p->d_apk_off.p;
+  a.bpk_off = (const int64_t*)p->d_bpk_off.p;
+  a.apk = (uint8_t*)p->d_apk.p;
+  a.bpk = (uint8_t*)p->d_bpk.p;
+  a.rowexp = (int16_t*)p->d_rowexp.p;
+  a.colexp = (int16_t*)p->d_colexp.p;
+  a.eA = (int32_t*)p->d_eA.p;
+  a.eB = (int32_t*)p->d_eB.p;
+  a.a_tiles = (const int32_t*)p->d_a_tiles.p;
+  a.b_tiles = (const int32_t*)p->d_b_tiles.p;
+  a.n_a_tiles = p->n_a_tiles;
+  a.n_b_tiles = p->n_b_tiles;
+  a.a_blocks = (const int32_t*)p->d_a_blocks.p;
+  a.b_blocks = (const int32_t*)p->d_b_blocks.p;
+  a.n_a_blocks = p->n_a_blocks;
+  a.n_b_blocks = p->n_b_blocks;
+  a.units = (const SplitUnit*)p->d_units.p;
+  a.sched_ptr = (const int32_t*)p->d_sched_ptr.p;
+  a.sched_units = (const int32_t*)p->d_sched_units.p;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.A = A;
+  a.a_off = a_off;
+  a.B = B;
+  a.b_off = b_off;
+  a.C = C;
+  a.c_off = c_off;
+  a.timings = p->opt.record_timings ? (int64_t*)p->d_timings.p : nullptr;
+  a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
+  a.err = (int32_t*)p->d_err.p;
+  a.debug = p->opt.debug_checks;
+  return BSMM_OK;
+}
+
+bsmm_status check_ptrs(bsmm_plan_s* p, const double* A, const int64_t* a_off, const double* B,
+                       const int64_t* b_off, double* C, const int64_t* c_off) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if ((int64_t)p->M * p->K && !a_off) return set_error("a_off is NULL"), BSMM_ERR_INVALID;
+  if ((int64_t)p->K * p->N && !b_off) return set_error("b_off is NULL"), BSMM_ERR_INVALID;
+  if (p->n_ctiles && (!c_off || !C)) return set_error("C or c_off is NULL"), BSMM_ERR_INVALID;
+  if (p->n_triples && (!A || !B)) return set_error("A or B is NULL"), BSMM_ERR_INVALID;
+  return BSMM_OK;
+}
+
+bsmm_status run(bsmm_plan_s* p, double alpha, const double* A, const int64_t* a_off, const double* B,
+                const int64_t* b_off, double beta, double* C, const int64_t* c_off, cudaStream_t st) {
+  if (p->n_units == 0) return BSMM_OK;
+  cudaError_t e;
+  if (p->opt.mode == BSMM_FP64) {
+    Fp64Args a{};
+    fill_fp64(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
+    e = launch_fp64(a, p->ctas, st);
+  } else {
+    SplitArgs a{};
+    fill_split(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
+    e = launch_split(a, p->ctas, st);
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+    return BSMM_ERR_CUDA;
+  }
+  return BSMM_OK;
+}
+
+bsmm_status grow(DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return BSMM_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BSMM_ERR_NOMEM : BSMM_ERR_CUDA;
+  }
+  b.bytes = bytes;
+  return BSMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bsmm_status bsmm_execute(bsmm_plan_t p, double alpha, const double* A, const int64_t* a_off, const double* B,
+                         const int64_t* b_off, double beta, double* C, const int64_t* c_off, void* stream) {
+  bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
+  if (s != BSMM_OK) return s;
+  return run(p, alpha, A, a_off, B, b_off, beta, C, c_off, (cudaStream_t)stream);
+}
+
+bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const double* A, int64_t a_elems,
+                              const int64_t* a_off, const double* B, int64_t b_elems, const int64_t* b_off,
+                              double beta, double* C, int64_t c_elems, const int64_t* c_off, void* stream) {
+  bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
+  if (s != BSMM_OK) return s;
+  if (a_elems < 0 || b_elems < 0 || c_elems < 0) return set_error("negative arena length"), BSMM_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t na = (size_t)p->M * p->K, nb = (size_t)p->K * p->N, nc = (size_t)p->M * p->N;
+  if ((s = grow(p->h_A, sizeof(double) * a_elems)) != BSMM_OK) return s;
+  if ((s = grow(p->h_B, sizeof(double) * b_elems)) != BSMM_OK) return s;
+  if ((s = grow(p->h_C, sizeof(double) * c_elems)) != BSMM_OK) return s;
+  if ((s = grow(p->h_aoff, sizeof(int64_t) * na)) != BSMM_OK) return s;
+  if ((s = grow(p->h_boff, sizeof(int64_t) * nb)) != BSMM_OK) return s;
+  if ((s = grow(p->h_coff, sizeof(int64_t) * nc)) != BSMM_OK) return s;
+#define H2D(dst, src, bytes)                                                                      \
+  if ((bytes) > 0) {                                                                              \
+    cudaError_t e_ = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st);          \
+    if (e_ != cudaSuccess) return set_error(std::string("H2D: ") + cudaGetErrorString(e_)), BSMM_ERR_CUDA; \
+  }
+  H2D(p->h_aoff.p, a_off, sizeof(int64_t) * na);
+  H2D(p->h_boff.p, b_off, sizeof(int64_t) * nb);
+  H2D(p->h_coff.p, c_off, sizeof(int64_t) * nc);
+  H2D(p->h_A.p, A, sizeof(double) * a_elems);
+  H2D(p->h_B.p, B, sizeof(double) * b_elems);
+  if (beta != 0.0) H2D(p->h_C.p, C, sizeof(double) * c_elems);
+#undef H2D
+  s = run(p, alpha, (const double*)p->h_A.p, (const int64_t*)p->h_aoff.p, (const double*)p->h_B.p,
+          (const int64_t*)p->h_boff.p, beta, (double*)p->h_C.p, (const int64_t*)p->h_coff.p, st);
+  if (s != BSMM_OK) return s;
+  if (c_elems > 0) {
+    cudaError_t e = cudaMemcpyAsync(C, p->h_C.p, sizeof(double) * c_elems, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return set_error(std::string("D2H: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(std::string("sync: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_status_device(bsmm_plan_t p, void* stream) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, p->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err.p, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(std::string("status: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  if (w & kErrTimeout) return set_error("a kernel wait timed out"), BSMM_ERR_TIMEOUT;
+  if (w & kErrBadOffset) return set_error("a kernel found a missing or invalid tile offset"), BSMM_ERR_DEVICE;
+  if (w & kErrNonFinite) return set_error("non-finite input element in a split mode"), BSMM_ERR_DEVICE;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_plan_timings(bsmm_plan_t p, int64_t* start_ns, int64_t* end_ns, int32_t* cta) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if (!p->opt.record_timings) return set_error("plan was built without record_timings"), BSMM_ERR_INVALID;
+  if (cudaDeviceSynchronize() != cudaSuccess) return set_error("device sync failed"), BSMM_ERR_CUDA;
+  std::vector<int64_t> t(2 * p->n_units);
+  if (p->n_units) {
+    if (cudaMemcpy(t.data(), p->d_timings.p, sizeof(int64_t) * t.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_error("timing copy failed"), BSMM_ERR_CUDA;
+    if (cta && cudaMemcpy(cta, p->d_unit_cta.p, sizeof(int32_t) * p->n_units, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_error("timing copy failed"), BSMM_ERR_CUDA;
+  }
+  for (int64_t u = 0; u < p->n_units; u++) {
+    if (start_ns) start_ns[u] = t[2 * u];
+    if (end_ns) end_ns[u] = t[2 * u + 1];
+  }
+  return BSMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Plain FP64 tile-task kernel.
+//
+// One persistent CTA walks its packed list of work units. A unit is a 64x64
+// region of one C tile C_ij; the CTA owns it for the whole task: it runs the
+// tile's ascending k-list (the rank-k updates C_ij <- A_ik B_kj + C_ij of the
+// paper's Sec. 2.1, multiply and reduction fused as in Sec. 3.2), then applies
+// C_ij = alpha*acc + beta*C_ij (Algorithm 1's alpha) and stores.
+//
+// GB300 has no FP64 tensor-core kind in tcgen05, and its warp-level FP64 MMA
+// (mma.sync m8n8k4) measures below its FP64 FMA pipe, so the contraction is a
+// register-tiled DFMA loop: 256 threads, 4x4 accumulators each, the A and B
+// sub-tiles (64x16 and 16x64) staged through shared memory with the next chunk's
+// global loads in flight during the current chunk's FMAs. Irregular tiles are
+// read in place from the caller's arena: edges beyond a tile's rows, columns or
+// inner size are zero-filled in shared memory.
+//
+// Rounding is fixed by construction: each accumulator element takes
+// acc = fma(a, b, acc) over k blocks in ascending order and, inside a block,
+// ascending kk; the epilogue rounds alpha*acc and beta*C separately before
+// adding. The result bits therefore do not depend on the schedule, the CTA count
+// or the unit order.
+#include <cstdint>
+
+#include "bsmm_internal.h"
+
+namespace bsmm {
+
+namespace {
+
+__device__ __forceinline__ int64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (int64_t)t;
+}
+
+constexpr int BM = kF64BM, BN = kF64BN, BK = kF64BK, NT = kF64Threads;
+constexpr int PAD = 2;
+constexpr int A_PER_T = BM * BK / NT;  // 4
+constexpr int B_PER_T = BK * BN / NT;  // 4
+
+struct ChunkIter {
+  int64_t t, t_end;  // position in the tile's k-list
+  int kk0, qk;
+  int k;
+};
+
+__global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
+  __shared__ double sA[BK][BM + PAD];  // transposed: [kk][row]
+  __shared__ double sB[BK][BN + PAD];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int cta = blockIdx.x;
+  const int beg = a.sched_ptr[cta], end = a.sched_ptr[cta + 1];
+
+  for (int idx = beg; idx < end; idx++) {
+    const int u = a.sched_units[idx];
+    const Fp64Unit un = a.units[u];
+    if (a.timings && tid == 0) a.timings[2 * (int64_t)u] = gtimer();
+    const int i = un.i, j = un.j;
+    const int ri = a.r[i], cj = a.c[j];
+    const int rows = min(BM, ri - un.r0), cols = min(BN, cj - un.c0);
+    const int64_t tile = (int64_t)i * a.N + j;
+
+    double acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; x++)
+#pragma unroll
+      for (int y = 0; y < 4; y++) acc[x][y] = 0.0;
+
+    ChunkIter it;
+    it.t = a.kptr[tile];
+    it.t_end = a.kptr[tile + 1];
+    it.kk0 = 0;
+    it.k = it.t < it.t_end ? a.klist[it.t] : 0;
+    it.qk = it.t < it.t_end ? a.q[it.k] : 0;
+    // skip empty inner blocks
+    while (it.t < it.t_end && it.qk == 0) {
+      it.t++;
+      if (it.t < it.t_end) {
+        it.k = a.klist[it.t];
+        it.qk = a.q[it.k];
+      }
+    }
+
+    double ra[A_PER_T], rb[B_PER_T];
+    auto load_chunk = [&](const ChunkIter& c) {
+      const int64_t ao = a.a_off[(int64_t)i * a.K + c.k];
+      const int64_t bo = a.b_off[(int64_t)c.k * a.N + j];
+      if (a.debug && tid == 0 && (ao < 0 || bo < 0)) atomicOr(a.err, kErrBadOffset);
+      const double* At = a.A + (ao < 0 ? 0 : ao) + (int64_t)un.r0 * c.qk;
+      const double* Bt = a.B + (bo < 0 ? 0 : bo) + un.c0;
+#pragma unroll
+      for (int m = 0; m < A_PER_T; m++) {
+        const int e = tid + NT * m;
+        const int row = e / BK, kc = e % BK;
+        const bool ok = ao >= 0 && row < rows && c.kk0 + kc < c.qk;
+        ra[m] = ok ? __ldg(At + (int64_t)row * c.qk + c.kk0 + kc) : 0.0;
+      }
+#pragma unroll
+      for (int m = 0; m < B_PER_T; m++) {
+        const int e = tid + NT * m;
+        const int kr = e / BN, cc = e % BN;
+        const bool ok = bo >= 0 && cc < cols && c.kk0 + kr < c.qk;
+        rb[m] = ok ? __ldg(Bt + (int64_t)(c.kk0 + kr) * cj + cc) : 0.0;
+      }
+    };
+    auto advance = [&](ChunkIter& c) {
+      c.kk0 += BK;
+      while (c.t < c.t_end && c.kk0 >= c.qk) {
+        c.t++;
+        c.kk0 = 0;
+        if (c.t < c.t_end) {
+          c.k = a.klist[c.t];
+          c.qk = a.q[c.k];
+        }
+      }
+    };
+
+    bool have = it.t < it.t_end;
+    if (have) load_chunk(it);
+    while (have) {
+#pragma unroll
+      for (int m = 0; m < A_PER_T; m++) {
+        const int e = tid + NT * m;
+        sA[e % BK][e / BK] = ra[m];
+      }
+#pragma unroll
+      for (int m = 0; m < B_PER_T; m++) {
+        const int e = tid + NT * m;
+        sB[e / BN][e % BN] = rb[m];
+      }
+      __syncthreads();
+      advance(it);
+      have = it.t < it.t_end;
+      if (have) load_chunk(it);  // next chunk's loads overlap this chunk's FMAs
+#pragma unroll
+      for (int kk = 0; kk < BK; kk++) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) av[x] = sA[kk][ty + 16 * x];
+#pragma unroll
+        for (int y = 0; y < 4; y++) bv[y] = sB[kk][tx + 16 * y];
+#pragma unroll
+        for (int x = 0; x < 4; x++)
+#pragma unroll
+          for (int y = 0; y < 4; y++) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+      }
+      __syncthreads();
+    }
+
+    // epilogue: C_ij = alpha*acc + beta*C_ij on the valid part of the region
+    const int64_t co = a.c_off[tile];
+    if (co < 0) {
+      if (tid == 0) atomicOr(a.err, kErrBadOffset);
+    } else {
+      double* Ct = a.C + co + (int64_t)un.r0 * cj + un.c0;
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int row = ty + 16 * x;
+        if (row >= rows) continue;
+#pragma unroll
+        for (int y = 0; y < 4; y++) {
+          const int col = tx + 16 * y;
+          if (col >= cols) continue;
+          double* dst = Ct + (int64_t)row * cj + col;
+          double v = __dmul_rn(a.alpha, acc[x][y]);
+          if (a.beta != 0.0) v = __dadd_rn(v, __dmul_rn(a.beta, *dst));
+          *dst = v;
+        }
+      }
+    }
+    if (a.timings) {
+      __syncthreads();
+      if (tid == 0) {
+        a.timings[2 * (int64_t)u + 1] = gtimer();
+        a.unit_cta[u] = cta;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int fp64_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_tile_kernel, NT, 0) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st) {
+  fp64_tile_kernel<<<ctas, NT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bsmm

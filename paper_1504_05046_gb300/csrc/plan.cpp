@@ -1,0 +1,552 @@
+// Host planner and C ABI of the block-sparse product.
+//
+// The planner turns the three tilings and two tile masks into the data-driven
+// task set of the paper's task-based SUMMA (Sec. 3.2): the C tile set S_C (the
+// boolean product of the masks), one task per C tile region with its ascending
+// k order (the rank-k updates of Sec. 2.1, each owned by one CTA so that the
+// multiply and the reduction into C are fused, Sec. 3.2 last paragraphs), the
+// useful flop count, and a packing of the tasks onto persistent CTAs
+// (longest-processing-time first onto the least-loaded CTA) that replaces the
+// paper's process grid and task queue on one GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+
+#include "bsmm_internal.h"
+
+using namespace bsmm;
+
+namespace bsmm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int split_max_depth(int s) {
+  // |S_d| <= q * 2^(2*beta-2) * max(4, d+1) with d <= s+1 (slice bounds |N_1| <= 2^beta,
+  // |N_t| <= 2^(beta-1)); require that to be <= 2^24.
+  const double per = std::ldexp(1.0, 2 * kSplitBeta - 2) * std::max(4, s + 2);
+  return (int)std::floor(std::ldexp(1.0, 24) / per);
+}
+
+int split_tile_n(int s) { return s >= 5 ? 32 : 64; }
+
+static size_t stage_bytes(int s, int tn) {
+  return (size_t)s * (kSplitBM * kSplitKC * 2) + (size_t)s * (tn * kSplitKC * 2);
+}
+
+int split_stages(int s, int tn) {
+  const size_t budget = 200 * 1024;
+  int st = (int)(budget / stage_bytes(s, tn));
+  return std::max(2, std::min(8, st));
+}
+
+size_t split_smem_bytes(int s, int tn, int stages) {
+  return 1024 /*alignment slack*/ + (size_t)stages * stage_bytes(s, tn) + 256 /*barriers*/;
+}
+
+}  // namespace bsmm
+
+namespace {
+
+#define CUDA_TRY(x)                                                              \
+  do {                                                                           \
+    cudaError_t e_ = (x);                                                        \
+    if (e_ != cudaSuccess) {                                                     \
+      set_error(std::string(#x) + ": " + cudaGetErrorString(e_));                \
+      return BSMM_ERR_CUDA;                                                      \
+    }                                                                            \
+  } while (0)
+
+bsmm_status dev_alloc(DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return BSMM_OK;
+  if (b.p) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BSMM_ERR_NOMEM : BSMM_ERR_CUDA;
+  }
+  b.bytes = bytes;
+  return BSMM_OK;
+}
+
+template <class T>
+bsmm_status upload(DevBuf& b, const std::vector<T>& v) {
+  bsmm_status st = dev_alloc(b, sizeof(T) * v.size());
+  if (st != BSMM_OK) return st;
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return BSMM_OK;
+}
+
+void dev_free(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+inline int log2i_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+inline float lg(double x) { return (float)std::log2(1.0 + x); }
+
+// Longest-processing-time packing onto `ctas` persistent CTAs.
+void pack_lpt(bsmm_plan_s* p) {
+  const int64_t n = p->n_units;
+  const int ctas = p->ctas;
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<std::vector<int32_t>> lists(ctas);
+  if (p->opt.schedule == BSMM_SCHED_NATURAL) {
+    for (int64_t u = 0; u < n; u++) lists[u % ctas].push_back((int32_t)u);
+  } else {
+    const std::vector<double>& cost = p->cost;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    using E = std::pair<double, int>;  // (load, cta) smallest first, ties to lower cta
+    std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
+    for (int t = 0; t < ctas; t++) heap.push({0.0, t});
+    for (int64_t u : order) {
+      E e = heap.top();
+      heap.pop();
+      lists[e.second].push_back((int32_t)u);
+      heap.push({e.first + cost[u], e.second});
+    }
+  }
+  p->sched_ptr.assign(ctas + 1, 0);
+  p->sched_units.clear();
+  p->sched_units.reserve(n);
+  for (int t = 0; t < ctas; t++) {
+    p->sched_ptr[t] = (int32_t)p->sched_units.size();
+    for (int32_t u : lists[t]) p->sched_units.push_back(u);
+  }
+  p->sched_ptr[ctas] = (int32_t)p->sched_units.size();
+}
+
+int default_ctas(const bsmm_plan_s* p) {
+  int per_sm = p->opt.mode == BSMM_FP64 ? fp64_ctas_per_sm() : 1;
+  int64_t c = (int64_t)p->sms * std::max(1, per_sm);
+  if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
+  c = std::min<int64_t>(c, std::max<int64_t>(1, p->n_units));
+  return (int)std::max<int64_t>(1, c);
+}
+
+bsmm_status upload_schedule(bsmm_plan_s* p) {
+  bsmm_status st;
+  if ((st = upload(p->d_sched_ptr, p->sched_ptr)) != BSMM_OK) return st;
+  if ((st = upload(p->d_sched_units, p->sched_units)) != BSMM_OK) return st;
+  return BSMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// FP64 mode: units are 64x64 sub-tiles of the C tiles of S_C; each runs the tile's
+// ascending k-list.
+// ------------------------------------------------------------------------------------
+bsmm_status plan_fp64(bsmm_plan_s* p) {
+  const int M = p->M, N = p->N, K = p->K;
+  for (int i = 0; i < M; i++)
+    for (int j = 0; j < N; j++) {
+      if (!p->cs[(int64_t)i * N + j]) continue;
+      const int ri = p->r[i], cj = p->c[j];
+      if (ri == 0 || cj == 0) continue;
+      int64_t kq = 0, kg = 0, nk = 0;
+      for (int64_t t = p->kptr[(int64_t)i * N + j]; t < p->kptr[(int64_t)i * N + j + 1]; t++) {
+        const int qk = p->q[p->klist[t]];
+        kq += qk;
+        kg += log2i_ceil_div(qk, kF64BK);
+        nk++;
+      }
+      for (int r0 = 0; r0 < ri; r0 += kF64BM)
+        for (int c0 = 0; c0 < cj; c0 += kF64BN) {
+          const int rows = std::min(kF64BM, ri - r0), cols = std::min(kF64BN, cj - c0);
+          p->f64_units.push_back({i, j, r0, c0});
+          const double fl = 2.0 * rows * cols * (double)kq;
+          p->flop_cost.push_back(std::max(fl, 1.0));
+          float f[BSMM_NFEATURES] = {lg(rows), lg(cols), lg((double)nk), lg((double)kq), lg((double)kg),
+                                     lg(fl), (float)(fl / std::max(1.0, 2.0 * kF64BM * kF64BN * kF64BK * (double)kg)),
+                                     0.0f, 0.0f, 0.0f, 0.0f, lg((double)kg)};
+          p->features.insert(p->features.end(), f, f + BSMM_NFEATURES);
+        }
+    }
+  p->n_units = (int64_t)p->f64_units.size();
+  return BSMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Split modes: units are (128-row block) x (tn-column block) of the global row and
+// column index spaces; a unit's k order is the ascending set of inner blocks for which
+// both its packed A row block and packed B column block are present.
+// ------------------------------------------------------------------------------------
+bsmm_status plan_split(bsmm_plan_s* p) {
+  const int M = p->M, N = p->N, K = p->K;
+  const int s = p->s, tn = p->tn;
+  const int64_t Mtot = p->Mtot, Ntot = p->Ntot;
+  p->RB = (int)((Mtot + kSplitBM - 1) / kSplitBM);
+  p->CB = (int)((Ntot + tn - 1) / tn);
+  p->kwords = std::max(1, (K + 63) / 64);
+  const int RB = p->RB, CB = p->CB, KW = p->kwords;
+  const int maxd = split_max_depth(s);
+  for (int k = 0; k < K; k++)
+    if (p->q[k] > maxd) {
+      set_error("inner block " + std::to_string(k) + " has " + std::to_string(p->q[k]) +
+                " > " + std::to_string(maxd) + " elements, the exact FP32 accumulation depth for " +
+                std::to_string(s) + " slices");
+      return BSMM_ERR_UNSUPPORTED;
+    }
+
+  std::vector<int32_t> row_tile(std::max<int64_t>(Mtot, 1), 0), col_tile(std::max<int64_t>(Ntot, 1), 0);
+  for (int i = 0; i < M; i++)
+    for (int64_t m = p->ro[i]; m < p->ro[i + 1]; m++) row_tile[m] = i;
+  for (int j = 0; j < N; j++)
+    for (int64_t n = p->co[j]; n < p->co[j + 1]; n++) col_tile[n] = j;
+
+  std::vector<uint64_t> presA((size_t)RB * KW, 0), presB((size_t)CB * KW, 0);
+  std::vector<int32_t> a_tiles, b_tiles;
+  for (int i = 0; i < M; i++)
+    for (int k = 0; k < K; k++) {
+      if (!p->am[(int64_t)i * K + k] || p->r[i] == 0 || p->q[k] == 0) continue;
+      a_tiles.push_back(i * K + k);
+      for (int64_t rb = p->ro[i] / kSplitBM; rb <= (p->ro[i + 1] - 1) / kSplitBM; rb++)
+        presA[rb * KW + k / 64] |= 1ull << (k % 64);
+    }
+  for (int k = 0; k < K; k++)
+    for (int j = 0; j < N; j++) {
+      if (!p->bm[(int64_t)k * N + j] || p->c[j] == 0 || p->q[k] == 0) continue;
+      b_tiles.push_back(k * N + j);
+      for (int64_t cb = p->co[j] / tn; cb <= (p->co[j + 1] - 1) / tn; cb++)
+        presB[cb * KW + k / 64] |= 1ull << (k % 64);
+    }
+  const int64_t a_chunk_bytes = (int64_t)s * kSplitBM * kSplitKC * 2;
+  const int64_t b_chunk_bytes = (int64_t)s * tn * kSplitKC * 2;
+  std::vector<int64_t> apk_off((size_t)RB * K, -1), bpk_off((size_t)K * CB, -1);
+  std::vector<int32_t> a_blocks, b_blocks;
+  int64_t cur = 0;
+  for (int rb = 0; rb < RB; rb++)
+    for (int k = 0; k < K; k++)
+      if (presA[(size_t)rb * KW + k / 64] >> (k % 64) & 1) {
+        apk_off[(size_t)rb * K + k] = cur;
+        a_blocks.push_back(rb * K + k);
+        cur += (int64_t)log2i_ceil_div(p->q[k], kSplitKC) * a_chunk_bytes;
+      }
+  p->apk_bytes = cur;
+  cur = 0;
+  for (int k = 0; k < K; k++)
+    for (int cb = 0; cb < CB; cb++)
+      if (presB[(size_t)cb * KW + k / 64] >> (k % 64) & 1) {
+        bpk_off[(size_t)k * CB + cb] = cur;
+        b_blocks.push_back(k * CB + cb);
+        cur += (int64_t)log2i_ceil_div(p->q[k], kSplitKC) * b_chunk_bytes;
+      }
+  p->bpk_bytes = cur;
+
+  // per C tile: sum over its k-list of 2*q_k (useful flops per element)
+  std::vector<double> w((size_t)M * N, 0.0);
+  for (int64_t t = 0; t < (int64_t)M * N; t++)
+    for (int64_t e = p->kptr[t]; e < p->kptr[t + 1]; e++) w[t] += 2.0 * p->q[p->klist[e]];
+
+  std::vector<uint8_t> umark((size_t)RB * CB, 0);
+  for (int i = 0; i < M; i++)
+    for (int j = 0; j < N; j++) {
+      if (!p->cs[(int64_t)i * N + j] || p->r[i] == 0 || p->c[j] == 0) continue;
+      for (int64_t rb = p->ro[i] / kSplitBM; rb <= (p->ro[i + 1] - 1) / kSplitBM; rb++)
+        for (int64_t cb = p->co[j] / tn; cb <= (p->co[j + 1] - 1) / tn; cb++) umark[rb * CB + cb] = 1;
+    }
+  for (int rb = 0; rb < RB; rb++)
+    for (int cb = 0; cb < CB; cb++) {
+      if (!umark[(size_t)rb * CB + cb]) continue;
+      p->sp_units.push_back({rb, cb});
+      const int64_t m0 = (int64_t)rb * kSplitBM, m1 = std::min<int64_t>(Mtot, m0 + kSplitBM);
+      const int64_t n0 = (int64_t)cb * tn, n1 = std::min<int64_t>(Ntot, n0 + tn);
+      double fl = 0.0;
+      int nrt = 0, nct = 0;
+      for (int i = row_tile[m0]; i < M && p->ro[i] < m1; i++) {
+        const int64_t ov_r = std::min(m1, p->ro[i + 1]) - std::max(m0, p->ro[i]);
+        if (ov_r <= 0) continue;
+        nrt++;
+        for (int j = col_tile[n0]; j < N && p->co[j] < n1; j++) {
+          const int64_t ov_c = std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]);
+          if (ov_c <= 0) continue;
+          fl += (double)ov_r * (double)ov_c * w[(int64_t)i * N + j];
+        }
+      }
+      for (int j = col_tile[n0]; j < N && p->co[j] < n1; j++)
+        if (std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]) > 0) nct++;
+      int64_t nk = 0, kq = 0, kg = 0, kc = 0;
+      for (int wd = 0; wd < KW; wd++) {
+        uint64_t bits = presA[(size_t)rb * KW + wd] & presB[(size_t)cb * KW + wd];
+        while (bits) {
+          const int k = wd * 64 + __builtin_ctzll(bits);
+          bits &= bits - 1;
+          nk++;
+          kq += p->q[k];
+          kg += log2i_ceil_div(p->q[k], 16);
+          kc += log2i_ceil_div(p->q[k], kSplitKC);
+        }
+      }
+      p->flop_cost.push_back(std::max(fl, 1.0));
+      const double padded = 2.0 * kSplitBM * tn * 16.0 * (double)kg;
+      float f[BSMM_NFEATURES] = {lg((double)(m1 - m0)), lg((double)(n1 - n0)), lg((double)nk), lg((double)kq),
+                                 lg((double)kg), lg(fl), (float)(padded > 0 ? fl / padded : 0.0),
+                                 1.0f, (float)s / 6.0f, lg(nrt), lg(nct), lg((double)kc)};
+      p->features.insert(p->features.end(), f, f + BSMM_NFEATURES);
+    }
+  p->n_units = (int64_t)p->sp_units.size();
+
+  bsmm_status st;
+  std::vector<int64_t> ro(p->ro), co(p->co);
+  if ((st = upload(p->d_ro, ro)) != BSMM_OK) return st;
+  if ((st = upload(p->d_co, co)) != BSMM_OK) return st;
+  if ((st = upload(p->d_row_tile, row_tile)) != BSMM_OK) return st;
+  if ((st = upload(p->d_col_tile, col_tile)) != BSMM_OK) return st;
+  if ((st = upload(p->d_presA, presA)) != BSMM_OK) return st;
+  if ((st = upload(p->d_presB, presB)) != BSMM_OK) return st;
+  if ((st = upload(p->d_apk_off, apk_off)) != BSMM_OK) return st;
+  if ((st = upload(p->d_bpk_off, bpk_off)) != BSMM_OK) return st;
+  if ((st = upload(p->d_a_tiles, a_tiles)) != BSMM_OK) return st;
+  if ((st = upload(p->d_b_tiles, b_tiles)) != BSMM_OK) return st;
+  if ((st = upload(p->d_a_blocks, a_blocks)) != BSMM_OK) return st;
+  if ((st = upload(p->d_b_blocks, b_blocks)) != BSMM_OK) return st;
+  if ((st = upload(p->d_units, p->sp_units)) != BSMM_OK) return st;
+  if ((st = upload(p->d_am, p->am)) != BSMM_OK) return st;
+  if ((st = upload(p->d_bm, p->bm)) != BSMM_OK) return st;
+  p->n_a_tiles = (int32_t)a_tiles.size();
+  p->n_b_tiles = (int32_t)b_tiles.size();
+  p->n_a_blocks = (int32_t)a_blocks.size();
+  p->n_b_blocks = (int32_t)b_blocks.size();
+  if ((st = dev_alloc(p->d_apk, (size_t)p->apk_bytes)) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_bpk, (size_t)p->bpk_bytes)) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_eA, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)M * K))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_eB, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)K * N))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_rowexp, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * Mtot))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_colexp, sizeof(int16_t) * ((int64_t)K * Ntot + 64))) != BSMM_OK) return st;
+  // exponents of absent tiles stay 0 (their slices are zero, so the scale is never used)
+  CUDA_TRY(cudaMemset(p->d_rowexp.p, 0, p->d_rowexp.bytes));
+  CUDA_TRY(cudaMemset(p->d_colexp.p, 0, p->d_colexp.bytes));
+  return BSMM_OK;
+}
+
+bsmm_status validate_options(const bsmm_options& o) {
+  if (o.mode < 0 || o.mode > 2) return set_error("unknown mode"), BSMM_ERR_INVALID;
+  if (o.mode != BSMM_FP64 && (o.nslices < 1 || o.nslices > kSplitMaxS))
+    return set_error("nslices must be in 1..6"), BSMM_ERR_INVALID;
+  if (o.schedule < 0 || o.schedule > 2) return set_error("unknown schedule"), BSMM_ERR_INVALID;
+  if (o.max_ctas < 0) return set_error("max_ctas < 0"), BSMM_ERR_INVALID;
+  for (int r : o.reserved)
+    if (r) return set_error("reserved option fields must be zero"), BSMM_ERR_INVALID;
+  return BSMM_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+void bsmm_options_default(bsmm_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->mode = BSMM_FP64;
+  opt->nslices = 6;
+  opt->schedule = BSMM_SCHED_FLOPS;
+}
+
+const char* bsmm_last_error(void) { return g_last_error.c_str(); }
+
+void bsmm_destroy(bsmm_plan_t p) {
+  if (!p) return;
+  DevBuf* bufs[] = {&p->d_r, &p->d_c, &p->d_q, &p->d_ro, &p->d_co, &p->d_kptr, &p->d_klist, &p->d_cs,
+                    &p->d_units, &p->d_sched_ptr, &p->d_sched_units, &p->d_row_tile, &p->d_col_tile,
+                    &p->d_presA, &p->d_presB, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
+                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_eA, &p->d_eB, &p->d_a_tiles, &p->d_b_tiles,
+                    &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta,
+                    &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
+  for (DevBuf* b : bufs) dev_free(*b);
+  delete p;
+}
+
+bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
+                      const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,
+                      const uint8_t* a_mask, const uint8_t* b_mask, const uint8_t* c_mask,
+                      const bsmm_options* opt) {
+  if (!out) return set_error("out is NULL"), BSMM_ERR_INVALID;
+  *out = nullptr;
+  if (M < 0 || N < 0 || K < 0) return set_error("negative block count"), BSMM_ERR_INVALID;
+  if ((M && !row_sizes) || (N && !col_sizes) || (K && !inner_sizes))
+    return set_error("NULL tiling"), BSMM_ERR_INVALID;
+  if (((int64_t)M * K && !a_mask) || ((int64_t)K * N && !b_mask))
+    return set_error("NULL mask"), BSMM_ERR_INVALID;
+  bsmm_options o;
+  if (opt)
+    o = *opt;
+  else
+    bsmm_options_default(&o);
+  bsmm_status st = validate_options(o);
+  if (st != BSMM_OK) return st;
+  for (int i = 0; i < M; i++)
+    if (row_sizes[i] < 0) return set_error("negative row block size"), BSMM_ERR_INVALID;
+  for (int j = 0; j < N; j++)
+    if (col_sizes[j] < 0) return set_error("negative column block size"), BSMM_ERR_INVALID;
+  for (int k = 0; k < K; k++)
+    if (inner_sizes[k] < 0) return set_error("negative inner block size"), BSMM_ERR_INVALID;
+
+  bsmm_plan_s* p = new (std::nothrow) bsmm_plan_s();
+  if (!p) return set_error("out of host memory"), BSMM_ERR_NOMEM;
+  p->M = M;
+  p->N = N;
+  p->K = K;
+  p->opt = o;
+  p->r.assign(row_sizes, row_sizes + M);
+  p->c.assign(col_sizes, col_sizes + N);
+  p->q.assign(inner_sizes, inner_sizes + K);
+  p->ro.assign(M + 1, 0);
+  p->co.assign(N + 1, 0);
+  p->qo.assign(K + 1, 0);
+  for (int i = 0; i < M; i++) p->ro[i + 1] = p->ro[i] + p->r[i];
+  for (int j = 0; j < N; j++) p->co[j + 1] = p->co[j] + p->c[j];
+  for (int k = 0; k < K; k++) p->qo[k + 1] = p->qo[k] + p->q[k];
+  p->Mtot = p->ro[M];
+  p->Ntot = p->co[N];
+  p->am.resize((size_t)M * K);
+  p->bm.resize((size_t)K * N);
+  for (int64_t t = 0; t < (int64_t)M * K; t++) p->am[t] = a_mask[t] ? 1 : 0;
+  for (int64_t t = 0; t < (int64_t)K * N; t++) p->bm[t] = b_mask[t] ? 1 : 0;
+
+  // S_C = boolean product of the masks (bitset rows), united with the C mask;
+  // per C tile the ascending k-list; the useful flop count.
+  const int KW = std::max(1, (K + 63) / 64);
+  std::vector<uint64_t> arow((size_t)M * KW, 0), bcol((size_t)N * KW, 0);
+  for (int i = 0; i < M; i++)
+    for (int k = 0; k < K; k++)
+      if (p->am[(int64_t)i * K + k]) arow[(size_t)i * KW + k / 64] |= 1ull << (k % 64);
+  for (int k = 0; k < K; k++)
+    for (int j = 0; j < N; j++)
+      if (p->bm[(int64_t)k * N + j]) bcol[(size_t)j * KW + k / 64] |= 1ull << (k % 64);
+  p->cs.assign((size_t)M * N, 0);
+  p->kptr.assign((size_t)M * N + 1, 0);
+  p->klist.clear();
+  double flops = 0.0;
+  for (int i = 0; i < M; i++)
+    for (int j = 0; j < N; j++) {
+      const int64_t t = (int64_t)i * N + j;
+      p->kptr[t] = (int64_t)p->klist.size();
+      for (int wd = 0; wd < KW; wd++) {
+        uint64_t bits = arow[(size_t)i * KW + wd] & bcol[(size_t)j * KW + wd];
+        while (bits) {
+          const int k = wd * 64 + __builtin_ctzll(bits);
+          bits &= bits - 1;
+          p->klist.push_back(k);
+          flops += 2.0 * (double)p->r[i] * (double)p->c[j] * (double)p->q[k];
+        }
+      }
+      const bool any = (int64_t)p->klist.size() > p->kptr[t];
+      p->cs[t] = (any || (c_mask && c_mask[t])) ? 1 : 0;
+      p->n_ctiles += p->cs[t];
+    }
+  p->kptr[(size_t)M * N] = (int64_t)p->klist.size();
+  p->n_triples = (int64_t)p->klist.size();
+  p->useful_flops = flops;
+
+  cudaError_t ce = cudaGetDevice(&p->device);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (ce != cudaSuccess) {
+    set_error(std::string("no CUDA device: ") + cudaGetErrorString(ce));
+    delete p;
+    return BSMM_ERR_CUDA;
+  }
+
+  if (o.mode == BSMM_FP64) {
+    st = plan_fp64(p);
+  } else {
+    p->s = o.nslices;
+    p->tn = split_tile_n(p->s);
+    p->stages = split_stages(p->s, p->tn);
+    st = plan_split(p);
+  }
+  if (st != BSMM_OK) {
+    bsmm_destroy(p);
+    return st;
+  }
+  p->cost = p->flop_cost;
+  p->ctas = default_ctas(p);
+  pack_lpt(p);
+
+  std::vector<int32_t> r(p->r), c(p->c), q(p->q);
+  std::vector<int32_t> klist(p->klist);
+  if (klist.empty()) klist.push_back(0);
+  if ((st = upload(p->d_r, r)) != BSMM_OK || (st = upload(p->d_c, c)) != BSMM_OK ||
+      (st = upload(p->d_q, q)) != BSMM_OK || (st = upload(p->d_kptr, p->kptr)) != BSMM_OK ||
+      (st = upload(p->d_klist, klist)) != BSMM_OK || (st = upload(p->d_cs, p->cs)) != BSMM_OK ||
+      (st = upload_schedule(p)) != BSMM_OK) {
+    bsmm_destroy(p);
+    return st;
+  }
+  if (o.mode == BSMM_FP64 && (st = upload(p->d_units, p->f64_units)) != BSMM_OK) {
+    bsmm_destroy(p);
+    return st;
+  }
+  if ((st = dev_alloc(p->d_err, sizeof(int32_t))) != BSMM_OK) {
+    bsmm_destroy(p);
+    return st;
+  }
+  if (cudaMemset(p->d_err.p, 0, sizeof(int32_t)) != cudaSuccess) {
+    set_error("cudaMemset of the error word failed");
+    bsmm_destroy(p);
+    return BSMM_ERR_CUDA;
+  }
+  if (o.record_timings) {
+    if ((st = dev_alloc(p->d_timings, sizeof(int64_t) * 2 * std::max<int64_t>(1, p->n_units))) != BSMM_OK ||
+        (st = dev_alloc(p->d_unit_cta, sizeof(int32_t) * std::max<int64_t>(1, p->n_units))) != BSMM_OK) {
+      bsmm_destroy(p);
+      return st;
+    }
+  }
+  *out = p;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_plan_query(bsmm_plan_t p, int64_t* n_ctiles, int64_t* n_triples, double* useful_flops,
+                            uint8_t* c_mask_out, int64_t* n_units) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if (n_ctiles) *n_ctiles = p->n_ctiles;
+  if (n_triples) *n_triples = p->n_triples;
+  if (useful_flops) *useful_flops = p->useful_flops;
+  if (c_mask_out && !p->cs.empty()) std::memcpy(c_mask_out, p->cs.data(), p->cs.size());
+  if (n_units) *n_units = p->n_units;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_plan_features(bsmm_plan_t p, float* features, double* flop_costs) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if (features && !p->features.empty())
+    std::memcpy(features, p->features.data(), sizeof(float) * p->features.size());
+  if (flop_costs && !p->flop_cost.empty())
+    std::memcpy(flop_costs, p->flop_cost.data(), sizeof(double) * p->flop_cost.size());
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_plan_set_costs(bsmm_plan_t p, const double* costs) {
+  if (!p || !costs) return set_error("NULL argument"), BSMM_ERR_INVALID;
+  for (int64_t u = 0; u < p->n_units; u++)
+    if (!(costs[u] > 0.0) || !std::isfinite(costs[u])) return set_error("costs must be finite and > 0"), BSMM_ERR_INVALID;
+  p->cost.assign(costs, costs + p->n_units);
+  p->opt.schedule = BSMM_SCHED_COSTS;
+  pack_lpt(p);
+  return upload_schedule(p);
+}
+
+bsmm_status bsmm_plan_set_ctas(bsmm_plan_t p, int32_t ctas) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if (ctas < 0 || ctas > 65535) return set_error("ctas out of range"), BSMM_ERR_INVALID;
+  p->ctas = ctas == 0 ? default_ctas(p) : (int)std::min<int64_t>(ctas, std::max<int64_t>(1, p->n_units));
+  pack_lpt(p);
+  return upload_schedule(p);
+}
+
+}  // extern "C"

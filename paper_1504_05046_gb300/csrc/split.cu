@@ -1,0 +1,686 @@
+// Split-precision tile tasks on the tcgen05 tensor cores.
+//
+// The tile tasks C_ij += A_ik B_kj (paper Sec. 2.1) are computed with
+// error-free Ozaki-style slicing (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms
+// 59, 2012), one power-of-two scale per tile:
+//   e = smallest integer with max|x| < 2^e over the tile, rho_0 = x 2^-e,
+//   N_t = rint(rho_{t-1} 2^(7t)), rho_t = rho_{t-1} - N_t 2^(-7t),  t = 1..s,
+// so every slice is an integer of at most 8 bits, exact in bfloat16 and float16.
+// For one tile pair the diagonal sums S_d = sum_{p+q=d} NA_p NB_q (d = 2..s+1)
+// are integer matrices; with |S_d| <= 2^24 (inner blocks up to 512 elements for
+// s = 6) the FP32 tensor-core accumulator holds them exactly. The epilogue forms
+// T = sum_d S_d 2^(7(s+1-d)) exactly in int64 and adds fl(T) 2^(eA+eB-7(s+1)) into
+// an FP64 accumulator, one k block at a time in ascending order. The result is
+// therefore fixed bit for bit, independent of schedule and unit order.
+//
+// Kernels, in launch order:
+//   1. split_exp_kernel   per stored tile: the exponent e (FP64 max reduction),
+//                         written per tile and expanded per row (A) / column (B).
+//   2. split_pack_kernel  per (128-row block, k block) of A and (k block, tn-column
+//                         block) of B: the s slices, stored as bf16/fp16 in the
+//                         exact shared-memory image the tensor core reads (K-major,
+//                         64-byte swizzle, 32-element chunks), so the contraction
+//                         kernel moves them with plain 1-D bulk copies.
+//   3. split_mma_kernel   persistent, one CTA per SM, warp-specialised:
+//                         warp 0 streams packed chunks into an S-stage shared-memory
+//                         ring with cp.async.bulk (several k panels in flight -- the
+//                         on-chip form of the paper's multiple-issue SUMMA
+//                         iterations, Sec. 3.2); warp 1 issues tcgen05.mma into
+//                         double-buffered TMEM accumulators; warps 2..9 drain TMEM,
+//                         recombine in integer + FP64 and store C = alpha*acc + beta*C.
+// A work unit is a 128-row x tn-column block of the global C index space; the CTA
+// that owns it runs every inner block in ascending order.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "bsmm_internal.h"
+
+namespace bsmm {
+
+namespace {
+
+constexpr int64_t kWaitNs = 4000000000LL;  // bounded waits: 4 s, then error + abort
+constexpr int kEpiThreads = kSplitEpiWarps * 32;
+constexpr int kThreads = 64 + kEpiThreads;  // producer warp + MMA warp + epilogue warps
+constexpr uint32_t kTmemCols = 512;
+constexpr int kAChunk = kSplitBM * kSplitKC * 2;  // bytes of one slice of a 128x32 A chunk
+
+__device__ __forceinline__ int64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (int64_t)t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Single-thread bounded wait. False on timeout (sets the error word and the abort
+// flag) or when another role aborted.
+__device__ bool wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const int64_t t0 = gtimer();
+  for (uint32_t spin = 1;; spin++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if ((spin & 63) == 0 && gtimer() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+
+// Warp-uniform bounded wait (every lane polls; the decision is taken by the warp).
+__device__ bool wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  const int64_t t0 = gtimer();
+  for (uint32_t spin = 1;; spin++) {
+    const bool ok = mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    int stop = *abort_flag;
+    if ((spin & 63) == 0 && gtimer() - t0 > kWaitNs) stop = 2;
+    if (__any_sync(0xffffffffu, stop != 0)) {
+      if (stop == 2 && (threadIdx.x & 31) == 0) {
+        *abort_flag = 1;
+        atomicOr(err, kErrTimeout);
+      }
+      __syncwarp();
+      return false;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- bulk copy
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------- tcgen05
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 or fp16 in, fp32 accumulate)
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups of
+// 64-byte rows (stride between 8-row groups = 512 bytes).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address (16-byte units)
+  d |= (uint64_t)0 << 16;                   // leading byte offset: unused (one swizzle atom along K)
+  d |= (uint64_t)(512u >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+  d |= (uint64_t)4 << 61;                   // layout: 64-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16 (or fp16), both K-major.
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N, bool fp16) {
+  const uint32_t fmt = fp16 ? 0u : 1u;
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (row, k) inside one 64-byte-swizzled chunk slice (rows of 32 elements)
+__device__ __forceinline__ uint32_t swz64(int row, int k) {
+  const int ch = k >> 3;
+  return (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ double pow2i(int e) {  // 2^e for -1022 <= e <= 1023
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// ---------------------------------------------------------------- kernel 1: exponents
+__global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
+  const int b = blockIdx.x;
+  const bool isA = b < a.n_a_tiles;
+  const int t = isA ? a.a_tiles[b] : a.b_tiles[b - a.n_a_tiles];
+  int rows, cols;
+  int64_t off;
+  if (isA) {
+    const int i = t / a.K, k = t % a.K;
+    rows = a.r[i];
+    cols = a.q[k];
+    off = a.a_off[t];
+  } else {
+    const int k = t / a.N, j = t % a.N;
+    rows = a.q[k];
+    cols = a.c[j];
+    off = a.b_off[t];
+  }
+  const double* x = (isA ? a.A : a.B) + (off < 0 ? 0 : off);
+  const int64_t n = (int64_t)rows * cols;
+  double mx = 0.0;
+  int bad = 0;
+  if (off >= 0) {
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const double v = fabs(__ldg(x + e));
+      if (!(v <= 1.7976931348623157e308)) bad = 1;  // NaN or infinity
+      mx = fmax(mx, v);
+    }
+  }
+  __shared__ double red[8];
+  __shared__ int redbad[8];
+  for (int o = 16; o; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = mx;
+    redbad[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  __shared__ int e_sh;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    int bb = off < 0 ? 1 : 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      m = fmax(m, red[w]);
+      bb |= redbad[w];
+    }
+    int e = 0;
+    if (bb) {
+      atomicOr(a.err, off < 0 ? kErrBadOffset : kErrNonFinite);
+    } else if (m > 0.0) {
+      frexp(m, &e);  // m = f 2^e, f in [0.5, 1): smallest e with m < 2^e
+    }
+    e_sh = e;
+    if (isA)
+      a.eA[t] = e;
+    else
+      a.eB[t] = e;
+  }
+  __syncthreads();
+  const int16_t e16 = (int16_t)e_sh;
+  if (isA) {
+    const int i = t / a.K, k = t % a.K;
+    int16_t* dst = a.rowexp + (int64_t)k * a.Mtot;
+    for (int64_t m = a.ro[i] + threadIdx.x; m < a.ro[i + 1]; m += blockDim.x) dst[m] = e16;
+  } else {
+    const int k = t / a.N, j = t % a.N;
+    int16_t* dst = a.colexp + (int64_t)k * a.Ntot;
+    for (int64_t m = a.co[j] + threadIdx.x; m < a.co[j + 1]; m += blockDim.x) dst[m] = e16;
+  }
+}
+
+// ---------------------------------------------------------------- kernel 2: slices
+// Slice 8 consecutive inner elements (one 16-byte chunk of a swizzled row) of one
+// packed row and store the s chunks.
+template <typename T>
+__device__ __forceinline__ void slice_store8(const double (&x)[8], int e, int s, uint8_t* base, int slice_stride,
+                                             uint32_t soff) {
+  // rho_0 = x 2^-e, in two exact power-of-two steps that stay in the normal range
+  const int e1 = e >> 1, e2 = e - e1;
+  const double p1 = pow2i(-e1), p2 = pow2i(-e2);
+  double rho[8];
+#pragma unroll
+  for (int u = 0; u < 8; u++) rho[u] = (x[u] * p1) * p2;
+  for (int t = 1; t <= s; t++) {
+    const double up = pow2i(kSplitBeta * t), dn = pow2i(-kSplitBeta * t);
+    T h[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const double n = rint(rho[u] * up);
+      rho[u] = fma(-n, dn, rho[u]);  // exact: the residual is representable
+      if constexpr (sizeof(T) == 2 && std::is_same<T, __nv_bfloat16>::value)
+        h[u] = __double2bfloat16(n);
+      else
+        h[u] = __double2half(n);
+    }
+    *reinterpret_cast<uint4*>(base + (size_t)(t - 1) * slice_stride + soff) = *reinterpret_cast<uint4*>(h);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
+  const int s = a.s;
+  if ((int)blockIdx.x < a.n_a_blocks) {
+    // A block (rb, kt): chunks of 128 rows x 32 inner elements
+    const int blk = a.a_blocks[blockIdx.x];
+    const int rb = blk / a.K, kt = blk % a.K;
+    const int q = a.q[kt];
+    const int nkc = (q + kSplitKC - 1) / kSplitKC;
+    uint8_t* out = a.apk + a.apk_off[blk];
+    for (int item = threadIdx.x; item < nkc * kSplitBM * 4; item += blockDim.x) {
+      const int ch = item & 3, rr = (item >> 2) % kSplitBM, kc = (item >> 2) / kSplitBM;
+      const int64_t m = (int64_t)rb * kSplitBM + rr;
+      double x[8];
+      int e = 0;
+      bool present = false;
+      int64_t off = -1;
+      int i = 0;
+      if (m < a.Mtot) {
+        i = a.row_tile[m];
+        present = a.am[(int64_t)i * a.K + kt] != 0;
+        off = a.a_off[(int64_t)i * a.K + kt];
+        if (present && off < 0) {
+          atomicOr(a.err, kErrBadOffset);
+          present = false;
+        }
+        e = a.rowexp[(int64_t)kt * a.Mtot + m];
+      }
+      const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int k = kc * kSplitKC + ch * 8 + u;
+        x[u] = (present && k < q) ? __ldg(a.A + off + lr * q + k) : 0.0;
+      }
+      slice_store8<T>(x, e, s, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
+    }
+  } else {
+    // B block (kt, cb): chunks of tn rows (columns of B) x 32 inner elements, transposed
+    const int blk = a.b_blocks[blockIdx.x - a.n_a_blocks];
+    const int kt = blk / a.CB, cb = blk % a.CB;
+    const int q = a.q[kt];
+    const int tn = a.tn;
+    const int nkc = (q + kSplitKC - 1) / kSplitKC;
+    const int bchunk = tn * kSplitKC * 2;
+    uint8_t* out = a.bpk + a.bpk_off[blk];
+    for (int item = threadIdx.x; item < nkc * tn * 4; item += blockDim.x) {
+      const int nn = item % tn, ch = (item / tn) & 3, kc = (item / tn) >> 2;
+      const int64_t n = (int64_t)cb * tn + nn;
+      double x[8];
+      int e = 0;
+      bool present = false;
+      int64_t off = -1;
+      int j = 0, cj = 0;
+      if (n < a.Ntot) {
+        j = a.col_tile[n];
+        cj = a.c[j];
+        present = a.bm[(int64_t)kt * a.N + j] != 0;
+        off = a.b_off[(int64_t)kt * a.N + j];
+        if (present && off < 0) {
+          atomicOr(a.err, kErrBadOffset);
+          present = false;
+        }
+        e = a.colexp[(int64_t)kt * a.Ntot + n];
+      }
+      const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int k = kc * kSplitKC + ch * 8 + u;
+        x[u] = (present && k < q) ? __ldg(a.B + off + (int64_t)k * cj + lc) : 0.0;
+      }
+      slice_store8<T>(x, e, s, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- kernel 3: contraction
+struct UnitIter {  // ascending k blocks of one unit: presA[rb] & presB[cb]
+  const uint64_t* pa;
+  const uint64_t* pb;
+  int kwords, wd;
+  uint64_t bits;
+  __device__ void init(const SplitArgs& a, int rb, int cb) {
+    pa = a.presA + (size_t)rb * a.kwords;
+    pb = a.presB + (size_t)cb * a.kwords;
+    kwords = a.kwords;
+    wd = 0;
+    bits = pa[0] & pb[0];
+  }
+  __device__ int next() {  // -1 when done
+    while (!bits) {
+      if (++wd >= kwords) return -1;
+      bits = pa[wd] & pb[wd];
+    }
+    const int k = wd * 64 + __ffsll((long long)bits) - 1;
+    bits &= bits - 1;
+    return k;
+  }
+};
+
+template <int S, int TN>
+__global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
+  constexpr int TH = TN / 2;                    // columns per epilogue thread
+  constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
+  constexpr int B_STAGE = S * TN * kSplitKC * 2;
+  constexpr int STAGE = A_STAGE + B_STAGE;
+  constexpr int BUF_COLS = S * TN;              // TMEM columns per accumulator buffer
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int stages = a.stages;
+  uint64_t* bars = (uint64_t*)(smem + (size_t)stages * STAGE);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + stages;
+  uint64_t* tfull = bars + 2 * stages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cta = blockIdx.x;
+  const int ubeg = a.sched_ptr[cta], uend = a.sched_ptr[cta + 1];
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < stages; st++) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kSplitEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued = 0;  // bit st: stage st holds an issued copy; its parity in issued_par
+      uint32_t issued_par = 0;
+      bool ok = true;
+      for (int idx = ubeg; idx < uend && ok; idx++) {
+        const SplitUnit un = a.units[a.sched_units[idx]];
+        UnitIter it;
+        it.init(a, un.rb, un.cb);
+        for (int kt = it.next(); kt >= 0 && ok; kt = it.next()) {
+          const int nkc = (a.q[kt] + kSplitKC - 1) / kSplitKC;
+          const uint8_t* asrc = a.apk + a.apk_off[(size_t)un.rb * a.K + kt];
+          const uint8_t* bsrc = a.bpk + a.bpk_off[(size_t)kt * a.CB + un.cb];
+          for (int kc = 0; kc < nkc; kc++) {
+            if (!wait1(&empty[stage], phase ^ 1, abort_flag, a.err)) {
+              ok = false;
+              break;
+            }
+            uint8_t* sa = smem + (size_t)stage * STAGE;
+            mbar_arrive_expect_tx(&full[stage], STAGE);
+            bulk_g2s(sa, asrc + (size_t)kc * A_STAGE, A_STAGE, &full[stage]);
+            bulk_g2s(sa + A_STAGE, bsrc + (size_t)kc * B_STAGE, B_STAGE, &full[stage]);
+            issued |= 1u << stage;
+            issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      // drain: every copy this thread issued has landed before the CTA may exit
+      for (int st = 0; st < stages; st++) {
+        if (!(issued >> st & 1)) continue;
+        const uint32_t par = issued_par >> st & 1;
+        const int64_t t0 = gtimer();
+        while (!mbar_try_wait(&full[st], par)) {
+          if (gtimer() - t0 > kWaitNs) {
+            atomicOr(a.err, kErrTimeout);
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t tcount = 0;
+      bool ok = true;
+      bool any = false;
+      for (int idx = ubeg; idx < uend && ok; idx++) {
+        const SplitUnit un = a.units[a.sched_units[idx]];
+        UnitIter it;
+        it.init(a, un.rb, un.cb);
+        for (int kt = it.next(); kt >= 0 && ok; kt = it.next()) {
+          const int q = a.q[kt];
+          const int nkc = (q + kSplitKC - 1) / kSplitKC;
+          const uint32_t buf = tcount & 1, use = tcount >> 1;
+          if (!wait1(&tempty[buf], (use & 1) ^ 1, abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dbase = tmem_base + buf * BUF_COLS;
+          for (int kc = 0; kc < nkc; kc++) {
+            if (!wait1(&full[stage], phase, abort_flag, a.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE);
+            const uint32_t sb = sa + A_STAGE;
+            const int rem = q - kc * kSplitKC;
+            const int nsteps = rem > 16 ? 2 : 1;
+            for (int ks = 0; ks < nsteps; ks++) {
+#pragma unroll
+              for (int p = 1; p <= S; p++) {
+                const uint64_t ad = sdesc_sw64(sa + (p - 1) * kAChunk + ks * 32);
+                const uint64_t bd = sdesc_sw64(sb + ks * 32);
+                const uint32_t id = idesc_f16(kSplitBM, (S + 1 - p) * TN, a.fp16 != 0);
+                const uint32_t acc = (kc | ks) != 0 || p > 1;
+                umma_f16(dbase + (p - 1) * TN, ad, bd, id, acc);
+              }
+            }
+            umma_commit(&empty[stage]);  // frees the stage when these MMAs finish
+            any = true;
+            if (++stage == stages) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          if (!ok) break;
+          umma_commit(&tfull[buf]);
+          tcount++;
+        }
+      }
+      // drain: every MMA this thread issued has completed before TMEM is released
+      if (any) {
+        umma_commit(drain);
+        const int64_t t0 = gtimer();
+        while (!mbar_try_wait(drain, 0)) {
+          if (gtimer() - t0 > kWaitNs) {
+            atomicOr(a.err, kErrTimeout);
+            break;
+          }
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    const int ew = warp - 2;           // 0..7
+    const int quad = warp & 3;         // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;          // which half of the tn columns
+    const int row = quad * 32 + lane;  // row inside the unit
+    uint32_t tcount = 0;
+    bool ok = true;
+    for (int idx = ubeg; idx < uend && ok; idx++) {
+      const int u = a.sched_units[idx];
+      const SplitUnit un = a.units[u];
+      if (a.timings && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = gtimer();
+      const int64_t m = (int64_t)un.rb * kSplitBM + row;
+      const bool row_ok = m < a.Mtot;
+      const int64_t n0 = (int64_t)un.cb * TN + half * TH;
+      double acc[TH];
+#pragma unroll
+      for (int c = 0; c < TH; c++) acc[c] = 0.0;
+      UnitIter it;
+      it.init(a, un.rb, un.cb);
+      for (int kt = it.next(); kt >= 0; kt = it.next()) {
+        const uint32_t buf = tcount & 1, use = tcount >> 1;
+        if (!wait_warp(&tfull[buf], use & 1, abort_flag, a.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int ea = row_ok ? (int)a.rowexp[(int64_t)kt * a.Mtot + m] : 0;
+        const int16_t* cex = a.colexp + (int64_t)kt * a.Ntot + n0;
+        const int ebase = ea - kSplitBeta * (S + 1);
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BUF_COLS + half * TH;
+#pragma unroll
+        for (int cc = 0; cc < TH / 8; cc++) {
+          uint32_t v[S][8];
+#pragma unroll
+          for (int d = 0; d < S; d++) tmem_ld8(taddr + d * TN + cc * 8, v[d]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < 8; c++) {
+            const int64_t n = n0 + cc * 8 + c;
+            const int eb = n < a.Ntot ? (int)cex[cc * 8 + c] : 0;
+            long long T = 0;
+#pragma unroll
+            for (int d = 0; d < S; d++) {
+              int iv;
+              asm("cvt.rni.s32.f32 %0, %1;" : "=r"(iv) : "f"(__uint_as_float(v[d][c])));
+              T = (T << kSplitBeta) + (long long)iv;
+            }
+            const int E = ebase + eb;
+            const double Td = __ll2double_rn(T);
+            if (E >= -1022 && E <= 1023)
+              acc[cc * 8 + c] = fma(Td, pow2i(E), acc[cc * 8 + c]);
+            else
+              acc[cc * 8 + c] = __dadd_rn(acc[cc * 8 + c], scalbn(Td, E));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        tcount++;
+      }
+      if (!ok) break;
+      // C = alpha*acc + beta*C on the unit's elements that lie in S_C tiles
+      if (row_ok) {
+        const int i = a.row_tile[m];
+        const int64_t lr = m - a.ro[i];
+#pragma unroll
+        for (int c = 0; c < TH; c++) {
+          const int64_t n = n0 + c;
+          if (n < a.Ntot) {
+            const int j = a.col_tile[n];
+            const int64_t tile = (int64_t)i * a.N + j;
+            const int64_t off = a.cs[tile] ? a.c_off[tile] : -2;
+            if (off == -1) atomicOr(a.err, kErrBadOffset);
+            if (off >= 0) {
+              double* dst = a.C + off + lr * a.c[j] + (n - a.co[j]);
+              double vv = __dmul_rn(a.alpha, acc[c]);
+              if (a.beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(a.beta, *dst));
+              *dst = vv;
+            }
+          }
+        }
+      }
+      if (a.timings) {
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+        if (ew == 0 && lane == 0) {
+          a.timings[2 * (int64_t)u + 1] = gtimer();
+          a.unit_cta[u] = cta;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, kTmemCols);
+}
+
+template <int S, int TN>
+cudaError_t launch_mma(const SplitArgs& a, int ctas, cudaStream_t st) {
+  const size_t smem = split_smem_bytes(S, TN, a.stages);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  split_mma_kernel<S, TN><<<ctas, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st) {
+  if (a.n_a_tiles + a.n_b_tiles > 0) {
+    split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.n_a_blocks + a.n_b_blocks > 0) {
+    if (a.fp16)
+      split_pack_kernel<__half><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
+    else
+      split_pack_kernel<__nv_bfloat16><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  switch (a.s) {
+    case 1: return launch_mma<1, 64>(a, ctas, st);
+    case 2: return launch_mma<2, 64>(a, ctas, st);
+    case 3: return launch_mma<3, 64>(a, ctas, st);
+    case 4: return launch_mma<4, 64>(a, ctas, st);
+    case 5: return launch_mma<5, 32>(a, ctas, st);
+    case 6: return launch_mma<6, 32>(a, ctas, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bsmm

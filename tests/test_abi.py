@@ -1,0 +1,67 @@
+"""The C ABI library without a GPU: it builds, loads, exports every declared
+symbol, and rejects invalid arguments with status codes (no compute calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1504_05046_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(bsmm_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.lib()
+    decl = declared_functions()
+    assert len(decl) >= 10
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(P.EXPORTED) == sorted(n for n in decl if n in P.EXPORTED)
+    assert set(decl) <= set(P.EXPORTED)
+
+
+def test_options_default():
+    o = P.bsmm_options_default()
+    assert (o.mode, o.nslices, o.schedule, o.max_ctas) == (P.BSMM_FP64, 6, P.BSMM_SCHED_FLOPS, 0)
+
+
+def test_invalid_arguments_return_status():
+    L = P.lib()
+    r = np.array([4, -1], np.int32)
+    m = np.ones((2, 2), np.uint8)
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan(r, r, r, m, m)
+    assert ei.value.status == 1 and "negative" in str(ei.value)
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan([4], [4], [4], [[1]], [[1]], mode=7)
+    assert ei.value.status == 1
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan([4], [4], [4], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=9)
+    assert ei.value.status == 1
+    # NULL handles are rejected, never dereferenced
+    assert L.bsmm_plan_query(None, None, None, None, None, None) == 1
+    assert L.bsmm_execute(None, 1.0, None, None, None, None, 0.0, None, None, None) == 1
+    assert L.bsmm_status_device(None, None) == 1
+    L.bsmm_destroy(None)
+    assert "NULL" in P.bsmm_last_error() or P.bsmm_last_error() != ""
+
+
+def test_plan_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan([4], [4], [4], [[1]], [[1]])
+    assert ei.value.status == 2

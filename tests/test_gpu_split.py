@@ -1,0 +1,125 @@
+"""GPU parity of the split-precision tensor-core path, through the C ABI.
+
+Two comparisons per case:
+  * against the split oracle (the slicing algorithm's steps in numpy): the
+    recombination is exact up to one stated rounding per k block, so the GPU must
+    agree bit for bit;
+  * against the FP64 oracle, at the stated accuracy bars: 6 slices <= 1e-11 and
+    3 slices <= 1e-5 relative Frobenius error.
+"""
+import numpy as np
+import pytest
+
+import bsmm_gen as G
+import oracle
+from oracle import split as OS
+import paper_1504_05046_gb300 as P
+from helpers import c_arena, rel_fro, struct_elements
+
+pytestmark = pytest.mark.gpu
+BARS = {1: 1e-1, 2: 1e-3, 3: 1e-5, 4: 1e-7, 5: 1e-9, 6: 1e-11}
+
+
+def check(prob, s, mode=P.BSMM_SPLIT_BF16, c_mask=None, bar=None, **kw):
+    from gpu_helpers import run_lib
+    cs, _, _ = oracle.structure(prob, c_mask)
+    off, C0 = c_arena(prob, cs, rng=np.random.default_rng(0))
+    Csplit = C0.copy()
+    OS.bsmm_split(prob, cs, Csplit, off, s)
+    C64 = C0.copy()
+    oracle.bsmm(prob, cs, C64, off)
+    Cg, plan = run_lib(prob, cs, C0, off, mode=mode, nslices=s, c_mask=c_mask, **kw)
+    got = struct_elements(prob, cs, off, Cg)
+    want = struct_elements(prob, cs, off, Csplit)
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        raise AssertionError(f"{bad.size} of {got.size} elements differ from the split oracle; "
+                             f"first {bad[:5]}: got {got[bad[:5]]} want {want[bad[:5]]}; "
+                             f"rel err {rel_fro(got, want):.3e}")
+    err = rel_fro(got, struct_elements(prob, cs, off, C64))
+    assert err <= (bar if bar is not None else BARS[s]), err
+    return Cg, plan, err
+
+
+def test_tiny_single_unit():
+    rng = np.random.default_rng(0)
+    r = np.array([20], np.int32)
+    q = np.array([24], np.int32)
+    c = np.array([12], np.int32)
+    am = np.ones((1, 1), np.uint8)
+    bm = np.ones((1, 1), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    prob = G.Problem("tiny", r, c, q, am, bm, a_off, b_off, rng.integers(-3, 4, at).astype(float),
+                     rng.integers(-3, 4, bt).astype(float), 1.0, 0.0)
+    check(prob, 1, bar=0.0)
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6])
+def test_slices_dense_nonuniform(s):
+    prob = G.make_problem("nonuniform_dense", 20 + s, 700, lo=64, hi=256)
+    check(prob, s)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_ragged(seed):
+    prob = G.random_small(seed, max_blocks=6, max_size=70)
+    check(prob, 6)
+
+
+def test_fp16_storage_bit_identical_to_bf16():
+    prob = G.make_problem("uniform_bernoulli", 3, 600, block=100, density=0.5)
+    a, _, _ = check(prob, 6, mode=P.BSMM_SPLIT_BF16)
+    b, _, _ = check(prob, 6, mode=P.BSMM_SPLIT_FP16)
+    assert np.array_equal(a, b)
+
+
+def test_banded_decay_wide_range():
+    prob = G.make_problem("banded_decay_wide", 5, 1500, lo=32, hi=160, band=4)
+    check(prob, 6, mode=P.BSMM_SPLIT_FP16)
+
+
+def test_clustered_small_blocks():
+    prob = G.make_problem("clustered", 6, 1200, lo=16, hi=200, nclusters=8, cluster_density=0.2)
+    check(prob, 6)
+
+
+def test_integer_inputs_equal_fp64():
+    prob = G.make_problem("nonuniform_dense", 7, 500, lo=30, hi=120, values="integers")
+    Cg, _, err = check(prob, 2, bar=0.0)
+    assert err == 0.0
+
+
+def test_alpha_beta_c_mask():
+    prob = G.make_problem("uniform_bernoulli", 8, 450, block=70, density=0.4)
+    prob.alpha, prob.beta = 0.5, -2.0
+    cm = (np.random.default_rng(3).random((prob.M, prob.N)) < 0.25).astype(np.uint8)
+    check(prob, 6, c_mask=cm)
+
+
+def test_max_depth_inner_block():
+    rng = np.random.default_rng(2)
+    r = np.array([130, 70], np.int32)
+    q = np.array([512, 1, 300], np.int32)
+    c = np.array([40, 96], np.int32)
+    am = np.ones((2, 3), np.uint8)
+    bm = np.ones((3, 2), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    prob = G.Problem("deep", r, c, q, am, bm, a_off, b_off, rng.uniform(-1, 1, at), rng.uniform(-1, 1, bt), 1.0, 0.0)
+    check(prob, 6)
+
+
+def test_too_deep_inner_block_is_rejected():
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan([8], [8], [513], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6)
+    assert ei.value.status == 5
+
+
+@pytest.mark.parametrize("ctas", [1, 5, 151])
+def test_schedule_independent_bits(ctas):
+    prob = G.make_problem("clustered", 9, 900, lo=16, hi=160, nclusters=6, cluster_density=0.25)
+    base, plan, _ = check(prob, 6)
+    n = P.bsmm_plan_query(plan)["n_units"]
+    again, _, _ = check(prob, 6, ctas=ctas, costs=np.random.default_rng(ctas).uniform(1, 5, n))
+    assert np.array_equal(base, again)
