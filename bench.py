@@ -1,0 +1,403 @@
+"""Benchmark: useful TFLOP/s of the block-sparse product on one GB300 per rank.
+
+Workload (one step = one pass of the whole device path: tile exponents, slicing,
+tensor-core contraction, recombination and epilogue): the dense square product
+of order 16384 with nonuniform block sizes drawn uniform-integer in [64, 256] on
+rows, columns and inner dimension, entries U[-1,1] in FP64 -- the paper's
+nonuniformly blocked square matrices (Sec. 4.1) at single-GPU scale. The headline
+path is the 6-slice split-bfloat16 mode (FP32 tensor-core accumulation, FP64
+recombination); the plain FP64 path is timed beside it on the same inputs, and
+the split result is compared with it (the FP64 path reproduces the CPU oracle bit
+for bit, so that error is the error against the oracle).
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the product does not need
+any exchange between GPUs); the reported value is the sum over ranks divided by
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "useful TFLOP/s (nonzero-tile flops) & % of peak; split vs FP64 at <=1e-11 rel err"
+PROFILE_FILE = os.path.join(ROOT, "profiles", "split_mma_kernel_nonuniform_dense.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=16384, help="matrix order")
+    ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return f"nonuniform_dense N={n} blocks U-int[64,256] (rows=cols=inner), dense masks, U[-1,1] FP64"
+
+
+# --------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("split.cu", "bsmm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1504_05046_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the contraction kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    try:
+        vals = {}
+        with open(PROFILE_FILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(vals["dram_bytes_per_full_launch"])
+    except Exception:
+        return None
+
+
+def make_inputs(n, seed):
+    import bsmm_gen as G
+    prob = G.make_problem("nonuniform_dense", seed, n, lo=64, hi=256)
+    return prob
+
+
+def run_reference(args, rank):
+    """The CPU oracle as it stands, on the host cores: each step computes a bounded
+    sample (whole C tile rows of the workload) and reports useful TFLOP/s."""
+    import bsmm_gen as G
+    import oracle
+    prob = make_inputs(args.n, args.seed)
+    cs, _, _ = oracle.structure(prob)
+    rows = pick_rows(prob, 1)
+    sub, subcs = row_subproblem(prob, cs, rows)
+    off, tot = G.layout_arena(subcs, sub.row_sizes, sub.col_sizes)
+    _, _, fl = oracle.structure(sub)
+    C = np.zeros(tot)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.bsmm(sub, subcs, C, off)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot_t = sum(times)
+    val = fl * len(times) / tot_t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.n), "sample": f"C tile row {rows[0]} of {prob.M} "
+                       f"({sub.row_sizes.sum()} rows x {prob.col_sizes.sum()} cols, full inner dim)"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"one C tile row per step ({fl / 1e9:.1f} GFLOP)"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def pick_rows(prob, count):
+    return list(range(min(count, prob.M)))
+
+
+def row_subproblem(prob, cs, rows):
+    """The C tile rows `rows` of the product as a problem of its own (same inner and
+    column tilings, the A tiles of those rows)."""
+    import bsmm_gen as G
+    r = prob.row_sizes[rows]
+    am = prob.a_mask[rows]
+    a_off, a_tot = G.layout_arena(am, r, prob.inner_sizes)
+    A = np.zeros(a_tot)
+    for ii, i in enumerate(rows):
+        for k in range(prob.K):
+            if am[ii, k]:
+                n = int(r[ii]) * int(prob.inner_sizes[k])
+                A[a_off[ii, k]:a_off[ii, k] + n] = prob.A[prob.a_off[i, k]:prob.a_off[i, k] + n]
+    sub = G.Problem(prob.name + "_rows", r, prob.col_sizes, prob.inner_sizes, am, prob.b_mask, a_off, prob.b_off, A,
+                    prob.B, prob.alpha, prob.beta)
+    return sub, cs[rows]
+
+
+def cpu_baseline(prob, cs, Cgpu, c_off, seconds):
+    """Oracle on host cores over whole C tile rows until `seconds` have passed; also
+    returns the max relative error of the GPU result on those rows."""
+    import bsmm_gen as G
+    import oracle
+    done_fl, done_t, errs, nrows = 0.0, 0.0, [], 0
+    for i in range(prob.M):
+        sub, subcs = row_subproblem(prob, cs, [i])
+        off, tot = G.layout_arena(subcs, sub.row_sizes, sub.col_sizes)
+        C = np.zeros(tot)
+        _, _, fl = oracle.structure(sub)
+        t0 = time.perf_counter()
+        oracle.bsmm(sub, subcs, C, off)
+        done_t += time.perf_counter() - t0
+        done_fl += fl
+        nrows += 1
+        # compare with the GPU's row
+        num = den = 0.0
+        for j in range(prob.N):
+            if subcs[0, j]:
+                n = int(sub.row_sizes[0]) * int(prob.col_sizes[j])
+                g = Cgpu[c_off[i, j]:c_off[i, j] + n]
+                o = C[off[0, j]:off[0, j] + n]
+                num += float(np.sum((g - o) ** 2))
+                den += float(np.sum(o ** 2))
+        errs.append((num / den) ** 0.5 if den else 0.0)
+        if done_t >= seconds:
+            break
+    return {"value": done_fl / done_t / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nrows} C tile row(s) of {prob.M} ({done_fl / 1e9:.1f} GFLOP, full inner dimension), "
+                      f"{done_t:.1f} s"}, max(errs) if errs else None
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import bsmm_gen as G
+    import paper_1504_05046_gb300 as P
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prob = make_inputs(args.n, args.seed + rank)
+    s = args.slices
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1)
+    q = P.bsmm_plan_query(plan)
+    F = q["useful_flops"]
+    cs = q["c_mask"]
+    c_off, c_tot = G.layout_arena(cs, prob.row_sizes, prob.col_sizes)
+    dev = torch.device("cuda", local)
+    A = torch.from_numpy(prob.A).to(dev)
+    B = torch.from_numpy(prob.B).to(dev)
+    ao = torch.from_numpy(prob.a_off).to(dev)
+    bo = torch.from_numpy(prob.b_off).to(dev)
+    co = torch.from_numpy(c_off).to(dev)
+    C = torch.zeros(c_tot, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
+    torch.cuda.synchronize()
+    P.bsmm_status_device(plan)
+
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kms = []
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
+        ks = P.bsmm_plan_kernel_ms(plan)
+        kms.append(ks)
+        launches += len(ks)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t_rank = torch.tensor([ms], dtype=torch.float64, device=dev)
+    f_rank = torch.tensor([F], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f_rank, op=dist.ReduceOp.SUM)
+    ms_max = float(t_rank.item())
+    value = float(f_rank.item()) / (ms_max * 1e-3) / 1e12
+    P.bsmm_status_device(plan)
+    Csplit = C.cpu().numpy()
+
+    # per-kernel live times (CUDA events on the launching stream)
+    kk = np.array(kms)
+    k_names = ["split_exp_kernel", "split_pack_kernel", "split_mma_kernel"]
+    k_avg = {nm: float(kk[:, i].mean()) for i, nm in enumerate(k_names)}
+    t_mma = k_avg["split_mma_kernel"] * 1e-3
+    pk, pk_src = peaks()
+    pair_flops = s * (s + 1) / 2 * F
+    mma_tflops = pair_flops / t_mma / 1e12
+    peak_tc = pk["bf16_tflops_sustained"]
+    roofline = {"bound": "tensor", "kernel": "split_mma_kernel", "achieved": mma_tflops, "peak": peak_tc,
+                "unit": "TFLOP/s", "frac": mma_tflops / peak_tc, "traffic": profiled_traffic(),
+                "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
+                "achieved_def": f"{s * (s + 1) // 2} slice-pair products x useful flops per launch / mean launch time",
+                "kernel_ms": k_avg}
+
+    extra = {}
+    if rank == 0 and not args.no_fp64:
+        plan64 = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                             mode=P.BSMM_FP64, profile=1)
+        C64 = torch.zeros_like(C)
+        P.bsmm_execute(plan64, 1.0, A, ao, B, bo, 0.0, C64, co)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            P.bsmm_execute(plan64, 1.0, A, ao, B, bo, 0.0, C64, co)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        P.bsmm_status_device(plan64)
+        ms64 = f0.elapsed_time(f1) / args.fp64_steps
+        c64 = C64.cpu().numpy()
+        d = Csplit - c64
+        err = float(np.linalg.norm(d) / np.linalg.norm(c64))
+        fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        extra["fp64_path"] = {"value": F / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
+                              "roofline": {"bound": "alu", "peak": fp64_peak, "unit": "TFLOP/s",
+                                           "frac": F / (ms64 * 1e-3) / 1e12 / fp64_peak,
+                                           "peak_def": "152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}}
+        extra["split_rel_err_vs_fp64"] = err
+        extra["split_speedup_vs_fp64"] = ms64 / ms_max
+        del plan64, C64
+
+    # end to end through the public C ABI with host buffers (pinned)
+    e2e = None
+    if args.e2e_steps > 0:
+        hA = torch.from_numpy(prob.A).pin_memory()
+        hB = torch.from_numpy(prob.B).pin_memory()
+        hC = torch.zeros(c_tot, dtype=torch.float64).pin_memory()
+        hao = torch.from_numpy(prob.a_off).pin_memory()
+        hbo = torch.from_numpy(prob.b_off).pin_memory()
+        hco = torch.from_numpy(c_off).pin_memory()
+        P.bsmm_execute_host(plan, 1.0, hA, hao, hB, hbo, 0.0, hC, hco)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            P.bsmm_execute_host(plan, 1.0, hA, hao, hB, hbo, 0.0, hC, hco)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        h2d = (prob.A.nbytes + prob.B.nbytes + prob.a_off.nbytes + prob.b_off.nbytes + c_off.nbytes)
+        e2e = {"value": float(f_rank.item()) / float(tt.item()) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(c_tot * 8),
+               "ms_per_step": float(tt.item()) * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, row_err = cpu_baseline(prob, cs, Csplit, c_off, args.cpu_seconds)
+        extra["split_rel_err_vs_oracle_sampled_rows"] = row_err
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": workload_name(args.n), "mode": f"split_bf16 s={s} (fp32 tensor-core accumulate,"
+                           " exact int64 diagonal combine, fp64 recombination)", "useful_flops_per_step": F,
+                           "l2": "inputs larger than L2 (A and B 2.1 GB each), no flush",
+                           "parallelism": f"replicas x{world}", "seed": args.seed},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

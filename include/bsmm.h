@@ -80,7 +80,8 @@ typedef struct {
   int32_t max_ctas;        /* persistent grid size cap; 0 = one per SM (times residency) */
   int32_t debug_checks;    /* 1 = kernels validate offsets against the plan */
   int32_t record_timings;  /* 1 = record per-unit start/end times (bsmm_plan_timings) */
-  int32_t reserved[6];     /* must be zero */
+  int32_t profile;         /* 1 = time each internal kernel with CUDA events (bsmm_plan_kernel_ms) */
+  int32_t reserved[5];     /* must be zero */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */
@@ -172,6 +173,15 @@ bsmm_status bsmm_status_device(bsmm_plan_t plan, void* stream);
  * Synchronises the device.
  */
 bsmm_status bsmm_plan_timings(bsmm_plan_t plan, int64_t* start_ns, int64_t* end_ns, int32_t* cta);
+
+/*
+ * Device time of each internal kernel of the last execute of a plan built with
+ * profile = 1, measured with CUDA events recorded on the execute's stream around
+ * every launch. ms[max_n] host output (kernel order: split modes = exponents,
+ * slicing, contraction; FP64 = contraction); *count = kernels recorded.
+ * Synchronises on the last event.
+ */
+bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t plan, float* ms, int32_t max_n, int32_t* count);
 
 /* Thread-local message for the last failing call ("" if none). */
 const char* bsmm_last_error(void);

@@ -22,13 +22,20 @@ power-of-two scale per tile:
     T   = sum_d S_d * 2^(beta*(s+1-d))    (an exact integer)
     contribution = T * 2^(e_A + e_B - beta*(s+1))
 
-  accumulation over k in ascending order, one rounding each:
-    acc <- fl( acc + fl(T) * 2^(e_A + e_B - beta*(s+1)) )
-  and the epilogue C_ij = fl(alpha*acc) + fl(beta*C_ij), as in the FP64 oracle.
+  accumulation, exact, then one rounding:
+    each C element of tile (i, j) is the exact sum over its k blocks of
+      T_k * 2^(E_k),  E_k = e_A(i,k) + e_B(k,j) - beta*(s+1),
+    held as an integer multiple of 2^L with
+      L = Emax_A(i) + Emax_B(j) - beta*(s+1) - GUARD_BITS,
+    where Emax_A(i) is the largest exponent of the stored A tiles of row block i
+    (Emax_B(j) likewise for column block j; 0 when there is none). A term with
+    E_k < L enters as floor(T_k 2^(E_k - L)) (never for exponent spans up to
+    GUARD_BITS binades); the sum is then rounded once to FP64 (round to nearest
+    even) and scaled by 2^L, and the epilogue is C_ij = fl(alpha*acc) + fl(beta*C_ij)
+    as in the FP64 oracle.
 
-fl(T) rounds the exact integer T to FP64 once (round to nearest even), and the
-multiplication by a power of two is exact, so every value here is determined
-independently of how the integer sums are formed.
+Because the sum is exact before its single rounding, the value does not depend on
+the order in which tile pairs, slice pairs or k blocks are added.
 
 All integer matrix products below go through a float64 matmul: every entry is an
 integer of magnitude below 2^53, so the library routine returns it exactly in
@@ -36,9 +43,12 @@ any summation order.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 BETA_BITS = 7
+GUARD_BITS = 55
 
 
 def tile_exponent(x: np.ndarray) -> int:
@@ -110,17 +120,29 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
             cacheB[(k, j)] = (e, sl)
         return cacheB[(k, j)]
 
+    def emax_a(i):
+        ks = [k for k in range(K) if am[i, k] and r[i] > 0 and q[k] > 0]
+        return max((a_sl(i, k)[0] for k in ks), default=0)
+
+    def emax_b(j):
+        ks = [k for k in range(K) if bm[k, j] and c[j] > 0 and q[k] > 0]
+        return max((b_sl(k, j)[0] for k in ks), default=0)
+
     todo = tiles if tiles is not None else [(i, j) for i in range(M) for j in range(N) if c_struct[i, j]]
     alpha, bet = float(prob_like.alpha), float(prob_like.beta)
     for (i, j) in todo:
-        acc = np.zeros((r[i], c[j]), np.float64)
+        L = emax_a(i) + emax_b(j) - beta * (s + 1) - GUARD_BITS
+        exact = np.zeros((r[i], c[j]), dtype=object)
+        exact[...] = 0
         for k in range(K):
             if not (am[i, k] and bm[k, j]):
                 continue
             eA, na = a_sl(i, k)
             eB, nb = b_sl(k, j)
-            T = pair_integer(na, nb, s, beta)
-            acc = acc + np.ldexp(T.astype(np.float64), eA + eB - beta * (s + 1))
+            T = pair_integer(na, nb, s, beta).astype(object)
+            sh = eA + eB - beta * (s + 1) - L
+            exact = exact + (T * (1 << sh) if sh >= 0 else T // (1 << -sh))  # floor below 2^L
+        acc = np.array([math.ldexp(float(v), L) for v in exact.reshape(-1)], np.float64).reshape(r[i], c[j])
         o = int(c_off[i, j])
         ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
         u = alpha * acc

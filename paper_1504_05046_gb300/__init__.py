@@ -23,7 +23,7 @@ __all__ = [
     "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
-    "bsmm_last_error", "bsmm_destroy", "EXPORTED",
+    "bsmm_plan_kernel_ms", "bsmm_last_error", "bsmm_destroy", "EXPORTED",
 ]
 
 BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
@@ -36,7 +36,7 @@ STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_
 EXPORTED = [
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
-    "bsmm_last_error", "bsmm_destroy",
+    "bsmm_plan_kernel_ms", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -49,7 +49,7 @@ class BsmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("nslices", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
-                ("record_timings", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -77,6 +77,7 @@ def lib():
         L.bsmm_execute_host.argtypes = [P, f64, P, i64, P, P, i64, P, f64, P, i64, P, P]
         L.bsmm_status_device.argtypes = [P, P]
         L.bsmm_plan_timings.argtypes = [P, P, P, P]
+        L.bsmm_plan_kernel_ms.argtypes = [P, P, i32, P]
         L.bsmm_last_error.argtypes = []
         L.bsmm_last_error.restype = ctypes.c_char_p
         L.bsmm_destroy.argtypes = [P]
@@ -150,7 +151,7 @@ class Plan:
 
 def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *, mode: int = BSMM_FP64,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
-              record_timings: int = 0) -> Plan:
+              record_timings: int = 0, profile: int = 0) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -159,7 +160,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     cm = None if c_mask is None else _np(c_mask, np.uint8)
     o = bsmm_options_default()
     o.mode, o.nslices, o.schedule, o.max_ctas = mode, nslices, schedule, max_ctas
-    o.debug_checks, o.record_timings = debug_checks, record_timings
+    o.debug_checks, o.record_timings, o.profile = debug_checks, record_timings, profile
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))
@@ -218,6 +219,14 @@ def bsmm_plan_timings(plan: Plan):
     cta = np.zeros(n, np.int32)
     _check(lib().bsmm_plan_timings(plan.handle, _ptr(s), _ptr(e), _ptr(cta)))
     return s, e, cta
+
+
+def bsmm_plan_kernel_ms(plan: Plan):
+    """Per-kernel device milliseconds of the last execute (plan built with profile=1)."""
+    ms = (ctypes.c_float * 8)()
+    n = ctypes.c_int32()
+    _check(lib().bsmm_plan_kernel_ms(plan.handle, ms, 8, ctypes.byref(n)))
+    return [float(ms[i]) for i in range(n.value)]
 
 
 def bsmm_destroy(plan: Plan):

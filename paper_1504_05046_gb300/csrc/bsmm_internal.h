@@ -24,6 +24,8 @@ constexpr int kSplitKC = 32;       // inner elements per staged chunk (64-byte s
 constexpr int kSplitBeta = 7;      // bits per slice
 constexpr int kSplitMaxS = 6;      // slices per operand
 constexpr int kSplitEpiWarps = 8;  // epilogue warps (2 per TMEM lane quadrant)
+constexpr int kSplitGuard = 55;    // guard bits of the 128-bit accumulator below the largest scale
+constexpr int kSplitMaxK = 8192;   // inner blocks per product (keeps the 128-bit sum from overflowing)
 
 // FP64-mode geometry.
 constexpr int kF64BM = 64, kF64BN = 64, kF64BK = 16, kF64Threads = 256;
@@ -95,8 +97,11 @@ struct SplitArgs {
   const int64_t* bpk_off;   // K x CB byte offsets into bpk (-1 absent)
   uint8_t* apk;
   uint8_t* bpk;
-  int16_t* rowexp;          // K x Mtot
-  int16_t* colexp;          // K x Ntot
+  int16_t* rowexp;          // K x Mtot: e_A(i,k) - Emax_A(i) per row (0 for absent tiles)
+  int16_t* colexp;          // K x colexp_ld: e_B(k,j) - Emax_B(j) per column
+  int64_t colexp_ld;        // row stride of colexp (Ntot rounded up to 64)
+  int32_t* eAmax;           // M: largest exponent of the stored A tiles of a row block
+  int32_t* eBmax;           // N
   int32_t* eA;              // M x K
   int32_t* eB;              // K x N
   const int32_t* a_tiles;   // present A tiles (i*K+k), count n_a_tiles
@@ -121,8 +126,11 @@ struct SplitArgs {
   int32_t debug;
 };
 
-cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st);
-cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st);
+// ev: null, or kMaxEvents events; ev[0] is recorded before the first kernel and
+// ev[i+1] after kernel i. *nk receives the number of kernels launched.
+constexpr int kMaxEvents = 8;
+cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk);
+cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk);
 int fp64_ctas_per_sm();
 
 void set_error(const std::string& msg);
@@ -153,15 +161,19 @@ struct bsmm_plan_s {
 
   // split geometry
   int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0;
-  int64_t Mtot = 0, Ntot = 0;
+  int64_t Mtot = 0, Ntot = 0, colexp_ld = 0;
   int64_t apk_bytes = 0, bpk_bytes = 0;
 
   // device memory
   bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
   bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_apk_off, d_bpk_off, d_apk, d_bpk;
-  bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_eA, d_eB, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
+  bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
   bsmm::DevBuf d_err, d_timings, d_unit_cta;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;
+
+  // per-kernel profiling events (profile option)
+  cudaEvent_t ev[bsmm::kMaxEvents] = {};
+  int ev_count = 0;
 
   // host-buffer execute staging (grown on demand)
   bsmm::DevBuf h_A, h_B, h_C, h_aoff, h_boff, h_coff;

@@ -1,4 +1,5 @@
 // C ABI: execution entry points, device status, timing records.
+#include <algorithm>
 #include <cstring>
 
 #include "bsmm_internal.h"
@@ -68,8 +69,11 @@ bsmm_status fill_split(bsmm_plan_s* p, SplitArgs& a, double alpha, const double*
   a.bpk = (uint8_t*)p->d_bpk.p;
   a.rowexp = (int16_t*)p->d_rowexp.p;
   a.colexp = (int16_t*)p->d_colexp.p;
+  a.colexp_ld = p->colexp_ld;
   a.eA = (int32_t*)p->d_eA.p;
   a.eB = (int32_t*)p->d_eB.p;
+  a.eAmax = (int32_t*)p->d_eAmax.p;
+  a.eBmax = (int32_t*)p->d_eBmax.p;
   a.a_tiles = (const int32_t*)p->d_a_tiles.p;
   a.b_tiles = (const int32_t*)p->d_b_tiles.p;
   a.n_a_tiles = p->n_a_tiles;
@@ -110,14 +114,21 @@ bsmm_status run(bsmm_plan_s* p, double alpha, const double* A, const int64_t* a_
                 const int64_t* b_off, double beta, double* C, const int64_t* c_off, cudaStream_t st) {
   if (p->n_units == 0) return BSMM_OK;
   cudaError_t e;
+  cudaEvent_t* ev = nullptr;
+  if (p->opt.profile) {
+    if (!p->ev[0])
+      for (int i = 0; i < kMaxEvents; i++)
+        if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return set_error("cudaEventCreate failed"), BSMM_ERR_CUDA;
+    ev = p->ev;
+  }
   if (p->opt.mode == BSMM_FP64) {
     Fp64Args a{};
     fill_fp64(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
-    e = launch_fp64(a, p->ctas, st);
+    e = launch_fp64(a, p->ctas, st, ev, &p->ev_count);
   } else {
     SplitArgs a{};
     fill_split(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
-    e = launch_split(a, p->ctas, st);
+    e = launch_split(a, p->ctas, st, ev, &p->ev_count);
   }
   if (e != cudaSuccess) {
     set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -203,6 +214,18 @@ bsmm_status bsmm_status_device(bsmm_plan_t p, void* stream) {
   if (w & kErrTimeout) return set_error("a kernel wait timed out"), BSMM_ERR_TIMEOUT;
   if (w & kErrBadOffset) return set_error("a kernel found a missing or invalid tile offset"), BSMM_ERR_DEVICE;
   if (w & kErrNonFinite) return set_error("non-finite input element in a split mode"), BSMM_ERR_DEVICE;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t p, float* ms, int32_t max_n, int32_t* count) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if (!p->opt.profile || !p->ev[0]) return set_error("plan has no profile events (profile option, one execute)"), BSMM_ERR_INVALID;
+  const int n = std::min<int>(p->ev_count, max_n);
+  if (cudaEventSynchronize(p->ev[p->ev_count]) != cudaSuccess) return set_error("event sync failed"), BSMM_ERR_CUDA;
+  for (int i = 0; i < n; i++)
+    if (cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]) != cudaSuccess)
+      return set_error("cudaEventElapsedTime failed"), BSMM_ERR_CUDA;
+  if (count) *count = p->ev_count;
   return BSMM_OK;
 }
 

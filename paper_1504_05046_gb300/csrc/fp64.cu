@@ -187,8 +187,11 @@ int fp64_ctas_per_sm() {
   return n;
 }
 
-cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st) {
+cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
+  if (ev) cudaEventRecord(ev[0], st);
   fp64_tile_kernel<<<ctas, NT, 0, st>>>(a);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (nk) *nk = 1;
   return cudaGetLastError();
 }
 

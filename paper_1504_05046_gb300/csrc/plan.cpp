@@ -31,7 +31,9 @@ int split_max_depth(int s) {
   return (int)std::floor(std::ldexp(1.0, 24) / per);
 }
 
-int split_tile_n(int s) { return s >= 5 ? 32 : 64; }
+// 32 columns per unit: 16 per epilogue thread keeps the 128-bit accumulators in registers,
+// and two TMEM buffers of s*32 columns fit the 512 columns for every s <= 6.
+int split_tile_n(int) { return 32; }
 
 static size_t stage_bytes(int s, int tn) {
   return (size_t)s * (kSplitBM * kSplitKC * 2) + (size_t)s * (tn * kSplitKC * 2);
@@ -192,6 +194,10 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   p->kwords = std::max(1, (K + 63) / 64);
   const int RB = p->RB, CB = p->CB, KW = p->kwords;
   const int maxd = split_max_depth(s);
+  if (K > kSplitMaxK) {
+    set_error("split modes take at most " + std::to_string(kSplitMaxK) + " inner blocks");
+    return BSMM_ERR_UNSUPPORTED;
+  }
   for (int k = 0; k < K; k++)
     if (p->q[k] > maxd) {
       set_error("inner block " + std::to_string(k) + " has " + std::to_string(p->q[k]) +
@@ -323,8 +329,11 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   if ((st = dev_alloc(p->d_bpk, (size_t)p->bpk_bytes)) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_eA, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)M * K))) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_eB, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)K * N))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_eAmax, sizeof(int32_t) * std::max(1, M))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_eBmax, sizeof(int32_t) * std::max(1, N))) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_rowexp, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * Mtot))) != BSMM_OK) return st;
-  if ((st = dev_alloc(p->d_colexp, sizeof(int16_t) * ((int64_t)K * Ntot + 64))) != BSMM_OK) return st;
+  p->colexp_ld = (Ntot + 63) / 64 * 64 + 64;  // padded rows: aligned 16-byte loads past the last column
+  if ((st = dev_alloc(p->d_colexp, sizeof(int16_t) * ((int64_t)K * p->colexp_ld + 64))) != BSMM_OK) return st;
   // exponents of absent tiles stay 0 (their slices are zero, so the scale is never used)
   CUDA_TRY(cudaMemset(p->d_rowexp.p, 0, p->d_rowexp.bytes));
   CUDA_TRY(cudaMemset(p->d_colexp.p, 0, p->d_colexp.bytes));
@@ -337,6 +346,7 @@ bsmm_status validate_options(const bsmm_options& o) {
     return set_error("nslices must be in 1..6"), BSMM_ERR_INVALID;
   if (o.schedule < 0 || o.schedule > 2) return set_error("unknown schedule"), BSMM_ERR_INVALID;
   if (o.max_ctas < 0) return set_error("max_ctas < 0"), BSMM_ERR_INVALID;
+  if (o.profile < 0 || o.profile > 1) return set_error("profile must be 0 or 1"), BSMM_ERR_INVALID;
   for (int r : o.reserved)
     if (r) return set_error("reserved option fields must be zero"), BSMM_ERR_INVALID;
   return BSMM_OK;
@@ -364,10 +374,12 @@ void bsmm_destroy(bsmm_plan_t p) {
   DevBuf* bufs[] = {&p->d_r, &p->d_c, &p->d_q, &p->d_ro, &p->d_co, &p->d_kptr, &p->d_klist, &p->d_cs,
                     &p->d_units, &p->d_sched_ptr, &p->d_sched_units, &p->d_row_tile, &p->d_col_tile,
                     &p->d_presA, &p->d_presB, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
-                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_eA, &p->d_eB, &p->d_a_tiles, &p->d_b_tiles,
+                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
                     &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
   for (DevBuf* b : bufs) dev_free(*b);
+  for (cudaEvent_t& e : p->ev)
+    if (e) cudaEventDestroy(e);
   delete p;
 }
 

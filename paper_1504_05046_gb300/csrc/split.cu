@@ -9,13 +9,16 @@
 // For one tile pair the diagonal sums S_d = sum_{p+q=d} NA_p NB_q (d = 2..s+1)
 // are integer matrices; with |S_d| <= 2^24 (inner blocks up to 512 elements for
 // s = 6) the FP32 tensor-core accumulator holds them exactly. The epilogue forms
-// T = sum_d S_d 2^(7(s+1-d)) exactly in int64 and adds fl(T) 2^(eA+eB-7(s+1)) into
-// an FP64 accumulator, one k block at a time in ascending order. The result is
-// therefore fixed bit for bit, independent of schedule and unit order.
+// T = sum_d S_d 2^(7(s+1-d)) exactly in int64 and adds T, shifted to its binary
+// position e_A + e_B - 7(s+1), into an exact 128-bit integer accumulator per C
+// element (no floating-point rounding and no FP64 instruction in the k loop; GB300's
+// FP64 pipe is narrow). The sum is rounded once to FP64 at the end of the unit, so
+// the result is fixed bit for bit, independent of schedule, unit order and k order.
 //
 // Kernels, in launch order:
-//   1. split_exp_kernel   per stored tile: the exponent e (FP64 max reduction),
-//                         written per tile and expanded per row (A) / column (B).
+//   1. split_exp_kernel   per stored tile: the exponent e (FP64 max reduction);
+//      split_scale_kernel per row / column block: the largest tile exponent and the
+//                         per-row / per-column offsets from it.
 //   2. split_pack_kernel  per (128-row block, k block) of A and (k block, tn-column
 //                         block) of B: the s slices, stored as bf16/fp16 in the
 //                         exact shared-memory image the tensor core reads (K-major,
@@ -27,12 +30,14 @@
 //                         on-chip form of the paper's multiple-issue SUMMA
 //                         iterations, Sec. 3.2); warp 1 issues tcgen05.mma into
 //                         double-buffered TMEM accumulators; warps 2..9 drain TMEM,
-//                         recombine in integer + FP64 and store C = alpha*acc + beta*C.
+//                         recombine in integer arithmetic and store
+//                         C = alpha*fl(sum) + beta*C.
 // A work unit is a 128-row x tn-column block of the global C index space; the CTA
 // that owns it runs every inner block in ascending order.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -181,9 +186,6 @@ __device__ __forceinline__ uint32_t swz64(int row, int k) {
   return (uint32_t)(row * 64 + ((ch ^ ((row >> 1) & 3)) << 4) + ((k & 7) << 1));
 }
 
-__device__ __forceinline__ double pow2i(int e) {  // 2^e for -1022 <= e <= 1023
-  return __longlong_as_double((long long)(e + 1023) << 52);
-}
 
 // ---------------------------------------------------------------- kernel 1: exponents
 __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
@@ -225,7 +227,6 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
     redbad[threadIdx.x >> 5] = bad;
   }
   __syncthreads();
-  __shared__ int e_sh;
   if (threadIdx.x == 0) {
     double m = 0.0;
     int bb = off < 0 ? 1 : 0;
@@ -239,48 +240,113 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
     } else if (m > 0.0) {
       frexp(m, &e);  // m = f 2^e, f in [0.5, 1): smallest e with m < 2^e
     }
-    e_sh = e;
     if (isA)
       a.eA[t] = e;
     else
       a.eB[t] = e;
   }
+}
+
+// ---------------------------------------------------------------- kernel 1b: relative scales
+// Per row block i: Emax_A(i) = largest exponent of its stored A tiles, and for every
+// k and every row of the block rowexp[k][m] = e_A(i,k) - Emax_A(i) (0 for an absent
+// tile); the same per column block for B. The contraction adds each tile pair's exact
+// integer at the binary position GUARD + rowexp + colexp of a 128-bit accumulator whose
+// unit is 2^(Emax_A(i) + Emax_B(j) - 7(s+1) - GUARD).
+__global__ void __launch_bounds__(256) split_scale_kernel(SplitArgs a) {
+  const bool isA = (int)blockIdx.x < a.M;
+  const int t = isA ? blockIdx.x : blockIdx.x - a.M;
+  __shared__ int emax_sh;
+  if (threadIdx.x == 0) {
+    int em = INT_MIN;
+    if (isA) {
+      if (a.r[t] > 0)
+        for (int k = 0; k < a.K; k++)
+          if (a.am[(int64_t)t * a.K + k] && a.q[k] > 0) em = max(em, a.eA[(int64_t)t * a.K + k]);
+    } else {
+      if (a.c[t] > 0)
+        for (int k = 0; k < a.K; k++)
+          if (a.bm[(int64_t)k * a.N + t] && a.q[k] > 0) em = max(em, a.eB[(int64_t)k * a.N + t]);
+    }
+    if (em == INT_MIN) em = 0;
+    emax_sh = em;
+    if (isA)
+      a.eAmax[t] = em;
+    else
+      a.eBmax[t] = em;
+  }
   __syncthreads();
-  const int16_t e16 = (int16_t)e_sh;
+  const int em = emax_sh;
   if (isA) {
-    const int i = t / a.K, k = t % a.K;
-    int16_t* dst = a.rowexp + (int64_t)k * a.Mtot;
-    for (int64_t m = a.ro[i] + threadIdx.x; m < a.ro[i + 1]; m += blockDim.x) dst[m] = e16;
+    const int64_t m0 = a.ro[t], n = a.ro[t + 1] - m0;
+    for (int64_t e = threadIdx.x; e < n * a.K; e += blockDim.x) {
+      const int k = (int)(e / n);
+      const bool pres = a.am[(int64_t)t * a.K + k] && a.q[k] > 0;
+      a.rowexp[(int64_t)k * a.Mtot + m0 + e % n] = (int16_t)(pres ? a.eA[(int64_t)t * a.K + k] - em : 0);
+    }
   } else {
-    const int k = t / a.N, j = t % a.N;
-    int16_t* dst = a.colexp + (int64_t)k * a.Ntot;
-    for (int64_t m = a.co[j] + threadIdx.x; m < a.co[j + 1]; m += blockDim.x) dst[m] = e16;
+    const int64_t n0 = a.co[t], n = a.co[t + 1] - n0;
+    for (int64_t e = threadIdx.x; e < n * a.K; e += blockDim.x) {
+      const int k = (int)(e / n);
+      const bool pres = a.bm[(int64_t)k * a.N + t] && a.q[k] > 0;
+      a.colexp[(int64_t)k * a.colexp_ld + n0 + e % n] = (int16_t)(pres ? a.eB[(int64_t)k * a.N + t] - em : 0);
+    }
   }
 }
 
 // ---------------------------------------------------------------- kernel 2: slices
 // Slice 8 consecutive inner elements (one 16-byte chunk of a swizzled row) of one
 // packed row and store the s chunks.
+// The slicing recurrence N_t = rint(rho_{t-1} 2^(7t)), rho_t = rho_{t-1} - N_t 2^(-7t)
+// telescopes: with Z_t = sum_{u<=t} N_u 2^(7(t-u)) one has Z_t = rint(x 2^(7t-e)) (the
+// subtracted 128 Z_{t-1} is even, so round-half-even commutes with it), hence
+// N_t = Z_t - 128 Z_{t-1}. Each Z_t is computed exactly from the mantissa with integer
+// shifts and a round-half-even step; no floating-point operation is involved.
+__device__ __forceinline__ long long rint_scaled(long long m, int sh) {  // rint(m 2^sh), m >= 0
+  if (sh >= 0) return m << sh;
+  const int k = -sh;
+  if (k >= 63) return 0;  // m < 2^53 <= 2^(k-1): below one half
+  const long long q = m >> k;
+  const long long rem = m & ((1ll << k) - 1);
+  const long long half = 1ll << (k - 1);
+  return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+}
+
+template <typename T>
+__device__ __forceinline__ uint16_t small_int_bits(int n) {  // |n| <= 256, exact in bf16/fp16
+  const float f = __int_as_float(0x4B400000 + n) - 12582912.0f;  // exact for |n| < 2^22
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    return (uint16_t)(__float_as_uint(f) >> 16);  // <= 8 significant bits: truncation is exact
+  } else {
+    return __half_as_ushort(__float2half_rn(f));
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void slice_store8(const double (&x)[8], int e, int s, uint8_t* base, int slice_stride,
                                              uint32_t soff) {
-  // rho_0 = x 2^-e, in two exact power-of-two steps that stay in the normal range
-  const int e1 = e >> 1, e2 = e - e1;
-  const double p1 = pow2i(-e1), p2 = pow2i(-e2);
-  double rho[8];
+  long long m[8], z[8];
+  int ex[8];
+  bool neg[8];
 #pragma unroll
-  for (int u = 0; u < 8; u++) rho[u] = (x[u] * p1) * p2;
+  for (int u = 0; u < 8; u++) {
+    const long long b = __double_as_longlong(x[u]);
+    neg[u] = b < 0;
+    const int be = (int)((b >> 52) & 0x7FF);
+    const long long frac = b & ((1ll << 52) - 1);
+    m[u] = be ? (frac | (1ll << 52)) : frac;
+    ex[u] = (be ? be : 1) - 1075 - e;  // x 2^-e = +-m 2^ex
+    z[u] = 0;
+  }
   for (int t = 1; t <= s; t++) {
-    const double up = pow2i(kSplitBeta * t), dn = pow2i(-kSplitBeta * t);
-    T h[8];
+    uint16_t h[8];
 #pragma unroll
     for (int u = 0; u < 8; u++) {
-      const double n = rint(rho[u] * up);
-      rho[u] = fma(-n, dn, rho[u]);  // exact: the residual is representable
-      if constexpr (sizeof(T) == 2 && std::is_same<T, __nv_bfloat16>::value)
-        h[u] = __double2bfloat16(n);
-      else
-        h[u] = __double2half(n);
+      long long zt = rint_scaled(m[u], ex[u] + kSplitBeta * t);
+      if (neg[u]) zt = -zt;
+      const int n = (int)(zt - (z[u] << kSplitBeta));
+      z[u] = zt;
+      h[u] = small_int_bits<T>(n);
     }
     *reinterpret_cast<uint4*>(base + (size_t)(t - 1) * slice_stride + soff) = *reinterpret_cast<uint4*>(h);
   }
@@ -312,7 +378,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
           atomicOr(a.err, kErrBadOffset);
           present = false;
         }
-        e = a.rowexp[(int64_t)kt * a.Mtot + m];
+        e = a.eA[(int64_t)i * a.K + kt];
       }
       const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
 #pragma unroll
@@ -348,7 +414,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
           atomicOr(a.err, kErrBadOffset);
           present = false;
         }
-        e = a.colexp[(int64_t)kt * a.Ntot + n];
+        e = a.eB[(int64_t)kt * a.N + j];
       }
       const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
 #pragma unroll
@@ -359,6 +425,71 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       slice_store8<T>(x, e, s, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
     }
   }
+}
+
+// ---------------------------------------------------------------- exact accumulation
+// w (four 32-bit words, two's complement) += T * 2^sh, with floor(T / 2^-sh) for sh < 0.
+// |T| < 2^59 and sh <= kSplitGuard for every stored tile pair; an absent pair has T = 0.
+__device__ __forceinline__ void acc_add(uint32_t (&w)[4], long long T, int sh) {
+  const int sl = min(max(sh, 0), 63);
+  long long lo = T << sl;
+  long long hi = sl ? (T >> (64 - sl)) : (T >> 63);
+  if (sh < 0) {
+    lo = T >> min(-sh, 63);
+    hi = T >> 63;
+  }
+  asm("add.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.cc.u32 %2, %2, %6;\n\t"
+      "addc.u32 %3, %3, %7;"
+      : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
+      : "r"((uint32_t)lo), "r"((uint32_t)((unsigned long long)lo >> 32)), "r"((uint32_t)hi),
+        "r"((uint32_t)((unsigned long long)hi >> 32)));
+}
+
+// 64-bit window of a 128-bit magnitude shifted right by r (0 <= r < 128)
+__device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsigned long long lo, int r) {
+  if (r == 0) return lo;
+  if (r < 64) return (lo >> r) | (hi << (64 - r));
+  return hi >> (r - 64);
+}
+
+// Round the 128-bit integer w to the nearest double (ties to even) and scale by 2^L.
+__device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
+  unsigned long long lo = ((unsigned long long)w[1] << 32) | w[0];
+  unsigned long long hi = ((unsigned long long)w[3] << 32) | w[2];
+  const bool neg = (long long)hi < 0;
+  if (neg) {
+    lo = ~lo;
+    hi = ~hi;
+    lo += 1;
+    if (lo == 0) hi += 1;
+  }
+  if (hi == 0 && lo == 0) return 0.0;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  int r = msb - 52;
+  unsigned long long mant;
+  if (r <= 0) {
+    mant = lo;  // fits in 53 bits: exact
+    r = 0;
+  } else {
+    mant = shr128(hi, lo, r);
+    const bool round = shr128(hi, lo, r - 1) & 1;
+    bool sticky;
+    if (r - 1 <= 64)
+      sticky = (r - 1 == 64) ? lo != 0 : (lo & ((1ull << (r - 1)) - 1)) != 0;
+    else
+      sticky = lo != 0 || (hi & ((1ull << (r - 1 - 64)) - 1)) != 0;
+    if (round && (sticky || (mant & 1))) {
+      mant += 1;
+      if (mant >> 53) {
+        mant >>= 1;
+        r += 1;
+      }
+    }
+  }
+  const double d = scalbn((double)mant, r + L);
+  return neg ? -d : d;
 }
 
 // ---------------------------------------------------------------- kernel 3: contraction
@@ -559,9 +690,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
       const int64_t m = (int64_t)un.rb * kSplitBM + row;
       const bool row_ok = m < a.Mtot;
       const int64_t n0 = (int64_t)un.cb * TN + half * TH;
-      double acc[TH];
+      uint32_t acc[TH][4];  // exact 128-bit two's-complement sums, unit 2^L per column
 #pragma unroll
-      for (int c = 0; c < TH; c++) acc[c] = 0.0;
+      for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
       UnitIter it;
       it.init(a, un.rb, un.cb);
       for (int kt = it.next(); kt >= 0; kt = it.next()) {
@@ -571,9 +702,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
           break;
         }
         tc_fence_after();
-        const int ea = row_ok ? (int)a.rowexp[(int64_t)kt * a.Mtot + m] : 0;
-        const int16_t* cex = a.colexp + (int64_t)kt * a.Ntot + n0;
-        const int ebase = ea - kSplitBeta * (S + 1);
+        // binary position of this k block's integer in the accumulator
+        const int shr = kSplitGuard + (row_ok ? (int)a.rowexp[(int64_t)kt * a.Mtot + m] : 0);
+        int16_t rb[TH];
+        {
+          const uint4* src = reinterpret_cast<const uint4*>(a.colexp + (int64_t)kt * a.colexp_ld + n0);
+#pragma unroll
+          for (int w = 0; w < TH / 8; w++) *reinterpret_cast<uint4*>(&rb[w * 8]) = __ldg(src + w);
+        }
         const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BUF_COLS + half * TH;
 #pragma unroll
         for (int cc = 0; cc < TH / 8; cc++) {
@@ -583,21 +719,15 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
           tmem_ld_wait();
 #pragma unroll
           for (int c = 0; c < 8; c++) {
-            const int64_t n = n0 + cc * 8 + c;
-            const int eb = n < a.Ntot ? (int)cex[cc * 8 + c] : 0;
+            // T = sum_d S_d 2^(7(S+1-d)), exact: the tensor core's FP32 sums are integers
             long long T = 0;
 #pragma unroll
             for (int d = 0; d < S; d++) {
               int iv;
               asm("cvt.rni.s32.f32 %0, %1;" : "=r"(iv) : "f"(__uint_as_float(v[d][c])));
-              T = (T << kSplitBeta) + (long long)iv;
+              T += (long long)iv * (1ll << (kSplitBeta * (S - 1 - d)));
             }
-            const int E = ebase + eb;
-            const double Td = __ll2double_rn(T);
-            if (E >= -1022 && E <= 1023)
-              acc[cc * 8 + c] = fma(Td, pow2i(E), acc[cc * 8 + c]);
-            else
-              acc[cc * 8 + c] = __dadd_rn(acc[cc * 8 + c], scalbn(Td, E));
+            acc_add(acc[cc * 8 + c], T, shr + rb[cc * 8 + c]);
           }
         }
         tc_fence_before();
@@ -606,10 +736,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
         tcount++;
       }
       if (!ok) break;
-      // C = alpha*acc + beta*C on the unit's elements that lie in S_C tiles
+      // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles
       if (row_ok) {
         const int i = a.row_tile[m];
         const int64_t lr = m - a.ro[i];
+        const int Lrow = a.eAmax[i] - kSplitBeta * (S + 1) - kSplitGuard;
 #pragma unroll
         for (int c = 0; c < TH; c++) {
           const int64_t n = n0 + c;
@@ -620,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
             if (off == -1) atomicOr(a.err, kErrBadOffset);
             if (off >= 0) {
               double* dst = a.C + off + lr * a.c[j] + (n - a.co[j]);
-              double vv = __dmul_rn(a.alpha, acc[c]);
+              double vv = __dmul_rn(a.alpha, acc_to_double(acc[c], Lrow + a.eBmax[j]));
               if (a.beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(a.beta, *dst));
               *dst = vv;
             }
@@ -658,29 +789,35 @@ cudaError_t launch_mma(const SplitArgs& a, int ctas, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st) {
-  if (a.n_a_tiles + a.n_b_tiles > 0) {
-    split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
+  int k = 0;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (a.n_a_tiles + a.n_b_tiles > 0) split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
+  if (a.M + a.N > 0) split_scale_kernel<<<a.M + a.N, 256, 0, st>>>(a);
+  if (ev) cudaEventRecord(ev[++k], st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   if (a.n_a_blocks + a.n_b_blocks > 0) {
     if (a.fp16)
       split_pack_kernel<__half><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
     else
       split_pack_kernel<__nv_bfloat16><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
+  if (ev) cudaEventRecord(ev[++k], st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   switch (a.s) {
-    case 1: return launch_mma<1, 64>(a, ctas, st);
-    case 2: return launch_mma<2, 64>(a, ctas, st);
-    case 3: return launch_mma<3, 64>(a, ctas, st);
-    case 4: return launch_mma<4, 64>(a, ctas, st);
-    case 5: return launch_mma<5, 32>(a, ctas, st);
-    case 6: return launch_mma<6, 32>(a, ctas, st);
-    default: return cudaErrorInvalidValue;
+    case 1: e = launch_mma<1, 32>(a, ctas, st); break;
+    case 2: e = launch_mma<2, 32>(a, ctas, st); break;
+    case 3: e = launch_mma<3, 32>(a, ctas, st); break;
+    case 4: e = launch_mma<4, 32>(a, ctas, st); break;
+    case 5: e = launch_mma<5, 32>(a, ctas, st); break;
+    case 6: e = launch_mma<6, 32>(a, ctas, st); break;
+    default: e = cudaErrorInvalidValue;
   }
+  if (ev) cudaEventRecord(ev[++k], st);
+  if (nk) *nk = k;
+  return e;
 }
 
 }  // namespace bsmm

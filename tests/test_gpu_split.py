@@ -110,6 +110,28 @@ def test_max_depth_inner_block():
     check(prob, 6)
 
 
+def test_exponent_span_beyond_guard_bits():
+    """Tiles of one row scaled 2^0 .. 2^-120: contributions more than the guard width
+    below the largest scale take the accumulator's floor step, as the oracle states."""
+    rng = np.random.default_rng(4)
+    r = np.array([50, 70], np.int32)
+    q = np.array([40, 33, 64, 20], np.int32)
+    c = np.array([45, 30], np.int32)
+    am = np.ones((2, 4), np.uint8)
+    bm = np.ones((4, 2), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    A = rng.uniform(-1, 1, at)
+    B = rng.uniform(-1, 1, bt)
+    for k, sc in enumerate([0, -40, -80, -120]):
+        for i in range(2):
+            o = a_off[i, k]
+            A[o:o + r[i] * q[k]] *= 2.0 ** sc
+    prob = G.Problem("span", r, c, q, am, bm, a_off, b_off, A, B, 1.0, 0.0)
+    check(prob, 6)
+    check(prob, 3)
+
+
 def test_too_deep_inner_block_is_rejected():
     with pytest.raises(P.BsmmError) as ei:
         P.bsmm_plan([8], [8], [513], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6)

@@ -103,6 +103,45 @@ def test_pair_integer_brute_force(s):
             assert int(T[i, j]) == tot
 
 
+@pytest.mark.parametrize("s", [2, 3, 6])
+@pytest.mark.parametrize("seed", range(3))
+def test_split_result_is_exact_sum_rounded_once(s, seed):
+    """Independent route: the exact rational sum over k blocks, kept slice pairs and
+    inner indices of N^A_p N^B_q 2^(eA+eB-7(p+q)), rounded once (Fraction -> float is
+    correctly rounded). The oracle's value must equal it bit for bit."""
+    prob = G.random_small(seed + 500, max_blocks=4, max_size=9)
+    prob.alpha, prob.beta = 1.0, 0.0
+    cs, _, _ = oracle.structure(prob)
+    off, C = c_arena(prob, cs, fill=0.0)
+    S.bsmm_split(prob, cs, C, off, s)
+    beta = S.BETA_BITS
+    for i in range(prob.M):
+        for j in range(prob.N):
+            if not cs[i, j]:
+                continue
+            r, c = int(prob.row_sizes[i]), int(prob.col_sizes[j])
+            exact = [[Fraction(0)] * c for _ in range(r)]
+            for k in range(prob.K):
+                if not (prob.a_mask[i, k] and prob.b_mask[k, j]):
+                    continue
+                At = G.tile_view(prob.A, prob.a_off, prob.row_sizes, prob.inner_sizes, i, k)
+                Bt = G.tile_view(prob.B, prob.b_off, prob.inner_sizes, prob.col_sizes, k, j)
+                eA, na, _ = S.slice_tile(At, s)
+                eB, nb, _ = S.slice_tile(Bt, s)
+                for p in range(1, s + 1):
+                    for qq in range(1, s + 2 - p):
+                        w = Fraction(2) ** (eA + eB - beta * (p + qq))
+                        for ii in range(r):
+                            for jj in range(c):
+                                dot = sum(int(na[p - 1][ii, kk]) * int(nb[qq - 1][kk, jj])
+                                          for kk in range(At.shape[1]))
+                                exact[ii][jj] += w * dot
+            got = C[off[i, j]:off[i, j] + r * c].reshape(r, c)
+            for ii in range(r):
+                for jj in range(c):
+                    assert got[ii, jj] == float(exact[ii][jj])
+
+
 @pytest.mark.parametrize("s", [2, 3, 4, 6])
 @pytest.mark.parametrize("seed", range(3))
 def test_split_within_truncation_bound(s, seed):
