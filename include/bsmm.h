@@ -183,6 +183,31 @@ bsmm_status bsmm_plan_timings(bsmm_plan_t plan, int64_t* start_ns, int64_t* end_
  */
 bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t plan, float* ms, int32_t max_n, int32_t* count);
 
+/*
+ * One dense tile task without any allocation (the paper has no counterpart: it is
+ * an addition for callers that cannot allocate device memory where they need the
+ * product -- for example code that runs while its allocator is locked or a graph
+ * is being built around it, or a host that reserved all device memory up front).
+ *
+ * Computes C = alpha * A*B + beta * C for one m x k tile A, k x n tile B and m x n
+ * tile C (row-major, contiguous, device pointers, 16-byte aligned) with the 6-or-
+ * fewer-slice split-bfloat16 method of bsmm_execute: the same bits as a plan of the
+ * 1 x 1 x 1 tiling (m), (n), (k) in BSMM_SPLIT_BF16 mode. beta == 0 does not read C.
+ * Limits: m, n <= 256, k <= 512, nslices in 1..6; larger sizes return
+ * BSMM_ERR_INVALID before anything runs.
+ *
+ * Scratch: a file-scope device array of about 3.2 MB inside the library, held by
+ * every GPU that loads the library until the process exits; no cudaMalloc,
+ * cudaFree or other allocating call is made. The first call on a device (with
+ * that device current) looks up the array's address and should come before any
+ * stream capture. All calls share the array and leave their contents in it, so
+ * calls that overlap on the GPU (several streams or host threads) race: the
+ * caller must serialise them. Asynchronous on `stream`; no device error word is
+ * reported for this entry point.
+ */
+bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, int32_t nslices, double alpha,
+                                    const double* A, const double* B, double beta, double* C, void* stream);
+
 /* Thread-local message for the last failing call ("" if none). */
 const char* bsmm_last_error(void);
 

@@ -23,7 +23,7 @@ __all__ = [
     "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
-    "bsmm_plan_kernel_ms", "bsmm_last_error", "bsmm_destroy", "EXPORTED",
+    "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy", "EXPORTED",
 ]
 
 BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
@@ -36,7 +36,7 @@ STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_
 EXPORTED = [
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
-    "bsmm_plan_kernel_ms", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -78,6 +78,7 @@ def lib():
         L.bsmm_status_device.argtypes = [P, P]
         L.bsmm_plan_timings.argtypes = [P, P, P, P]
         L.bsmm_plan_kernel_ms.argtypes = [P, P, i32, P]
+        L.bsmm_split_tile_noalloc.argtypes = [i32, i32, i32, i32, f64, P, P, f64, P, P]
         L.bsmm_last_error.argtypes = []
         L.bsmm_last_error.restype = ctypes.c_char_p
         L.bsmm_destroy.argtypes = [P]
@@ -227,6 +228,15 @@ def bsmm_plan_kernel_ms(plan: Plan):
     n = ctypes.c_int32()
     _check(lib().bsmm_plan_kernel_ms(plan.handle, ms, 8, ctypes.byref(n)))
     return [float(ms[i]) for i in range(n.value)]
+
+
+def bsmm_split_tile_noalloc(m, n, k, nslices, alpha, A, B, beta, C, stream=None):
+    """One dense split-precision tile task with no device allocation (device tensors:
+    A m x k, B k x n, C m x n, row-major float64). For callers that cannot allocate
+    device memory at the point of the call; see include/bsmm.h for the limits and the
+    shared-scratch rules (calls overlapping on the GPU race)."""
+    _check(lib().bsmm_split_tile_noalloc(int(m), int(n), int(k), int(nslices), float(alpha), _ptr(A), _ptr(B),
+                                         float(beta), _ptr(C), _stream(stream)))
 
 
 def bsmm_destroy(plan: Plan):

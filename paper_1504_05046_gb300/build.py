@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbsmm.so")
-SOURCES = ["plan.cpp", "execute.cpp", "fp64.cu", "split.cu", "mlp.cu", "batch.cu"]
+SOURCES = ["plan.cpp", "execute.cpp", "fp64.cu", "split.cu", "noalloc.cu", "mlp.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
