@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=16384, help="matrix order")
     ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs sharing the A stream (0 = library default)")
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -264,7 +265,7 @@ def main():
     prob = make_inputs(args.n, args.seed + rank)
     s = args.slices
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1)
+                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster)
     q = P.bsmm_plan_query(plan)
     F = q["useful_flops"]
     cs = q["c_mask"]

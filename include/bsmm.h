@@ -81,7 +81,9 @@ typedef struct {
   int32_t debug_checks;    /* 1 = kernels validate offsets against the plan */
   int32_t record_timings;  /* 1 = record per-unit start/end times (bsmm_plan_timings) */
   int32_t profile;         /* 1 = time each internal kernel with CUDA events (bsmm_plan_kernel_ms) */
-  int32_t reserved[5];     /* must be zero */
+  int32_t cluster;         /* split modes: CTAs per thread-block cluster sharing the A stream
+                              by multicast, 1, 2 or 4 (0 = default) */
+  int32_t reserved[4];     /* must be zero */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */

@@ -36,6 +36,9 @@ int split_max_depth(int s);
 int split_tile_n(int s);          // work-unit width (32 or 64)
 int split_stages(int s, int tn);  // smem ring depth
 size_t split_smem_bytes(int s, int tn, int stages);
+constexpr int kSplitDefaultCluster = 2;
+// Largest number of clusters of `cl` contraction CTAs that can be resident at once.
+int split_max_clusters(int s, int cl);
 
 // Device arrays owned by a plan.
 struct DevBuf {
@@ -79,6 +82,7 @@ struct Fp64Args {
 // Arguments of the split-mode kernels.
 struct SplitArgs {
   int32_t M, N, K, s, tn, stages, fp16;
+  int32_t cl, CBG;          // CTAs per cluster; column-block groups (units are (rb, group))
   int64_t Mtot, Ntot;
   int32_t RB, CB, kwords;
   const int32_t* r;
@@ -93,6 +97,7 @@ struct SplitArgs {
   const uint8_t* bm;        // B tile mask (K x N)
   const uint64_t* presA;    // RB x kwords
   const uint64_t* presB;    // CB x kwords
+  const uint64_t* presBg;   // CBG x kwords: union over the cl column blocks of a group
   const int64_t* apk_off;   // RB x K byte offsets into apk (-1 absent)
   const int64_t* bpk_off;   // K x CB byte offsets into bpk (-1 absent)
   uint8_t* apk;
@@ -160,13 +165,13 @@ struct bsmm_plan_s {
   std::vector<int32_t> sched_ptr, sched_units;
 
   // split geometry
-  int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0;
+  int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0, cl = 1, CBG = 0;
   int64_t Mtot = 0, Ntot = 0, colexp_ld = 0;
   int64_t apk_bytes = 0, bpk_bytes = 0;
 
   // device memory
   bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
-  bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_apk_off, d_bpk_off, d_apk, d_bpk;
+  bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_presBg, d_apk_off, d_bpk_off, d_apk, d_bpk;
   bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
   bsmm::DevBuf d_err, d_timings, d_unit_cta;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;

@@ -63,6 +63,9 @@ bsmm_status fill_split(bsmm_plan_s* p, SplitArgs& a, double alpha, const double*
   a.bm = (const uint8_t*)p->d_bm.p;
   a.presA = (const uint64_t*)p->d_presA.p;
   a.presB = (const uint64_t*)p->d_presB.p;
+  a.presBg = (const uint64_t*)p->d_presBg.p;
+  a.cl = p->cl;
+  a.CBG = p->CBG;
   a.apk_off = (const int64_t*)p->d_apk_off.p;
   a.bpk_off = (const int64_t*)p->d_bpk_off.p;
   a.apk = (uint8_t*)p->d_apk.p;

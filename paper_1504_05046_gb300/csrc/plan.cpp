@@ -131,9 +131,13 @@ void pack_lpt(bsmm_plan_s* p) {
   p->sched_ptr[ctas] = (int32_t)p->sched_units.size();
 }
 
+// FP64: persistent CTAs; split modes: persistent clusters of p->cl CTAs.
 int default_ctas(const bsmm_plan_s* p) {
-  int per_sm = p->opt.mode == BSMM_FP64 ? fp64_ctas_per_sm() : 1;
-  int64_t c = (int64_t)p->sms * std::max(1, per_sm);
+  int64_t c;
+  if (p->opt.mode == BSMM_FP64)
+    c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm());
+  else
+    c = std::max(1, split_max_clusters(p->s, p->cl));
   if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
   c = std::min<int64_t>(c, std::max<int64_t>(1, p->n_units));
   return (int)std::max<int64_t>(1, c);
@@ -256,19 +260,33 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   for (int64_t t = 0; t < (int64_t)M * N; t++)
     for (int64_t e = p->kptr[t]; e < p->kptr[t + 1]; e++) w[t] += 2.0 * p->q[p->klist[e]];
 
-  std::vector<uint8_t> umark((size_t)RB * CB, 0);
+  // A work unit is one cluster's task: a 128-row block times CL consecutive column
+  // blocks (CL * tn columns); the CL CTAs of the cluster share the A stream by multicast.
+  const int CL = p->cl;
+  const int CBG = (CB + CL - 1) / CL;
+  p->CBG = CBG;
+  std::vector<uint64_t> presBg((size_t)CBG * KW, 0);
+  for (int cb = 0; cb < CB; cb++)
+    for (int wd = 0; wd < KW; wd++) presBg[(size_t)(cb / CL) * KW + wd] |= presB[(size_t)cb * KW + wd];
+  std::vector<uint8_t> umark((size_t)RB * CBG, 0);
   for (int i = 0; i < M; i++)
     for (int j = 0; j < N; j++) {
       if (!p->cs[(int64_t)i * N + j] || p->r[i] == 0 || p->c[j] == 0) continue;
       for (int64_t rb = p->ro[i] / kSplitBM; rb <= (p->ro[i + 1] - 1) / kSplitBM; rb++)
-        for (int64_t cb = p->co[j] / tn; cb <= (p->co[j + 1] - 1) / tn; cb++) umark[rb * CB + cb] = 1;
+        for (int64_t cb = p->co[j] / tn; cb <= (p->co[j + 1] - 1) / tn; cb++) umark[rb * CBG + cb / CL] = 1;
     }
-  for (int rb = 0; rb < RB; rb++)
-    for (int cb = 0; cb < CB; cb++) {
-      if (!umark[(size_t)rb * CB + cb]) continue;
+  // Units are numbered in bands of kRasterRows row blocks, column group by column group
+  // inside a band: the persistent CTAs, which take units in this order when costs tie,
+  // then work concurrently on a few A row panels and a few B column panels at a time,
+  // so both stay in L2 while the CTAs stream through k.
+  constexpr int kRasterRows = 8;
+  for (int rb0 = 0; rb0 < RB; rb0 += kRasterRows)
+    for (int cb = 0; cb < CBG; cb++)  // cb indexes column-block groups here
+      for (int rb = rb0; rb < std::min(RB, rb0 + kRasterRows); rb++) {
+      if (!umark[(size_t)rb * CBG + cb]) continue;
       p->sp_units.push_back({rb, cb});
       const int64_t m0 = (int64_t)rb * kSplitBM, m1 = std::min<int64_t>(Mtot, m0 + kSplitBM);
-      const int64_t n0 = (int64_t)cb * tn, n1 = std::min<int64_t>(Ntot, n0 + tn);
+      const int64_t n0 = (int64_t)cb * CL * tn, n1 = std::min<int64_t>(Ntot, n0 + (int64_t)CL * tn);
       double fl = 0.0;
       int nrt = 0, nct = 0;
       for (int i = row_tile[m0]; i < M && p->ro[i] < m1; i++) {
@@ -285,7 +303,7 @@ bsmm_status plan_split(bsmm_plan_s* p) {
         if (std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]) > 0) nct++;
       int64_t nk = 0, kq = 0, kg = 0, kc = 0;
       for (int wd = 0; wd < KW; wd++) {
-        uint64_t bits = presA[(size_t)rb * KW + wd] & presB[(size_t)cb * KW + wd];
+        uint64_t bits = presA[(size_t)rb * KW + wd] & presBg[(size_t)cb * KW + wd];
         while (bits) {
           const int k = wd * 64 + __builtin_ctzll(bits);
           bits &= bits - 1;
@@ -296,7 +314,7 @@ bsmm_status plan_split(bsmm_plan_s* p) {
         }
       }
       p->flop_cost.push_back(std::max(fl, 1.0));
-      const double padded = 2.0 * kSplitBM * tn * 16.0 * (double)kg;
+      const double padded = 2.0 * kSplitBM * tn * CL * 16.0 * (double)kg;
       float f[BSMM_NFEATURES] = {lg((double)(m1 - m0)), lg((double)(n1 - n0)), lg((double)nk), lg((double)kq),
                                  lg((double)kg), lg(fl), (float)(padded > 0 ? fl / padded : 0.0),
                                  1.0f, (float)s / 6.0f, lg(nrt), lg(nct), lg((double)kc)};
@@ -312,6 +330,7 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   if ((st = upload(p->d_col_tile, col_tile)) != BSMM_OK) return st;
   if ((st = upload(p->d_presA, presA)) != BSMM_OK) return st;
   if ((st = upload(p->d_presB, presB)) != BSMM_OK) return st;
+  if ((st = upload(p->d_presBg, presBg)) != BSMM_OK) return st;
   if ((st = upload(p->d_apk_off, apk_off)) != BSMM_OK) return st;
   if ((st = upload(p->d_bpk_off, bpk_off)) != BSMM_OK) return st;
   if ((st = upload(p->d_a_tiles, a_tiles)) != BSMM_OK) return st;
@@ -347,6 +366,8 @@ bsmm_status validate_options(const bsmm_options& o) {
   if (o.schedule < 0 || o.schedule > 2) return set_error("unknown schedule"), BSMM_ERR_INVALID;
   if (o.max_ctas < 0) return set_error("max_ctas < 0"), BSMM_ERR_INVALID;
   if (o.profile < 0 || o.profile > 1) return set_error("profile must be 0 or 1"), BSMM_ERR_INVALID;
+  if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4)
+    return set_error("cluster must be 0, 1, 2 or 4"), BSMM_ERR_INVALID;
   for (int r : o.reserved)
     if (r) return set_error("reserved option fields must be zero"), BSMM_ERR_INVALID;
   return BSMM_OK;
@@ -373,7 +394,7 @@ void bsmm_destroy(bsmm_plan_t p) {
   if (!p) return;
   DevBuf* bufs[] = {&p->d_r, &p->d_c, &p->d_q, &p->d_ro, &p->d_co, &p->d_kptr, &p->d_klist, &p->d_cs,
                     &p->d_units, &p->d_sched_ptr, &p->d_sched_units, &p->d_row_tile, &p->d_col_tile,
-                    &p->d_presA, &p->d_presB, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
+                    &p->d_presA, &p->d_presB, &p->d_presBg, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
                     &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
                     &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
@@ -477,6 +498,7 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
     st = plan_fp64(p);
   } else {
     p->s = o.nslices;
+    p->cl = o.cluster ? o.cluster : kSplitDefaultCluster;
     p->tn = split_tile_n(p->s);
     p->stages = split_stages(p->s, p->tn);
     st = plan_split(p);

@@ -127,6 +127,28 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Same copy delivered to the same shared-memory offset of every CTA in `mask` (cluster
+// multicast within this GPU's memory); each destination's mbarrier at `bar`'s offset
+// receives the byte count.
+__device__ __forceinline__ void bulk_g2s_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
@@ -154,6 +176,15 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+// arrive on the mbarrier at `bar`'s offset in every CTA of `mask` once this thread's
+// earlier tcgen05 operations have completed
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -493,17 +524,28 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
 }
 
 // ---------------------------------------------------------------- kernel 3: contraction
-struct UnitIter {  // ascending k blocks of one unit: presA[rb] & presB[cb]
+// Ascending k blocks of one unit (a 128-row block times a group of cl column blocks):
+// presA[rb] & presBg[group]. Every CTA of the cluster walks the same list, because they
+// share the A stream; own_b() tells whether the CTA's own column block has that k block.
+struct UnitIter {
   const uint64_t* pa;
   const uint64_t* pb;
+  const uint64_t* po;  // this CTA's own column block (null: beyond the last one)
   int kwords, wd;
   uint64_t bits;
-  __device__ void init(const SplitArgs& a, int rb, int cb) {
+  __device__ void init(const SplitArgs& a, int rb, int grp, int cb) {
     pa = a.presA + (size_t)rb * a.kwords;
-    pb = a.presB + (size_t)cb * a.kwords;
+    pb = a.presBg + (size_t)grp * a.kwords;
+    po = cb < a.CB ? a.presB + (size_t)cb * a.kwords : nullptr;
     kwords = a.kwords;
     wd = 0;
     bits = pa[0] & pb[0];
+  }
+  __device__ bool own_b(int k) const { return po && ((po[k >> 6] >> (k & 63)) & 1); }
+  __device__ int next_own() {  // next k block that also has a B tile in this CTA's column block
+    for (int k = next(); k >= 0; k = next())
+      if (own_b(k)) return k;
+    return -1;
   }
   __device__ int next() {  // -1 when done
     while (!bits) {
@@ -516,13 +558,69 @@ struct UnitIter {  // ascending k blocks of one unit: presA[rb] & presB[cb]
   }
 };
 
-template <int S, int TN>
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+constexpr int kPrefetch = 8;  // chunks the producer pulls into L2 ahead of its copies
+
+// The chunks of one CTA's unit list in order: unit by unit, k block by k block
+// (ascending), 32-deep chunk by chunk.
+struct ChunkCursor {
+  int idx, uend;
+  int rb, cb;  // this CTA's row block and column block
+  UnitIter it;
+  int kt, kc, nkc;
+  bool ownb, in_unit;
+  const uint8_t* asrc;
+  const uint8_t* bsrc;
+  __device__ void start(int beg, int end) {
+    idx = beg - 1;
+    uend = end;
+    in_unit = false;
+    kc = 0;
+    nkc = 0;
+  }
+  __device__ bool advance(const SplitArgs& a, int cl, int rank) {  // false when exhausted
+    if (++kc < nkc) return true;
+    for (;;) {
+      if (in_unit) {
+        kt = it.next();
+        if (kt >= 0) {
+          nkc = (a.q[kt] + kSplitKC - 1) / kSplitKC;  // >= 1: blocks with q = 0 are never present
+          kc = 0;
+          ownb = it.own_b(kt);
+          asrc = a.apk + a.apk_off[(size_t)rb * a.K + kt];
+          bsrc = ownb ? a.bpk + a.bpk_off[(size_t)kt * a.CB + cb] : nullptr;
+          return true;
+        }
+        in_unit = false;
+      }
+      if (++idx >= uend) return false;
+      const SplitUnit un = a.units[a.sched_units[idx]];
+      rb = un.rb;
+      cb = un.cb * cl + rank;
+      it.init(a, un.rb, un.cb, cb);
+      in_unit = true;
+    }
+  }
+  template <int A_STAGE, int A_SLICE, int B_STAGE>
+  __device__ void prefetch(int rank) const {
+    prefetch_l2(asrc + (size_t)kc * A_STAGE + rank * A_SLICE, A_SLICE);
+    if (ownb) prefetch_l2(bsrc + (size_t)kc * B_STAGE, B_STAGE);
+  }
+};
+
+template <int S, int TN, int CL>
 __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
   constexpr int TH = TN / 2;                    // columns per epilogue thread
   constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
+  constexpr int A_SLICE = A_STAGE / CL;         // bytes of A each cluster CTA loads and multicasts
   constexpr int B_STAGE = S * TN * kSplitKC * 2;
   constexpr int STAGE = A_STAGE + B_STAGE;
   constexpr int BUF_COLS = S * TN;              // TMEM columns per accumulator buffer
+  constexpr uint16_t MASK = (uint16_t)((1u << CL) - 1);
+  static_assert(A_SLICE % 16 == 0, "bulk copies move multiples of 16 bytes");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -537,13 +635,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cta = blockIdx.x;
+  const int cta = blockIdx.x / CL;  // the cluster: schedules are per cluster
+  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
   const int ubeg = a.sched_ptr[cta], uend = a.sched_ptr[cta + 1];
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < stages; st++) {
       mbar_init(&full[st], 1);
-      mbar_init(&empty[st], 1);
+      mbar_init(&empty[st], CL);  // released by the MMA issuer of every CTA of the cluster
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(&tfull[b], 1);
@@ -559,6 +658,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL > 1) cluster_sync();  // peers' barriers exist before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -570,31 +670,34 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
       uint32_t issued = 0;  // bit st: stage st holds an issued copy; its parity in issued_par
       uint32_t issued_par = 0;
       bool ok = true;
-      for (int idx = ubeg; idx < uend && ok; idx++) {
-        const SplitUnit un = a.units[a.sched_units[idx]];
-        UnitIter it;
-        it.init(a, un.rb, un.cb);
-        for (int kt = it.next(); kt >= 0 && ok; kt = it.next()) {
-          const int nkc = (a.q[kt] + kSplitKC - 1) / kSplitKC;
-          const uint8_t* asrc = a.apk + a.apk_off[(size_t)un.rb * a.K + kt];
-          const uint8_t* bsrc = a.bpk + a.bpk_off[(size_t)kt * a.CB + un.cb];
-          for (int kc = 0; kc < nkc; kc++) {
-            if (!wait1(&empty[stage], phase ^ 1, abort_flag, a.err)) {
-              ok = false;
-              break;
-            }
-            uint8_t* sa = smem + (size_t)stage * STAGE;
-            mbar_arrive_expect_tx(&full[stage], STAGE);
-            bulk_g2s(sa, asrc + (size_t)kc * A_STAGE, A_STAGE, &full[stage]);
-            bulk_g2s(sa + A_STAGE, bsrc + (size_t)kc * B_STAGE, B_STAGE, &full[stage]);
-            issued |= 1u << stage;
-            issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
-            if (++stage == stages) {
-              stage = 0;
-              phase ^= 1;
-            }
-          }
+      // a second cursor runs kPrefetch chunks ahead and pulls them into L2, so that the
+      // copies into shared memory hit L2 instead of waiting on HBM
+      ChunkCursor ahead;
+      ahead.start(ubeg, uend);
+      for (int i = 0; i < kPrefetch && ahead.advance(a, CL, rank); i++) ahead.prefetch<A_STAGE, A_SLICE, B_STAGE>(rank);
+      ChunkCursor cur;
+      cur.start(ubeg, uend);
+      while (ok && cur.advance(a, CL, rank)) {
+        // the slot is free in every CTA of the cluster (the multicast writes all of them)
+        if (!wait1(&empty[stage], phase ^ 1, abort_flag, a.err)) {
+          ok = false;
+          break;
         }
+        uint8_t* sa = smem + (size_t)stage * STAGE;
+        mbar_arrive_expect_tx(&full[stage], A_STAGE + (cur.ownb ? B_STAGE : 0));
+        const uint8_t* asrc = cur.asrc + (size_t)cur.kc * A_STAGE;
+        if constexpr (CL > 1)
+          bulk_g2s_mc(sa + rank * A_SLICE, asrc + rank * A_SLICE, A_SLICE, &full[stage], MASK);
+        else
+          bulk_g2s(sa, asrc, A_STAGE, &full[stage]);
+        if (cur.ownb) bulk_g2s(sa + A_STAGE, cur.bsrc + (size_t)cur.kc * B_STAGE, B_STAGE, &full[stage]);
+        issued |= 1u << stage;
+        issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+        if (++stage == stages) {
+          stage = 0;
+          phase ^= 1;
+        }
+        if (ahead.advance(a, CL, rank)) ahead.prefetch<A_STAGE, A_SLICE, B_STAGE>(rank);
       }
       // drain: every copy this thread issued has landed before the CTA may exit
       for (int st = 0; st < stages; st++) {
@@ -617,19 +720,31 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
       uint32_t tcount = 0;
       bool ok = true;
       bool any = false;
+      // Descriptors are built once: within a stage, slice p of A starts (p-1)*kAChunk bytes
+      // in and the second 16-deep step 32 bytes in, i.e. fixed additions to the 16-byte
+      // start-address field (which cannot carry: shared addresses are below 256 KB).
+      const uint64_t adesc0 = sdesc_sw64(smem_u32(smem));
+      const uint64_t bdesc0 = sdesc_sw64(smem_u32(smem) + A_STAGE);
+      uint32_t idp[S];
+#pragma unroll
+      for (int p = 1; p <= S; p++) idp[p - 1] = idesc_f16(kSplitBM, (S + 1 - p) * TN, a.fp16 != 0);
       for (int idx = ubeg; idx < uend && ok; idx++) {
         const SplitUnit un = a.units[a.sched_units[idx]];
+        const int cb = un.cb * CL + rank;
         UnitIter it;
-        it.init(a, un.rb, un.cb);
+        it.init(a, un.rb, un.cb, cb);
         for (int kt = it.next(); kt >= 0 && ok; kt = it.next()) {
           const int q = a.q[kt];
           const int nkc = (q + kSplitKC - 1) / kSplitKC;
+          const bool ownb = it.own_b(kt);
           const uint32_t buf = tcount & 1, use = tcount >> 1;
-          if (!wait1(&tempty[buf], (use & 1) ^ 1, abort_flag, a.err)) {
-            ok = false;
-            break;
+          if (ownb) {
+            if (!wait1(&tempty[buf], (use & 1) ^ 1, abort_flag, a.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
           }
-          tc_fence_after();
           const uint32_t dbase = tmem_base + buf * BUF_COLS;
           for (int kc = 0; kc < nkc; kc++) {
             if (!wait1(&full[stage], phase, abort_flag, a.err)) {
@@ -637,21 +752,24 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
               break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE);
-            const uint32_t sb = sa + A_STAGE;
-            const int rem = q - kc * kSplitKC;
-            const int nsteps = rem > 16 ? 2 : 1;
-            for (int ks = 0; ks < nsteps; ks++) {
+            if (ownb) {
+              const uint64_t soff = (uint64_t)((stage * STAGE) >> 4);
+              const uint64_t ad = adesc0 + soff, bd = bdesc0 + soff;
+              const uint32_t first = (kc == 0) ? 0u : 1u;  // 0: this k block's first MMA overwrites
 #pragma unroll
-              for (int p = 1; p <= S; p++) {
-                const uint64_t ad = sdesc_sw64(sa + (p - 1) * kAChunk + ks * 32);
-                const uint64_t bd = sdesc_sw64(sb + ks * 32);
-                const uint32_t id = idesc_f16(kSplitBM, (S + 1 - p) * TN, a.fp16 != 0);
-                const uint32_t acc = (kc | ks) != 0 || p > 1;
-                umma_f16(dbase + (p - 1) * TN, ad, bd, id, acc);
+              for (int p = 1; p <= S; p++)
+                umma_f16(dbase + (p - 1) * TN, ad + (p - 1) * (kAChunk >> 4), bd, idp[p - 1], p > 1 ? 1u : first);
+              if (q - kc * kSplitKC > 16) {  // second 16-deep step of the 32-deep chunk
+#pragma unroll
+                for (int p = 1; p <= S; p++)
+                  umma_f16(dbase + (p - 1) * TN, ad + (p - 1) * (kAChunk >> 4) + 2, bd + 2, idp[p - 1], 1u);
               }
             }
-            umma_commit(&empty[stage]);  // frees the stage when these MMAs finish
+            // release the stage in every CTA of the cluster once these MMAs finished
+            if constexpr (CL > 1)
+              umma_commit_mc(&empty[stage], MASK);
+            else
+              umma_commit(&empty[stage]);
             any = true;
             if (++stage == stages) {
               stage = 0;
@@ -659,8 +777,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
             }
           }
           if (!ok) break;
-          umma_commit(&tfull[buf]);
-          tcount++;
+          if (ownb) {
+            umma_commit(&tfull[buf]);
+            tcount++;
+          }
         }
       }
       // drain: every MMA this thread issued has completed before TMEM is released
@@ -686,30 +806,44 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
     for (int idx = ubeg; idx < uend && ok; idx++) {
       const int u = a.sched_units[idx];
       const SplitUnit un = a.units[u];
-      if (a.timings && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = gtimer();
+      const int cb = un.cb * CL + rank;
+      if (cb >= a.CB) continue;  // this CTA only helps stream the cluster's A panel
+      if (a.timings && rank == 0 && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = gtimer();
       const int64_t m = (int64_t)un.rb * kSplitBM + row;
       const bool row_ok = m < a.Mtot;
-      const int64_t n0 = (int64_t)un.cb * TN + half * TH;
+      const int64_t n0 = (int64_t)cb * TN + half * TH;
       uint32_t acc[TH][4];  // exact 128-bit two's-complement sums, unit 2^L per column
 #pragma unroll
       for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
       UnitIter it;
-      it.init(a, un.rb, un.cb);
-      for (int kt = it.next(); kt >= 0; kt = it.next()) {
+      it.init(a, un.rb, un.cb, cb);
+      // the exponent offsets of the next k block are loaded while this one is processed
+      // (k blocks where this column block has no B tile add nothing and are skipped)
+      int kt = it.next_own();
+      int shr_n = 0;
+      int16_t rb_n[TH];
+      auto load_exps = [&](int k) {
+        shr_n = kSplitGuard + (row_ok ? (int)a.rowexp[(int64_t)k * a.Mtot + m] : 0);
+        const uint4* src = reinterpret_cast<const uint4*>(a.colexp + (int64_t)k * a.colexp_ld + n0);
+#pragma unroll
+        for (int w = 0; w < TH / 8; w++) *reinterpret_cast<uint4*>(&rb_n[w * 8]) = __ldg(src + w);
+      };
+      if (kt >= 0) load_exps(kt);
+      while (kt >= 0) {
+        // binary position of this k block's integer in the accumulator
+        const int shr = shr_n;
+        int16_t rb[TH];
+#pragma unroll
+        for (int c = 0; c < TH; c++) rb[c] = rb_n[c];
+        const int kt_next = it.next_own();
+        if (kt_next >= 0) load_exps(kt_next);
+        kt = kt_next;
         const uint32_t buf = tcount & 1, use = tcount >> 1;
         if (!wait_warp(&tfull[buf], use & 1, abort_flag, a.err)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        // binary position of this k block's integer in the accumulator
-        const int shr = kSplitGuard + (row_ok ? (int)a.rowexp[(int64_t)kt * a.Mtot + m] : 0);
-        int16_t rb[TH];
-        {
-          const uint4* src = reinterpret_cast<const uint4*>(a.colexp + (int64_t)kt * a.colexp_ld + n0);
-#pragma unroll
-          for (int w = 0; w < TH / 8; w++) *reinterpret_cast<uint4*>(&rb[w * 8]) = __ldg(src + w);
-        }
         const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BUF_COLS + half * TH;
 #pragma unroll
         for (int cc = 0; cc < TH / 8; cc++) {
@@ -758,7 +892,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
           }
         }
       }
-      if (a.timings) {
+      if (a.timings && rank == 0) {
         asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
         if (ew == 0 && lane == 0) {
           a.timings[2 * (int64_t)u + 1] = gtimer();
@@ -770,21 +904,72 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
 
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL > 1) cluster_sync();  // no peer multicasts into or signals this CTA any more
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, kTmemCols);
 }
 
-template <int S, int TN>
-cudaError_t launch_mma(const SplitArgs& a, int ctas, cudaStream_t st) {
+template <int S, int TN, int CL>
+cudaError_t launch_mma(const SplitArgs& a, int clusters, cudaStream_t st) {
   const size_t smem = split_smem_bytes(S, TN, a.stages);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, split_mma_kernel<S, TN, CL>, a);
+}
+
+template <int S>
+cudaError_t launch_mma_cl(const SplitArgs& a, int clusters, cudaStream_t st) {
+  switch (a.cl) {
+    case 1: return launch_mma<S, 32, 1>(a, clusters, st);
+    case 2: return launch_mma<S, 32, 2>(a, clusters, st);
+    case 4: return launch_mma<S, 32, 4>(a, clusters, st);
+    default: return cudaErrorInvalidValue;
   }
-  split_mma_kernel<S, TN><<<ctas, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
+}
+
+template <int S, int CL>
+int max_clusters_for() {
+  const size_t smem = split_smem_bytes(S, 32, split_stages(S, 32));
+  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, split_mma_kernel<S, 32, CL>, &cfg) != cudaSuccess) return 0;
+  return n;
+}
+
+template <int S>
+int max_clusters_s(int cl) {
+  switch (cl) {
+    case 1: return max_clusters_for<S, 1>();
+    case 2: return max_clusters_for<S, 2>();
+    case 4: return max_clusters_for<S, 4>();
+    default: return 0;
+  }
 }
 
 }  // namespace
@@ -806,18 +991,30 @@ cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEven
   if (ev) cudaEventRecord(ev[++k], st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  switch (a.s) {
-    case 1: e = launch_mma<1, 32>(a, ctas, st); break;
-    case 2: e = launch_mma<2, 32>(a, ctas, st); break;
-    case 3: e = launch_mma<3, 32>(a, ctas, st); break;
-    case 4: e = launch_mma<4, 32>(a, ctas, st); break;
-    case 5: e = launch_mma<5, 32>(a, ctas, st); break;
-    case 6: e = launch_mma<6, 32>(a, ctas, st); break;
+  switch (a.s) {  // `ctas` counts clusters of a.cl CTAs
+    case 1: e = launch_mma_cl<1>(a, ctas, st); break;
+    case 2: e = launch_mma_cl<2>(a, ctas, st); break;
+    case 3: e = launch_mma_cl<3>(a, ctas, st); break;
+    case 4: e = launch_mma_cl<4>(a, ctas, st); break;
+    case 5: e = launch_mma_cl<5>(a, ctas, st); break;
+    case 6: e = launch_mma_cl<6>(a, ctas, st); break;
     default: e = cudaErrorInvalidValue;
   }
   if (ev) cudaEventRecord(ev[++k], st);
   if (nk) *nk = k;
   return e;
+}
+
+int split_max_clusters(int s, int cl) {
+  switch (s) {
+    case 1: return max_clusters_s<1>(cl);
+    case 2: return max_clusters_s<2>(cl);
+    case 3: return max_clusters_s<3>(cl);
+    case 4: return max_clusters_s<4>(cl);
+    case 5: return max_clusters_s<5>(cl);
+    case 6: return max_clusters_s<6>(cl);
+    default: return 0;
+  }
 }
 
 }  // namespace bsmm

@@ -138,6 +138,21 @@ def test_too_deep_inner_block_is_rejected():
     assert ei.value.status == 5
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("recipe", ["nonuniform_dense", "clustered", "ragged"])
+def test_cluster_multicast_sizes(cluster, recipe):
+    """The A stream shared by multicast across 1, 2 or 4 CTAs: same bits, including
+    column-block groups whose last members fall beyond the matrix and CTAs whose own
+    column block has no B tile at some k block."""
+    if recipe == "nonuniform_dense":
+        prob = G.make_problem("nonuniform_dense", 31, 777, lo=40, hi=200)
+    elif recipe == "clustered":
+        prob = G.make_problem("clustered", 32, 1100, lo=16, hi=180, nclusters=7, cluster_density=0.2)
+    else:
+        prob = G.random_small(33, max_blocks=6, max_size=90)
+    check(prob, 6, cluster=cluster)
+
+
 @pytest.mark.parametrize("ctas", [1, 5, 151])
 def test_schedule_independent_bits(ctas):
     prob = G.make_problem("clustered", 9, 900, lo=16, hi=160, nclusters=6, cluster_density=0.25)
