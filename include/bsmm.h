@@ -163,6 +163,39 @@ bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const double* A, i
                               const int64_t* c_off, void* stream);
 
 /*
+ * Batches: many independent products in one persistent launch. The task set of the
+ * paper's Sec. 3.2 extended across products: the work units of every plan are
+ * packed together (longest first onto the least-loaded CTA) so one contraction
+ * launch runs them all.
+ *
+ * bsmm_batch_create: `count` plans, all with the same mode, slice count and cluster
+ *   size, on one device. The plans must outlive the batch. Allocates device memory.
+ * bsmm_batch_set_args: per-product arguments as in bsmm_execute, given as host arrays
+ *   of length `count` (alpha[i], beta[i], and DEVICE pointers A[i], a_off[i], ...).
+ *   Copied to the device synchronously; call again when any of them changes.
+ * bsmm_batch_execute: issues the kernels of the whole batch on `stream` (per-product
+ *   exponent and slicing kernels in the split modes, then one contraction launch). It
+ *   allocates, copies and synchronises nothing, so it can be captured into a CUDA
+ *   graph and replayed. Products must not overlap in C.
+ * bsmm_batch_query: units over the batch, summed useful flops, persistent bins (CTAs
+ *   for FP64, clusters for the split modes); pointers may be NULL.
+ * bsmm_batch_set_costs: costs[n_units] (> 0, units in plan order) and re-pack.
+ * bsmm_batch_status_device: synchronise and return the batch's and the plans' device
+ *   error words (cleared).
+ */
+typedef struct bsmm_batch_s* bsmm_batch_t;
+bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_t* plans);
+bsmm_status bsmm_batch_set_args(bsmm_batch_t batch, const double* alpha, const double* const* A,
+                                const int64_t* const* a_off, const double* const* B,
+                                const int64_t* const* b_off, const double* beta, double* const* C,
+                                const int64_t* const* c_off);
+bsmm_status bsmm_batch_execute(bsmm_batch_t batch, void* stream);
+bsmm_status bsmm_batch_query(bsmm_batch_t batch, int64_t* n_units, double* useful_flops, int32_t* bins);
+bsmm_status bsmm_batch_set_costs(bsmm_batch_t batch, const double* costs);
+bsmm_status bsmm_batch_status_device(bsmm_batch_t batch, void* stream);
+void bsmm_batch_destroy(bsmm_batch_t batch);
+
+/*
  * Synchronise `stream` and return the plan's device error word as a status
  * (BSMM_OK, BSMM_ERR_TIMEOUT or BSMM_ERR_DEVICE), clearing it.
  */

@@ -36,7 +36,9 @@ STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_
 EXPORTED = [
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
-    "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_batch_create", "bsmm_batch_set_args",
+    "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_set_costs", "bsmm_batch_status_device",
+    "bsmm_batch_destroy", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -80,12 +82,20 @@ def lib():
         L.bsmm_plan_timings.argtypes = [P, P, P, P]
         L.bsmm_plan_kernel_ms.argtypes = [P, P, i32, P]
         L.bsmm_split_tile_noalloc.argtypes = [i32, i32, i32, i32, f64, P, P, f64, P, P]
+        L.bsmm_batch_create.argtypes = [ctypes.POINTER(P), i32, P]
+        L.bsmm_batch_set_args.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.bsmm_batch_execute.argtypes = [P, P]
+        L.bsmm_batch_query.argtypes = [P, P, P, P]
+        L.bsmm_batch_set_costs.argtypes = [P, P]
+        L.bsmm_batch_status_device.argtypes = [P, P]
+        L.bsmm_batch_destroy.argtypes = [P]
+        L.bsmm_batch_destroy.restype = None
         L.bsmm_last_error.argtypes = []
         L.bsmm_last_error.restype = ctypes.c_char_p
         L.bsmm_destroy.argtypes = [P]
         L.bsmm_destroy.restype = None
         for name in EXPORTED:
-            if name not in ("bsmm_options_default", "bsmm_last_error", "bsmm_destroy"):
+            if name not in ("bsmm_options_default", "bsmm_last_error", "bsmm_destroy", "bsmm_batch_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -238,6 +248,64 @@ def bsmm_split_tile_noalloc(m, n, k, nslices, alpha, A, B, beta, C, stream=None)
     shared-scratch rules (calls overlapping on the GPU race)."""
     _check(lib().bsmm_split_tile_noalloc(int(m), int(n), int(k), int(nslices), float(alpha), _ptr(A), _ptr(B),
                                          float(beta), _ptr(C), _stream(stream)))
+
+
+class Batch:
+    """Owns one bsmm_batch_t (and keeps its plans alive)."""
+
+    def __init__(self, handle: int, plans):
+        self.handle = handle
+        self.plans = list(plans)
+
+    def __del__(self):
+        try:
+            bsmm_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def bsmm_batch_create(plans) -> Batch:
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    h = ctypes.c_void_p()
+    _check(lib().bsmm_batch_create(ctypes.byref(h), len(plans), arr))
+    return Batch(h.value, plans)
+
+
+def bsmm_batch_set_args(batch: Batch, alpha, A, a_off, B, b_off, beta, C, c_off):
+    """Per-product lists: alpha, beta floats; A, a_off, B, b_off, C, c_off device tensors."""
+    n = len(batch.plans)
+    def ptrs(xs):
+        return (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    al = (ctypes.c_double * n)(*[float(x) for x in alpha])
+    be = (ctypes.c_double * n)(*[float(x) for x in beta])
+    batch._keep = (A, a_off, B, b_off, C, c_off)
+    _check(lib().bsmm_batch_set_args(batch.handle, al, ptrs(A), ptrs(a_off), ptrs(B), ptrs(b_off), be, ptrs(C),
+                                     ptrs(c_off)))
+
+
+def bsmm_batch_execute(batch: Batch, stream=None):
+    _check(lib().bsmm_batch_execute(batch.handle, _stream(stream)))
+
+
+def bsmm_batch_query(batch: Batch) -> dict:
+    nu, fl, bins = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().bsmm_batch_query(batch.handle, ctypes.byref(nu), ctypes.byref(fl), ctypes.byref(bins)))
+    return {"n_units": nu.value, "useful_flops": fl.value, "bins": bins.value}
+
+
+def bsmm_batch_set_costs(batch: Batch, costs):
+    c = _np(costs, np.float64)
+    _check(lib().bsmm_batch_set_costs(batch.handle, _ptr(c)))
+
+
+def bsmm_batch_status_device(batch: Batch, stream=None):
+    _check(lib().bsmm_batch_status_device(batch.handle, _stream(stream)))
+
+
+def bsmm_batch_destroy(batch: Batch):
+    if batch is not None and batch.handle:
+        lib().bsmm_batch_destroy(batch.handle)
+        batch.handle = None
 
 
 def bsmm_destroy(plan: Plan):

@@ -77,6 +77,11 @@ struct Fp64Args {
   int32_t* unit_cta;       // per unit or null
   int32_t* err;
   int32_t debug;
+  // batch: per-product arguments in device memory; the schedule then lists batch-wide
+  // unit ids, each mapped to (product, unit of that product)
+  const Fp64Args* prods;
+  const int32_t* unit_prod;
+  const int32_t* unit_local;
 };
 
 // Arguments of the split-mode kernels.
@@ -129,6 +134,10 @@ struct SplitArgs {
   int32_t* unit_cta;
   int32_t* err;
   int32_t debug;
+  // batch (see Fp64Args)
+  const SplitArgs* prods;
+  const int32_t* unit_prod;
+  const int32_t* unit_local;
 };
 
 // ev: null, or kMaxEvents events; ev[0] is recorded before the first kernel and
@@ -136,6 +145,21 @@ struct SplitArgs {
 constexpr int kMaxEvents = 8;
 cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk);
 cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk);
+// the two halves of launch_split: per-product exponents, scales and slices; the
+// persistent contraction over the schedule in `a` (clusters of a.cl CTAs)
+cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k);
+cudaError_t launch_split_mma(const SplitArgs& a, int clusters, cudaStream_t st);
+
+// Longest-processing-time packing of n units with `cost` onto `bins` persistent CTAs
+// (or clusters); natural = round robin in unit order. CSR output.
+void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vector<int32_t>& ptr,
+              std::vector<int32_t>& units);
+// Kernel arguments of one product (device pointers from the caller).
+void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
+                    const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
+void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
+                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
+int default_bins(const bsmm_plan_s* p);
 int fp64_ctas_per_sm();
 
 void set_error(const std::string& msg);

@@ -6,10 +6,10 @@
 
 using namespace bsmm;
 
-namespace {
+namespace bsmm {
 
-bsmm_status fill_fp64(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
-                      const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
+void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
+                    const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
   a.r = (const int32_t*)p->d_r.p;
   a.c = (const int32_t*)p->d_c.p;
   a.q = (const int32_t*)p->d_q.p;
@@ -34,11 +34,12 @@ bsmm_status fill_fp64(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A
   a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
   a.err = (int32_t*)p->d_err.p;
   a.debug = p->opt.debug_checks;
-  return BSMM_OK;
+  a.prods = nullptr;
+  a.unit_prod = a.unit_local = nullptr;
 }
 
-bsmm_status fill_split(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
-                       const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
+void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
+                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
   a.M = p->M;
   a.N = p->N;
   a.K = p->K;
@@ -100,8 +101,13 @@ bsmm_status fill_split(bsmm_plan_s* p, SplitArgs& a, double alpha, const double*
   a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
   a.err = (int32_t*)p->d_err.p;
   a.debug = p->opt.debug_checks;
-  return BSMM_OK;
+  a.prods = nullptr;
+  a.unit_prod = a.unit_local = nullptr;
 }
+
+}  // namespace bsmm
+
+namespace {
 
 bsmm_status check_ptrs(bsmm_plan_s* p, const double* A, const int64_t* a_off, const double* B,
                        const int64_t* b_off, double* C, const int64_t* c_off) {
@@ -126,11 +132,11 @@ bsmm_status run(bsmm_plan_s* p, double alpha, const double* A, const int64_t* a_
   }
   if (p->opt.mode == BSMM_FP64) {
     Fp64Args a{};
-    fill_fp64(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
+    fill_fp64_args(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
     e = launch_fp64(a, p->ctas, st, ev, &p->ev_count);
   } else {
     SplitArgs a{};
-    fill_split(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
+    fill_split_args(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
     e = launch_split(a, p->ctas, st, ev, &p->ev_count);
   }
   if (e != cudaSuccess) {

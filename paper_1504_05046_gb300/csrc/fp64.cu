@@ -44,7 +44,7 @@ struct ChunkIter {
   int k;
 };
 
-__global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
+__global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(const __grid_constant__ Fp64Args a) {
   __shared__ double sA[BK][BM + PAD];  // transposed: [kk][row]
   __shared__ double sB[BK][BN + PAD];
   const int tid = threadIdx.x;
@@ -53,13 +53,16 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
   const int beg = a.sched_ptr[cta], end = a.sched_ptr[cta + 1];
 
   for (int idx = beg; idx < end; idx++) {
-    const int u = a.sched_units[idx];
-    const Fp64Unit un = a.units[u];
+    // batch: the schedule lists batch-wide unit ids, each of one product
+    int u = a.sched_units[idx];
+    const Fp64Args& P = a.prods ? a.prods[a.unit_prod[u]] : a;
+    if (a.prods) u = a.unit_local[u];
+    const Fp64Unit un = P.units[u];
     if (a.timings && tid == 0) a.timings[2 * (int64_t)u] = gtimer();
     const int i = un.i, j = un.j;
-    const int ri = a.r[i], cj = a.c[j];
+    const int ri = P.r[i], cj = P.c[j];
     const int rows = min(BM, ri - un.r0), cols = min(BN, cj - un.c0);
-    const int64_t tile = (int64_t)i * a.N + j;
+    const int64_t tile = (int64_t)i * P.N + j;
 
     double acc[4][4];
 #pragma unroll
@@ -68,27 +71,27 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
       for (int y = 0; y < 4; y++) acc[x][y] = 0.0;
 
     ChunkIter it;
-    it.t = a.kptr[tile];
-    it.t_end = a.kptr[tile + 1];
+    it.t = P.kptr[tile];
+    it.t_end = P.kptr[tile + 1];
     it.kk0 = 0;
-    it.k = it.t < it.t_end ? a.klist[it.t] : 0;
-    it.qk = it.t < it.t_end ? a.q[it.k] : 0;
+    it.k = it.t < it.t_end ? P.klist[it.t] : 0;
+    it.qk = it.t < it.t_end ? P.q[it.k] : 0;
     // skip empty inner blocks
     while (it.t < it.t_end && it.qk == 0) {
       it.t++;
       if (it.t < it.t_end) {
-        it.k = a.klist[it.t];
-        it.qk = a.q[it.k];
+        it.k = P.klist[it.t];
+        it.qk = P.q[it.k];
       }
     }
 
     double ra[A_PER_T], rb[B_PER_T];
     auto load_chunk = [&](const ChunkIter& c) {
-      const int64_t ao = a.a_off[(int64_t)i * a.K + c.k];
-      const int64_t bo = a.b_off[(int64_t)c.k * a.N + j];
-      if (a.debug && tid == 0 && (ao < 0 || bo < 0)) atomicOr(a.err, kErrBadOffset);
-      const double* At = a.A + (ao < 0 ? 0 : ao) + (int64_t)un.r0 * c.qk;
-      const double* Bt = a.B + (bo < 0 ? 0 : bo) + un.c0;
+      const int64_t ao = P.a_off[(int64_t)i * P.K + c.k];
+      const int64_t bo = P.b_off[(int64_t)c.k * P.N + j];
+      if (P.debug && tid == 0 && (ao < 0 || bo < 0)) atomicOr(a.err, kErrBadOffset);
+      const double* At = P.A + (ao < 0 ? 0 : ao) + (int64_t)un.r0 * c.qk;
+      const double* Bt = P.B + (bo < 0 ? 0 : bo) + un.c0;
 #pragma unroll
       for (int m = 0; m < A_PER_T; m++) {
         const int e = tid + NT * m;
@@ -110,8 +113,8 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
         c.t++;
         c.kk0 = 0;
         if (c.t < c.t_end) {
-          c.k = a.klist[c.t];
-          c.qk = a.q[c.k];
+          c.k = P.klist[c.t];
+          c.qk = P.q[c.k];
         }
       }
     };
@@ -149,11 +152,11 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
     }
 
     // epilogue: C_ij = alpha*acc + beta*C_ij on the valid part of the region
-    const int64_t co = a.c_off[tile];
+    const int64_t co = P.c_off[tile];
     if (co < 0) {
       if (tid == 0) atomicOr(a.err, kErrBadOffset);
     } else {
-      double* Ct = a.C + co + (int64_t)un.r0 * cj + un.c0;
+      double* Ct = P.C + co + (int64_t)un.r0 * cj + un.c0;
 #pragma unroll
       for (int x = 0; x < 4; x++) {
         const int row = ty + 16 * x;
@@ -163,8 +166,8 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(Fp64Args a) {
           const int col = tx + 16 * y;
           if (col >= cols) continue;
           double* dst = Ct + (int64_t)row * cj + col;
-          double v = __dmul_rn(a.alpha, acc[x][y]);
-          if (a.beta != 0.0) v = __dadd_rn(v, __dmul_rn(a.beta, *dst));
+          double v = __dmul_rn(P.alpha, acc[x][y]);
+          if (P.beta != 0.0) v = __dadd_rn(v, __dmul_rn(P.beta, *dst));
           *dst = v;
         }
       }

@@ -49,6 +49,50 @@ size_t split_smem_bytes(int s, int tn, int stages) {
   return 1024 /*alignment slack*/ + (size_t)stages * stage_bytes(s, tn) + 256 /*barriers*/;
 }
 
+// Longest processing time first: units by descending cost (ties keep unit order), each
+// to the least-loaded bin (ties to the lowest bin). A bin runs its list in that order.
+void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vector<int32_t>& ptr,
+              std::vector<int32_t>& units) {
+  const int64_t n = (int64_t)cost.size();
+  std::vector<std::vector<int32_t>> lists(bins);
+  if (natural) {
+    for (int64_t u = 0; u < n; u++) lists[u % bins].push_back((int32_t)u);
+  } else {
+    std::vector<int64_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    using E = std::pair<double, int>;  // (load, bin), smallest first
+    std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
+    for (int t = 0; t < bins; t++) heap.push({0.0, t});
+    for (int64_t u : order) {
+      E e = heap.top();
+      heap.pop();
+      lists[e.second].push_back((int32_t)u);
+      heap.push({e.first + cost[u], e.second});
+    }
+  }
+  ptr.assign(bins + 1, 0);
+  units.clear();
+  units.reserve(n);
+  for (int t = 0; t < bins; t++) {
+    ptr[t] = (int32_t)units.size();
+    for (int32_t u : lists[t]) units.push_back(u);
+  }
+  ptr[bins] = (int32_t)units.size();
+}
+
+// FP64: persistent CTAs; split modes: persistent clusters of p->cl CTAs.
+int default_bins(const bsmm_plan_s* p) {
+  int64_t c;
+  if (p->opt.mode == BSMM_FP64)
+    c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm());
+  else
+    c = std::max(1, split_max_clusters(p->s, p->cl));
+  if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
+  c = std::min<int64_t>(c, std::max<int64_t>(1, p->n_units));
+  return (int)std::max<int64_t>(1, c);
+}
+
 }  // namespace bsmm
 
 namespace {
@@ -98,50 +142,11 @@ inline int log2i_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b);
 
 inline float lg(double x) { return (float)std::log2(1.0 + x); }
 
-// Longest-processing-time packing onto `ctas` persistent CTAs.
 void pack_lpt(bsmm_plan_s* p) {
-  const int64_t n = p->n_units;
-  const int ctas = p->ctas;
-  std::vector<int64_t> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::vector<std::vector<int32_t>> lists(ctas);
-  if (p->opt.schedule == BSMM_SCHED_NATURAL) {
-    for (int64_t u = 0; u < n; u++) lists[u % ctas].push_back((int32_t)u);
-  } else {
-    const std::vector<double>& cost = p->cost;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
-    using E = std::pair<double, int>;  // (load, cta) smallest first, ties to lower cta
-    std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
-    for (int t = 0; t < ctas; t++) heap.push({0.0, t});
-    for (int64_t u : order) {
-      E e = heap.top();
-      heap.pop();
-      lists[e.second].push_back((int32_t)u);
-      heap.push({e.first + cost[u], e.second});
-    }
-  }
-  p->sched_ptr.assign(ctas + 1, 0);
-  p->sched_units.clear();
-  p->sched_units.reserve(n);
-  for (int t = 0; t < ctas; t++) {
-    p->sched_ptr[t] = (int32_t)p->sched_units.size();
-    for (int32_t u : lists[t]) p->sched_units.push_back(u);
-  }
-  p->sched_ptr[ctas] = (int32_t)p->sched_units.size();
+  lpt_pack(p->cost, p->ctas, p->opt.schedule == BSMM_SCHED_NATURAL, p->sched_ptr, p->sched_units);
 }
 
-// FP64: persistent CTAs; split modes: persistent clusters of p->cl CTAs.
-int default_ctas(const bsmm_plan_s* p) {
-  int64_t c;
-  if (p->opt.mode == BSMM_FP64)
-    c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm());
-  else
-    c = std::max(1, split_max_clusters(p->s, p->cl));
-  if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
-  c = std::min<int64_t>(c, std::max<int64_t>(1, p->n_units));
-  return (int)std::max<int64_t>(1, c);
-}
+int default_ctas(const bsmm_plan_s* p) { return default_bins(p); }
 
 bsmm_status upload_schedule(bsmm_plan_s* p) {
   bsmm_status st;

@@ -567,6 +567,7 @@ constexpr int kPrefetch = 8;  // chunks the producer pulls into L2 ahead of its 
 // The chunks of one CTA's unit list in order: unit by unit, k block by k block
 // (ascending), 32-deep chunk by chunk.
 struct ChunkCursor {
+  const SplitArgs* P;  // the product of the current unit (the batch-wide args for one product)
   int idx, uend;
   int rb, cb;  // this CTA's row block and column block
   UnitIter it;
@@ -587,20 +588,23 @@ struct ChunkCursor {
       if (in_unit) {
         kt = it.next();
         if (kt >= 0) {
-          nkc = (a.q[kt] + kSplitKC - 1) / kSplitKC;  // >= 1: blocks with q = 0 are never present
+          nkc = (P->q[kt] + kSplitKC - 1) / kSplitKC;  // >= 1: blocks with q = 0 are never present
           kc = 0;
           ownb = it.own_b(kt);
-          asrc = a.apk + a.apk_off[(size_t)rb * a.K + kt];
-          bsrc = ownb ? a.bpk + a.bpk_off[(size_t)kt * a.CB + cb] : nullptr;
+          asrc = P->apk + P->apk_off[(size_t)rb * P->K + kt];
+          bsrc = ownb ? P->bpk + P->bpk_off[(size_t)kt * P->CB + cb] : nullptr;
           return true;
         }
         in_unit = false;
       }
       if (++idx >= uend) return false;
-      const SplitUnit un = a.units[a.sched_units[idx]];
+      int g = a.sched_units[idx];
+      P = a.prods ? &a.prods[a.unit_prod[g]] : &a;
+      if (a.prods) g = a.unit_local[g];
+      const SplitUnit un = P->units[g];
       rb = un.rb;
       cb = un.cb * cl + rank;
-      it.init(a, un.rb, un.cb, cb);
+      it.init(*P, un.rb, un.cb, cb);
       in_unit = true;
     }
   }
@@ -612,7 +616,7 @@ struct ChunkCursor {
 };
 
 template <int S, int TN, int CL>
-__global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_constant__ SplitArgs a) {
   constexpr int TH = TN / 2;                    // columns per epilogue thread
   constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
   constexpr int A_SLICE = A_STAGE / CL;         // bytes of A each cluster CTA loads and multicasts
@@ -729,12 +733,15 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
 #pragma unroll
       for (int p = 1; p <= S; p++) idp[p - 1] = idesc_f16(kSplitBM, (S + 1 - p) * TN, a.fp16 != 0);
       for (int idx = ubeg; idx < uend && ok; idx++) {
-        const SplitUnit un = a.units[a.sched_units[idx]];
+        int g = a.sched_units[idx];
+        const SplitArgs& P = a.prods ? a.prods[a.unit_prod[g]] : a;
+        if (a.prods) g = a.unit_local[g];
+        const SplitUnit un = P.units[g];
         const int cb = un.cb * CL + rank;
         UnitIter it;
-        it.init(a, un.rb, un.cb, cb);
+        it.init(P, un.rb, un.cb, cb);
         for (int kt = it.next(); kt >= 0 && ok; kt = it.next()) {
-          const int q = a.q[kt];
+          const int q = P.q[kt];
           const int nkc = (q + kSplitKC - 1) / kSplitKC;
           const bool ownb = it.own_b(kt);
           const uint32_t buf = tcount & 1, use = tcount >> 1;
@@ -804,27 +811,29 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
     uint32_t tcount = 0;
     bool ok = true;
     for (int idx = ubeg; idx < uend && ok; idx++) {
-      const int u = a.sched_units[idx];
-      const SplitUnit un = a.units[u];
+      int u = a.sched_units[idx];
+      const SplitArgs& P = a.prods ? a.prods[a.unit_prod[u]] : a;
+      if (a.prods) u = a.unit_local[u];
+      const SplitUnit un = P.units[u];
       const int cb = un.cb * CL + rank;
-      if (cb >= a.CB) continue;  // this CTA only helps stream the cluster's A panel
+      if (cb >= P.CB) continue;  // this CTA only helps stream the cluster's A panel
       if (a.timings && rank == 0 && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = gtimer();
       const int64_t m = (int64_t)un.rb * kSplitBM + row;
-      const bool row_ok = m < a.Mtot;
+      const bool row_ok = m < P.Mtot;
       const int64_t n0 = (int64_t)cb * TN + half * TH;
       uint32_t acc[TH][4];  // exact 128-bit two's-complement sums, unit 2^L per column
 #pragma unroll
       for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
       UnitIter it;
-      it.init(a, un.rb, un.cb, cb);
+      it.init(P, un.rb, un.cb, cb);
       // the exponent offsets of the next k block are loaded while this one is processed
       // (k blocks where this column block has no B tile add nothing and are skipped)
       int kt = it.next_own();
       int shr_n = 0;
       int16_t rb_n[TH];
       auto load_exps = [&](int k) {
-        shr_n = kSplitGuard + (row_ok ? (int)a.rowexp[(int64_t)k * a.Mtot + m] : 0);
-        const uint4* src = reinterpret_cast<const uint4*>(a.colexp + (int64_t)k * a.colexp_ld + n0);
+        shr_n = kSplitGuard + (row_ok ? (int)P.rowexp[(int64_t)k * P.Mtot + m] : 0);
+        const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)k * P.colexp_ld + n0);
 #pragma unroll
         for (int w = 0; w < TH / 8; w++) *reinterpret_cast<uint4*>(&rb_n[w * 8]) = __ldg(src + w);
       };
@@ -872,21 +881,21 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(SplitArgs a) {
       if (!ok) break;
       // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles
       if (row_ok) {
-        const int i = a.row_tile[m];
-        const int64_t lr = m - a.ro[i];
-        const int Lrow = a.eAmax[i] - kSplitBeta * (S + 1) - kSplitGuard;
+        const int i = P.row_tile[m];
+        const int64_t lr = m - P.ro[i];
+        const int Lrow = P.eAmax[i] - kSplitBeta * (S + 1) - kSplitGuard;
 #pragma unroll
         for (int c = 0; c < TH; c++) {
           const int64_t n = n0 + c;
-          if (n < a.Ntot) {
-            const int j = a.col_tile[n];
-            const int64_t tile = (int64_t)i * a.N + j;
-            const int64_t off = a.cs[tile] ? a.c_off[tile] : -2;
+          if (n < P.Ntot) {
+            const int j = P.col_tile[n];
+            const int64_t tile = (int64_t)i * P.N + j;
+            const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
             if (off == -1) atomicOr(a.err, kErrBadOffset);
             if (off >= 0) {
-              double* dst = a.C + off + lr * a.c[j] + (n - a.co[j]);
-              double vv = __dmul_rn(a.alpha, acc_to_double(acc[c], Lrow + a.eBmax[j]));
-              if (a.beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(a.beta, *dst));
+              double* dst = P.C + off + lr * P.c[j] + (n - P.co[j]);
+              double vv = __dmul_rn(P.alpha, acc_to_double(acc[c], Lrow + P.eBmax[j]));
+              if (P.beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(P.beta, *dst));
               *dst = vv;
             }
           }
@@ -974,12 +983,10 @@ int max_clusters_s(int cl) {
 
 }  // namespace
 
-cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
-  int k = 0;
-  if (ev) cudaEventRecord(ev[0], st);
+cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k) {
   if (a.n_a_tiles + a.n_b_tiles > 0) split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
   if (a.M + a.N > 0) split_scale_kernel<<<a.M + a.N, 256, 0, st>>>(a);
-  if (ev) cudaEventRecord(ev[++k], st);
+  if (ev) cudaEventRecord(ev[++*k], st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.n_a_blocks + a.n_b_blocks > 0) {
@@ -988,9 +995,23 @@ cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEven
     else
       split_pack_kernel<__nv_bfloat16><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
   }
-  if (ev) cudaEventRecord(ev[++k], st);
-  e = cudaGetLastError();
+  if (ev) cudaEventRecord(ev[++*k], st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
+  int k = 0;
+  if (ev) cudaEventRecord(ev[0], st);
+  cudaError_t e = launch_split_prep(a, st, ev, &k);
   if (e != cudaSuccess) return e;
+  e = launch_split_mma(a, ctas, st);
+  if (ev) cudaEventRecord(ev[++k], st);
+  if (nk) *nk = k;
+  return e;
+}
+
+cudaError_t launch_split_mma(const SplitArgs& a, int ctas, cudaStream_t st) {
+  cudaError_t e;
   switch (a.s) {  // `ctas` counts clusters of a.cl CTAs
     case 1: e = launch_mma_cl<1>(a, ctas, st); break;
     case 2: e = launch_mma_cl<2>(a, ctas, st); break;
@@ -1000,8 +1021,6 @@ cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEven
     case 6: e = launch_mma_cl<6>(a, ctas, st); break;
     default: e = cudaErrorInvalidValue;
   }
-  if (ev) cudaEventRecord(ev[++k], st);
-  if (nk) *nk = k;
   return e;
 }
 

@@ -1,0 +1,105 @@
+"""Batched products through one persistent launch (eager and replayed from a CUDA
+graph) against each product run on its own and against the oracles."""
+import numpy as np
+import pytest
+
+import bsmm_gen as G
+import oracle
+from oracle import split as OS
+import paper_1504_05046_gb300 as P
+from helpers import c_arena, struct_elements
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(mode, count=7, seed=5):
+    import torch
+    probs = G.make_batch(count, seed, n_lo=150, n_hi=900, b_lo=24, b_hi=140)
+    items = []
+    for i, prob in enumerate(probs):
+        prob.alpha, prob.beta = [1.0, -0.5, 2.0][i % 3], [0.0, 1.0, 0.5][i % 3]
+        cs, _, _ = oracle.structure(prob)
+        off, C0 = c_arena(prob, cs, rng=np.random.default_rng(i))
+        plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                           mode=mode, nslices=6, debug_checks=1)
+        d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        items.append(dict(prob=prob, cs=cs, off=off, C0=C0, plan=plan, A=d(prob.A if prob.A.size else np.zeros(2)),
+                          B=d(prob.B if prob.B.size else np.zeros(2)), ao=d(prob.a_off), bo=d(prob.b_off), co=d(off),
+                          C=d(C0 if C0.size else np.zeros(2))))
+    return items
+
+
+def _reference(it, mode):
+    want = it["C0"].copy()
+    if mode == P.BSMM_FP64:
+        oracle.bsmm(it["prob"], it["cs"], want, it["off"])
+    else:
+        OS.bsmm_split(it["prob"], it["cs"], want, it["off"], 6)
+    return want
+
+
+@pytest.mark.parametrize("mode", [P.BSMM_FP64, P.BSMM_SPLIT_BF16])
+def test_batch_matches_oracle_eager_and_graph(mode):
+    import torch
+    items = _setup(mode)
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    q = P.bsmm_batch_query(batch)
+    assert q["n_units"] == sum(P.bsmm_plan_query(it["plan"])["n_units"] for it in items)
+    P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                          [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                          [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    P.bsmm_batch_status_device(batch)
+    wants = [_reference(it, mode) for it in items]
+    for it, want in zip(items, wants):
+        got = it["C"].cpu().numpy()
+        assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
+                              struct_elements(it["prob"], it["cs"], it["off"], want))
+    # capture the batch into a CUDA graph; replay it from the initial C twice
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        P.bsmm_batch_execute(batch)
+    for _ in range(2):
+        for it in items:
+            if it["C0"].size:
+                it["C"].copy_(torch.from_numpy(it["C0"]))
+        g.replay()
+        torch.cuda.synchronize()
+        for it, want in zip(items, wants):
+            got = it["C"].cpu().numpy()
+            assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
+                                  struct_elements(it["prob"], it["cs"], it["off"], want))
+    P.bsmm_batch_status_device(batch)
+
+
+def test_batch_reordered_costs_same_bits():
+    import torch
+    items = _setup(P.BSMM_SPLIT_BF16, count=5, seed=9)
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    args = ([it["prob"].alpha for it in items], [it["A"] for it in items], [it["ao"] for it in items],
+            [it["B"] for it in items], [it["bo"] for it in items], [it["prob"].beta for it in items],
+            [it["C"] for it in items], [it["co"] for it in items])
+    P.bsmm_batch_set_args(batch, *args)
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    first = [it["C"].cpu().numpy().copy() for it in items]
+    n = P.bsmm_batch_query(batch)["n_units"]
+    P.bsmm_batch_set_costs(batch, np.random.default_rng(1).uniform(1, 100, n))
+    for it in items:
+        if it["C0"].size:
+            it["C"].copy_(torch.from_numpy(it["C0"]))
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    for it, f in zip(items, first):
+        assert np.array_equal(it["C"].cpu().numpy(), f)
+
+
+def test_batch_rejects_mixed_modes():
+    import torch  # noqa: F401
+    p1 = P.bsmm_plan([64], [64], [64], [[1]], [[1]], mode=P.BSMM_FP64)
+    p2 = P.bsmm_plan([64], [64], [64], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16)
+    with pytest.raises(P.BsmmError):
+        P.bsmm_batch_create([p1, p2])
