@@ -196,6 +196,47 @@ bsmm_status bsmm_batch_status_device(bsmm_batch_t batch, void* stream);
 void bsmm_batch_destroy(bsmm_batch_t batch);
 
 /*
+ * Learned task-cost model. The paper tolerates the load variation of nonuniform
+ * blocks (Sec. 4.4, Table 1) with many small tasks and a dynamic scheduler (Sec.
+ * 3.2); here work units are packed statically onto persistent CTAs, so the packing
+ * needs cost estimates. A small MLP (BSMM_NFEATURES inputs from bsmm_plan_features,
+ * two tanh layers of 32, one output = log unit time) is trained on the GPU from
+ * measured unit times (bsmm_plan_timings) and its predictions replace the flop-count
+ * costs. Results never depend on it (only the order of the units).
+ *
+ * Parameters: one float vector of bsmm_mlp_num_params() entries, in this order:
+ * W1[32][F], b1[32], W2[32][32], b2[32], w3[32], b3. Inputs are standardised with the
+ * model's stored means/deviations and the output de-standardised (bsmm_mlp_set_norm,
+ * or set from the data by bsmm_mlp_fit).
+ *
+ * bsmm_mlp_create      deterministic initialisation from `seed`; allocates device memory
+ * bsmm_mlp_loss_grad   X[n x F], t[n] device (raw features, raw log times): mean squared
+ *                      error of the standardised prediction and its gradient (host
+ *                      outputs, grad may be NULL); synchronises `stream`
+ * bsmm_mlp_fit         sets the standardisation from (X, t), then `steps` full-batch Adam
+ *                      steps (beta1 0.9, beta2 0.999, eps 1e-8) at rate `lr`; reductions
+ *                      run in a fixed order, so training is reproducible bit for bit;
+ *                      *final_loss (host, may be NULL) after the last step
+ * bsmm_mlp_predict     y[n] device = predicted log time for X (device), asynchronous
+ * bsmm_plan_predict_costs  predicts every unit of `plan` and re-packs it with the
+ *                      predicted times as costs (bsmm_plan_set_costs); synchronises
+ */
+typedef struct bsmm_mlp_s* bsmm_mlp_t;
+bsmm_status bsmm_mlp_create(bsmm_mlp_t* out, uint64_t seed);
+int32_t bsmm_mlp_num_params(void);
+bsmm_status bsmm_mlp_set_params(bsmm_mlp_t mlp, const float* params, int64_t n);
+bsmm_status bsmm_mlp_get_params(bsmm_mlp_t mlp, float* params, int64_t n);
+bsmm_status bsmm_mlp_set_norm(bsmm_mlp_t mlp, const float* x_mean, const float* x_sd, float y_mean, float y_sd);
+bsmm_status bsmm_mlp_get_norm(bsmm_mlp_t mlp, float* x_mean, float* x_sd, float* y_mean, float* y_sd);
+bsmm_status bsmm_mlp_loss_grad(bsmm_mlp_t mlp, const float* X, const float* t, int64_t n, float* loss,
+                               float* grad, void* stream);
+bsmm_status bsmm_mlp_fit(bsmm_mlp_t mlp, const float* X, const float* t, int64_t n, int32_t steps, float lr,
+                         float* final_loss, void* stream);
+bsmm_status bsmm_mlp_predict(bsmm_mlp_t mlp, const float* X, int64_t n, float* y, void* stream);
+bsmm_status bsmm_plan_predict_costs(bsmm_plan_t plan, bsmm_mlp_t mlp, void* stream);
+void bsmm_mlp_destroy(bsmm_mlp_t mlp);
+
+/*
  * Synchronise `stream` and return the plan's device error word as a status
  * (BSMM_OK, BSMM_ERR_TIMEOUT or BSMM_ERR_DEVICE), clearing it.
  */

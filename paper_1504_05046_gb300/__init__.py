@@ -38,7 +38,9 @@ EXPORTED = [
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
     "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_batch_create", "bsmm_batch_set_args",
     "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_set_costs", "bsmm_batch_status_device",
-    "bsmm_batch_destroy", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_batch_destroy", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
+    "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
+    "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -90,12 +92,25 @@ def lib():
         L.bsmm_batch_status_device.argtypes = [P, P]
         L.bsmm_batch_destroy.argtypes = [P]
         L.bsmm_batch_destroy.restype = None
+        L.bsmm_mlp_create.argtypes = [ctypes.POINTER(P), ctypes.c_uint64]
+        L.bsmm_mlp_num_params.argtypes = []
+        L.bsmm_mlp_set_params.argtypes = [P, P, i64]
+        L.bsmm_mlp_get_params.argtypes = [P, P, i64]
+        L.bsmm_mlp_set_norm.argtypes = [P, P, P, ctypes.c_float, ctypes.c_float]
+        L.bsmm_mlp_get_norm.argtypes = [P, P, P, P, P]
+        L.bsmm_mlp_loss_grad.argtypes = [P, P, P, i64, P, P, P]
+        L.bsmm_mlp_fit.argtypes = [P, P, P, i64, i32, ctypes.c_float, P, P]
+        L.bsmm_mlp_predict.argtypes = [P, P, i64, P, P]
+        L.bsmm_plan_predict_costs.argtypes = [P, P, P]
+        L.bsmm_mlp_destroy.argtypes = [P]
+        L.bsmm_mlp_destroy.restype = None
         L.bsmm_last_error.argtypes = []
         L.bsmm_last_error.restype = ctypes.c_char_p
         L.bsmm_destroy.argtypes = [P]
         L.bsmm_destroy.restype = None
         for name in EXPORTED:
-            if name not in ("bsmm_options_default", "bsmm_last_error", "bsmm_destroy", "bsmm_batch_destroy"):
+            if name not in ("bsmm_options_default", "bsmm_last_error", "bsmm_destroy", "bsmm_batch_destroy",
+                            "bsmm_mlp_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -306,6 +321,84 @@ def bsmm_batch_destroy(batch: Batch):
     if batch is not None and batch.handle:
         lib().bsmm_batch_destroy(batch.handle)
         batch.handle = None
+
+
+class Mlp:
+    """Owns one bsmm_mlp_t (the learned task-cost model)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        try:
+            bsmm_mlp_destroy(self)
+        except Exception:
+            pass
+
+
+def bsmm_mlp_create(seed: int = 0) -> Mlp:
+    h = ctypes.c_void_p()
+    _check(lib().bsmm_mlp_create(ctypes.byref(h), ctypes.c_uint64(seed)))
+    return Mlp(h.value)
+
+
+def bsmm_mlp_num_params() -> int:
+    return int(lib().bsmm_mlp_num_params())
+
+
+def bsmm_mlp_set_params(mlp: Mlp, params):
+    p = _np(params, np.float32)
+    _check(lib().bsmm_mlp_set_params(mlp.handle, _ptr(p), p.size))
+
+
+def bsmm_mlp_get_params(mlp: Mlp) -> np.ndarray:
+    p = np.zeros(bsmm_mlp_num_params(), np.float32)
+    _check(lib().bsmm_mlp_get_params(mlp.handle, _ptr(p), p.size))
+    return p
+
+
+def bsmm_mlp_set_norm(mlp: Mlp, x_mean, x_sd, y_mean: float, y_sd: float):
+    m = _np(x_mean, np.float32)
+    s = _np(x_sd, np.float32)
+    _check(lib().bsmm_mlp_set_norm(mlp.handle, _ptr(m), _ptr(s), float(y_mean), float(y_sd)))
+
+
+def bsmm_mlp_get_norm(mlp: Mlp):
+    m = np.zeros(BSMM_NFEATURES, np.float32)
+    s = np.zeros(BSMM_NFEATURES, np.float32)
+    ym, ys = ctypes.c_float(), ctypes.c_float()
+    _check(lib().bsmm_mlp_get_norm(mlp.handle, _ptr(m), _ptr(s), ctypes.byref(ym), ctypes.byref(ys)))
+    return m, s, ym.value, ys.value
+
+
+def bsmm_mlp_loss_grad(mlp: Mlp, X, t, stream=None):
+    """X (n x F) and t (n) float32 device tensors; returns (loss, grad numpy)."""
+    g = np.zeros(bsmm_mlp_num_params(), np.float32)
+    loss = ctypes.c_float()
+    _check(lib().bsmm_mlp_loss_grad(mlp.handle, _ptr(X), _ptr(t), int(t.numel()), ctypes.byref(loss), _ptr(g),
+                                    _stream(stream)))
+    return loss.value, g
+
+
+def bsmm_mlp_fit(mlp: Mlp, X, t, steps: int, lr: float, stream=None) -> float:
+    loss = ctypes.c_float()
+    _check(lib().bsmm_mlp_fit(mlp.handle, _ptr(X), _ptr(t), int(t.numel()), int(steps), float(lr), ctypes.byref(loss),
+                              _stream(stream)))
+    return loss.value
+
+
+def bsmm_mlp_predict(mlp: Mlp, X, y, stream=None):
+    _check(lib().bsmm_mlp_predict(mlp.handle, _ptr(X), int(y.numel()), _ptr(y), _stream(stream)))
+
+
+def bsmm_plan_predict_costs(plan: Plan, mlp: Mlp, stream=None):
+    _check(lib().bsmm_plan_predict_costs(plan.handle, mlp.handle, _stream(stream)))
+
+
+def bsmm_mlp_destroy(mlp: Mlp):
+    if mlp is not None and mlp.handle:
+        lib().bsmm_mlp_destroy(mlp.handle)
+        mlp.handle = None
 
 
 def bsmm_destroy(plan: Plan):

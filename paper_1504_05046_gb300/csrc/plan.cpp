@@ -50,7 +50,10 @@ size_t split_smem_bytes(int s, int tn, int stages) {
 }
 
 // Longest processing time first: units by descending cost (ties keep unit order), each
-// to the least-loaded bin (ties to the lowest bin). A bin runs its list in that order.
+// to the least-loaded bin (ties to the lowest bin). A bin then runs its units in unit
+// order: the bins' loads are set by the assignment alone, and walking every list in
+// the planner's raster order keeps the units that run at the same time close in the
+// index space, so their A and B panels are shared through L2.
 void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vector<int32_t>& ptr,
               std::vector<int32_t>& units) {
   const int64_t n = (int64_t)cost.size();
@@ -70,6 +73,7 @@ void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vect
       lists[e.second].push_back((int32_t)u);
       heap.push({e.first + cost[u], e.second});
     }
+    for (auto& l : lists) std::sort(l.begin(), l.end());
   }
   ptr.assign(bins + 1, 0);
   units.clear();
