@@ -83,7 +83,9 @@ typedef struct {
   int32_t profile;         /* 1 = time each internal kernel with CUDA events (bsmm_plan_kernel_ms) */
   int32_t cluster;         /* split modes: CTAs per thread-block cluster sharing the A stream
                               by multicast, 1, 2 or 4 (0 = default) */
-  int32_t reserved[4];     /* must be zero */
+  int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = chosen
+                              from the tiling: 32 when 64 would pad ragged tiles by > 5%) */
+  int32_t reserved[3];     /* must be zero */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */

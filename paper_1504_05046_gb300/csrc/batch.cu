@@ -84,6 +84,9 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
     const bsmm_plan_s* p = plans[i];
     if (p->opt.mode != p0->opt.mode || p->s != p0->s || p->cl != p0->cl || p->stages != p0->stages)
       return set_error("all plans of a batch need the same mode, slice count and cluster size"), BSMM_ERR_INVALID;
+    if (p->opt.mode == BSMM_FP64 && p->f64_tile != p0->f64_tile)
+      return set_error("all FP64 plans of a batch need the same sub-tile edge (set bsmm_options.fp64_tile)"),
+             BSMM_ERR_INVALID;
     if (p->device != p0->device) return set_error("all plans of a batch need the same device"), BSMM_ERR_INVALID;
   }
   bsmm_batch_s* b = new (std::nothrow) bsmm_batch_s();

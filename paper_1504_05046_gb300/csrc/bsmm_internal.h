@@ -28,7 +28,7 @@ constexpr int kSplitGuard = 55;    // guard bits of the 128-bit accumulator belo
 constexpr int kSplitMaxK = 8192;   // inner blocks per product (keeps the 128-bit sum from overflowing)
 
 // FP64-mode geometry.
-constexpr int kF64BM = 64, kF64BN = 64, kF64BK = 16, kF64Threads = 256;
+constexpr int kF64BK = 16;  // inner depth of one staged chunk (FP64 path)
 
 // Largest inner block for which every diagonal sum of slice products stays an
 // integer of magnitude <= 2^24 (exact in the FP32 tensor-core accumulator).
@@ -77,6 +77,7 @@ struct Fp64Args {
   int32_t* unit_cta;       // per unit or null
   int32_t* err;
   int32_t debug;
+  int32_t tile;            // sub-tile edge of the units (64 or 32)
   // batch: per-product arguments in device memory; the schedule then lists batch-wide
   // unit ids, each mapped to (product, unit of that product)
   const Fp64Args* prods;
@@ -160,7 +161,7 @@ void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, 
 void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
                      const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
 int default_bins(const bsmm_plan_s* p);
-int fp64_ctas_per_sm();
+int fp64_ctas_per_sm(int tile);
 
 void set_error(const std::string& msg);
 
@@ -179,6 +180,7 @@ struct bsmm_plan_s {
 
   // work units (one kind per mode)
   std::vector<bsmm::Fp64Unit> f64_units;
+  int f64_tile = 64;           // FP64 sub-tile edge (64 or 32)
   std::vector<bsmm::SplitUnit> sp_units;
   std::vector<int64_t> kptr;   // FP64: CSR over M*N tiles
   std::vector<int32_t> klist;

@@ -34,6 +34,7 @@ void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, 
   a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
   a.err = (int32_t*)p->d_err.p;
   a.debug = p->opt.debug_checks;
+  a.tile = p->f64_tile;
   a.prods = nullptr;
   a.unit_prod = a.unit_local = nullptr;
 }

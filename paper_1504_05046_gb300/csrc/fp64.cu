@@ -33,10 +33,8 @@ __device__ __forceinline__ int64_t gtimer() {
   return (int64_t)t;
 }
 
-constexpr int BM = kF64BM, BN = kF64BN, BK = kF64BK, NT = kF64Threads;
+constexpr int BK = kF64BK;
 constexpr int PAD = 2;
-constexpr int A_PER_T = BM * BK / NT;  // 4
-constexpr int B_PER_T = BK * BN / NT;  // 4
 
 struct ChunkIter {
   int64_t t, t_end;  // position in the tile's k-list
@@ -44,11 +42,18 @@ struct ChunkIter {
   int k;
 };
 
-__global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(const __grid_constant__ Fp64Args a) {
+// T x T sub-tiles (T = 64 or 32): (T/4)^2 threads, each with a 4 x 4 register tile at
+// rows ty + (T/4)x and columns tx + (T/4)y. The smaller edge wastes less on ragged tiles.
+template <int T>
+__global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 : 4096 / (T * T) * 2)
+    fp64_tile_kernel(const __grid_constant__ Fp64Args a) {
+  constexpr int BM = T, BN = T, TX = T / 4, NT = TX * TX;
+  constexpr int A_PER_T = BM * BK / NT;
+  constexpr int B_PER_T = BK * BN / NT;
   __shared__ double sA[BK][BM + PAD];  // transposed: [kk][row]
   __shared__ double sB[BK][BN + PAD];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid % TX, ty = tid / TX;
   const int cta = blockIdx.x;
   const int beg = a.sched_ptr[cta], end = a.sched_ptr[cta + 1];
 
@@ -140,9 +145,9 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(const __grid_constant_
       for (int kk = 0; kk < BK; kk++) {
         double av[4], bv[4];
 #pragma unroll
-        for (int x = 0; x < 4; x++) av[x] = sA[kk][ty + 16 * x];
+        for (int x = 0; x < 4; x++) av[x] = sA[kk][ty + TX * x];
 #pragma unroll
-        for (int y = 0; y < 4; y++) bv[y] = sB[kk][tx + 16 * y];
+        for (int y = 0; y < 4; y++) bv[y] = sB[kk][tx + TX * y];
 #pragma unroll
         for (int x = 0; x < 4; x++)
 #pragma unroll
@@ -159,11 +164,11 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(const __grid_constant_
       double* Ct = P.C + co + (int64_t)un.r0 * cj + un.c0;
 #pragma unroll
       for (int x = 0; x < 4; x++) {
-        const int row = ty + 16 * x;
+        const int row = ty + TX * x;
         if (row >= rows) continue;
 #pragma unroll
         for (int y = 0; y < 4; y++) {
-          const int col = tx + 16 * y;
+          const int col = tx + TX * y;
           if (col >= cols) continue;
           double* dst = Ct + (int64_t)row * cj + col;
           double v = __dmul_rn(P.alpha, acc[x][y]);
@@ -184,15 +189,21 @@ __global__ void __launch_bounds__(NT, 2) fp64_tile_kernel(const __grid_constant_
 
 }  // namespace
 
-int fp64_ctas_per_sm() {
+int fp64_ctas_per_sm(int tile) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_tile_kernel, NT, 0) != cudaSuccess || n < 1) n = 1;
+  const cudaError_t e = tile == 32
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_tile_kernel<32>, 64, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_tile_kernel<64>, 256, 0);
+  if (e != cudaSuccess || n < 1) n = 1;
   return n;
 }
 
 cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
   if (ev) cudaEventRecord(ev[0], st);
-  fp64_tile_kernel<<<ctas, NT, 0, st>>>(a);
+  if (a.tile == 32)
+    fp64_tile_kernel<32><<<ctas, 64, 0, st>>>(a);
+  else
+    fp64_tile_kernel<64><<<ctas, 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[1], st);
   if (nk) *nk = 1;
   return cudaGetLastError();

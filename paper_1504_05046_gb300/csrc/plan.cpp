@@ -89,7 +89,7 @@ void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vect
 int default_bins(const bsmm_plan_s* p) {
   int64_t c;
   if (p->opt.mode == BSMM_FP64)
-    c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm());
+    c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm(p->f64_tile));
   else
     c = std::max(1, split_max_clusters(p->s, p->cl));
   if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
@@ -165,6 +165,22 @@ bsmm_status upload_schedule(bsmm_plan_s* p) {
 // ------------------------------------------------------------------------------------
 bsmm_status plan_fp64(bsmm_plan_s* p) {
   const int M = p->M, N = p->N, K = p->K;
+  // Sub-tile edge: 64 reuses each staged element more, 32 pads ragged tiles less. Take 32
+  // when the padded work of 64-wide sub-tiles exceeds that of 32-wide ones by over 5%.
+  {
+    double pad64 = 0, pad32 = 0;
+    for (int i = 0; i < M; i++)
+      for (int j = 0; j < N; j++) {
+        const int64_t t = (int64_t)i * N + j;
+        if (!p->cs[t]) continue;
+        const double kq = (double)(p->kptr[t + 1] - p->kptr[t]);
+        auto up = [](int x, int e) { return (double)((x + e - 1) / e * e); };
+        pad64 += up(p->r[i], 64) * up(p->c[j], 64) * kq;
+        pad32 += up(p->r[i], 32) * up(p->c[j], 32) * kq;
+      }
+    p->f64_tile = p->opt.fp64_tile ? p->opt.fp64_tile : (pad64 > 1.05 * pad32 ? 32 : 64);
+  }
+  const int T = p->f64_tile;
   for (int i = 0; i < M; i++)
     for (int j = 0; j < N; j++) {
       if (!p->cs[(int64_t)i * N + j]) continue;
@@ -177,14 +193,14 @@ bsmm_status plan_fp64(bsmm_plan_s* p) {
         kg += log2i_ceil_div(qk, kF64BK);
         nk++;
       }
-      for (int r0 = 0; r0 < ri; r0 += kF64BM)
-        for (int c0 = 0; c0 < cj; c0 += kF64BN) {
-          const int rows = std::min(kF64BM, ri - r0), cols = std::min(kF64BN, cj - c0);
+      for (int r0 = 0; r0 < ri; r0 += T)
+        for (int c0 = 0; c0 < cj; c0 += T) {
+          const int rows = std::min(T, ri - r0), cols = std::min(T, cj - c0);
           p->f64_units.push_back({i, j, r0, c0});
           const double fl = 2.0 * rows * cols * (double)kq;
           p->flop_cost.push_back(std::max(fl, 1.0));
           float f[BSMM_NFEATURES] = {lg(rows), lg(cols), lg((double)nk), lg((double)kq), lg((double)kg),
-                                     lg(fl), (float)(fl / std::max(1.0, 2.0 * kF64BM * kF64BN * kF64BK * (double)kg)),
+                                     lg(fl), (float)(fl / std::max(1.0, 2.0 * T * T * kF64BK * (double)kg)),
                                      0.0f, 0.0f, 0.0f, 0.0f, lg((double)kg)};
           p->features.insert(p->features.end(), f, f + BSMM_NFEATURES);
         }
@@ -377,6 +393,8 @@ bsmm_status validate_options(const bsmm_options& o) {
   if (o.profile < 0 || o.profile > 1) return set_error("profile must be 0 or 1"), BSMM_ERR_INVALID;
   if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4)
     return set_error("cluster must be 0, 1, 2 or 4"), BSMM_ERR_INVALID;
+  if (o.fp64_tile != 0 && o.fp64_tile != 32 && o.fp64_tile != 64)
+    return set_error("fp64_tile must be 0, 32 or 64"), BSMM_ERR_INVALID;
   for (int r : o.reserved)
     if (r) return set_error("reserved option fields must be zero"), BSMM_ERR_INVALID;
   return BSMM_OK;

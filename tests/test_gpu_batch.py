@@ -12,7 +12,7 @@ from helpers import c_arena, struct_elements
 pytestmark = pytest.mark.gpu
 
 
-def _setup(mode, count=7, seed=5):
+def _setup(mode, count=7, seed=5, fp64_tile=0):
     import torch
     probs = G.make_batch(count, seed, n_lo=150, n_hi=900, b_lo=24, b_hi=140)
     items = []
@@ -21,7 +21,7 @@ def _setup(mode, count=7, seed=5):
         cs, _, _ = oracle.structure(prob)
         off, C0 = c_arena(prob, cs, rng=np.random.default_rng(i))
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                           mode=mode, nslices=6, debug_checks=1)
+                           mode=mode, nslices=6, debug_checks=1, fp64_tile=fp64_tile)
         d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
         items.append(dict(prob=prob, cs=cs, off=off, C0=C0, plan=plan, A=d(prob.A if prob.A.size else np.zeros(2)),
                           B=d(prob.B if prob.B.size else np.zeros(2)), ao=d(prob.a_off), bo=d(prob.b_off), co=d(off),
@@ -38,10 +38,18 @@ def _reference(it, mode):
     return want
 
 
+def test_batch_rejects_mixed_fp64_subtiles():
+    import torch  # noqa: F401
+    p1 = P.bsmm_plan([64], [64], [64], [[1]], [[1]], mode=P.BSMM_FP64, fp64_tile=32)
+    p2 = P.bsmm_plan([64], [64], [64], [[1]], [[1]], mode=P.BSMM_FP64, fp64_tile=64)
+    with pytest.raises(P.BsmmError):
+        P.bsmm_batch_create([p1, p2])
+
+
 @pytest.mark.parametrize("mode", [P.BSMM_FP64, P.BSMM_SPLIT_BF16])
 def test_batch_matches_oracle_eager_and_graph(mode):
     import torch
-    items = _setup(mode)
+    items = _setup(mode, fp64_tile=32)
     batch = P.bsmm_batch_create([it["plan"] for it in items])
     q = P.bsmm_batch_query(batch)
     assert q["n_units"] == sum(P.bsmm_plan_query(it["plan"])["n_units"] for it in items)
