@@ -85,7 +85,10 @@ typedef struct {
                               by multicast, 1, 2 or 4 (0 = default) */
   int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = chosen
                               from the tiling: 32 when 64 would pad ragged tiles by > 5%) */
-  int32_t reserved[3];     /* must be zero */
+  int32_t stages;          /* split modes: depth of the shared-memory ring of 32-deep k chunks
+                              (k panels in flight), 2..8 and within the 227 KB shared memory of
+                              one CTA (0 = as many as fit in 200 KB) */
+  int32_t reserved[2];     /* must be zero */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */

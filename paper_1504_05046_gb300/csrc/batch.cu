@@ -113,6 +113,7 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   tmp_view.sms = p0->sms;
   tmp_view.s = p0->s;
   tmp_view.cl = p0->cl;
+  tmp_view.stages = p0->stages;
   tmp_view.n_units = std::max<int64_t>(1, b->n_units);
   b->bins = default_bins(&tmp_view);
   bsmm_status st;

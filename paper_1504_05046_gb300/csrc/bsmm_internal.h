@@ -36,9 +36,10 @@ int split_max_depth(int s);
 int split_tile_n(int s);          // work-unit width (32 or 64)
 int split_stages(int s, int tn);  // smem ring depth
 size_t split_smem_bytes(int s, int tn, int stages);
+constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory of one CTA
 constexpr int kSplitDefaultCluster = 2;
 // Largest number of clusters of `cl` contraction CTAs that can be resident at once.
-int split_max_clusters(int s, int cl);
+int split_max_clusters(int s, int cl, int stages);
 
 // Device arrays owned by a plan.
 struct DevBuf {

@@ -91,7 +91,7 @@ int default_bins(const bsmm_plan_s* p) {
   if (p->opt.mode == BSMM_FP64)
     c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm(p->f64_tile));
   else
-    c = std::max(1, split_max_clusters(p->s, p->cl));
+    c = std::max(1, split_max_clusters(p->s, p->cl, p->stages));
   if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
   c = std::min<int64_t>(c, std::max<int64_t>(1, p->n_units));
   return (int)std::max<int64_t>(1, c);
@@ -395,6 +395,9 @@ bsmm_status validate_options(const bsmm_options& o) {
     return set_error("cluster must be 0, 1, 2 or 4"), BSMM_ERR_INVALID;
   if (o.fp64_tile != 0 && o.fp64_tile != 32 && o.fp64_tile != 64)
     return set_error("fp64_tile must be 0, 32 or 64"), BSMM_ERR_INVALID;
+  if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) return set_error("stages must be 0 or 2..8"), BSMM_ERR_INVALID;
+  if (o.mode != BSMM_FP64 && o.stages && split_smem_bytes(o.nslices, split_tile_n(o.nslices), o.stages) > kMaxSmemPerCta)
+    return set_error("stages: the ring does not fit the shared memory of one CTA"), BSMM_ERR_UNSUPPORTED;
   for (int r : o.reserved)
     if (r) return set_error("reserved option fields must be zero"), BSMM_ERR_INVALID;
   return BSMM_OK;
@@ -527,7 +530,7 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
     p->s = o.nslices;
     p->cl = o.cluster ? o.cluster : kSplitDefaultCluster;
     p->tn = split_tile_n(p->s);
-    p->stages = split_stages(p->s, p->tn);
+    p->stages = o.stages ? o.stages : split_stages(p->s, p->tn);
     st = plan_split(p);
   }
   if (st != BSMM_OK) {

@@ -28,9 +28,10 @@
 //                         warp 0 streams packed chunks into an S-stage shared-memory
 //                         ring with cp.async.bulk (several k panels in flight -- the
 //                         on-chip form of the paper's multiple-issue SUMMA
-//                         iterations, Sec. 3.2); warp 1 issues tcgen05.mma into
-//                         double-buffered TMEM accumulators; warps 2..9 drain TMEM,
-//                         recombine in integer arithmetic and store
+//                         iterations, Sec. 3.2); warps 1..3 share the issue of the
+//                         tcgen05.mma slice products into double-buffered TMEM
+//                         accumulators; warps 4..11 drain TMEM (zeroing it behind
+//                         them), recombine in integer arithmetic and store
 //                         C = alpha*fl(sum) + beta*C.
 // A work unit is a 128-row x tn-column block of the global C index space; the CTA
 // that owns it runs every inner block in ascending order.
@@ -49,7 +50,11 @@ namespace {
 
 constexpr int64_t kWaitNs = 4000000000LL;  // bounded waits: 4 s, then error + abort
 constexpr int kEpiThreads = kSplitEpiWarps * 32;
-constexpr int kThreads = 64 + kEpiThreads;  // producer warp + MMA warp + epilogue warps
+// MMA issue: one thread issues tcgen05.mma instructions about one per 100 cycles, whatever
+// their N, so the slice products of a step are spread over kMmaWarps issuing warps.
+constexpr int kMmaWarps = 3;
+constexpr int kEpiWarp0 = 1 + kMmaWarps;                    // first epilogue warp
+constexpr int kThreads = 32 * kEpiWarp0 + kEpiThreads;     // producer + MMA warps + epilogue warps
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAChunk = kSplitBM * kSplitKC * 2;  // bytes of one slice of a 128x32 A chunk
 
@@ -191,7 +196,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_zero4(uint32_t taddr) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%1,%1,%1};" ::"r"(taddr), "r"(0u) : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(0u) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups of
 // 64-byte rows (stride between 8-row groups = 512 bytes).
@@ -624,6 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   constexpr int STAGE = A_STAGE + B_STAGE;
   constexpr int BUF_COLS = S * TN;              // TMEM columns per accumulator buffer
   constexpr uint16_t MASK = (uint16_t)((1u << CL) - 1);
+  constexpr int W = S < kMmaWarps ? S : kMmaWarps;  // MMA warps with work: warp 1+w issues slices p = w+1, w+1+W, ...
   static_assert(A_SLICE % 16 == 0, "bulk copies move multiples of 16 bytes");
 
   extern __shared__ uint8_t smem_raw[];
@@ -634,8 +652,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   uint64_t* empty = bars + stages;
   uint64_t* tfull = bars + 2 * stages;
   uint64_t* tempty = tfull + 2;
-  uint64_t* drain = tempty + 2;
-  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  uint64_t* drain = tempty + 2;  // one per MMA warp
+  uint32_t* tmem_slot = (uint32_t*)(drain + kMmaWarps);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -646,13 +664,13 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   if (threadIdx.x == 0) {
     for (int st = 0; st < stages; st++) {
       mbar_init(&full[st], 1);
-      mbar_init(&empty[st], CL);  // released by the MMA issuer of every CTA of the cluster
+      mbar_init(&empty[st], CL * W);  // released by every MMA warp of every CTA of the cluster
     }
     for (int b = 0; b < 2; b++) {
-      mbar_init(&tfull[b], 1);
+      mbar_init(&tfull[b], W);
       mbar_init(&tempty[b], kSplitEpiWarps);
     }
-    mbar_init(drain, 1);
+    for (int w = 0; w < kMmaWarps; w++) mbar_init(&drain[w], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -716,9 +734,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         }
       }
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp <= W) {
+    // ------------------------------------------------------------ MMA issuers
+    // Every MMA warp walks the same chunks and issues its share of each step's slice
+    // products; all of them accumulate (the epilogue zeroes a buffer once drained), and
+    // the order in which the tensor core applies them does not matter: every partial sum
+    // is an integer below 2^24, exact in FP32.
     if (lane == 0) {
+      const int mw = warp - 1;
       int stage = 0;
       uint32_t phase = 0;
       uint32_t tcount = 0;
@@ -729,9 +752,17 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       // start-address field (which cannot carry: shared addresses are below 256 KB).
       const uint64_t adesc0 = sdesc_sw64(smem_u32(smem));
       const uint64_t bdesc0 = sdesc_sw64(smem_u32(smem) + A_STAGE);
-      uint32_t idp[S];
+      constexpr int NP = (S + W - 1) / W;  // slices per warp (upper bound)
+      uint32_t idp[NP];
+      uint32_t dcol[NP];
+      uint64_t aoff[NP];
 #pragma unroll
-      for (int p = 1; p <= S; p++) idp[p - 1] = idesc_f16(kSplitBM, (S + 1 - p) * TN, a.fp16 != 0);
+      for (int j = 0; j < NP; j++) {
+        const int p = mw + 1 + j * W;
+        idp[j] = idesc_f16(kSplitBM, (S + 1 - (p <= S ? p : S)) * TN, a.fp16 != 0);
+        dcol[j] = (uint32_t)((p - 1) * TN);
+        aoff[j] = (uint64_t)((p - 1) * (kAChunk >> 4));
+      }
       for (int idx = ubeg; idx < uend && ok; idx++) {
         int g = a.sched_units[idx];
         const SplitArgs& P = a.prods ? a.prods[a.unit_prod[g]] : a;
@@ -746,7 +777,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           const bool ownb = it.own_b(kt);
           const uint32_t buf = tcount & 1, use = tcount >> 1;
           if (ownb) {
-            if (!wait1(&tempty[buf], (use & 1) ^ 1, abort_flag, a.err)) {
+            // the buffer was drained and zeroed by the epilogue (use 0: zeroed at start)
+            if (!wait1(&tempty[buf], use & 1, abort_flag, a.err)) {
               ok = false;
               break;
             }
@@ -762,14 +794,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
             if (ownb) {
               const uint64_t soff = (uint64_t)((stage * STAGE) >> 4);
               const uint64_t ad = adesc0 + soff, bd = bdesc0 + soff;
-              const uint32_t first = (kc == 0) ? 0u : 1u;  // 0: this k block's first MMA overwrites
+              const bool two = q - kc * kSplitKC > 16;  // second 16-deep step of the 32-deep chunk
 #pragma unroll
-              for (int p = 1; p <= S; p++)
-                umma_f16(dbase + (p - 1) * TN, ad + (p - 1) * (kAChunk >> 4), bd, idp[p - 1], p > 1 ? 1u : first);
-              if (q - kc * kSplitKC > 16) {  // second 16-deep step of the 32-deep chunk
-#pragma unroll
-                for (int p = 1; p <= S; p++)
-                  umma_f16(dbase + (p - 1) * TN, ad + (p - 1) * (kAChunk >> 4) + 2, bd + 2, idp[p - 1], 1u);
+              for (int j = 0; j < NP; j++) {
+                if (mw + 1 + j * W > S) break;
+                umma_f16(dbase + dcol[j], ad + aoff[j], bd, idp[j], 1u);
+                if (two) umma_f16(dbase + dcol[j], ad + aoff[j] + 2, bd + 2, idp[j], 1u);
               }
             }
             // release the stage in every CTA of the cluster once these MMAs finished
@@ -792,9 +822,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       }
       // drain: every MMA this thread issued has completed before TMEM is released
       if (any) {
-        umma_commit(drain);
+        umma_commit(&drain[mw]);
         const int64_t t0 = gtimer();
-        while (!mbar_try_wait(drain, 0)) {
+        while (!mbar_try_wait(&drain[mw], 0)) {
           if (gtimer() - t0 > kWaitNs) {
             atomicOr(a.err, kErrTimeout);
             break;
@@ -802,12 +832,27 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         }
       }
     }
-  } else {
+  } else if (warp >= kEpiWarp0) {
     // ------------------------------------------------------------ epilogue warps
-    const int ew = warp - 2;           // 0..7
+    const int ew = warp - kEpiWarp0;   // 0..7
     const int quad = warp & 3;         // TMEM lane quadrant this warp may access
     const int half = ew >> 2;          // which half of the tn columns
     const int row = quad * 32 + lane;  // row inside the unit
+    const uint32_t tq = tmem_base + ((uint32_t)(quad * 32) << 16) + half * TH;  // this warp's lanes and columns
+    // both accumulator buffers start at zero; the MMA warps only ever accumulate
+#pragma unroll 1
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+      for (int d = 0; d < S; d++)
+#pragma unroll
+        for (int cc = 0; cc < TH / 8; cc++) tmem_zero8(tq + b * BUF_COLS + d * TN + cc * 8);
+    tmem_st_wait();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&tempty[0]);
+      mbar_arrive(&tempty[1]);
+    }
     uint32_t tcount = 0;
     bool ok = true;
     for (int idx = ubeg; idx < uend && ok; idx++) {
@@ -830,20 +875,20 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       // (k blocks where this column block has no B tile add nothing and are skipped)
       int kt = it.next_own();
       int shr_n = 0;
-      int16_t rb_n[TH];
+      uint4 cx_n[TH / 8];  // column offsets of the next k block, two int16 per word
       auto load_exps = [&](int k) {
         shr_n = kSplitGuard + (row_ok ? (int)P.rowexp[(int64_t)k * P.Mtot + m] : 0);
         const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)k * P.colexp_ld + n0);
 #pragma unroll
-        for (int w = 0; w < TH / 8; w++) *reinterpret_cast<uint4*>(&rb_n[w * 8]) = __ldg(src + w);
+        for (int w = 0; w < TH / 8; w++) cx_n[w] = __ldg(src + w);
       };
       if (kt >= 0) load_exps(kt);
       while (kt >= 0) {
         // binary position of this k block's integer in the accumulator
         const int shr = shr_n;
-        int16_t rb[TH];
+        uint4 cx[TH / 8];
 #pragma unroll
-        for (int c = 0; c < TH; c++) rb[c] = rb_n[c];
+        for (int w = 0; w < TH / 8; w++) cx[w] = cx_n[w];
         const int kt_next = it.next_own();
         if (kt_next >= 0) load_exps(kt_next);
         kt = kt_next;
@@ -853,15 +898,30 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + buf * BUF_COLS + half * TH;
+        const uint32_t taddr = tq + buf * BUF_COLS;
+        // columns in batches of CW (4 for s >= 5 keeps the TMEM values and the 128-bit
+        // sums within the register budget)
+        constexpr int CW = S >= 5 ? 4 : 8;
 #pragma unroll
-        for (int cc = 0; cc < TH / 8; cc++) {
-          uint32_t v[S][8];
+        for (int cc = 0; cc < TH / CW; cc++) {
+          uint32_t v[S][CW];
 #pragma unroll
-          for (int d = 0; d < S; d++) tmem_ld8(taddr + d * TN + cc * 8, v[d]);
+          for (int d = 0; d < S; d++) {
+            if constexpr (CW == 8)
+              tmem_ld8(taddr + d * TN + cc * CW, v[d]);
+            else
+              tmem_ld4(taddr + d * TN + cc * CW, v[d]);
+          }
           tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < 8; c++) {
+          for (int d = 0; d < S; d++) {  // ready for the buffer's next use
+            if constexpr (CW == 8)
+              tmem_zero8(taddr + d * TN + cc * CW);
+            else
+              tmem_zero4(taddr + d * TN + cc * CW);
+          }
+#pragma unroll
+          for (int c = 0; c < CW; c++) {
             // T = sum_d S_d 2^(7(S+1-d)), exact: the tensor core's FP32 sums are integers
             long long T = 0;
 #pragma unroll
@@ -870,9 +930,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
               asm("cvt.rni.s32.f32 %0, %1;" : "=r"(iv) : "f"(__uint_as_float(v[d][c])));
               T += (long long)iv * (1ll << (kSplitBeta * (S - 1 - d)));
             }
-            acc_add(acc[cc * 8 + c], T, shr + rb[cc * 8 + c]);
+            const int col = cc * CW + c;  // column within this thread's TH
+            const uint4& w4 = cx[col >> 3];
+            const int e = col & 7;
+            const uint32_t wd = e < 2 ? w4.x : e < 4 ? w4.y : e < 6 ? w4.z : w4.w;
+            acc_add(acc[col], T, shr + (int)(int16_t)(wd >> (16 * (e & 1))));
           }
         }
+        tmem_st_wait();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -950,8 +1015,8 @@ cudaError_t launch_mma_cl(const SplitArgs& a, int clusters, cudaStream_t st) {
 }
 
 template <int S, int CL>
-int max_clusters_for() {
-  const size_t smem = split_smem_bytes(S, 32, split_stages(S, 32));
+int max_clusters_for(int stages) {
+  const size_t smem = split_smem_bytes(S, 32, stages);
   if (cudaFuncSetAttribute(split_mma_kernel<S, 32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -972,11 +1037,11 @@ int max_clusters_for() {
 }
 
 template <int S>
-int max_clusters_s(int cl) {
+int max_clusters_s(int cl, int stages) {
   switch (cl) {
-    case 1: return max_clusters_for<S, 1>();
-    case 2: return max_clusters_for<S, 2>();
-    case 4: return max_clusters_for<S, 4>();
+    case 1: return max_clusters_for<S, 1>(stages);
+    case 2: return max_clusters_for<S, 2>(stages);
+    case 4: return max_clusters_for<S, 4>(stages);
     default: return 0;
   }
 }
@@ -1024,14 +1089,14 @@ cudaError_t launch_split_mma(const SplitArgs& a, int ctas, cudaStream_t st) {
   return e;
 }
 
-int split_max_clusters(int s, int cl) {
+int split_max_clusters(int s, int cl, int stages) {
   switch (s) {
-    case 1: return max_clusters_s<1>(cl);
-    case 2: return max_clusters_s<2>(cl);
-    case 3: return max_clusters_s<3>(cl);
-    case 4: return max_clusters_s<4>(cl);
-    case 5: return max_clusters_s<5>(cl);
-    case 6: return max_clusters_s<6>(cl);
+    case 1: return max_clusters_s<1>(cl, stages);
+    case 2: return max_clusters_s<2>(cl, stages);
+    case 3: return max_clusters_s<3>(cl, stages);
+    case 4: return max_clusters_s<4>(cl, stages);
+    case 5: return max_clusters_s<5>(cl, stages);
+    case 6: return max_clusters_s<6>(cl, stages);
     default: return 0;
   }
 }
