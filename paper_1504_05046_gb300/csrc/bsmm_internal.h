@@ -37,6 +37,8 @@ int split_tile_n(int s);          // work-unit width (32 or 64)
 int split_stages(int s, int tn);  // smem ring depth
 size_t split_smem_bytes(int s, int tn, int stages);
 constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory of one CTA
+constexpr int16_t kNonUniform = 0x7FFF;         // scale-class sentinel (offsets are <= 0)
+int split_max_depth(int s);
 constexpr int kSplitDefaultCluster = 2;
 // Largest number of clusters of `cl` contraction CTAs that can be resident at once.
 int split_max_clusters(int s, int cl, int stages);
@@ -112,6 +114,13 @@ struct SplitArgs {
   int16_t* rowexp;          // K x Mtot: e_A(i,k) - Emax_A(i) per row (0 for absent tiles)
   int16_t* colexp;          // K x colexp_ld: e_B(k,j) - Emax_B(j) per column
   int64_t colexp_ld;        // row stride of colexp (Ntot rounded up to 64)
+  // Scale classes for merging k blocks into one TMEM accumulation: urow[k*RB+rb] is the
+  // common rowexp of the present rows of row block rb at k block k, ucol[k*CB+cb] the
+  // common colexp of the present columns of column block cb (kNonUniform when they
+  // differ); null: every k block is drained on its own.
+  int16_t* urow;
+  int16_t* ucol;
+  int32_t kdepth;           // deepest exact FP32 accumulation (inner elements) for s slices
   int32_t* eAmax;           // M: largest exponent of the stored A tiles of a row block
   int32_t* eBmax;           // N
   int32_t* eA;              // M x K
@@ -199,7 +208,7 @@ struct bsmm_plan_s {
   // device memory
   bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
   bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_presBg, d_apk_off, d_bpk_off, d_apk, d_bpk;
-  bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
+  bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_urow, d_ucol, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
   bsmm::DevBuf d_err, d_timings, d_unit_cta;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;
 

@@ -75,6 +75,9 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
   a.rowexp = (int16_t*)p->d_rowexp.p;
   a.colexp = (int16_t*)p->d_colexp.p;
   a.colexp_ld = p->colexp_ld;
+  a.urow = (int16_t*)p->d_urow.p;
+  a.ucol = (int16_t*)p->d_ucol.p;
+  a.kdepth = split_max_depth(p->s);
   a.eA = (int32_t*)p->d_eA.p;
   a.eB = (int32_t*)p->d_eB.p;
   a.eAmax = (int32_t*)p->d_eAmax.p;

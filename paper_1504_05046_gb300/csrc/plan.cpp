@@ -378,6 +378,8 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   if ((st = dev_alloc(p->d_rowexp, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * Mtot))) != BSMM_OK) return st;
   p->colexp_ld = (Ntot + 63) / 64 * 64 + 64;  // padded rows: aligned 16-byte loads past the last column
   if ((st = dev_alloc(p->d_colexp, sizeof(int16_t) * ((int64_t)K * p->colexp_ld + 64))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_urow, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * p->RB))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_ucol, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * p->CB))) != BSMM_OK) return st;
   // exponents of absent tiles stay 0 (their slices are zero, so the scale is never used)
   CUDA_TRY(cudaMemset(p->d_rowexp.p, 0, p->d_rowexp.bytes));
   CUDA_TRY(cudaMemset(p->d_colexp.p, 0, p->d_colexp.bytes));
@@ -425,7 +427,7 @@ void bsmm_destroy(bsmm_plan_t p) {
   DevBuf* bufs[] = {&p->d_r, &p->d_c, &p->d_q, &p->d_ro, &p->d_co, &p->d_kptr, &p->d_klist, &p->d_cs,
                     &p->d_units, &p->d_sched_ptr, &p->d_sched_units, &p->d_row_tile, &p->d_col_tile,
                     &p->d_presA, &p->d_presB, &p->d_presBg, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
-                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
+                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_urow, &p->d_ucol, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
                     &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
   for (DevBuf* b : bufs) dev_free(*b);

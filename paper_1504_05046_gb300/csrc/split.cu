@@ -342,6 +342,44 @@ __global__ void __launch_bounds__(256) split_scale_kernel(SplitArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- kernel 1c: scale classes
+// One thread per (k block, row block) and per (k block, column block): the common
+// rowexp (colexp) of the rows (columns) whose tile is present, or kNonUniform. Two k
+// blocks whose row and column classes add up to the same value put every product of a
+// unit at the same binary position, so the contraction may accumulate them together.
+__global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nr = (int64_t)a.K * a.RB, nc = (int64_t)a.K * a.CB;
+  if (t < nr) {
+    const int k = (int)(t / a.RB), rb = (int)(t % a.RB);
+    int lo = INT_MAX, hi = INT_MIN;
+    if (a.q[k] > 0) {
+      const int64_t m1 = (int64_t)(rb + 1) * kSplitBM < a.Mtot ? (int64_t)(rb + 1) * kSplitBM : a.Mtot;
+      for (int64_t m = (int64_t)rb * kSplitBM; m < m1; m++) {
+        if (!a.am[(int64_t)a.row_tile[m] * a.K + k]) continue;
+        const int v = a.rowexp[(int64_t)k * a.Mtot + m];
+        lo = min(lo, v);
+        hi = max(hi, v);
+      }
+    }
+    a.urow[t] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
+  } else if (t < nr + nc) {
+    const int64_t u = t - nr;
+    const int k = (int)(u / a.CB), cb = (int)(u % a.CB);
+    int lo = INT_MAX, hi = INT_MIN;
+    if (a.q[k] > 0) {
+      const int64_t n1 = (int64_t)(cb + 1) * a.tn < a.Ntot ? (int64_t)(cb + 1) * a.tn : a.Ntot;
+      for (int64_t n = (int64_t)cb * a.tn; n < n1; n++) {
+        if (!a.bm[(int64_t)k * a.N + a.col_tile[n]]) continue;
+        const int v = a.colexp[(int64_t)k * a.colexp_ld + n];
+        lo = min(lo, v);
+        hi = max(hi, v);
+      }
+    }
+    a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
+  }
+}
+
 // ---------------------------------------------------------------- kernel 2: slices
 // Slice 8 consecutive inner elements (one 16-byte chunk of a swizzled row) of one
 // packed row and store the s chunks.
@@ -575,6 +613,55 @@ struct UnitIter {
   }
 };
 
+// Accumulation groups: consecutive k blocks of a CTA's own list (those where its column
+// block has a B tile) share one TMEM accumulation when each has a uniform scale class
+// for the unit, the classes add up to the same binary position, and the total inner depth
+// keeps every FP32 partial sum exact. The MMA warps and the epilogue apply the same rule
+// to the same list, so they agree on where the accumulator is drained.
+// The scale class of k block k for the unit's row block rb and column block cb: true
+// and the binary offset sig of its products when both classes are uniform.
+__device__ __forceinline__ bool scale_class(const SplitArgs& P, int k, int rb, int cb, int& sig) {
+  if (!P.urow) return false;
+  const int u = P.urow[(size_t)k * P.RB + rb], v = P.ucol[(size_t)k * P.CB + cb];
+  if (u == kNonUniform || v == kNonUniform) return false;
+  sig = u + v;
+  return true;
+}
+
+struct GroupRule {
+  bool uni;
+  int sig, depth, kdepth;
+  __device__ void start(bool uni_, int sig_, int q, int kdepth_) {
+    uni = uni_;
+    sig = sig_;
+    depth = q;
+    kdepth = kdepth_;
+  }
+  __device__ bool joins(bool uni_, int sig_, int q) {  // true: the k block joins (its depth is added)
+    if (!uni || !uni_ || sig_ != sig || depth + q > kdepth) return false;
+    depth += q;
+    return true;
+  }
+};
+
+// The values of one k block of a unit's list that the MMA warps need, loaded ahead.
+struct KAhead {
+  int k, q;
+  bool own, uni;
+  int sig;
+  __device__ void load(const SplitArgs& P, const UnitIter& it, int k_, int rb, int cb) {
+    k = k_;
+    q = 0;
+    own = false;
+    uni = false;
+    sig = 0;
+    if (k < 0) return;
+    q = P.q[k];
+    own = it.own_b(k);
+    if (own) uni = scale_class(P, k, rb, cb, sig);
+  }
+};
+
 __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
@@ -771,18 +858,35 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         const int cb = un.cb * CL + rank;
         UnitIter it;
         it.init(P, un.rb, un.cb, cb);
-        for (int kt = it.next(); kt >= 0 && ok; kt = it.next()) {
-          const int q = P.q[kt];
+        GroupRule grp;
+        bool in_group = false;
+        uint32_t buf = 0;
+        // per-k values are loaded one k block ahead, so their latency hides behind the
+        // current block's MMAs; a group is closed when the next own k block does not join
+        KAhead cur, nxt;
+        cur.load(P, it, it.next(), un.rb, cb);
+        while (cur.k >= 0 && ok) {
+          nxt.load(P, it, it.next(), un.rb, cb);
+          const int kt = cur.k;
+          const int q = cur.q;
           const int nkc = (q + kSplitKC - 1) / kSplitKC;
-          const bool ownb = it.own_b(kt);
-          const uint32_t buf = tcount & 1, use = tcount >> 1;
-          if (ownb) {
+          const bool ownb = cur.own;
+          if (ownb && !(in_group && grp.joins(cur.uni, cur.sig, cur.q))) {
+            if (in_group) {  // the previous group is complete
+              umma_commit(&tfull[buf]);
+              tcount++;
+            }
+            buf = tcount & 1;
+            const uint32_t use = tcount >> 1;
             // the buffer was drained and zeroed by the epilogue (use 0: zeroed at start)
             if (!wait1(&tempty[buf], use & 1, abort_flag, a.err)) {
               ok = false;
+              in_group = false;
               break;
             }
             tc_fence_after();
+            grp.start(cur.uni, cur.sig, cur.q, P.kdepth);
+            in_group = true;
           }
           const uint32_t dbase = tmem_base + buf * BUF_COLS;
           for (int kc = 0; kc < nkc; kc++) {
@@ -813,11 +917,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
               phase ^= 1;
             }
           }
-          if (!ok) break;
-          if (ownb) {
-            umma_commit(&tfull[buf]);
-            tcount++;
-          }
+          (void)kt;
+          cur = nxt;
+        }
+        if (in_group && ok) {  // the unit's last group
+          umma_commit(&tfull[buf]);
+          tcount++;
         }
       }
       // drain: every MMA this thread issued has completed before TMEM is released
@@ -871,27 +976,35 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
       UnitIter it;
       it.init(P, un.rb, un.cb, cb);
-      // the exponent offsets of the next k block are loaded while this one is processed
-      // (k blocks where this column block has no B tile add nothing and are skipped)
       int kt = it.next_own();
-      int shr_n = 0;
-      uint4 cx_n[TH / 8];  // column offsets of the next k block, two int16 per word
-      auto load_exps = [&](int k) {
-        shr_n = kSplitGuard + (row_ok ? (int)P.rowexp[(int64_t)k * P.Mtot + m] : 0);
-        const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)k * P.colexp_ld + n0);
-#pragma unroll
-        for (int w = 0; w < TH / 8; w++) cx_n[w] = __ldg(src + w);
-      };
-      if (kt >= 0) load_exps(kt);
       while (kt >= 0) {
-        // binary position of this k block's integer in the accumulator
-        const int shr = shr_n;
+        // the accumulation group starting at kt, and the binary position of its integers:
+        // one shift for a uniform group, per-row and per-column offsets for a lone k block
+        GroupRule grp;
+        {
+          int sg = 0;
+          const bool uni = scale_class(P, kt, un.rb, cb, sg);
+          grp.start(uni, sg, P.q[kt], P.kdepth);
+        }
+        int kn = it.next_own();
+        for (; kn >= 0; kn = it.next_own()) {
+          int sg = 0;
+          const bool uni = scale_class(P, kn, un.rb, cb, sg);
+          if (!grp.joins(uni, sg, P.q[kn])) break;
+        }
+        int shr = kSplitGuard;
         uint4 cx[TH / 8];
+        if (grp.uni) {
+          shr += grp.sig;
 #pragma unroll
-        for (int w = 0; w < TH / 8; w++) cx[w] = cx_n[w];
-        const int kt_next = it.next_own();
-        if (kt_next >= 0) load_exps(kt_next);
-        kt = kt_next;
+          for (int w = 0; w < TH / 8; w++) cx[w] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+          shr += row_ok ? (int)P.rowexp[(int64_t)kt * P.Mtot + m] : 0;
+          const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)kt * P.colexp_ld + n0);
+#pragma unroll
+          for (int w = 0; w < TH / 8; w++) cx[w] = __ldg(src + w);
+        }
+        kt = kn;
         const uint32_t buf = tcount & 1, use = tcount >> 1;
         if (!wait_warp(&tfull[buf], use & 1, abort_flag, a.err)) {
           ok = false;
@@ -1051,6 +1164,8 @@ int max_clusters_s(int cl, int stages) {
 cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k) {
   if (a.n_a_tiles + a.n_b_tiles > 0) split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
   if (a.M + a.N > 0) split_scale_kernel<<<a.M + a.N, 256, 0, st>>>(a);
+  const int64_t ncls = (int64_t)a.K * (a.RB + a.CB);
+  if (a.urow && ncls > 0) split_class_kernel<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[++*k], st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -1,9 +1,9 @@
 """GPU parity of the split-precision tensor-core path, through the C ABI.
 
 Two comparisons per case:
-  * against the split oracle (the slicing algorithm's steps in numpy): the
-    recombination is exact up to one stated rounding per k block, so the GPU must
-    agree bit for bit;
+  * against the split oracle (the slicing algorithm's steps in numpy): the tile
+    products are summed exactly and rounded once, so the GPU must agree bit for bit
+    whatever its accumulation order;
   * against the FP64 oracle, at the stated accuracy bars: 6 slices <= 1e-11 and
     3 slices <= 1e-5 relative Frobenius error.
 """
@@ -160,3 +160,44 @@ def test_schedule_independent_bits(ctas):
     n = P.bsmm_plan_query(plan)["n_units"]
     again, _, _ = check(prob, 6, ctas=ctas, costs=np.random.default_rng(ctas).uniform(1, 5, n))
     assert np.array_equal(base, again)
+
+
+def _scaled_problem(seed, r, q, c, a_scale, b_scale):
+    """Dense problem whose A tile (i,k) is scaled by 2^a_scale(i,k) and B tile (k,j) by 2^b_scale(k,j)."""
+    rng = np.random.default_rng(seed)
+    r, q, c = (np.asarray(x, np.int32) for x in (r, q, c))
+    am = np.ones((len(r), len(q)), np.uint8)
+    bm = np.ones((len(q), len(c)), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    A = rng.uniform(-1, 1, at)
+    B = rng.uniform(-1, 1, bt)
+    for i in range(len(r)):
+        for k in range(len(q)):
+            A[a_off[i, k]:a_off[i, k] + r[i] * q[k]] *= 2.0 ** a_scale(i, k)
+    for k in range(len(q)):
+        for j in range(len(c)):
+            B[b_off[k, j]:b_off[k, j] + q[k] * c[j]] *= 2.0 ** b_scale(k, j)
+    return G.Problem("scaled", r, c, q, am, bm, a_off, b_off, A, B, 1.0, 0.0)
+
+
+@pytest.mark.parametrize("case", ["same_position", "shifting_position", "row_tiles_differ", "col_tiles_differ"])
+def test_merged_accumulation_groups(case):
+    """k blocks whose products land at the same binary position share one TMEM
+    accumulation (up to the exact depth); the others are drained one by one. Every
+    variant must give the split oracle's bits."""
+    r = [100, 60, 90, 140]            # 128-row blocks straddle row tiles
+    q = [256, 256, 128, 384, 1, 511, 64, 64, 64, 40]  # group depths hitting exactly 512
+    c = [50, 20, 70]
+    if case == "same_position":       # e_A + e_B constant over k: merged
+        fa, fb = (lambda i, k: k % 3), (lambda k, j: -(k % 3))
+    elif case == "shifting_position":  # uniform classes whose sums differ: one k block per group
+        fa, fb = (lambda i, k: k % 3), (lambda k, j: 0)
+    elif case == "row_tiles_differ":   # row blocks whose tiles have different exponents
+        fa, fb = (lambda i, k: 3 * (i % 2) - k % 2), (lambda k, j: k % 2)
+    else:                              # column blocks straddling tiles of different exponents
+        fa, fb = (lambda i, k: 0), (lambda k, j: 2 * (j % 2))
+    prob = _scaled_problem(11, r, q, c, fa, fb)
+    for cl in (1, 2):
+        check(prob, 6, cluster=cl)
+    check(prob, 3)
