@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "useful TFLOP/s (nonzero-tile flops) & % of peak; split vs FP64 at <=1e-11 rel err"
 PROFILE_FILE = os.path.join(ROOT, "profiles", "split_mma_kernel_nonuniform_dense.txt")
+# exponents, scales, scale classes, slices, contraction
+SPLIT_KERNELS_PER_EXECUTE = 5
 
 
 def parse():
@@ -51,6 +53,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batch"],
+                    help="dense: the 16384 nonuniform dense product (headline); batch: 256 independent products of "
+                         "uneven size, separate launches vs one graph-replayed batch launch, before and after autotuning")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -239,6 +245,103 @@ def cpu_baseline(prob, cs, Cgpu, c_off, seconds):
                       f"{done_t:.1f} s"}, max(errs) if errs else None
 
 
+def run_batch(args, rank, world):
+    """256 independent square products (n ~ U-int[512, 8192], blocks U-int[32, 192], one
+    tile density d ~ U[0.1, 1] per product, U[-1,1] entries), 6-slice split-bfloat16:
+    the whole batch per step, as 256 separate launches, as one persistent batch launch
+    replayed from a CUDA graph with the default launch shape, and the same after the
+    library's autotuner picked the shape."""
+    import torch
+    import bsmm_gen as G
+    import paper_1504_05046_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    t_gen = time.perf_counter()
+    probs = G.make_batch(args.batch_count, args.seed + rank)
+    t_gen = time.perf_counter() - t_gen
+    s = args.slices
+    plans, items = [], []
+    F = 0.0
+    for p in probs:
+        pl = P.bsmm_plan(p.row_sizes, p.col_sizes, p.inner_sizes, p.a_mask, p.b_mask, mode=P.BSMM_SPLIT_BF16,
+                         nslices=s)
+        q = P.bsmm_plan_query(pl)
+        F += q["useful_flops"]
+        off, tot = G.layout_arena(q["c_mask"], p.row_sizes, p.col_sizes)
+        d = lambda x: torch.from_numpy(x if x.size else np.zeros(2, x.dtype)).to(dev)
+        items.append(dict(A=d(p.A), B=d(p.B), ao=d(p.a_off), bo=d(p.b_off), co=d(off),
+                          C=torch.zeros(max(tot, 1), dtype=torch.float64, device=dev)))
+        plans.append(pl)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def separate():
+        for pl, it in zip(plans, items):
+            P.bsmm_execute(pl, 1.0, it["A"], it["ao"], it["B"], it["bo"], 0.0, it["C"], it["co"])
+
+    batch = P.bsmm_batch_create(plans)
+    P.bsmm_batch_set_args(batch, [1.0] * len(plans), [it["A"] for it in items], [it["ao"] for it in items],
+                          [it["B"] for it in items], [it["bo"] for it in items], [0.0] * len(plans),
+                          [it["C"] for it in items], [it["co"] for it in items])
+
+    def capture():
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            P.bsmm_batch_execute(batch)
+        torch.cuda.synchronize()
+        return g
+
+    for _ in range(args.warmup):
+        separate()
+    torch.cuda.synchronize()
+    ms_sep = timed(separate, args.steps)
+    g = capture()
+    for _ in range(args.warmup):
+        g.replay()
+    ms_batch = timed(g.replay, args.steps)
+    default_bins = P.bsmm_batch_query(batch)["bins"]
+    t_tune = time.perf_counter()
+    chosen, tune_ms = P.bsmm_batch_autotune(batch, reps=2)
+    t_tune = time.perf_counter() - t_tune
+    g = capture()
+    for _ in range(args.warmup):
+        g.replay()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    ms_tuned = timed(g.replay, args.steps)
+    clocks = clk.stop()
+    P.bsmm_batch_status_device(batch)
+    space = P.bsmm_tune_space(P.BSMM_SPLIT_BF16, s)
+    tf = lambda ms: F / (ms * 1e-3) / 1e12
+    launches_per_step = 4 * len(plans) + 1
+    line = {"metric": METRIC, "value": tf(ms_tuned), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_tuned, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"batch of {len(plans)} products, n ~ U-int[512,8192], blocks U-int[32,192], "
+                                   f"density ~ U[0.1,1], U[-1,1] FP64", "mode": f"split_bf16 s={s}",
+                       "useful_flops_per_step": F, "seed": args.seed, "generation_s": t_gen},
+            "batch_graph_autotuned": {"value": tf(ms_tuned), "ms_per_step": ms_tuned, "chosen": chosen,
+                                      "tuning_s": t_tune,
+                                      "candidates_ms": {f"cluster={c['cluster']} stages={c['stages']}": m
+                                                        for c, m in zip(space, tune_ms)}},
+            "batch_graph_default": {"value": tf(ms_batch), "ms_per_step": ms_batch, "bins": default_bins},
+            "separate_launches": {"value": tf(ms_sep), "ms_per_step": ms_sep, "launches_per_step":
+                                  SPLIT_KERNELS_PER_EXECUTE * len(plans)},
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,6 +358,9 @@ def main():
     import paper_1504_05046_gb300 as P
 
     torch.cuda.set_device(local)
+    if args.workload == "batch":
+        run_batch(args, rank, world)
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
@@ -298,7 +404,7 @@ def main():
         P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
         ks = P.bsmm_plan_kernel_ms(plan)
         kms.append(ks)
-        launches += len(ks)
+        launches += SPLIT_KERNELS_PER_EXECUTE
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -316,7 +422,7 @@ def main():
 
     # per-kernel live times (CUDA events on the launching stream)
     kk = np.array(kms)
-    k_names = ["split_exp_kernel", "split_pack_kernel", "split_mma_kernel"]
+    k_names = ["split_exp_scale_class_kernels", "split_pack_kernel", "split_mma_kernel"]
     k_avg = {nm: float(kk[:, i].mean()) for i, nm in enumerate(k_names)}
     t_mma = k_avg["split_mma_kernel"] * 1e-3
     pk, pk_src = peaks()

@@ -178,8 +178,10 @@ bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const double* A, i
  * bsmm_batch_set_args: per-product arguments as in bsmm_execute, given as host arrays
  *   of length `count` (alpha[i], beta[i], and DEVICE pointers A[i], a_off[i], ...).
  *   Copied to the device synchronously; call again when any of them changes.
- * bsmm_batch_execute: issues the kernels of the whole batch on `stream` (per-product
- *   exponent and slicing kernels in the split modes, then one contraction launch). It
+ * bsmm_batch_execute: issues the kernels of the whole batch on `stream`. FP64: one
+ *   contraction launch. Split modes: the products are taken in waves whose slice
+ *   workspaces fit in half of L2 (a larger product is a wave of its own); each wave
+ *   issues its products' exponent and slicing kernels, then one contraction launch. It
  *   allocates, copies and synchronises nothing, so it can be captured into a CUDA
  *   graph and replayed. Products must not overlap in C.
  * bsmm_batch_query: units over the batch, summed useful flops, persistent bins (CTAs
@@ -199,6 +201,42 @@ bsmm_status bsmm_batch_query(bsmm_batch_t batch, int64_t* n_units, double* usefu
 bsmm_status bsmm_batch_set_costs(bsmm_batch_t batch, const double* costs);
 bsmm_status bsmm_batch_status_device(bsmm_batch_t batch, void* stream);
 void bsmm_batch_destroy(bsmm_batch_t batch);
+
+/*
+ * Autotuning of a batch's launch shape. The paper has no counterpart (its tile kernel
+ * is a library DGEMM); these pick, by measurement, the knobs that set the contraction's
+ * work-unit shape and pipeline depth.
+ *
+ * bsmm_tune_point: one candidate. Split modes: `cluster` CTAs per thread-block cluster
+ *   (a work unit is 128 rows x 32*cluster columns) and `stages`, the depth of the
+ *   shared-memory ring (k panels in flight). FP64 mode: `fp64_tile`, the sub-tile edge
+ *   of a work unit (32 or 64). Fields that do not apply to the mode must be 0.
+ * bsmm_tune_space: the candidate list for a mode and slice count (split: cluster
+ *   1, 2, 4 x every ring depth from 2 that fits one CTA's shared memory; FP64: 32 and
+ *   64). Writes at most `cap` points to `out` (nullable) and their total to *count.
+ * bsmm_batch_autotune: times the batch (bsmm_batch_set_args called before) under each
+ *   candidate: every product is re-planned with that candidate's options (flop-count
+ *   schedule; costs set earlier do not carry over), run once to warm up, then `reps`
+ *   times (>= 1) between CUDA events on `stream`; the median is the candidate's time.
+ *   Each run writes a scratch C of the caller's C extent, allocated here and freed on
+ *   return, so the caller's C is not touched. The batch then keeps its products
+ *   re-planned under the fastest candidate (it owns those plans; the plans given to
+ *   bsmm_batch_create are left as they were) with the arguments already set. Those
+ *   new plans share the slice workspace of the plans given to bsmm_batch_create, which
+ *   must therefore still outlive the batch and must not run while the batch runs.
+ *   chosen (nullable) receives the fastest candidate's index; ms (nullable, n entries)
+ *   the median times in milliseconds, +infinity for a candidate that does not fit.
+ *   Synchronises `stream`. Fails with BSMM_ERR_UNSUPPORTED when no candidate fits.
+ */
+typedef struct {
+  int32_t cluster;    /* split modes: 1, 2 or 4 */
+  int32_t stages;     /* split modes: 2..8 (0 = as many as fit) */
+  int32_t fp64_tile;  /* FP64 mode: 32 or 64 */
+  int32_t reserved;   /* must be zero */
+} bsmm_tune_point;
+bsmm_status bsmm_tune_space(int32_t mode, int32_t nslices, bsmm_tune_point* out, int32_t cap, int32_t* count);
+bsmm_status bsmm_batch_autotune(bsmm_batch_t batch, int32_t n, const bsmm_tune_point* candidates, int32_t reps,
+                                void* stream, int32_t* chosen, float* ms);
 
 /*
  * Learned task-cost model. The paper tolerates the load variation of nonuniform

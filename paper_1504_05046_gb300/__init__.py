@@ -38,7 +38,7 @@ EXPORTED = [
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
     "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_batch_create", "bsmm_batch_set_args",
     "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_set_costs", "bsmm_batch_status_device",
-    "bsmm_batch_destroy", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
+    "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
     "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_last_error", "bsmm_destroy",
 ]
@@ -92,6 +92,8 @@ def lib():
         L.bsmm_batch_status_device.argtypes = [P, P]
         L.bsmm_batch_destroy.argtypes = [P]
         L.bsmm_batch_destroy.restype = None
+        L.bsmm_tune_space.argtypes = [i32, i32, P, i32, P]
+        L.bsmm_batch_autotune.argtypes = [P, i32, P, i32, P, P, P]
         L.bsmm_mlp_create.argtypes = [ctypes.POINTER(P), ctypes.c_uint64]
         L.bsmm_mlp_num_params.argtypes = []
         L.bsmm_mlp_set_params.argtypes = [P, P, i64]
@@ -165,9 +167,9 @@ def bsmm_options_default() -> Options:
 class Plan:
     """Owns one bsmm_plan_t; destroyed with the object or by bsmm_destroy."""
 
-    def __init__(self, handle: int, M: int, N: int, K: int, mode: int):
+    def __init__(self, handle: int, M: int, N: int, K: int, mode: int, nslices: int = 6):
         self.handle = handle
-        self.M, self.N, self.K, self.mode = M, N, K, mode
+        self.M, self.N, self.K, self.mode, self.nslices = M, N, K, mode, nslices
 
     def __del__(self):
         try:
@@ -194,7 +196,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))
-    return Plan(h.value, len(r), len(c), len(q), mode)
+    return Plan(h.value, len(r), len(c), len(q), mode, nslices)
 
 
 def bsmm_plan_query(plan: Plan) -> dict:
@@ -324,6 +326,35 @@ def bsmm_batch_destroy(batch: Batch):
     if batch is not None and batch.handle:
         lib().bsmm_batch_destroy(batch.handle)
         batch.handle = None
+
+
+class TunePoint(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int32), ("stages", ctypes.c_int32), ("fp64_tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def bsmm_tune_space(mode: int, nslices: int = 6) -> list:
+    """The library's candidate list for a mode: dicts with cluster, stages, fp64_tile."""
+    n = ctypes.c_int32()
+    _check(lib().bsmm_tune_space(mode, nslices, None, 0, ctypes.byref(n)))
+    arr = (TunePoint * max(n.value, 1))()
+    _check(lib().bsmm_tune_space(mode, nslices, arr, n.value, ctypes.byref(n)))
+    return [{"cluster": t.cluster, "stages": t.stages, "fp64_tile": t.fp64_tile} for t in arr[:n.value]]
+
+
+def bsmm_batch_autotune(batch: Batch, candidates=None, reps: int = 3, stream=None):
+    """Time the batch under each candidate (default: the library's space for its mode)
+    and keep the fastest. Returns (chosen candidate dict, list of median ms)."""
+    if candidates is None:
+        p0 = batch.plans[0]
+        candidates = bsmm_tune_space(p0.mode, p0.nslices)
+    n = len(candidates)
+    arr = (TunePoint * n)(*[TunePoint(c.get("cluster", 0), c.get("stages", 0), c.get("fp64_tile", 0), 0)
+                            for c in candidates])
+    ms = (ctypes.c_float * n)()
+    ch = ctypes.c_int32(-1)
+    _check(lib().bsmm_batch_autotune(batch.handle, n, arr, reps, _stream(stream), ctypes.byref(ch), ms))
+    return candidates[ch.value], list(ms)
 
 
 class Mlp:

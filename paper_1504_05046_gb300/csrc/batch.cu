@@ -1,15 +1,20 @@
-// Many independent block-sparse products in one persistent launch.
+// Many independent block-sparse products in few persistent launches.
 //
 // The paper schedules the tasks of one product over a process grid (Sec. 3.2); a
-// batch is the same idea across products: the work units of every product form one
-// task set, packed longest-processing-time first onto the persistent CTAs (FP64)
-// or clusters (split modes) of a single contraction launch, so short products fill
-// the gaps left by long ones instead of each paying a launch and a tail. Each unit
-// reads its product's arguments from a device table. The per-product preparation
-// (exponents and slices, split modes only) is issued as ordinary kernels before the
-// contraction. bsmm_batch_execute issues kernels only, so a stream capture of it
-// records a CUDA graph that replays the whole batch with one graph launch.
+// batch is the same idea across products: the work units of many products form one
+// task set, packed longest-processing-time first onto the persistent CTAs (FP64) or
+// clusters (split modes) of one contraction launch, so short products fill the gaps
+// left by long ones instead of each paying a launch and a tail. Each unit reads its
+// product's arguments from a device table. In the split modes the products are cut
+// into waves whose slice workspaces fit in half of L2: a wave issues its products'
+// exponent and slicing kernels and then its contraction launch, which finds the slices
+// still in L2 (a product larger than that is a wave of its own). FP64 is one wave.
+// bsmm_batch_execute issues kernels only, so a stream capture of it records a CUDA
+// graph that replays the whole batch with one graph launch.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <limits>
 
 #include "bsmm_internal.h"
 
@@ -21,13 +26,23 @@ struct bsmm_batch_s {
   int64_t n_units = 0;
   double useful_flops = 0.0;
   std::vector<int32_t> unit_prod, unit_local;
+  std::vector<int64_t> prod_begin;  // first batch-wide unit of each product (+ total)
   std::vector<double> cost;
-  int bins = 0;
+  int bins = 0;  // persistent CTAs (FP64) or clusters (split) of a full launch
+  // Waves: consecutive products whose slice workspace fits in half of L2 run their
+  // slicing kernels and then one contraction launch, so the contraction reads slices
+  // the slicing kernels just left in L2; a product larger than that is a wave of its
+  // own. FP64 has no slice workspace: one wave. wave_prod[w] is the first product of
+  // wave w (+ count), wave_bins[w] its grid, wave_ptr[w] the start of its schedule in
+  // sched_ptr (wave_bins[w] + 1 entries, absolute positions in sched_units).
+  std::vector<int32_t> wave_prod, wave_bins;
+  std::vector<int64_t> wave_ptr;
   std::vector<int32_t> sched_ptr, sched_units;
   std::vector<Fp64Args> fargs;
   std::vector<SplitArgs> sargs;
   bool args_set = false;
   DevBuf d_prods, d_unit_prod, d_unit_local, d_sched_ptr, d_sched_units, d_err;
+  std::vector<bsmm_plan_t> owned;  // plans made by bsmm_batch_autotune, destroyed with the batch
 };
 
 namespace {
@@ -57,7 +72,21 @@ bsmm_status put(DevBuf& b, const std::vector<T>& v) {
 }
 
 bsmm_status repack(bsmm_batch_s* b) {
-  lpt_pack(b->cost, b->bins, false, b->sched_ptr, b->sched_units);
+  b->sched_ptr.clear();
+  b->sched_units.clear();
+  b->wave_ptr.clear();
+  for (size_t w = 0; w + 1 < b->wave_prod.size(); w++) {
+    const int64_t u0 = b->prod_begin[b->wave_prod[w]], u1 = b->prod_begin[b->wave_prod[w + 1]];
+    std::vector<double> cost(b->cost.begin() + u0, b->cost.begin() + u1);
+    std::vector<int64_t> seg;
+    for (int32_t p = b->wave_prod[w]; p <= b->wave_prod[w + 1]; p++) seg.push_back(b->prod_begin[p] - u0);
+    std::vector<int32_t> ptr, units;
+    lpt_pack(cost, b->wave_bins[w], false, ptr, units, &seg);
+    b->wave_ptr.push_back((int64_t)b->sched_ptr.size());
+    const int32_t base = (int32_t)b->sched_units.size();
+    for (int32_t x : ptr) b->sched_ptr.push_back(base + x);
+    for (int32_t u : units) b->sched_units.push_back((int32_t)(u0 + u));
+  }
   bsmm_status st;
   if ((st = put(b->d_sched_ptr, b->sched_ptr)) != BSMM_OK) return st;
   return put(b->d_sched_units, b->sched_units);
@@ -66,7 +95,60 @@ bsmm_status repack(bsmm_batch_s* b) {
 void free_batch(bsmm_batch_s* b) {
   for (DevBuf* d : {&b->d_prods, &b->d_unit_prod, &b->d_unit_local, &b->d_sched_ptr, &b->d_sched_units, &b->d_err})
     if (d->p) cudaFree(d->p);
+  for (bsmm_plan_t p : b->owned) bsmm_destroy(p);
   delete b;
+}
+
+// The caller's per-product arguments, as stored by bsmm_batch_set_args.
+struct BatchArgs {
+  std::vector<double> alpha, beta;
+  std::vector<const double*> A, B;
+  std::vector<const int64_t*> ao, bo, co;
+  std::vector<double*> C;
+  explicit BatchArgs(const bsmm_batch_s* b) {
+    const size_t n = b->plans.size();
+    alpha.resize(n), beta.resize(n), A.resize(n), B.resize(n), ao.resize(n), bo.resize(n), co.resize(n), C.resize(n);
+    for (size_t i = 0; i < n; i++) {
+      if (b->mode == BSMM_FP64) {
+        const Fp64Args& a = b->fargs[i];
+        alpha[i] = a.alpha, beta[i] = a.beta, A[i] = a.A, B[i] = a.B, ao[i] = a.a_off, bo[i] = a.b_off;
+        co[i] = a.c_off, C[i] = a.C;
+      } else {
+        const SplitArgs& a = b->sargs[i];
+        alpha[i] = a.alpha, beta[i] = a.beta, A[i] = a.A, B[i] = a.B, ao[i] = a.a_off, bo[i] = a.b_off;
+        co[i] = a.c_off, C[i] = a.C;
+      }
+    }
+  }
+  bsmm_status set(bsmm_batch_t b, const std::vector<double*>& Cs) const;
+};
+
+// Plans of every product of `src` under options `o` (sharing the slice workspace of the
+// batch's own plans); on failure none is left.
+bsmm_status replan(const bsmm_batch_s* src, const bsmm_tune_point& t, std::vector<bsmm_plan_t>& out) {
+  out.clear();
+  for (const bsmm_plan_s* p : src->plans) {
+    bsmm_options o = p->opt;
+    o.profile = 0;
+    o.record_timings = 0;
+    if (o.schedule == BSMM_SCHED_COSTS) o.schedule = BSMM_SCHED_FLOPS;
+    if (o.mode == BSMM_FP64) {
+      o.fp64_tile = t.fp64_tile;
+    } else {
+      o.cluster = t.cluster;
+      o.stages = t.stages;
+    }
+    bsmm_plan_t np = nullptr;
+    const bsmm_status st = plan_build(&np, p->M, p->r.data(), p->N, p->c.data(), p->K, p->q.data(), p->am.data(),
+                                      p->bm.data(), p->cs.data(), &o, p);
+    if (st != BSMM_OK) {
+      for (bsmm_plan_t q : out) bsmm_destroy(q);
+      out.clear();
+      return st;
+    }
+    out.push_back(np);
+  }
+  return BSMM_OK;
 }
 
 }  // namespace
@@ -98,6 +180,7 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   b->stages = p0->stages;
   for (int32_t i = 0; i < count; i++) {
     const bsmm_plan_s* p = plans[i];
+    b->prod_begin.push_back((int64_t)b->unit_prod.size());
     for (int64_t u = 0; u < p->n_units; u++) {
       b->unit_prod.push_back(i);
       b->unit_local.push_back((int32_t)u);
@@ -106,6 +189,7 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
     b->useful_flops += p->useful_flops;
   }
   b->n_units = (int64_t)b->unit_prod.size();
+  b->prod_begin.push_back(b->n_units);
   // one product's default bin count describes the machine (CTAs or clusters)
   bsmm_plan_s tmp_view = bsmm_plan_s();
   tmp_view.opt = p0->opt;
@@ -116,6 +200,25 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   tmp_view.stages = p0->stages;
   tmp_view.n_units = std::max<int64_t>(1, b->n_units);
   b->bins = default_bins(&tmp_view);
+  // waves (see bsmm_batch_s)
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p0->device) != cudaSuccess || l2 <= 0) l2 = 64 << 20;
+  const int64_t budget = (int64_t)l2 / 2;
+  b->wave_prod.push_back(0);
+  int64_t used = 0;
+  for (int32_t i = 0; i < count; i++) {
+    const int64_t ws = b->mode == BSMM_FP64 ? 0 : plans[i]->apk_bytes + plans[i]->bpk_bytes;
+    if (i > b->wave_prod.back() && used + ws > budget) {
+      b->wave_prod.push_back(i);
+      used = 0;
+    }
+    used += ws;
+  }
+  b->wave_prod.push_back(count);
+  for (size_t w = 0; w + 1 < b->wave_prod.size(); w++) {
+    const int64_t nu = b->prod_begin[b->wave_prod[w + 1]] - b->prod_begin[b->wave_prod[w]];
+    b->wave_bins.push_back((int32_t)std::max<int64_t>(1, std::min<int64_t>(b->bins, nu)));
+  }
   bsmm_status st;
   if ((st = put(b->d_unit_prod, b->unit_prod)) != BSMM_OK || (st = put(b->d_unit_local, b->unit_local)) != BSMM_OK ||
       (st = repack(b)) != BSMM_OK || (st = dalloc(b->d_err, sizeof(int32_t))) != BSMM_OK) {
@@ -164,30 +267,34 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
   if (!b->args_set) return set_error("bsmm_batch_set_args has not been called"), BSMM_ERR_INVALID;
   if (b->n_units == 0) return BSMM_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e;
-  if (b->mode == BSMM_FP64) {
-    Fp64Args a = b->fargs[0];
-    a.sched_ptr = (const int32_t*)b->d_sched_ptr.p;
-    a.sched_units = (const int32_t*)b->d_sched_units.p;
-    a.prods = (const Fp64Args*)b->d_prods.p;
-    a.unit_prod = (const int32_t*)b->d_unit_prod.p;
-    a.unit_local = (const int32_t*)b->d_unit_local.p;
-    a.err = (int32_t*)b->d_err.p;
-    e = launch_fp64(a, b->bins, st, nullptr, nullptr);
-  } else {
-    for (const SplitArgs& pa : b->sargs) {
-      int k = 0;
-      e = launch_split_prep(pa, st, nullptr, &k);
-      if (e != cudaSuccess) return set_error(std::string("batch prep: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  for (size_t w = 0; w + 1 < b->wave_prod.size() && e == cudaSuccess; w++) {
+    if (b->prod_begin[b->wave_prod[w + 1]] == b->prod_begin[b->wave_prod[w]]) continue;  // no units
+    const int32_t* sp = (const int32_t*)b->d_sched_ptr.p + b->wave_ptr[w];
+    if (b->mode == BSMM_FP64) {
+      Fp64Args a = b->fargs[0];
+      a.sched_ptr = sp;
+      a.sched_units = (const int32_t*)b->d_sched_units.p;
+      a.prods = (const Fp64Args*)b->d_prods.p;
+      a.unit_prod = (const int32_t*)b->d_unit_prod.p;
+      a.unit_local = (const int32_t*)b->d_unit_local.p;
+      a.err = (int32_t*)b->d_err.p;
+      e = launch_fp64(a, b->wave_bins[w], st, nullptr, nullptr);
+    } else {
+      for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1] && e == cudaSuccess; i++) {
+        int k = 0;
+        e = launch_split_prep(b->sargs[i], st, nullptr, &k);
+      }
+      if (e != cudaSuccess) break;
+      SplitArgs a = b->sargs[0];
+      a.sched_ptr = sp;
+      a.sched_units = (const int32_t*)b->d_sched_units.p;
+      a.prods = (const SplitArgs*)b->d_prods.p;
+      a.unit_prod = (const int32_t*)b->d_unit_prod.p;
+      a.unit_local = (const int32_t*)b->d_unit_local.p;
+      a.err = (int32_t*)b->d_err.p;
+      e = launch_split_mma(a, b->wave_bins[w], st);
     }
-    SplitArgs a = b->sargs[0];
-    a.sched_ptr = (const int32_t*)b->d_sched_ptr.p;
-    a.sched_units = (const int32_t*)b->d_sched_units.p;
-    a.prods = (const SplitArgs*)b->d_prods.p;
-    a.unit_prod = (const int32_t*)b->d_unit_prod.p;
-    a.unit_local = (const int32_t*)b->d_unit_local.p;
-    a.err = (int32_t*)b->d_err.p;
-    e = launch_split_mma(a, b->bins, st);
   }
   if (e != cudaSuccess) return set_error(std::string("batch launch: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   return BSMM_OK;
@@ -207,6 +314,142 @@ bsmm_status bsmm_batch_set_costs(bsmm_batch_t b, const double* costs) {
     if (!(costs[u] > 0.0)) return set_error("costs must be > 0"), BSMM_ERR_INVALID;
   b->cost.assign(costs, costs + b->n_units);
   return repack(b);
+}
+
+bsmm_status BatchArgs::set(bsmm_batch_t b, const std::vector<double*>& Cs) const {
+  return bsmm_batch_set_args(b, alpha.data(), A.data(), ao.data(), B.data(), bo.data(), beta.data(), Cs.data(),
+                             co.data());
+}
+
+bsmm_status bsmm_tune_space(int32_t mode, int32_t nslices, bsmm_tune_point* out, int32_t cap, int32_t* count) {
+  if (!count) return set_error("count is NULL"), BSMM_ERR_INVALID;
+  std::vector<bsmm_tune_point> v;
+  if (mode == BSMM_FP64) {
+    v.push_back({0, 0, 32, 0});
+    v.push_back({0, 0, 64, 0});
+  } else if (mode == BSMM_SPLIT_BF16 || mode == BSMM_SPLIT_FP16) {
+    if (nslices < 1 || nslices > kSplitMaxS) return set_error("nslices must be in 1..6"), BSMM_ERR_INVALID;
+    for (int cl : {1, 2, 4})
+      for (int st = 2; st <= 8; st++)
+        if (split_smem_bytes(nslices, split_tile_n(nslices), st) <= kMaxSmemPerCta) v.push_back({cl, st, 0, 0});
+  } else {
+    return set_error("unknown mode"), BSMM_ERR_INVALID;
+  }
+  *count = (int32_t)v.size();
+  if (out)
+    for (int32_t i = 0; i < std::min<int32_t>(cap, *count); i++) out[i] = v[i];
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_batch_autotune(bsmm_batch_t b, int32_t n, const bsmm_tune_point* cand, int32_t reps, void* stream,
+                                int32_t* chosen, float* ms) {
+  if (!b || !cand || n <= 0 || reps < 1) return set_error("batch, candidates and reps >= 1 are required"), BSMM_ERR_INVALID;
+  if (!b->args_set) return set_error("bsmm_batch_set_args has not been called"), BSMM_ERR_INVALID;
+  for (int32_t c = 0; c < n; c++) {
+    const bsmm_tune_point& t = cand[c];
+    const bool ok = b->mode == BSMM_FP64 ? (t.cluster == 0 && t.stages == 0 && (t.fp64_tile == 32 || t.fp64_tile == 64))
+                                         : (t.fp64_tile == 0 && (t.cluster == 1 || t.cluster == 2 || t.cluster == 4) &&
+                                            (t.stages == 0 || (t.stages >= 2 && t.stages <= 8)));
+    if (!ok || t.reserved) return set_error("candidate " + std::to_string(c) + " does not fit the batch's mode"), BSMM_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const BatchArgs args(b);
+  const size_t count = b->plans.size();
+  // scratch C per product, as long as the caller's C extent
+  std::vector<DevBuf> scratch(count);
+  std::vector<double*> scratch_c(count);
+  bsmm_status res = BSMM_OK;
+  auto cleanup_scratch = [&]() {
+    for (DevBuf& d : scratch)
+      if (d.p) cudaFree(d.p);
+  };
+  for (size_t i = 0; i < count && res == BSMM_OK; i++) {
+    const bsmm_plan_s* p = b->plans[i];
+    std::vector<int64_t> off((size_t)p->M * p->N);
+    if (!off.empty() && cudaMemcpy(off.data(), args.co[i], sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      res = (set_error("reading c_off failed"), BSMM_ERR_CUDA);
+      break;
+    }
+    int64_t extent = 1;
+    for (int ii = 0; ii < p->M; ii++)
+      for (int jj = 0; jj < p->N; jj++) {
+        const size_t t = (size_t)ii * p->N + jj;
+        if (p->cs[t] && off[t] >= 0) extent = std::max<int64_t>(extent, off[t] + (int64_t)p->r[ii] * p->c[jj]);
+      }
+    if ((res = dalloc(scratch[i], sizeof(double) * extent)) != BSMM_OK) break;
+    if (cudaMemset(scratch[i].p, 0, sizeof(double) * extent) != cudaSuccess) res = (set_error("cudaMemset failed"), BSMM_ERR_CUDA);
+    scratch_c[i] = (double*)scratch[i].p;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (res == BSMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    res = (set_error("cudaEventCreate failed"), BSMM_ERR_CUDA);
+  int best = -1;
+  float best_ms = std::numeric_limits<float>::infinity();
+  for (int32_t c = 0; c < n && res == BSMM_OK; c++) {
+    float med = std::numeric_limits<float>::infinity();
+    std::vector<bsmm_plan_t> plans;
+    bsmm_status s = replan(b, cand[c], plans);
+    if (s == BSMM_ERR_UNSUPPORTED) {  // this candidate does not fit (e.g. the ring in shared memory)
+      if (ms) ms[c] = med;
+      continue;
+    }
+    if (s != BSMM_OK) {
+      res = s;
+      break;
+    }
+    bsmm_batch_t tb = nullptr;
+    s = bsmm_batch_create(&tb, (int32_t)count, plans.data());
+    if (s == BSMM_OK) s = args.set(tb, scratch_c);
+    if (s == BSMM_OK) s = bsmm_batch_execute(tb, stream);  // warm-up
+    std::vector<float> t;
+    for (int r = 0; r < reps && s == BSMM_OK; r++) {
+      cudaEventRecord(e0, st);
+      s = bsmm_batch_execute(tb, stream);
+      cudaEventRecord(e1, st);
+      float x = 0.0f;
+      if (s == BSMM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
+        s = (set_error("timing the candidate failed"), BSMM_ERR_CUDA);
+      t.push_back(x);
+    }
+    if (s == BSMM_OK) s = bsmm_batch_status_device(tb, stream);
+    if (tb) bsmm_batch_destroy(tb);
+    for (bsmm_plan_t q : plans) bsmm_destroy(q);
+    if (s != BSMM_OK) {
+      res = s;
+      break;
+    }
+    std::sort(t.begin(), t.end());
+    med = t[t.size() / 2];
+    if (ms) ms[c] = med;
+    if (med < best_ms) {
+      best_ms = med;
+      best = c;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cleanup_scratch();
+  if (res != BSMM_OK) return res;
+  if (best < 0) return set_error("no candidate fits"), BSMM_ERR_UNSUPPORTED;
+  // the batch takes its products re-planned under the fastest candidate
+  std::vector<bsmm_plan_t> plans;
+  bsmm_status s = replan(b, cand[best], plans);
+  bsmm_batch_t nb = nullptr;
+  if (s == BSMM_OK) s = bsmm_batch_create(&nb, (int32_t)count, plans.data());
+  if (s == BSMM_OK) s = args.set(nb, args.C);
+  if (s != BSMM_OK) {
+    if (nb) bsmm_batch_destroy(nb);
+    for (bsmm_plan_t q : plans) bsmm_destroy(q);
+    return s;
+  }
+  nb->owned = plans;
+  std::swap(*b, *nb);
+  // nb now holds the batch's previous tables (and the plans of an earlier autotune),
+  // which are released; the plans given to bsmm_batch_create keep owning the slice
+  // workspace the new plans share
+  free_batch(nb);
+  if (chosen) *chosen = best;
+  return BSMM_OK;
 }
 
 bsmm_status bsmm_batch_status_device(bsmm_batch_t b, void* stream) {

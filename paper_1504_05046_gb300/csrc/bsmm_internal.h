@@ -47,6 +47,7 @@ int split_max_clusters(int s, int cl, int stages);
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool borrowed = false;  // memory of another plan: not freed with this one
 };
 
 struct Fp64Unit {  // one C sub-tile of one C tile
@@ -164,7 +165,7 @@ cudaError_t launch_split_mma(const SplitArgs& a, int clusters, cudaStream_t st);
 // Longest-processing-time packing of n units with `cost` onto `bins` persistent CTAs
 // (or clusters); natural = round robin in unit order. CSR output.
 void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vector<int32_t>& ptr,
-              std::vector<int32_t>& units);
+              std::vector<int32_t>& units, const std::vector<int64_t>* segments = nullptr);
 // Kernel arguments of one product (device pointers from the caller).
 void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
@@ -174,6 +175,13 @@ int default_bins(const bsmm_plan_s* p);
 int fp64_ctas_per_sm(int tile);
 
 void set_error(const std::string& msg);
+
+// bsmm_plan with an optional donor: a split plan of the same structure and slice count
+// whose slice workspace the new plan shares instead of allocating its own (the packed
+// layout does not depend on the cluster size or the ring depth).
+bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N, const int32_t* col_sizes,
+                       int32_t K, const int32_t* inner_sizes, const uint8_t* a_mask, const uint8_t* b_mask,
+                       const uint8_t* c_mask, const bsmm_options* opt, const bsmm_plan_s* donor);
 
 }  // namespace bsmm
 
@@ -215,6 +223,9 @@ struct bsmm_plan_s {
   // per-kernel profiling events (profile option)
   cudaEvent_t ev[bsmm::kMaxEvents] = {};
   int ev_count = 0;
+
+  // a plan whose slice workspace (d_apk, d_bpk) this one shares, or null
+  const bsmm_plan_s* donor = nullptr;
 
   // host-buffer execute staging (grown on demand)
   bsmm::DevBuf h_A, h_B, h_C, h_aoff, h_boff, h_coff;

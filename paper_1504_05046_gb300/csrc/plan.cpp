@@ -55,23 +55,30 @@ size_t split_smem_bytes(int s, int tn, int stages) {
 // the planner's raster order keeps the units that run at the same time close in the
 // index space, so their A and B panels are shared through L2.
 void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vector<int32_t>& ptr,
-              std::vector<int32_t>& units) {
+              std::vector<int32_t>& units, const std::vector<int64_t>* segments) {
   const int64_t n = (int64_t)cost.size();
   std::vector<std::vector<int32_t>> lists(bins);
   if (natural) {
     for (int64_t u = 0; u < n; u++) lists[u % bins].push_back((int32_t)u);
   } else {
-    std::vector<int64_t> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    // segments (the products of a batch) are packed one after the other, the bins
+    // carrying their loads over, so every bin runs its share of segment 0, then of
+    // segment 1, ...: the bins move through the segments together and the panels they
+    // read at any time belong to one or two products (shared in L2)
+    std::vector<int64_t> seg = segments ? *segments : std::vector<int64_t>{0, n};
     using E = std::pair<double, int>;  // (load, bin), smallest first
     std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
     for (int t = 0; t < bins; t++) heap.push({0.0, t});
-    for (int64_t u : order) {
-      E e = heap.top();
-      heap.pop();
-      lists[e.second].push_back((int32_t)u);
-      heap.push({e.first + cost[u], e.second});
+    for (size_t g = 0; g + 1 < seg.size(); g++) {
+      std::vector<int64_t> order(seg[g + 1] - seg[g]);
+      std::iota(order.begin(), order.end(), seg[g]);
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+      for (int64_t u : order) {
+        E e = heap.top();
+        heap.pop();
+        lists[e.second].push_back((int32_t)u);
+        heap.push({e.first + cost[u], e.second});
+      }
     }
     for (auto& l : lists) std::sort(l.begin(), l.end());
   }
@@ -137,9 +144,10 @@ bsmm_status upload(DevBuf& b, const std::vector<T>& v) {
 }
 
 void dev_free(DevBuf& b) {
-  if (b.p) cudaFree(b.p);
+  if (b.p && !b.borrowed) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
+  b.borrowed = false;
 }
 
 inline int log2i_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -369,8 +377,17 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   p->n_b_tiles = (int32_t)b_tiles.size();
   p->n_a_blocks = (int32_t)a_blocks.size();
   p->n_b_blocks = (int32_t)b_blocks.size();
-  if ((st = dev_alloc(p->d_apk, (size_t)p->apk_bytes)) != BSMM_OK) return st;
-  if ((st = dev_alloc(p->d_bpk, (size_t)p->bpk_bytes)) != BSMM_OK) return st;
+  const bsmm_plan_s* d = p->donor;
+  if (d && d->opt.mode != BSMM_FP64 && d->s == p->s && d->apk_bytes == p->apk_bytes && d->bpk_bytes == p->bpk_bytes &&
+      d->d_apk.p && d->d_bpk.p) {
+    p->d_apk = d->d_apk;
+    p->d_bpk = d->d_bpk;
+    p->d_apk.borrowed = p->d_bpk.borrowed = true;
+  } else {
+    p->donor = nullptr;
+    if ((st = dev_alloc(p->d_apk, (size_t)p->apk_bytes)) != BSMM_OK) return st;
+    if ((st = dev_alloc(p->d_bpk, (size_t)p->bpk_bytes)) != BSMM_OK) return st;
+  }
   if ((st = dev_alloc(p->d_eA, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)M * K))) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_eB, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)K * N))) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_eAmax, sizeof(int32_t) * std::max(1, M))) != BSMM_OK) return st;
@@ -436,10 +453,13 @@ void bsmm_destroy(bsmm_plan_t p) {
   delete p;
 }
 
-bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
-                      const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,
-                      const uint8_t* a_mask, const uint8_t* b_mask, const uint8_t* c_mask,
-                      const bsmm_options* opt) {
+}  // extern "C"
+
+namespace bsmm {
+
+bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N, const int32_t* col_sizes,
+                       int32_t K, const int32_t* inner_sizes, const uint8_t* a_mask, const uint8_t* b_mask,
+                       const uint8_t* c_mask, const bsmm_options* opt, const bsmm_plan_s* donor) {
   if (!out) return set_error("out is NULL"), BSMM_ERR_INVALID;
   *out = nullptr;
   if (M < 0 || N < 0 || K < 0) return set_error("negative block count"), BSMM_ERR_INVALID;
@@ -467,6 +487,7 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
   p->N = N;
   p->K = K;
   p->opt = o;
+  p->donor = donor;
   p->r.assign(row_sizes, row_sizes + M);
   p->c.assign(col_sizes, col_sizes + N);
   p->q.assign(inner_sizes, inner_sizes + K);
@@ -539,6 +560,7 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
     bsmm_destroy(p);
     return st;
   }
+  p->donor = nullptr;  // only planning reads it
   p->cost = p->flop_cost;
   p->ctas = default_ctas(p);
   pack_lpt(p);
@@ -575,6 +597,17 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
   }
   *out = p;
   return BSMM_OK;
+}
+
+}  // namespace bsmm
+
+extern "C" {
+
+bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
+                      const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,
+                      const uint8_t* a_mask, const uint8_t* b_mask, const uint8_t* c_mask,
+                      const bsmm_options* opt) {
+  return plan_build(out, M, row_sizes, N, col_sizes, K, inner_sizes, a_mask, b_mask, c_mask, opt, nullptr);
 }
 
 bsmm_status bsmm_plan_query(bsmm_plan_t p, int64_t* n_ctiles, int64_t* n_triples, double* useful_flops,

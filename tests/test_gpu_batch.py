@@ -111,3 +111,39 @@ def test_batch_rejects_mixed_modes():
     p2 = P.bsmm_plan([64], [64], [64], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16)
     with pytest.raises(P.BsmmError):
         P.bsmm_batch_create([p1, p2])
+
+
+@pytest.mark.parametrize("mode", [P.BSMM_FP64, P.BSMM_SPLIT_BF16])
+def test_autotune_keeps_caller_c_and_bits(mode):
+    """Autotuning times every candidate on a scratch C (the caller's C keeps its
+    content), then the batch runs under the fastest one and still gives the oracles'
+    bits; the original plans stay usable on their own."""
+    import torch
+    items = _setup(mode, count=5, seed=12, fp64_tile=32)
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                          [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                          [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+    before = [it["C"].clone() for it in items]
+    space = P.bsmm_tune_space(mode, 6)
+    chosen, ms = P.bsmm_batch_autotune(batch, reps=2)
+    assert chosen in space and len(ms) == len(space)
+    assert all(np.isfinite(ms)) and min(ms) == ms[space.index(chosen)]
+    for it, b in zip(items, before):
+        assert bool((it["C"] == b).all())
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    P.bsmm_batch_status_device(batch)
+    for it in items:
+        want = _reference(it, mode)
+        got = it["C"].cpu().numpy()
+        assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
+                              struct_elements(it["prob"], it["cs"], it["off"], want))
+    # a second autotune (over a narrower space) re-plans from the tuned plans
+    P.bsmm_batch_autotune(batch, candidates=space[:2], reps=1)
+    it = items[0]
+    it["C"].copy_(torch.from_numpy(it["C0"] if it["C0"].size else np.zeros(2)))
+    from gpu_helpers import run_lib
+    alone, _ = run_lib(it["prob"], it["cs"], it["C0"], it["off"], mode=mode, plan=it["plan"])
+    assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], alone),
+                          struct_elements(it["prob"], it["cs"], it["off"], _reference(it, mode)))
