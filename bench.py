@@ -53,9 +53,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batch"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batch", "uniform", "banded", "banded_wide",
+                                                                "clustered"],
                     help="dense: the 16384 nonuniform dense product (headline); batch: 256 independent products of "
-                         "uneven size, separate launches vs one graph-replayed batch launch, before and after autotuning")
+                         "uneven size, separate launches vs one graph-replayed batch launch, before and after "
+                         "autotuning; uniform: N=2048, blocks 128, Bernoulli(0.5) masks (FP64 path); banded / "
+                         "banded_wide: N=32768 band |i-j|<=6 with distance-decaying values (FP64 vs split-fp16); "
+                         "clustered: M=N=24576, K=49152 clustered masks, learned vs flop-count schedule")
     ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
@@ -342,6 +346,139 @@ def run_batch(args, rank, world):
         print(json.dumps(line))
 
 
+SINGLE = {
+    "uniform": dict(recipe="uniform_bernoulli", n=2048, kw=dict(block=128, density=0.5), mode="BSMM_SPLIT_BF16",
+                    head="fp64", desc="uniform_bernoulli N=2048 blocks 128, Bernoulli(0.5) masks, U[-1,1] FP64, beta=0"),
+    "banded": dict(recipe="banded_decay", n=32768, kw=dict(lo=32, hi=256, band=6), mode="BSMM_SPLIT_FP16", head="split",
+                   desc="banded_decay N=32768 blocks U-int[32,256], |i-j|<=6, N(0,1)exp(-|i-j|/2)"),
+    "banded_wide": dict(recipe="banded_decay_wide", n=32768, kw=dict(lo=32, hi=256, band=6), mode="BSMM_SPLIT_FP16",
+                        head="split", desc="banded_decay_wide N=32768 blocks U-int[32,256], |i-j|<=6, "
+                                           "N(0,1)exp(-2.3|i-j|)"),
+    "clustered": dict(recipe="clustered", n=24576, kw=dict(lo=16, hi=512, nclusters=40, cluster_density=0.10),
+                      mode="BSMM_SPLIT_BF16", head="split",
+                      desc="clustered M=N=24576 K=49152, log-uniform blocks [16,512], 40 clusters at 10%, U[-1,1]"),
+}
+
+
+def run_single(args, rank, world):
+    """One of the other workloads: the split path (and, for the clustered one, the
+    learned schedule against the flop-count schedule) and the FP64 path on the same
+    inputs, each timed over the steps with CUDA events; the split result compared with
+    the FP64 result over the whole C."""
+    import torch
+    import bsmm_gen as G
+    import paper_1504_05046_gb300 as P
+    from paper_1504_05046_gb300 import costmodel as CM
+    w = SINGLE[args.workload]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    s = args.slices
+    mode = getattr(P, w["mode"])
+
+    def setup(seed, mode, **opt):
+        prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
+        plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,
+                           nslices=s, profile=1, **opt)
+        q = P.bsmm_plan_query(plan)
+        off, tot = G.layout_arena(q["c_mask"], prob.row_sizes, prob.col_sizes)
+        d = lambda x: torch.from_numpy(x if x.size else np.zeros(2, x.dtype)).to(dev)
+        t = dict(A=d(prob.A), B=d(prob.B), ao=d(prob.a_off), bo=d(prob.b_off), co=d(off),
+                 C=torch.zeros(max(tot, 1), dtype=torch.float64, device=dev))
+        run = lambda: P.bsmm_execute(plan, 1.0, t["A"], t["ao"], t["B"], t["bo"], 0.0, t["C"], t["co"])
+        return prob, plan, q, t, run
+
+    def timed(plan, run, steps):
+        stream = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = []
+        e0.record(stream)
+        for _ in range(steps):
+            run()
+            ks.append(P.bsmm_plan_kernel_ms(plan))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        P.bsmm_status_device(plan)
+        return e0.elapsed_time(e1) / steps, np.mean(np.array(ks), axis=0).tolist()
+
+    extra = {}
+    seed = args.seed + rank
+    if args.workload == "clustered":
+        # learned schedule: train on unit timings of three other inputs of the same shape
+        rows = []
+        for ts in (seed + 101, seed + 102, seed + 103):
+            _, tplan, _, _, trun = setup(ts, mode, record_timings=1)
+            trun()
+            rows.append(CM.training_rows(tplan, CM.unit_times(tplan, trun, repeats=3)))
+            del tplan
+        mlp, loss = CM.fit(rows, steps=2000, lr=3e-3)
+        prob, plan, q, t, run = setup(seed, mode, record_timings=1)
+        run()
+        times = CM.unit_times(plan, run, repeats=3)
+        CM.apply_flops(plan)
+        ms_flops, k_flops = timed(plan, run, args.steps)
+        ref = t["C"].clone()
+        CM.apply(plan, mlp)
+        clk = ClockSampler(dev.index)
+        clk.start()
+        time.sleep(0.3)
+        ms_split, k_split = timed(plan, run, args.steps)
+        clocks = clk.stop()
+        same = bool((t["C"] == ref).all())
+        feats, flops = P.bsmm_plan_features(plan)
+        y = torch.zeros(len(feats), dtype=torch.float32, device=dev)
+        P.bsmm_mlp_predict(mlp, torch.from_numpy(feats).to(dev), y)
+        extra["learned_schedule"] = {
+            "makespan_ms_flop_count": k_flops[-1], "makespan_ms_mlp": k_split[-1], "step_ms_flop_count": ms_flops,
+            "step_ms_mlp": ms_split, "bits_identical": same, "train_loss": loss,
+            "log_rms_err_flop_count": CM.prediction_error(plan, times, np.maximum(flops, 1.0)),
+            "log_rms_err_mlp": CM.prediction_error(plan, times, np.exp(y.cpu().numpy().astype(np.float64))),
+            "train_inputs": "3 other seeds of the same workload, 3 timed runs each"}
+    else:
+        prob, plan, q, t, run = setup(seed, mode)
+        clk = ClockSampler(dev.index)
+        clk.start()
+        time.sleep(0.3)
+        ms_split, k_split = timed(plan, run, args.steps)
+        clocks = clk.stop()
+    F = q["useful_flops"]
+    Csplit = t["C"].clone()
+    prob64, plan64, _, t64, run64 = setup(seed, P.BSMM_FP64)
+    ms64, k64 = timed(plan64, run64, args.steps if w["head"] == "fp64" else max(1, args.fp64_steps))
+    c64 = t64["C"]
+    err = float(torch.linalg.norm(Csplit - c64) / torch.linalg.norm(c64))
+    tf = lambda ms: F / (ms * 1e-3) / 1e12
+    pk, pk_src = peaks()
+    head_split = w["head"] == "split"
+    split = {"value": tf(ms_split), "ms_per_step": ms_split, "kernel_ms": k_split,
+             "mode": f"{w['mode'][5:].lower()} s={s}", "rel_err_vs_fp64": err}
+    fp64 = {"value": tf(ms64), "ms_per_step": ms64, "kernel_ms": k64}
+    pair = s * (s + 1) / 2 * F
+    if head_split:
+        roof = {"bound": "tensor", "kernel": "split_mma_kernel", "achieved": pair / (k_split[-1] * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
+                "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"}
+    else:
+        fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "fp64_tile_kernel", "achieved": F / (k64[-1] * 1e-3) / 1e12,
+                "peak": fp64_peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    head = split if head_split else fp64
+    line = {"metric": METRIC, "value": head["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if head_split and "BF16" in w["mode"] else
+            ("f16" if head_split else "f64"), "data": "synthetic",
+            "config": {"workload": w["desc"], "useful_flops_per_step": F, "seed": seed,
+                       "headline_path": "split" if head_split else "fp64"},
+            "split_path": split, "fp64_path": fp64, "roofline": roof, "gpu_launches":
+                (SPLIT_KERNELS_PER_EXECUTE if head_split else 1) * args.steps, "clocks": clocks}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -360,6 +497,9 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "batch":
         run_batch(args, rank, world)
+        return
+    if args.workload in SINGLE:
+        run_single(args, rank, world)
         return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
