@@ -156,6 +156,20 @@ def profiled_traffic():
         return None
 
 
+def aggregate(t, work, device):
+    """Whole-job figures over the ranks of an initialised process group (else this
+    rank's): the slowest rank's time and the summed work."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t), float(work)
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    ww = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ww.item())
+
+
 def make_inputs(n, seed):
     import bsmm_gen as G
     prob = G.make_problem("nonuniform_dense", seed, n, lo=64, hi=256)
@@ -324,6 +338,9 @@ def run_batch(args, rank, world):
     time.sleep(0.3)
     ms_tuned = timed(g.replay, args.steps)
     clocks = clk.stop()
+    ms_sep, _ = aggregate(ms_sep, 0.0, dev)
+    ms_batch, _ = aggregate(ms_batch, 0.0, dev)
+    ms_tuned, F = aggregate(ms_tuned, F, dev)
     P.bsmm_batch_status_device(batch)
     space = P.bsmm_tune_space(P.BSMM_SPLIT_BF16, s)
     tf = lambda ms: F / (ms * 1e-3) / 1e12
@@ -442,10 +459,11 @@ def run_single(args, rank, world):
         time.sleep(0.3)
         ms_split, k_split = timed(plan, run, args.steps)
         clocks = clk.stop()
-    F = q["useful_flops"]
     Csplit = t["C"].clone()
     prob64, plan64, _, t64, run64 = setup(seed, P.BSMM_FP64)
     ms64, k64 = timed(plan64, run64, args.steps if w["head"] == "fp64" else max(1, args.fp64_steps))
+    ms_split, _ = aggregate(ms_split, 0.0, dev)
+    ms64, F = aggregate(ms64, q["useful_flops"], dev)
     c64 = t64["C"]
     err = float(torch.linalg.norm(Csplit - c64) / torch.linalg.norm(c64))
     tf = lambda ms: F / (ms * 1e-3) / 1e12
@@ -491,18 +509,26 @@ def main():
 
     import torch
     import torch.distributed as dist
-    import bsmm_gen as G
-    import paper_1504_05046_gb300 as P
 
     torch.cuda.set_device(local)
-    if args.workload == "batch":
-        run_batch(args, rank, world)
-        return
-    if args.workload in SINGLE:
-        run_single(args, rank, world)
-        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "batch":
+        run_batch(args, rank, world)
+    elif args.workload in SINGLE:
+        run_single(args, rank, world)
+    else:
+        run_dense(args, rank, world, local)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_dense(args, rank, world, local):
+    """The headline workload: the 16384 nonuniform dense product, 6-slice split-bf16."""
+    import torch
+    import torch.distributed as dist
+    import bsmm_gen as G
+    import paper_1504_05046_gb300 as P
 
     def barrier():
         if world > 1:
@@ -550,13 +576,8 @@ def main():
     barrier()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    t_rank = torch.tensor([ms], dtype=torch.float64, device=dev)
-    f_rank = torch.tensor([F], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-        dist.all_reduce(f_rank, op=dist.ReduceOp.SUM)
-    ms_max = float(t_rank.item())
-    value = float(f_rank.item()) / (ms_max * 1e-3) / 1e12
+    ms_max, F_all = aggregate(ms, F, dev)
+    value = F_all / (ms_max * 1e-3) / 1e12
     P.bsmm_status_device(plan)
     Csplit = C.cpu().numpy()
 
@@ -618,13 +639,11 @@ def main():
         for _ in range(args.e2e_steps):
             P.bsmm_execute_host(plan, 1.0, hA, hao, hB, hbo, 0.0, hC, hco)
         dt = (time.perf_counter() - t0) / args.e2e_steps
-        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt_max, _ = aggregate(dt, 0.0, dev)
         h2d = (prob.A.nbytes + prob.B.nbytes + prob.a_off.nbytes + prob.b_off.nbytes + c_off.nbytes)
-        e2e = {"value": float(f_rank.item()) / float(tt.item()) / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": F_all / dt_max / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(c_tot * 8),
-               "ms_per_step": float(tt.item()) * 1e3}
+               "ms_per_step": dt_max * 1e3}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -642,8 +661,6 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         line.update(extra)
         print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

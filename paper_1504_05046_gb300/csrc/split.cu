@@ -389,7 +389,9 @@ __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
 // N_t = Z_t - 128 Z_{t-1}. Each Z_t is computed exactly from the mantissa with integer
 // shifts and a round-half-even step; no floating-point operation is involved.
 __device__ __forceinline__ long long rint_scaled(long long m, int sh) {  // rint(m 2^sh), m >= 0
-  if (sh >= 0) return m << sh;
+  // finite inputs always have sh < 0 (|x 2^-e| < 1); a non-finite one (already reported
+  // by the exponent kernel) must still not shift by the register width or more
+  if (sh >= 0) return sh >= 63 ? 0 : m << sh;
   const int k = -sh;
   if (k >= 63) return 0;  // m < 2^53 <= 2^(k-1): below one half
   const long long q = m >> k;

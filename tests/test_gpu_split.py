@@ -201,3 +201,79 @@ def test_merged_accumulation_groups(case):
     for cl in (1, 2):
         check(prob, 6, cluster=cl)
     check(prob, 3)
+
+
+def test_zero_size_blocks_empty_rows_and_zero_tiles():
+    """Zero-size row, column and inner blocks, a row block without A tiles, and stored
+    tiles that are all zero (exponent 0, every slice zero)."""
+    rng = np.random.default_rng(8)
+    r = np.array([0, 33, 0, 165, 1], np.int32)
+    q = np.array([17, 0, 80, 3], np.int32)
+    c = np.array([64, 0, 9, 130], np.int32)
+    am = (rng.random((5, 4)) < 0.7).astype(np.uint8)
+    bm = (rng.random((4, 4)) < 0.7).astype(np.uint8)
+    am[3, :] = 0
+    am[1, :] = 1
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    A, B = rng.uniform(-1, 1, at), rng.uniform(-1, 1, bt)
+    o = a_off[1, 2]
+    A[o:o + 33 * 80] = 0.0  # an all-zero stored tile
+    prob = G.Problem("zeros", r, c, q, am, bm, a_off, b_off, A, B, 1.0, 0.0)
+    for s in (6, 3):
+        check(prob, s)
+
+
+def test_empty_product_keeps_beta_c():
+    """No nonzero triple: every C tile of the user mask is beta*C."""
+    prob = G.random_small(3)
+    prob.a_mask[:] = 0
+    prob.a_off[:] = -1
+    prob.A = np.zeros(0)
+    prob.beta = 2.0
+    cm = np.ones((prob.M, prob.N), np.uint8)
+    check(prob, 6, c_mask=cm, bar=0.0)
+
+
+def test_beta_zero_ignores_nan_in_c():
+    from gpu_helpers import run_lib
+    prob = G.make_problem("nonuniform_dense", 5, 300, lo=40, hi=90)
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, fill=np.nan)
+    want = C0.copy()
+    OS.bsmm_split(prob, cs, want, off, 6)
+    Cg, _ = run_lib(prob, cs, C0, off, mode=P.BSMM_SPLIT_BF16, nslices=6)
+    got = struct_elements(prob, cs, off, Cg)
+    assert not np.isnan(got).any()
+    assert np.array_equal(got, struct_elements(prob, cs, off, want))
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_non_finite_input_is_reported(bad):
+    """A NaN or infinity in A has no slicing; the exponent kernel records it in the
+    device error word and bsmm_status_device returns BSMM_ERR_DEVICE (no trap)."""
+    from gpu_helpers import run_lib
+    prob = G.make_problem("nonuniform_dense", 7, 200, lo=40, hi=90)
+    prob.A = prob.A.copy()
+    prob.A[5] = bad
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, rng=np.random.default_rng(1))
+    with pytest.raises(P.BsmmError) as ei:
+        run_lib(prob, cs, C0, off, mode=P.BSMM_SPLIT_BF16, nslices=6)
+    assert ei.value.status == 6
+    # the context stays usable: the same structure with finite values runs clean
+    prob.A[5] = 0.25
+    check(prob, 6)
+
+
+def test_stages_option():
+    """Every ring depth that fits gives the same bits; one that does not fit is refused."""
+    prob = G.make_problem("nonuniform_dense", 12, 600, lo=40, hi=200)
+    base, _, _ = check(prob, 6)
+    again, _, _ = check(prob, 6, stages=2)
+    assert np.array_equal(base, again)
+    for st in (2, 5, 7):
+        check(prob, 3, stages=st)
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan([8], [8], [8], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6, stages=4)
+    assert ei.value.status == 5
