@@ -78,8 +78,10 @@ bsmm_status repack(bsmm_batch_s* b) {
   for (size_t w = 0; w + 1 < b->wave_prod.size(); w++) {
     const int64_t u0 = b->prod_begin[b->wave_prod[w]], u1 = b->prod_begin[b->wave_prod[w + 1]];
     std::vector<double> cost(b->cost.begin() + u0, b->cost.begin() + u1);
-    std::vector<int64_t> seg;
-    for (int32_t p = b->wave_prod[w]; p <= b->wave_prod[w + 1]; p++) seg.push_back(b->prod_begin[p] - u0);
+    std::vector<int64_t> seg;  // product by product, each in waves of one unit per bin
+    for (int32_t p = b->wave_prod[w]; p < b->wave_prod[w + 1]; p++)
+      wave_segments(b->prod_begin[p] - u0, b->prod_begin[p + 1] - u0, b->wave_bins[w], seg);
+    if (seg.empty()) seg.push_back(0);
     std::vector<int32_t> ptr, units;
     lpt_pack(cost, b->wave_bins[w], false, ptr, units, &seg);
     b->wave_ptr.push_back((int64_t)b->sched_ptr.size());

@@ -37,6 +37,7 @@ int split_tile_n(int s);          // work-unit width (32 or 64)
 int split_stages(int s, int tn);  // smem ring depth
 size_t split_smem_bytes(int s, int tn, int stages);
 constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory of one CTA
+constexpr size_t kSplitBarBytes = 256;          // mbarriers, TMEM slot and flags after the ring
 constexpr int16_t kNonUniform = 0x7FFF;         // scale-class sentinel (offsets are <= 0)
 int split_max_depth(int s);
 constexpr int kSplitDefaultCluster = 2;
@@ -166,6 +167,7 @@ cudaError_t launch_split_mma(const SplitArgs& a, int clusters, cudaStream_t st);
 // (or clusters); natural = round robin in unit order. CSR output.
 void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vector<int32_t>& ptr,
               std::vector<int32_t>& units, const std::vector<int64_t>* segments = nullptr);
+void wave_segments(int64_t u0, int64_t u1, int bins, std::vector<int64_t>& seg);
 // Kernel arguments of one product (device pointers from the caller).
 void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);

@@ -39,14 +39,16 @@ static size_t stage_bytes(int s, int tn) {
   return (size_t)s * (kSplitBM * kSplitKC * 2) + (size_t)s * (tn * kSplitKC * 2);
 }
 
+// the deepest ring (at most 8 stages) that fits one CTA's shared memory
 int split_stages(int s, int tn) {
-  const size_t budget = 200 * 1024;
-  int st = (int)(budget / stage_bytes(s, tn));
-  return std::max(2, std::min(8, st));
+  int st = 8;
+  while (st > 2 && split_smem_bytes(s, tn, st) > kMaxSmemPerCta) st--;
+  return st;
 }
 
 size_t split_smem_bytes(int s, int tn, int stages) {
-  return 1024 /*alignment slack*/ + (size_t)stages * stage_bytes(s, tn) + 256 /*barriers*/;
+  return 1024 /*alignment slack*/ + (size_t)stages * stage_bytes(s, tn) + kSplitBarBytes +
+         (size_t)kSplitBM * (tn + 1) * sizeof(double) /*C staging*/;
 }
 
 // Longest processing time first: units by descending cost (ties keep unit order), each
@@ -90,6 +92,16 @@ void lpt_pack(const std::vector<double>& cost, int bins, bool natural, std::vect
     for (int32_t u : lists[t]) units.push_back(u);
   }
   ptr[bins] = (int32_t)units.size();
+}
+
+// Units [u0, u1) in waves of `bins` consecutive units (segment starts, then u1): packed
+// wave by wave, every bin's i-th unit comes from wave i, so the bins walk the raster
+// order together and the units that run at the same time share their panels in L2
+// (one LPT pass over all units would let costlier bins fall behind in unit order).
+void wave_segments(int64_t u0, int64_t u1, int bins, std::vector<int64_t>& seg) {
+  if (seg.empty() || seg.back() != u0) seg.push_back(u0);
+  for (int64_t u = u0 + bins; u < u1; u += bins) seg.push_back(u);
+  if (u1 > u0) seg.push_back(u1);
 }
 
 // FP64: persistent CTAs; split modes: persistent clusters of p->cl CTAs.
@@ -155,7 +167,9 @@ inline int log2i_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b);
 inline float lg(double x) { return (float)std::log2(1.0 + x); }
 
 void pack_lpt(bsmm_plan_s* p) {
-  lpt_pack(p->cost, p->ctas, p->opt.schedule == BSMM_SCHED_NATURAL, p->sched_ptr, p->sched_units);
+  std::vector<int64_t> seg;
+  wave_segments(0, (int64_t)p->cost.size(), p->ctas, seg);
+  lpt_pack(p->cost, p->ctas, p->opt.schedule == BSMM_SCHED_NATURAL, p->sched_ptr, p->sched_units, &seg);
 }
 
 int default_ctas(const bsmm_plan_s* p) { return default_bins(p); }

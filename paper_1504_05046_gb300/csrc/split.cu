@@ -542,7 +542,11 @@ __device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsi
   return hi >> (r - 64);
 }
 
-// Round the 128-bit integer w to the nearest double (ties to even) and scale by 2^L.
+// Round the 128-bit two's-complement integer w to the nearest double (ties to even) and
+// scale by 2^L, in integer arithmetic: the rounded 53-bit significand and the exponent are
+// assembled into the double's bit pattern (GB300's FP64 pipe is narrow, so no FP64
+// instruction is spent per element). Only a result outside the normal range takes the
+// library scaling.
 __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   unsigned long long lo = ((unsigned long long)w[1] << 32) | w[0];
   unsigned long long hi = ((unsigned long long)w[3] << 32) | w[2];
@@ -555,11 +559,10 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   }
   if (hi == 0 && lo == 0) return 0.0;
   const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  int r = msb - 52;
   unsigned long long mant;
+  int r = msb - 52;  // value = mant * 2^(r + L), mant in [2^52, 2^53) after rounding
   if (r <= 0) {
-    mant = lo;  // fits in 53 bits: exact
-    r = 0;
+    mant = lo << (-r);  // exact
   } else {
     mant = shr128(hi, lo, r);
     const bool round = shr128(hi, lo, r - 1) & 1;
@@ -576,7 +579,13 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
       }
     }
   }
-  const double d = scalbn((double)mant, r + L);
+  const int biased = r + L + 52 + 1023;
+  double d;
+  if (biased >= 1 && biased <= 2046) {
+    d = __longlong_as_double((long long)(((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
+  } else {
+    d = scalbn((double)mant, r + L);  // subnormal or overflowing result
+  }
   return neg ? -d : d;
 }
 
@@ -664,12 +673,6 @@ struct KAhead {
   }
 };
 
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
-constexpr int kPrefetch = 8;  // chunks the producer pulls into L2 ahead of its copies
-
 // The chunks of one CTA's unit list in order: unit by unit, k block by k block
 // (ascending), 32-deep chunk by chunk.
 struct ChunkCursor {
@@ -714,11 +717,6 @@ struct ChunkCursor {
       in_unit = true;
     }
   }
-  template <int A_STAGE, int A_SLICE, int B_STAGE>
-  __device__ void prefetch(int rank) const {
-    prefetch_l2(asrc + (size_t)kc * A_STAGE + rank * A_SLICE, A_SLICE);
-    if (ownb) prefetch_l2(bsrc + (size_t)kc * B_STAGE, B_STAGE);
-  }
 };
 
 template <int S, int TN, int CL>
@@ -732,6 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   constexpr uint16_t MASK = (uint16_t)((1u << CL) - 1);
   constexpr int W = S < kMmaWarps ? S : kMmaWarps;  // MMA warps with work: warp 1+w issues slices p = w+1, w+1+W, ...
   static_assert(A_SLICE % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(TN == 32, "the coalesced C store maps one column to each lane");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -744,6 +743,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   uint64_t* drain = tempty + 2;  // one per MMA warp
   uint32_t* tmem_slot = (uint32_t*)(drain + kMmaWarps);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // the unit's results on their way to C: 128 rows x (TN + 1) doubles (padded rows)
+  double* cstage = (double*)(smem + (size_t)stages * STAGE + kSplitBarBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cta = blockIdx.x / CL;  // the cluster: schedules are per cluster
@@ -781,11 +782,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       uint32_t issued = 0;  // bit st: stage st holds an issued copy; its parity in issued_par
       uint32_t issued_par = 0;
       bool ok = true;
-      // a second cursor runs kPrefetch chunks ahead and pulls them into L2, so that the
-      // copies into shared memory hit L2 instead of waiting on HBM
-      ChunkCursor ahead;
-      ahead.start(ubeg, uend);
-      for (int i = 0; i < kPrefetch && ahead.advance(a, CL, rank); i++) ahead.prefetch<A_STAGE, A_SLICE, B_STAGE>(rank);
       ChunkCursor cur;
       cur.start(ubeg, uend);
       while (ok && cur.advance(a, CL, rank)) {
@@ -808,7 +804,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           stage = 0;
           phase ^= 1;
         }
-        if (ahead.advance(a, CL, rank)) ahead.prefetch<A_STAGE, A_SLICE, B_STAGE>(rank);
       }
       // drain: every copy this thread issued has landed before the CTA may exit
       for (int st = 0; st < stages; st++) {
@@ -1058,31 +1053,58 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         if (lane == 0) mbar_arrive(&tempty[buf]);
         tcount++;
       }
-      if (!ok) break;
-      // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles
-      if (row_ok) {
-        const int i = P.row_tile[m];
-        const int64_t lr = m - P.ro[i];
-        const int Lrow = P.eAmax[i] - kSplitBeta * (S + 1) - kSplitGuard;
+      // (a warp whose wait gave up still passes the two barriers below, so that no other
+      // epilogue warp waits at them for it; every wait before them is bounded and sees the
+      // abort flag, so all eight warps reach them)
+      // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles.
+      // Each thread rounds its row's sums to doubles into shared memory; then every warp
+      // stores whole rows, lane = column, so a store instruction writes one or two
+      // contiguous row segments instead of 32 scattered elements.
+      if (ok) {
+        const int Lrow = row_ok ? P.eAmax[P.row_tile[m]] - kSplitBeta * (S + 1) - kSplitGuard : 0;
+        double* srow = cstage + row * (TN + 1) + half * TH;
 #pragma unroll
         for (int c = 0; c < TH; c++) {
           const int64_t n = n0 + c;
-          if (n < P.Ntot) {
-            const int j = P.col_tile[n];
-            const int64_t tile = (int64_t)i * P.N + j;
+          srow[c] = (row_ok && n < P.Ntot) ? acc_to_double(acc[c], Lrow + P.eBmax[P.col_tile[n]]) : 0.0;
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+      if (ok && !*abort_flag) {
+        const int64_t nl = (int64_t)cb * TN + lane;  // TN == 32: one column per lane
+        const bool col_ok = nl < P.Ntot;
+        const int jl = col_ok ? P.col_tile[nl] : 0;
+        const int64_t lcl = col_ok ? nl - P.co[jl] : 0;
+        const int64_t cjl = col_ok ? P.c[jl] : 0;
+        constexpr int kRowsPerWarp = kSplitBM / kSplitEpiWarps;
+        // lane r < kRowsPerWarp fetches row r's tile and row-in-tile; shuffles hand them out
+        const int64_t mr = (int64_t)un.rb * kSplitBM + ew * kRowsPerWarp + (lane % kRowsPerWarp);
+        const int ir = mr < P.Mtot ? P.row_tile[mr] : 0;
+        const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
+        const double alpha = P.alpha, beta = P.beta;
+#pragma unroll
+        for (int rr = 0; rr < kRowsPerWarp; rr++) {
+          const int r2 = ew * kRowsPerWarp + rr;
+          const int64_t m2 = (int64_t)un.rb * kSplitBM + r2;
+          const int i2 = __shfl_sync(0xffffffffu, ir, rr);
+          const int lr2 = __shfl_sync(0xffffffffu, lrr, rr);
+          if (m2 < P.Mtot && col_ok) {
+            const int64_t tile = (int64_t)i2 * P.N + jl;
             const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
             if (off == -1) atomicOr(a.err, kErrBadOffset);
             if (off >= 0) {
-              double* dst = P.C + off + lr * P.c[j] + (n - P.co[j]);
-              double vv = __dmul_rn(P.alpha, acc_to_double(acc[c], Lrow + P.eBmax[j]));
-              if (P.beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(P.beta, *dst));
+              double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
+              double vv = cstage[r2 * (TN + 1) + lane];
+              if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
+              if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
               *dst = vv;
             }
           }
         }
       }
+      asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");  // cstage is free again
+      if (!ok) break;
       if (a.timings && rank == 0) {
-        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
         if (ew == 0 && lane == 0) {
           a.timings[2 * (int64_t)u + 1] = gtimer();
           a.unit_cta[u] = cta;

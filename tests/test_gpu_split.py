@@ -272,7 +272,7 @@ def test_stages_option():
     base, _, _ = check(prob, 6)
     again, _, _ = check(prob, 6, stages=2)
     assert np.array_equal(base, again)
-    for st in (2, 5, 7):
+    for st in (2, 4, 6):
         check(prob, 3, stages=st)
     with pytest.raises(P.BsmmError) as ei:
         P.bsmm_plan([8], [8], [8], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6, stages=4)
