@@ -61,6 +61,8 @@ def parse():
                          "banded_wide: N=32768 band |i-j|<=6 with distance-decaying values (FP64 vs split-fp16); "
                          "clustered: M=N=24576, K=49152 clustered masks, learned vs flop-count schedule")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--other-slices", type=int, nargs="*", default=[3, 4, 5],
+                    help="slice counts also timed on the dense workload, each with its error against FP64")
     return ap.parse_args()
 
 
@@ -622,6 +624,30 @@ def run_dense(args, rank, world, local):
                                            "peak_def": "152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}}
         extra["split_rel_err_vs_fp64"] = err
         extra["split_speedup_vs_fp64"] = ms64 / ms_max
+        # the other slice counts on the same inputs: throughput and error against the FP64 result
+        modes = {}
+        for s2 in args.other_slices:
+            if s2 == s:
+                continue
+            plan2 = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                                mode=P.BSMM_SPLIT_BF16, nslices=s2, cluster=args.cluster)
+            C2 = torch.zeros_like(C)
+            for _ in range(2):
+                P.bsmm_execute(plan2, 1.0, A, ao, B, bo, 0.0, C2, co)
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(3):
+                P.bsmm_execute(plan2, 1.0, A, ao, B, bo, 0.0, C2, co)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            P.bsmm_status_device(plan2)
+            ms2 = g0.elapsed_time(g1) / 3
+            e2 = float(np.linalg.norm(C2.cpu().numpy() - c64) / np.linalg.norm(c64))
+            modes[f"s={s2}"] = {"value": F / (ms2 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms2,
+                                "rel_err_vs_fp64": e2, "bar": {3: 1e-5}.get(s2)}
+            del plan2, C2
+        extra["split_modes"] = modes
         del plan64, C64
 
     # end to end through the public C ABI with host buffers (pinned)

@@ -277,3 +277,22 @@ def test_stages_option():
     with pytest.raises(P.BsmmError) as ei:
         P.bsmm_plan([8], [8], [8], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6, stages=4)
     assert ei.value.status == 5
+
+
+def test_subnormal_results_match_split_oracle():
+    """Tiles scaled by 2^-528 put every result in the subnormal range: the rounding takes its
+    library-scaling path for results below the normal range, as the oracle does (one
+    rounding to 53 bits, then the scaling)."""
+    prob = G.make_problem("nonuniform_dense", 13, 300, lo=40, hi=120)
+    prob.A = prob.A * 2.0 ** -528
+    prob.B = prob.B * 2.0 ** -528
+    from gpu_helpers import run_lib
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, fill=0.0)
+    want = C0.copy()
+    OS.bsmm_split(prob, cs, want, off, 6)
+    Cg, _ = run_lib(prob, cs, C0, off, mode=P.BSMM_SPLIT_BF16, nslices=6)
+    got = struct_elements(prob, cs, off, Cg)
+    w = struct_elements(prob, cs, off, want)
+    assert np.all(np.abs(w) < 2.0 ** -1022) and np.any(w != 0)
+    assert np.array_equal(got, w)
