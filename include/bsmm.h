@@ -83,8 +83,7 @@ typedef struct {
   int32_t profile;         /* 1 = time each internal kernel with CUDA events (bsmm_plan_kernel_ms) */
   int32_t cluster;         /* split modes: CTAs per thread-block cluster sharing the A stream
                               by multicast, 1, 2 or 4 (0 = default) */
-  int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = chosen
-                              from the tiling: 32 when 64 would pad ragged tiles by > 5%) */
+  int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = 32) */
   int32_t stages;          /* split modes: depth of the shared-memory ring of 32-deep k chunks
                               (k panels in flight), 2..8 and within the 227 KB shared memory of
                               one CTA (0 = as many as fit in 200 KB) */

@@ -1,18 +1,19 @@
 // Plain FP64 tile-task kernel.
 //
-// One persistent CTA walks its packed list of work units. A unit is a 64x64
-// region of one C tile C_ij; the CTA owns it for the whole task: it runs the
+// One persistent CTA walks its packed list of work units. A unit is a 32x32 (or
+// 64x64) region of one C tile C_ij; the CTA owns it for the whole task: it runs the
 // tile's ascending k-list (the rank-k updates C_ij <- A_ik B_kj + C_ij of the
 // paper's Sec. 2.1, multiply and reduction fused as in Sec. 3.2), then applies
 // C_ij = alpha*acc + beta*C_ij (Algorithm 1's alpha) and stores.
 //
 // GB300 has no FP64 tensor-core kind in tcgen05, and its warp-level FP64 MMA
 // (mma.sync m8n8k4) measures below its FP64 FMA pipe, so the contraction is a
-// register-tiled DFMA loop: 256 threads, 4x4 accumulators each, the A and B
-// sub-tiles (64x16 and 16x64) staged through shared memory with the next chunk's
+// register-tiled DFMA loop: (T/4)^2 threads, 4x4 accumulators each, the A and B
+// sub-tiles (Tx16 and 16xT) staged through shared memory with the next chunk's
 // global loads in flight during the current chunk's FMAs. Irregular tiles are
 // read in place from the caller's arena: edges beyond a tile's rows, columns or
-// inner size are zero-filled in shared memory.
+// inner size are zero-filled in shared memory, and the FMAs a whole warp would spend
+// on them are skipped (see fma_chunk).
 //
 // Rounding is fixed by construction: each accumulator element takes
 // acc = fma(a, b, acc) over k blocks in ascending order and, inside a block,
@@ -35,6 +36,45 @@ __device__ __forceinline__ int64_t gtimer() {
 
 constexpr int BK = kF64BK;
 constexpr int PAD = 2;
+
+// FMAs of one staged chunk for the register-tile rows x < XM and columns y < YM that some
+// lane of this warp needs, over the chunk's kv valid inner indices. XM, YM and kv are the
+// same for every lane of a warp, so the rows, columns and inner tail a ragged sub-tile does
+// not have cost no instructions; each accumulator still takes its FMAs in ascending kk.
+template <int XM, int YM, int BK_, int TX, int LDA, int LDB>
+__device__ __forceinline__ void fma_chunk(double (&acc)[4][4], const double (*sA)[LDA], const double (*sB)[LDB], int ty,
+                                          int tx, int kv) {
+  auto step = [&](int kk) {
+    double av[XM], bv[YM];
+#pragma unroll
+    for (int x = 0; x < XM; x++) av[x] = sA[kk][ty + TX * x];
+#pragma unroll
+    for (int y = 0; y < YM; y++) bv[y] = sB[kk][tx + TX * y];
+#pragma unroll
+    for (int x = 0; x < XM; x++)
+#pragma unroll
+      for (int y = 0; y < YM; y++) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+  };
+  if (kv == BK_) {
+#pragma unroll
+    for (int kk = 0; kk < BK_; kk++) step(kk);
+  } else {
+#pragma unroll 4
+    for (int kk = 0; kk < kv; kk++) step(kk);
+  }
+}
+
+template <int XM, int BK_, int TX, int LDA, int LDB>
+__device__ __forceinline__ void fma_chunk_y(double (&acc)[4][4], const double (*sA)[LDA], const double (*sB)[LDB],
+                                            int ty, int tx, int kv, int ym) {
+  switch (ym) {
+    case 4: fma_chunk<XM, 4, BK_, TX, LDA, LDB>(acc, sA, sB, ty, tx, kv); break;
+    case 3: fma_chunk<XM, 3, BK_, TX, LDA, LDB>(acc, sA, sB, ty, tx, kv); break;
+    case 2: fma_chunk<XM, 2, BK_, TX, LDA, LDB>(acc, sA, sB, ty, tx, kv); break;
+    case 1: fma_chunk<XM, 1, BK_, TX, LDA, LDB>(acc, sA, sB, ty, tx, kv); break;
+    default: break;
+  }
+}
 
 struct ChunkIter {
   int64_t t, t_end;  // position in the tile's k-list
@@ -124,9 +164,15 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
       }
     };
 
+    // register-tile rows and columns some lane of this warp needs: warp w holds ty in
+    // [w*32/TX, (w+1)*32/TX), rows ty + TX*x, and every tx, columns tx + TX*y
+    const int wty = (tid / 32) * (32 / TX);
+    const int xm = rows > wty ? min(4, (rows - wty + TX - 1) / TX) : 0;
+    const int ym = min(4, (cols + TX - 1) / TX);
     bool have = it.t < it.t_end;
     if (have) load_chunk(it);
     while (have) {
+      const int kv = min(BK, it.qk - it.kk0);  // valid inner indices of the chunk being staged
 #pragma unroll
       for (int m = 0; m < A_PER_T; m++) {
         const int e = tid + NT * m;
@@ -141,17 +187,12 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
       advance(it);
       have = it.t < it.t_end;
       if (have) load_chunk(it);  // next chunk's loads overlap this chunk's FMAs
-#pragma unroll
-      for (int kk = 0; kk < BK; kk++) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int x = 0; x < 4; x++) av[x] = sA[kk][ty + TX * x];
-#pragma unroll
-        for (int y = 0; y < 4; y++) bv[y] = sB[kk][tx + TX * y];
-#pragma unroll
-        for (int x = 0; x < 4; x++)
-#pragma unroll
-          for (int y = 0; y < 4; y++) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+      switch (xm) {
+        case 4: fma_chunk_y<4, BK, TX, BM + PAD, BN + PAD>(acc, sA, sB, ty, tx, kv, ym); break;
+        case 3: fma_chunk_y<3, BK, TX, BM + PAD, BN + PAD>(acc, sA, sB, ty, tx, kv, ym); break;
+        case 2: fma_chunk_y<2, BK, TX, BM + PAD, BN + PAD>(acc, sA, sB, ty, tx, kv, ym); break;
+        case 1: fma_chunk_y<1, BK, TX, BM + PAD, BN + PAD>(acc, sA, sB, ty, tx, kv, ym); break;
+        default: break;
       }
       __syncthreads();
     }
