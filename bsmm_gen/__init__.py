@@ -235,6 +235,11 @@ class Problem:
     beta: float = 0.0
     c_mask: Optional[np.ndarray] = None   # extra C tiles kept (None = only the mask product)
     recipe: str = ""
+    # transposed storage: the A arguments describe the K x M block matrix A' = A^T (a_mask
+    # and a_off K x M, every tile A'_ki = (A_ik)^T stored q_k x r_i row-major); likewise B
+    # as the N x K block matrix B' (b_mask and b_off N x K, tiles c_j x q_k)
+    transa: bool = False
+    transb: bool = False
 
     @property
     def M(self):
@@ -321,6 +326,32 @@ def make_problem(recipe: str, seed: int, n: int, *, values: Optional[str] = None
         bm = mask_dense(nb, nb)
         return _assemble(f"{recipe}_n{n}_s{seed}", r, r, r, am, bm, rv, values or "uniform", recipe, alpha, beta)
     raise ValueError(f"unknown recipe {recipe}")
+
+
+def transposed_storage(prob: Problem, transa: bool, transb: bool) -> Problem:
+    """The same product with A and/or B supplied as the transposed block matrix: masks and
+    offset tables transposed, every tile copied as its transpose into a fresh arena."""
+    def move(mask, off, arena, rows, cols):
+        # tile (u, v) of a rows[u] x cols[v] grid -> tile (v, u) of the transposed grid
+        mt = np.ascontiguousarray(mask.T)
+        new_off, tot = layout_arena(mt, cols, rows)
+        out = np.zeros(tot)
+        for u in range(mask.shape[0]):
+            for v in range(mask.shape[1]):
+                if mask[u, v]:
+                    n = int(rows[u]) * int(cols[v])
+                    x = arena[off[u, v]:off[u, v] + n].reshape(int(rows[u]), int(cols[v]))
+                    out[new_off[v, u]:new_off[v, u] + n] = x.T.reshape(-1)
+        return mt, new_off, out
+    am, ao, A = (prob.a_mask, prob.a_off, prob.A)
+    bm, bo, B = (prob.b_mask, prob.b_off, prob.B)
+    if transa:
+        am, ao, A = move(prob.a_mask, prob.a_off, prob.A, prob.row_sizes, prob.inner_sizes)
+    if transb:
+        bm, bo, B = move(prob.b_mask, prob.b_off, prob.B, prob.inner_sizes, prob.col_sizes)
+    return Problem(prob.name + f"_t{int(transa)}{int(transb)}", prob.row_sizes, prob.col_sizes, prob.inner_sizes,
+                   am, bm, ao, bo, A, B, prob.alpha, prob.beta, prob.c_mask, prob.recipe, bool(transa),
+                   bool(transb))
 
 
 def make_batch(count: int, seed: int, n_lo: int = 512, n_hi: int = 8192, b_lo: int = 32,

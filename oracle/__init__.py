@@ -33,9 +33,10 @@ def lib():
         L.oracle_structure.restype = ctypes.c_int
         L.oracle_klists.argtypes = [ctypes.c_int] * 3 + [P] * 4
         L.oracle_klists.restype = ctypes.c_int
-        L.oracle_bsmm.argtypes = [ctypes.c_int] * 3 + [P] * 6 + [f64, P, P, P, P, f64, P, P, ctypes.c_int]
+        L.oracle_bsmm.argtypes = [ctypes.c_int] * 3 + [P] * 6 + [f64, P, P, P, P, f64, P, P, ctypes.c_int,
+                                                                   ctypes.c_int]
         L.oracle_bsmm.restype = ctypes.c_int
-        L.oracle_bsmm_tile.argtypes = [ctypes.c_int] * 5 + [P] * 5 + [f64, P, P, P, P, f64, P, P]
+        L.oracle_bsmm_tile.argtypes = [ctypes.c_int] * 5 + [P] * 5 + [f64, P, P, P, P, f64, P, P, ctypes.c_int]
         L.oracle_bsmm_tile.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
@@ -51,9 +52,20 @@ def _c(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
 
 
+def _std(prob):
+    """Masks and offset tables in the (i,k) / (k,j) indexing, and the transposed-storage
+    bits (1: A tiles stored transposed, 2: B tiles) for the in-tile addressing."""
+    ta, tb = bool(getattr(prob, "transa", False)), bool(getattr(prob, "transb", False))
+    am = prob.a_mask.T if ta else prob.a_mask
+    ao = prob.a_off.T if ta else prob.a_off
+    bm = prob.b_mask.T if tb else prob.b_mask
+    bo = prob.b_off.T if tb else prob.b_off
+    return _c(am, np.uint8), _c(ao, np.int64), _c(bm, np.uint8), _c(bo, np.int64), int(ta) | (int(tb) << 1)
+
+
 def _common(prob):
-    return (_c(prob.row_sizes, np.int32), _c(prob.col_sizes, np.int32), _c(prob.inner_sizes, np.int32),
-            _c(prob.a_mask, np.uint8), _c(prob.b_mask, np.uint8))
+    am, _, bm, _, _ = _std(prob)
+    return (_c(prob.row_sizes, np.int32), _c(prob.col_sizes, np.int32), _c(prob.inner_sizes, np.int32), am, bm)
 
 
 def structure(prob, c_mask=None):
@@ -89,10 +101,10 @@ def bsmm(prob, c_struct, C, c_off, nthreads: int = 0):
     A = _c(prob.A, np.float64)
     B = _c(prob.B, np.float64)
     assert C.dtype == np.float64 and C.flags.c_contiguous
+    _, ao, _, bo, trans = _std(prob)
     rc = lib().oracle_bsmm(M, N, K, _p(r), _p(c), _p(q), _p(am), _p(bm), _p(_c(c_struct, np.uint8)),
-                           float(prob.alpha), _p(A), _p(_c(prob.a_off, np.int64)), _p(B),
-                           _p(_c(prob.b_off, np.int64)), float(prob.beta), _p(C),
-                           _p(_c(c_off, np.int64)), int(nthreads))
+                           float(prob.alpha), _p(A), _p(ao), _p(B), _p(bo), float(prob.beta), _p(C),
+                           _p(_c(c_off, np.int64)), int(nthreads), trans)
     assert rc == 0, "oracle_bsmm failed"
     return C
 
@@ -105,10 +117,10 @@ def bsmm_tile(prob, i, j, cin=None):
     cin_a = None if cin is None else _c(cin, np.float64)
     if float(prob.beta) != 0.0:
         assert cin_a is not None
+    _, ao, _, bo, trans = _std(prob)
     rc = lib().oracle_bsmm_tile(i, j, M, N, K, _p(r), _p(c), _p(q), _p(am), _p(bm), float(prob.alpha),
-                                _p(_c(prob.A, np.float64)), _p(_c(prob.a_off, np.int64)),
-                                _p(_c(prob.B, np.float64)), _p(_c(prob.b_off, np.int64)),
-                                float(prob.beta), _p(cin_a), _p(out))
+                                _p(_c(prob.A, np.float64)), _p(ao), _p(_c(prob.B, np.float64)), _p(bo),
+                                float(prob.beta), _p(cin_a), _p(out), trans)
     assert rc == 0
     return out
 

@@ -25,6 +25,13 @@
  * Storage (matches the generator module): each stored tile is row-major and
  * contiguous with leading dimension = its column-block size; offset tables are
  * int64 element offsets, -1 for an absent tile.
+ *
+ * Transposed operands (Sec. 2.1 notes that transposed multiplies such as C = A B^T
+ * are handled the same way): bit 0 of `trans` says every A tile A_ik is stored as its
+ * transpose (q_k x r_i, row-major), bit 1 that every B tile B_kj is stored as its
+ * transpose (c_j x q_k). Masks and offset tables keep the (i,k) and (k,j) indexing
+ * here; only the element addressing inside a tile changes, so the arithmetic, its
+ * order and its rounding are the same as for untransposed storage.
  */
 #include <math.h>
 #include <stdint.h>
@@ -85,7 +92,7 @@ int oracle_klists(int M, int N, int K, const uint8_t* a_mask, const uint8_t* b_m
 static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t* c, const int32_t* q,
                      const uint8_t* a_mask, const uint8_t* b_mask, double alpha, const double* A,
                      const int64_t* a_off, const double* B, const int64_t* b_off, double beta,
-                     const double* cin, double* out, double* acc) {
+                     const double* cin, double* out, double* acc, int trans) {
   const int ri = r[i], cj = c[j];
   const int64_t nel = (int64_t)ri * cj;
   for (int64_t e = 0; e < nel; e++) acc[e] = 0.0;
@@ -97,9 +104,12 @@ static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t
     for (int ii = 0; ii < ri; ii++) {
       double* arow = acc + (int64_t)ii * cj;
       for (int kk = 0; kk < qk; kk++) {
-        const double a = At[(int64_t)ii * qk + kk];
-        const double* brow = Bt + (int64_t)kk * cj;
-        for (int jj = 0; jj < cj; jj++) arow[jj] = fma(a, brow[jj], arow[jj]);
+        /* element (ii, kk) of A_ik and (kk, jj) of B_kj */
+        const double a = (trans & 1) ? At[(int64_t)kk * ri + ii] : At[(int64_t)ii * qk + kk];
+        for (int jj = 0; jj < cj; jj++) {
+          const double b = (trans & 2) ? Bt[(int64_t)jj * qk + kk] : Bt[(int64_t)kk * cj + jj];
+          arow[jj] = fma(a, b, arow[jj]);
+        }
       }
     }
   }
@@ -119,7 +129,7 @@ static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t
 int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const int32_t* q,
                 const uint8_t* a_mask, const uint8_t* b_mask, const uint8_t* c_struct,
                 double alpha, const double* A, const int64_t* a_off, const double* B,
-                const int64_t* b_off, double beta, double* C, const int64_t* c_off, int nthreads) {
+                const int64_t* b_off, double beta, double* C, const int64_t* c_off, int nthreads, int trans) {
   int64_t maxel = 1;
   for (int i = 0; i < M; i++)
     for (int j = 0; j < N; j++) {
@@ -150,7 +160,7 @@ int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const i
           continue;
         }
         double* Ct = C + co;
-        one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, Ct, tmp, acc);
+        one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, Ct, tmp, acc, trans);
         memcpy(Ct, tmp, sizeof(double) * (size_t)((int64_t)r[i] * c[j]));
       }
     }
@@ -165,12 +175,12 @@ int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const i
 int oracle_bsmm_tile(int i, int j, int M, int N, int K, const int32_t* r, const int32_t* c,
                      const int32_t* q, const uint8_t* a_mask, const uint8_t* b_mask, double alpha,
                      const double* A, const int64_t* a_off, const double* B, const int64_t* b_off,
-                     double beta, const double* cin, double* out) {
+                     double beta, const double* cin, double* out, int trans) {
   if (i < 0 || i >= M || j < 0 || j >= N) return OR_ERR;
   int64_t nel = (int64_t)r[i] * c[j];
   double* acc = (double*)malloc(sizeof(double) * (size_t)(nel > 0 ? nel : 1));
   if (!acc) return OR_ERR;
-  one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, cin, out, acc);
+  one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, cin, out, acc, trans);
   free(acc);
   return OR_OK;
 }

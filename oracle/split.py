@@ -101,21 +101,29 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
     c = np.asarray(prob_like.col_sizes, np.int64)
     q = np.asarray(prob_like.inner_sizes, np.int64)
     M, N, K = len(r), len(c), len(q)
-    am, bm = prob_like.a_mask, prob_like.b_mask
+    # transposed storage (see the generator's Problem): masks and offsets in (i,k) / (k,j)
+    # indexing, tiles read back to their r_i x q_k / q_k x c_j shape
+    ta, tb = bool(getattr(prob_like, "transa", False)), bool(getattr(prob_like, "transb", False))
+    am = prob_like.a_mask.T if ta else prob_like.a_mask
+    bm = prob_like.b_mask.T if tb else prob_like.b_mask
+    a_off = prob_like.a_off.T if ta else prob_like.a_off
+    b_off = prob_like.b_off.T if tb else prob_like.b_off
     cacheA, cacheB = {}, {}
 
     def a_sl(i, k):
         if (i, k) not in cacheA:
-            o = int(prob_like.a_off[i, k])
-            x = prob_like.A[o:o + r[i] * q[k]].reshape(r[i], q[k])
+            o = int(a_off[i, k])
+            x = (prob_like.A[o:o + r[i] * q[k]].reshape(q[k], r[i]).T if ta
+                 else prob_like.A[o:o + r[i] * q[k]].reshape(r[i], q[k]))
             e, sl, _ = slice_tile(x, s, beta)
             cacheA[(i, k)] = (e, sl)
         return cacheA[(i, k)]
 
     def b_sl(k, j):
         if (k, j) not in cacheB:
-            o = int(prob_like.b_off[k, j])
-            x = prob_like.B[o:o + q[k] * c[j]].reshape(q[k], c[j])
+            o = int(b_off[k, j])
+            x = (prob_like.B[o:o + q[k] * c[j]].reshape(c[j], q[k]).T if tb
+                 else prob_like.B[o:o + q[k] * c[j]].reshape(q[k], c[j]))
             e, sl, _ = slice_tile(x, s, beta)
             cacheB[(k, j)] = (e, sl)
         return cacheB[(k, j)]
