@@ -61,6 +61,8 @@ def parse():
                          "banded_wide: N=32768 band |i-j|<=6 with distance-decaying values (FP64 vs split-fp16); "
                          "clustered: M=N=24576, K=49152 clustered masks, learned vs flop-count schedule")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--trans", default="none", choices=["none", "a", "b", "ab"],
+                    help="dense workload: supply A and/or B as the transposed block matrix (C = A'^T B, A B'^T)")
     ap.add_argument("--other-slices", type=int, nargs="*", default=[3, 4, 5],
                     help="slice counts also timed on the dense workload, each with its error against FP64")
     return ap.parse_args()
@@ -536,10 +538,13 @@ def run_dense(args, rank, world, local):
         if world > 1:
             dist.barrier()
 
-    prob = make_inputs(args.n, args.seed + rank)
+    prob0 = make_inputs(args.n, args.seed + rank)
+    ta, tb = "a" in args.trans, "b" in args.trans
+    prob = G.transposed_storage(prob0, ta, tb) if (ta or tb) else prob0
+    tr = dict(transa=int(ta), transb=int(tb))
     s = args.slices
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster)
+                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster, **tr)
     q = P.bsmm_plan_query(plan)
     F = q["useful_flops"]
     cs = q["c_mask"]
@@ -601,7 +606,7 @@ def run_dense(args, rank, world, local):
     extra = {}
     if rank == 0 and not args.no_fp64:
         plan64 = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                             mode=P.BSMM_FP64, profile=1)
+                             mode=P.BSMM_FP64, profile=1, **tr)
         C64 = torch.zeros_like(C)
         P.bsmm_execute(plan64, 1.0, A, ao, B, bo, 0.0, C64, co)
         torch.cuda.synchronize()
@@ -630,7 +635,7 @@ def run_dense(args, rank, world, local):
             if s2 == s:
                 continue
             plan2 = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                                mode=P.BSMM_SPLIT_BF16, nslices=s2, cluster=args.cluster)
+                                mode=P.BSMM_SPLIT_BF16, nslices=s2, cluster=args.cluster, **tr)
             C2 = torch.zeros_like(C)
             for _ in range(2):
                 P.bsmm_execute(plan2, 1.0, A, ao, B, bo, 0.0, C2, co)
@@ -673,14 +678,16 @@ def run_dense(args, rank, world, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu, row_err = cpu_baseline(prob, cs, Csplit, c_off, args.cpu_seconds)
+        cpu, row_err = cpu_baseline(prob0, cs, Csplit, c_off, args.cpu_seconds)
         extra["split_rel_err_vs_oracle_sampled_rows"] = row_err
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-                "config": {"workload": workload_name(args.n), "mode": f"split_bf16 s={s} (fp32 tensor-core accumulate,"
+                "config": {"workload": workload_name(args.n) + ("" if args.trans == "none" else
+                                                                 f", operands supplied transposed: {args.trans}"),
+                           "mode": f"split_bf16 s={s} (fp32 tensor-core accumulate,"
                            " exact int64 diagonal combine, fp64 recombination)", "useful_flops_per_step": F,
                            "l2": "inputs larger than L2 (A and B 2.1 GB each), no flush",
                            "parallelism": f"replicas x{world}", "seed": args.seed},

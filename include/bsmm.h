@@ -86,8 +86,14 @@ typedef struct {
   int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = 32) */
   int32_t stages;          /* split modes: depth of the shared-memory ring of 32-deep k chunks
                               (k panels in flight), 2..8 and within the 227 KB shared memory of
-                              one CTA (0 = as many as fit in 200 KB) */
-  int32_t reserved[2];     /* must be zero */
+                              one CTA (0 = as many as fit next to the C staging buffer) */
+  int32_t transa;          /* 1: the A arguments describe the K x M block matrix A' and the
+                              product is C = alpha*A'^T*B + beta*C: a_mask and a_off are K x M
+                              (row-major over (k,i)) and tile (k,i) is q_k x r_i row-major */
+  int32_t transb;          /* 1: the B arguments describe the N x K block matrix B' and the
+                              product is C = alpha*A*B'^T + beta*C: b_mask and b_off are N x K
+                              and tile (j,k) is c_j x q_k row-major (Sec. 2.1: transposed
+                              multiplies such as C = A B^T) */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */

@@ -54,7 +54,8 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("nslices", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("transa", ctypes.c_int32),
+                ("transb", ctypes.c_int32)]
 
 
 _lib = None
@@ -181,7 +182,7 @@ class Plan:
 def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *, mode: int = BSMM_FP64,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
               record_timings: int = 0, profile: int = 0, cluster: int = 0, fp64_tile: int = 0,
-              stages: int = 0) -> Plan:
+              stages: int = 0, transa: int = 0, transb: int = 0) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -193,6 +194,8 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     o.debug_checks, o.record_timings, o.profile, o.cluster = debug_checks, record_timings, profile, cluster
     o.fp64_tile = fp64_tile
     o.stages = stages
+    o.transa = transa
+    o.transb = transb
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))

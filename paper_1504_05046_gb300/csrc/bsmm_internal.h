@@ -83,6 +83,7 @@ struct Fp64Args {
   int32_t* err;
   int32_t debug;
   int32_t tile;            // sub-tile edge of the units (64 or 32)
+  int32_t transa, transb;  // transposed operand storage (bsmm_options)
   // batch: per-product arguments in device memory; the schedule then lists batch-wide
   // unit ids, each mapped to (product, unit of that product)
   const Fp64Args* prods;
@@ -123,6 +124,7 @@ struct SplitArgs {
   int16_t* urow;
   int16_t* ucol;
   int32_t kdepth;           // deepest exact FP32 accumulation (inner elements) for s slices
+  int32_t transa, transb;   // transposed operand storage (bsmm_options)
   int32_t* eAmax;           // M: largest exponent of the stored A tiles of a row block
   int32_t* eBmax;           // N
   int32_t* eA;              // M x K

@@ -35,6 +35,8 @@ void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, 
   a.err = (int32_t*)p->d_err.p;
   a.debug = p->opt.debug_checks;
   a.tile = p->f64_tile;
+  a.transa = p->opt.transa;
+  a.transb = p->opt.transb;
   a.prods = nullptr;
   a.unit_prod = a.unit_local = nullptr;
 }
@@ -78,6 +80,8 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
   a.urow = (int16_t*)p->d_urow.p;
   a.ucol = (int16_t*)p->d_ucol.p;
   a.kdepth = split_max_depth(p->s);
+  a.transa = p->opt.transa;
+  a.transb = p->opt.transb;
   a.eA = (int32_t*)p->d_eA.p;
   a.eB = (int32_t*)p->d_eB.p;
   a.eAmax = (int32_t*)p->d_eAmax.p;

@@ -132,24 +132,46 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
 
     double ra[A_PER_T], rb[B_PER_T];
     auto load_chunk = [&](const ChunkIter& c) {
-      const int64_t ao = P.a_off[(int64_t)i * P.K + c.k];
-      const int64_t bo = P.b_off[(int64_t)c.k * P.N + j];
+      // offsets of A_ik and B_kj; transposed storage indexes the tables (k,i) / (j,k)
+      // and keeps every tile transposed (q_k x r_i, c_j x q_k)
+      const int64_t ao = P.transa ? P.a_off[(int64_t)c.k * P.M + i] : P.a_off[(int64_t)i * P.K + c.k];
+      const int64_t bo = P.transb ? P.b_off[(int64_t)j * P.K + c.k] : P.b_off[(int64_t)c.k * P.N + j];
       if (P.debug && tid == 0 && (ao < 0 || bo < 0)) atomicOr(a.err, kErrBadOffset);
-      const double* At = P.A + (ao < 0 ? 0 : ao) + (int64_t)un.r0 * c.qk;
-      const double* Bt = P.B + (bo < 0 ? 0 : bo) + un.c0;
+      const double* At = P.A + (ao < 0 ? 0 : ao);
+      const double* Bt = P.B + (bo < 0 ? 0 : bo);
+      if (!P.transa) {
 #pragma unroll
-      for (int m = 0; m < A_PER_T; m++) {
-        const int e = tid + NT * m;
-        const int row = e / BK, kc = e % BK;
-        const bool ok = ao >= 0 && row < rows && c.kk0 + kc < c.qk;
-        ra[m] = ok ? __ldg(At + (int64_t)row * c.qk + c.kk0 + kc) : 0.0;
+        for (int m = 0; m < A_PER_T; m++) {  // consecutive threads along k
+          const int e = tid + NT * m;
+          const int row = e / BK, kc = e % BK;
+          const bool ok = ao >= 0 && row < rows && c.kk0 + kc < c.qk;
+          ra[m] = ok ? __ldg(At + (int64_t)(un.r0 + row) * c.qk + c.kk0 + kc) : 0.0;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < A_PER_T; m++) {  // consecutive threads along the tile's rows
+          const int e = tid + NT * m;
+          const int row = e % BM, kc = e / BM;
+          const bool ok = ao >= 0 && row < rows && c.kk0 + kc < c.qk;
+          ra[m] = ok ? __ldg(At + (int64_t)(c.kk0 + kc) * ri + un.r0 + row) : 0.0;
+        }
       }
+      if (!P.transb) {
 #pragma unroll
-      for (int m = 0; m < B_PER_T; m++) {
-        const int e = tid + NT * m;
-        const int kr = e / BN, cc = e % BN;
-        const bool ok = bo >= 0 && cc < cols && c.kk0 + kr < c.qk;
-        rb[m] = ok ? __ldg(Bt + (int64_t)(c.kk0 + kr) * cj + cc) : 0.0;
+        for (int m = 0; m < B_PER_T; m++) {  // consecutive threads along the tile's columns
+          const int e = tid + NT * m;
+          const int kr = e / BN, cc = e % BN;
+          const bool ok = bo >= 0 && cc < cols && c.kk0 + kr < c.qk;
+          rb[m] = ok ? __ldg(Bt + (int64_t)(c.kk0 + kr) * cj + un.c0 + cc) : 0.0;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < B_PER_T; m++) {  // consecutive threads along k
+          const int e = tid + NT * m;
+          const int kr = e % BK, cc = e / BK;
+          const bool ok = bo >= 0 && cc < cols && c.kk0 + kr < c.qk;
+          rb[m] = ok ? __ldg(Bt + (int64_t)(un.c0 + cc) * c.qk + c.kk0 + kr) : 0.0;
+        }
       }
     };
     auto advance = [&](ChunkIter& c) {
@@ -173,15 +195,32 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
     if (have) load_chunk(it);
     while (have) {
       const int kv = min(BK, it.qk - it.kk0);  // valid inner indices of the chunk being staged
+      // staged as sA[kk][row], sB[kk][col] whichever order the loads took
+      if (!P.transa) {
 #pragma unroll
-      for (int m = 0; m < A_PER_T; m++) {
-        const int e = tid + NT * m;
-        sA[e % BK][e / BK] = ra[m];
+        for (int m = 0; m < A_PER_T; m++) {
+          const int e = tid + NT * m;
+          sA[e % BK][e / BK] = ra[m];
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < A_PER_T; m++) {
+          const int e = tid + NT * m;
+          sA[e / BM][e % BM] = ra[m];
+        }
       }
+      if (!P.transb) {
 #pragma unroll
-      for (int m = 0; m < B_PER_T; m++) {
-        const int e = tid + NT * m;
-        sB[e / BN][e % BN] = rb[m];
+        for (int m = 0; m < B_PER_T; m++) {
+          const int e = tid + NT * m;
+          sB[e / BN][e % BN] = rb[m];
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < B_PER_T; m++) {
+          const int e = tid + NT * m;
+          sB[e % BK][e / BK] = rb[m];
+        }
       }
       __syncthreads();
       advance(it);

@@ -426,8 +426,8 @@ bsmm_status validate_options(const bsmm_options& o) {
   if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) return set_error("stages must be 0 or 2..8"), BSMM_ERR_INVALID;
   if (o.mode != BSMM_FP64 && o.stages && split_smem_bytes(o.nslices, split_tile_n(o.nslices), o.stages) > kMaxSmemPerCta)
     return set_error("stages: the ring does not fit the shared memory of one CTA"), BSMM_ERR_UNSUPPORTED;
-  for (int r : o.reserved)
-    if (r) return set_error("reserved option fields must be zero"), BSMM_ERR_INVALID;
+  if ((o.transa != 0 && o.transa != 1) || (o.transb != 0 && o.transb != 1))
+    return set_error("transa and transb must be 0 or 1"), BSMM_ERR_INVALID;
   return BSMM_OK;
 }
 
@@ -510,8 +510,14 @@ bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, in
   p->Ntot = p->co[N];
   p->am.resize((size_t)M * K);
   p->bm.resize((size_t)K * N);
-  for (int64_t t = 0; t < (int64_t)M * K; t++) p->am[t] = a_mask[t] ? 1 : 0;
-  for (int64_t t = 0; t < (int64_t)K * N; t++) p->bm[t] = b_mask[t] ? 1 : 0;
+  // masks in the (i,k) / (k,j) orientation the planner works in (transposed inputs are
+  // read transposed; the kernels index the caller's offset tables accordingly)
+  for (int i = 0; i < M; i++)
+    for (int k = 0; k < K; k++)
+      p->am[(int64_t)i * K + k] = (o.transa ? a_mask[(int64_t)k * M + i] : a_mask[(int64_t)i * K + k]) ? 1 : 0;
+  for (int k = 0; k < K; k++)
+    for (int j = 0; j < N; j++)
+      p->bm[(int64_t)k * N + j] = (o.transb ? b_mask[(int64_t)j * K + k] : b_mask[(int64_t)k * N + j]) ? 1 : 0;
 
   // S_C = boolean product of the masks (bitset rows), united with the C mask;
   // per C tile the ascending k-list; the useful flop count.

@@ -242,16 +242,17 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
   const int t = isA ? a.a_tiles[b] : a.b_tiles[b - a.n_a_tiles];
   int rows, cols;
   int64_t off;
-  if (isA) {
+  if (isA) {  // (transposed storage indexes the caller's tables (k,i) / (j,k); the
+              // maximum does not depend on the element order inside a tile)
     const int i = t / a.K, k = t % a.K;
     rows = a.r[i];
     cols = a.q[k];
-    off = a.a_off[t];
+    off = a.transa ? a.a_off[(int64_t)k * a.M + i] : a.a_off[t];
   } else {
     const int k = t / a.N, j = t % a.N;
     rows = a.q[k];
     cols = a.c[j];
-    off = a.b_off[t];
+    off = a.transb ? a.b_off[(int64_t)j * a.K + k] : a.b_off[t];
   }
   const double* x = (isA ? a.A : a.B) + (off < 0 ? 0 : off);
   const int64_t n = (int64_t)rows * cols;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       if (m < a.Mtot) {
         i = a.row_tile[m];
         present = a.am[(int64_t)i * a.K + kt] != 0;
-        off = a.a_off[(int64_t)i * a.K + kt];
+        off = a.transa ? a.a_off[(int64_t)kt * a.M + i] : a.a_off[(int64_t)i * a.K + kt];
         if (present && off < 0) {
           atomicOr(a.err, kErrBadOffset);
           present = false;
@@ -469,10 +470,11 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
         e = a.eA[(int64_t)i * a.K + kt];
       }
       const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
+      const int64_t ri = m < a.Mtot ? a.r[i] : 0;
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
+      for (int u = 0; u < 8; u++) {  // element (lr, k) of A_ik, stored transposed or not
         const int k = kc * kSplitKC + ch * 8 + u;
-        x[u] = (present && k < q) ? __ldg(a.A + off + lr * q + k) : 0.0;
+        x[u] = (present && k < q) ? __ldg(a.A + off + (a.transa ? (int64_t)k * ri + lr : lr * q + k)) : 0.0;
       }
       slice_store8<T>(x, e, s, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
     }
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
         j = a.col_tile[n];
         cj = a.c[j];
         present = a.bm[(int64_t)kt * a.N + j] != 0;
-        off = a.b_off[(int64_t)kt * a.N + j];
+        off = a.transb ? a.b_off[(int64_t)j * a.K + kt] : a.b_off[(int64_t)kt * a.N + j];
         if (present && off < 0) {
           atomicOr(a.err, kErrBadOffset);
           present = false;
@@ -506,9 +508,9 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       }
       const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
+      for (int u = 0; u < 8; u++) {  // element (k, lc) of B_kj, stored transposed or not
         const int k = kc * kSplitKC + ch * 8 + u;
-        x[u] = (present && k < q) ? __ldg(a.B + off + (int64_t)k * cj + lc) : 0.0;
+        x[u] = (present && k < q) ? __ldg(a.B + off + (a.transb ? lc * q + k : (int64_t)k * cj + lc)) : 0.0;
       }
       slice_store8<T>(x, e, s, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
     }

@@ -21,7 +21,8 @@ def run_lib(prob, c_struct, C0, c_off, *, mode=P.BSMM_FP64, nslices=6, c_mask=No
     if plan is None:
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, c_mask,
                            mode=mode, nslices=nslices, schedule=schedule, max_ctas=max_ctas, debug_checks=debug,
-                           record_timings=record_timings, cluster=cluster, stages=stages)
+                           record_timings=record_timings, cluster=cluster, stages=stages,
+                           transa=int(getattr(prob, "transa", False)), transb=int(getattr(prob, "transb", False)))
     if ctas is not None:
         P.bsmm_plan_set_ctas(plan, ctas)
     if costs is not None:
