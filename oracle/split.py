@@ -37,6 +37,14 @@ power-of-two scale per tile:
 Because the sum is exact before its single rounding, the value does not depend on
 the order in which tile pairs, slice pairs or k blocks are added.
 
+Row/column scaling (scaling="rows"): the same slicing with one exponent per row of an
+A tile and per column of a B tile (e_A(i,k)[ii], e_B(k,j)[jj]); an all-zero row or
+column has zero slices and takes no part in the maxima below. The contribution of a
+tile pair to element (ii, jj) is T[ii,jj] * 2^(e_A[ii] + e_B[jj] - beta*(s+1)), and the
+accumulator unit is per element: L[ii,jj] = Emax_A(row ii) + Emax_B(col jj) - beta*(s+1)
+- GUARD_BITS, with Emax_A(row) the largest exponent of that row over its stored tiles
+(0 when none) and Emax_B(col) likewise.
+
 All integer matrix products below go through a float64 matmul: every entry is an
 integer of magnitude below 2^53, so the library routine returns it exactly in
 any summation order.
@@ -75,6 +83,22 @@ def slice_tile(x: np.ndarray, s: int, beta: int = BETA_BITS):
     return e, slices, rho
 
 
+def slice_rows(x: np.ndarray, s: int, beta: int = BETA_BITS):
+    """Error-free slicing with one exponent per row. Returns (e per row, nonzero-row
+    flags, [N_1..N_s], rho_s residual in units of 2^e per row); an all-zero row has
+    e = 0 and zero slices."""
+    x = np.asarray(x, np.float64)
+    e = np.array([tile_exponent(row) for row in x], np.int64) if x.shape[0] else np.zeros(0, np.int64)
+    nz = np.array([bool(np.any(row != 0)) for row in x], bool) if x.shape[0] else np.zeros(0, bool)
+    rho = np.ldexp(x, -e[:, None]) if x.size else x.copy()
+    slices = []
+    for t in range(1, s + 1):
+        n_t = np.rint(np.ldexp(rho, beta * t))
+        rho = rho - np.ldexp(n_t, -beta * t)
+        slices.append(n_t)
+    return e, nz, slices, rho
+
+
 def pair_integer(na, nb, s: int, beta: int = BETA_BITS) -> np.ndarray:
     """T = sum_d S_d 2^(beta(s+1-d)) for one tile pair, as an int64 matrix."""
     r = na[0].shape[0]
@@ -93,10 +117,14 @@ def pair_integer(na, nb, s: int, beta: int = BETA_BITS) -> np.ndarray:
     return T
 
 
-def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, tiles=None):
+def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, tiles=None, scaling: str = "tile"):
     """Split-mode product in place on the C arena (numpy arrays). ``prob_like``
     carries row_sizes, col_sizes, inner_sizes, a_mask, b_mask, a_off, b_off, A, B,
-    alpha, beta. ``tiles`` restricts the work to a list of (i, j) C tiles."""
+    alpha, beta. ``tiles`` restricts the work to a list of (i, j) C tiles; ``scaling``
+    is "tile" (one exponent per tile) or "rows" (per row of A, per column of B)."""
+    if scaling == "rows":
+        return _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles)
+    assert scaling == "tile", scaling
     r = np.asarray(prob_like.row_sizes, np.int64)
     c = np.asarray(prob_like.col_sizes, np.int64)
     q = np.asarray(prob_like.inner_sizes, np.int64)
@@ -151,6 +179,77 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
             sh = eA + eB - beta * (s + 1) - L
             exact = exact + (T * (1 << sh) if sh >= 0 else T // (1 << -sh))  # floor below 2^L
         acc = np.array([math.ldexp(float(v), L) for v in exact.reshape(-1)], np.float64).reshape(r[i], c[j])
+        o = int(c_off[i, j])
+        ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
+        u = alpha * acc
+        if bet != 0.0:
+            ct[...] = u + bet * ct
+        else:
+            ct[...] = u
+    return C
+
+
+def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
+    """bsmm_split with one exponent per row of A and per column of B."""
+    r = np.asarray(prob_like.row_sizes, np.int64)
+    c = np.asarray(prob_like.col_sizes, np.int64)
+    q = np.asarray(prob_like.inner_sizes, np.int64)
+    M, N, K = len(r), len(c), len(q)
+    ta, tb = bool(getattr(prob_like, "transa", False)), bool(getattr(prob_like, "transb", False))
+    am = prob_like.a_mask.T if ta else prob_like.a_mask
+    bm = prob_like.b_mask.T if tb else prob_like.b_mask
+    a_off = prob_like.a_off.T if ta else prob_like.a_off
+    b_off = prob_like.b_off.T if tb else prob_like.b_off
+    cacheA, cacheB = {}, {}
+
+    def a_sl(i, k):  # per row of A_ik: (e[r_i], nonzero[r_i], slices)
+        if (i, k) not in cacheA:
+            o = int(a_off[i, k])
+            x = (prob_like.A[o:o + r[i] * q[k]].reshape(q[k], r[i]).T if ta
+                 else prob_like.A[o:o + r[i] * q[k]].reshape(r[i], q[k]))
+            e, nz, sl, _ = slice_rows(x, s, beta)
+            cacheA[(i, k)] = (e, nz, sl)
+        return cacheA[(i, k)]
+
+    def b_sl(k, j):  # per column of B_kj: slicing of the transpose, slices turned back
+        if (k, j) not in cacheB:
+            o = int(b_off[k, j])
+            x = (prob_like.B[o:o + q[k] * c[j]].reshape(c[j], q[k]).T if tb
+                 else prob_like.B[o:o + q[k] * c[j]].reshape(q[k], c[j]))
+            e, nz, sl, _ = slice_rows(x.T, s, beta)
+            cacheB[(k, j)] = (e, nz, [t.T for t in sl])
+        return cacheB[(k, j)]
+
+    def emax(vals, n):  # largest exponent of nonzero rows, per row (0 when none)
+        out = np.full(n, -(1 << 40), np.int64)
+        for e, nz in vals:
+            out = np.where(nz, np.maximum(out, e), out)
+        return np.where(out == -(1 << 40), 0, out)
+
+    def emax_a(i):
+        return emax([a_sl(i, k)[:2] for k in range(K) if am[i, k] and r[i] > 0 and q[k] > 0], int(r[i]))
+
+    def emax_b(j):
+        return emax([b_sl(k, j)[:2] for k in range(K) if bm[k, j] and c[j] > 0 and q[k] > 0], int(c[j]))
+
+    shift = np.vectorize(lambda t, h: t << h if h >= 0 else t >> (-h), otypes=[object])  # floor below 2^L
+    todo = tiles if tiles is not None else [(i, j) for i in range(M) for j in range(N) if c_struct[i, j]]
+    alpha, bet = float(prob_like.alpha), float(prob_like.beta)
+    for (i, j) in todo:
+        L = emax_a(i)[:, None] + emax_b(j)[None, :] - beta * (s + 1) - GUARD_BITS
+        exact = np.zeros((r[i], c[j]), dtype=object)
+        exact[...] = 0
+        for k in range(K):
+            if not (am[i, k] and bm[k, j]):
+                continue
+            eA, _, na = a_sl(i, k)
+            eB, _, nb = b_sl(k, j)
+            T = pair_integer(na, nb, s, beta).astype(object)
+            sh = eA[:, None] + eB[None, :] - beta * (s + 1) - L
+            if T.size:
+                exact = exact + shift(T, sh)
+        acc = np.array([math.ldexp(float(v), int(l)) for v, l in zip(exact.reshape(-1), L.reshape(-1))],
+                       np.float64).reshape(r[i], c[j])
         o = int(c_off[i, j])
         ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
         u = alpha * acc
