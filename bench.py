@@ -61,6 +61,8 @@ def parse():
                          "banded_wide: N=32768 band |i-j|<=6 with distance-decaying values (FP64 vs split-fp16); "
                          "clustered: M=N=24576, K=49152 clustered masks, learned vs flop-count schedule")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--split-scale", default="tile", choices=["tile", "rows"],
+                    help="split modes: one power-of-two scale per tile, or per row of A and column of B")
     ap.add_argument("--trans", default="none", choices=["none", "a", "b", "ab"],
                     help="dense workload: supply A and/or B as the transposed block matrix (C = A'^T B, A B'^T)")
     ap.add_argument("--other-slices", type=int, nargs="*", default=[3, 4, 5],
@@ -396,6 +398,8 @@ def run_single(args, rank, world):
     mode = getattr(P, w["mode"])
 
     def setup(seed, mode, **opt):
+        if mode != P.BSMM_FP64:
+            opt.setdefault("split_scale", int(args.split_scale == "rows"))
         prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,
                            nslices=s, profile=1, **opt)
@@ -474,7 +478,8 @@ def run_single(args, rank, world):
     pk, pk_src = peaks()
     head_split = w["head"] == "split"
     split = {"value": tf(ms_split), "ms_per_step": ms_split, "kernel_ms": k_split,
-             "mode": f"{w['mode'][5:].lower()} s={s}", "rel_err_vs_fp64": err}
+             "mode": f"{w['mode'][5:].lower()} s={s}" + (", scale per row/column" if args.split_scale == "rows" else ""),
+             "rel_err_vs_fp64": err}
     fp64 = {"value": tf(ms64), "ms_per_step": ms64, "kernel_ms": k64}
     pair = s * (s + 1) / 2 * F
     if head_split:
@@ -542,9 +547,10 @@ def run_dense(args, rank, world, local):
     ta, tb = "a" in args.trans, "b" in args.trans
     prob = G.transposed_storage(prob0, ta, tb) if (ta or tb) else prob0
     tr = dict(transa=int(ta), transb=int(tb))
+    sc = dict(split_scale=int(args.split_scale == "rows"))
     s = args.slices
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster, **tr)
+                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster, **tr, **sc)
     q = P.bsmm_plan_query(plan)
     F = q["useful_flops"]
     cs = q["c_mask"]
@@ -635,7 +641,7 @@ def run_dense(args, rank, world, local):
             if s2 == s:
                 continue
             plan2 = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                                mode=P.BSMM_SPLIT_BF16, nslices=s2, cluster=args.cluster, **tr)
+                                mode=P.BSMM_SPLIT_BF16, nslices=s2, cluster=args.cluster, **tr, **sc)
             C2 = torch.zeros_like(C)
             for _ in range(2):
                 P.bsmm_execute(plan2, 1.0, A, ao, B, bo, 0.0, C2, co)
@@ -688,7 +694,9 @@ def run_dense(args, rank, world, local):
                 "config": {"workload": workload_name(args.n) + ("" if args.trans == "none" else
                                                                  f", operands supplied transposed: {args.trans}"),
                            "mode": f"split_bf16 s={s} (fp32 tensor-core accumulate,"
-                           " exact int64 diagonal combine, fp64 recombination)", "useful_flops_per_step": F,
+                           " exact int64 diagonal combine, fp64 recombination)" +
+                           (", one scale per row of A and column of B" if args.split_scale == "rows" else ""),
+                           "useful_flops_per_step": F,
                            "l2": "inputs larger than L2 (A and B 2.1 GB each), no flush",
                            "parallelism": f"replicas x{world}", "seed": args.seed},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}

@@ -94,6 +94,11 @@ typedef struct {
                               product is C = alpha*A*B'^T + beta*C: b_mask and b_off are N x K
                               and tile (j,k) is c_j x q_k row-major (Sec. 2.1: transposed
                               multiplies such as C = A B^T) */
+  int32_t split_scale;     /* split modes: 0 = one power-of-two scale per tile (default);
+                              1 = one per row of each A tile and per column of each B tile, for
+                              tiles whose rows or columns span many binades (an all-zero row
+                              or column takes no part in the maxima that set the accumulator's
+                              unit) */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */

@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
                 ("max_ctas", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("transa", ctypes.c_int32),
-                ("transb", ctypes.c_int32)]
+                ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32)]
 
 
 _lib = None
@@ -182,7 +182,7 @@ class Plan:
 def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *, mode: int = BSMM_FP64,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
               record_timings: int = 0, profile: int = 0, cluster: int = 0, fp64_tile: int = 0,
-              stages: int = 0, transa: int = 0, transb: int = 0) -> Plan:
+              stages: int = 0, transa: int = 0, transb: int = 0, split_scale: int = 0) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -196,6 +196,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     o.stages = stages
     o.transa = transa
     o.transb = transb
+    o.split_scale = split_scale
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))

@@ -39,6 +39,7 @@ size_t split_smem_bytes(int s, int tn, int stages);
 constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory of one CTA
 constexpr size_t kSplitBarBytes = 256;          // mbarriers, TMEM slot and flags after the ring
 constexpr int16_t kNonUniform = 0x7FFF;         // scale-class sentinel (offsets are <= 0)
+constexpr int32_t kZeroLine = -(1 << 20);       // exponent of an all-zero row or column
 int split_max_depth(int s);
 constexpr int kSplitDefaultCluster = 2;
 // Largest number of clusters of `cl` contraction CTAs that can be resident at once.
@@ -125,6 +126,14 @@ struct SplitArgs {
   int16_t* ucol;
   int32_t kdepth;           // deepest exact FP32 accumulation (inner elements) for s slices
   int32_t transa, transb;   // transposed operand storage (bsmm_options)
+  // per-row / per-column scaling (split_scale = 1): exponents of every row of every A tile
+  // (K x Mtot) and column of every B tile (K x Ntot; kZeroLine for an all-zero line), and
+  // the row / column maxima that set the accumulator unit (Mtot, Ntot)
+  int32_t rowscale;
+  int32_t* eArow;
+  int32_t* eBcol;
+  int32_t* eAmaxr;
+  int32_t* eBmaxc;
   int32_t* eAmax;           // M: largest exponent of the stored A tiles of a row block
   int32_t* eBmax;           // N
   int32_t* eA;              // M x K
@@ -220,6 +229,7 @@ struct bsmm_plan_s {
   // device memory
   bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
   bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_presBg, d_apk_off, d_bpk_off, d_apk, d_bpk;
+  bsmm::DevBuf d_eArow, d_eBcol, d_eAmaxr, d_eBmaxc;
   bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_urow, d_ucol, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
   bsmm::DevBuf d_err, d_timings, d_unit_cta;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;

@@ -82,6 +82,11 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
   a.kdepth = split_max_depth(p->s);
   a.transa = p->opt.transa;
   a.transb = p->opt.transb;
+  a.rowscale = p->opt.split_scale;
+  a.eArow = (int32_t*)p->d_eArow.p;
+  a.eBcol = (int32_t*)p->d_eBcol.p;
+  a.eAmaxr = (int32_t*)p->d_eAmaxr.p;
+  a.eBmaxc = (int32_t*)p->d_eBmaxc.p;
   a.eA = (int32_t*)p->d_eA.p;
   a.eB = (int32_t*)p->d_eB.p;
   a.eAmax = (int32_t*)p->d_eAmax.p;

@@ -404,6 +404,12 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   if ((st = dev_alloc(p->d_rowexp, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * Mtot))) != BSMM_OK) return st;
   p->colexp_ld = (Ntot + 63) / 64 * 64 + 64;  // padded rows: aligned 16-byte loads past the last column
   if ((st = dev_alloc(p->d_colexp, sizeof(int16_t) * ((int64_t)K * p->colexp_ld + 64))) != BSMM_OK) return st;
+  if (p->opt.split_scale) {
+    if ((st = dev_alloc(p->d_eArow, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)K * Mtot))) != BSMM_OK) return st;
+    if ((st = dev_alloc(p->d_eBcol, sizeof(int32_t) * std::max<int64_t>(1, (int64_t)K * Ntot))) != BSMM_OK) return st;
+    if ((st = dev_alloc(p->d_eAmaxr, sizeof(int32_t) * std::max<int64_t>(1, Mtot))) != BSMM_OK) return st;
+    if ((st = dev_alloc(p->d_eBmaxc, sizeof(int32_t) * std::max<int64_t>(1, Ntot))) != BSMM_OK) return st;
+  }
   if ((st = dev_alloc(p->d_urow, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * p->RB))) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_ucol, sizeof(int16_t) * std::max<int64_t>(1, (int64_t)K * p->CB))) != BSMM_OK) return st;
   // exponents of absent tiles stay 0 (their slices are zero, so the scale is never used)
@@ -428,6 +434,7 @@ bsmm_status validate_options(const bsmm_options& o) {
     return set_error("stages: the ring does not fit the shared memory of one CTA"), BSMM_ERR_UNSUPPORTED;
   if ((o.transa != 0 && o.transa != 1) || (o.transb != 0 && o.transb != 1))
     return set_error("transa and transb must be 0 or 1"), BSMM_ERR_INVALID;
+  if (o.split_scale != 0 && o.split_scale != 1) return set_error("split_scale must be 0 or 1"), BSMM_ERR_INVALID;
   return BSMM_OK;
 }
 
@@ -453,6 +460,7 @@ void bsmm_destroy(bsmm_plan_t p) {
   DevBuf* bufs[] = {&p->d_r, &p->d_c, &p->d_q, &p->d_ro, &p->d_co, &p->d_kptr, &p->d_klist, &p->d_cs,
                     &p->d_units, &p->d_sched_ptr, &p->d_sched_units, &p->d_row_tile, &p->d_col_tile,
                     &p->d_presA, &p->d_presB, &p->d_presBg, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
+                    &p->d_eArow, &p->d_eBcol, &p->d_eAmaxr, &p->d_eBmaxc,
                     &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_urow, &p->d_ucol, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
                     &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};

@@ -256,6 +256,30 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
   }
   const double* x = (isA ? a.A : a.B) + (off < 0 ? 0 : off);
   const int64_t n = (int64_t)rows * cols;
+  if (a.rowscale) {
+    // one exponent per row of an A tile / per column of a B tile (the tile-wide exponent
+    // below is still computed: it is not used for slicing in this mode)
+    const int i_or_k = isA ? t / a.K : t / a.N;
+    const int k_or_j = isA ? t % a.K : t % a.N;
+    const int nl = isA ? rows : cols;    // lines
+    const int len = isA ? cols : rows;   // elements per line
+    const bool tr = isA ? a.transa != 0 : a.transb != 0;
+    for (int l = threadIdx.x; l < nl && off >= 0; l += blockDim.x) {
+      double lm = 0.0;
+      for (int u = 0; u < len; u++) {
+        // element u of line l: A row l is (l, u), B column l is (u, l); stored transposed or not
+        const int64_t at = isA ? (tr ? (int64_t)u * rows + l : (int64_t)l * cols + u)
+                               : (tr ? (int64_t)l * rows + u : (int64_t)u * cols + l);
+        lm = fmax(lm, fabs(__ldg(x + at)));
+      }
+      int e = kZeroLine;
+      if (lm > 0.0 && lm <= 1.7976931348623157e308) frexp(lm, &e);
+      if (isA)
+        a.eArow[(int64_t)k_or_j * a.Mtot + a.ro[i_or_k] + l] = e;
+      else
+        a.eBcol[(int64_t)i_or_k * a.Ntot + a.co[k_or_j] + l] = e;
+    }
+  }
   double mx = 0.0;
   int bad = 0;
   if (off >= 0) {
@@ -339,6 +363,46 @@ __global__ void __launch_bounds__(256) split_scale_kernel(SplitArgs a) {
       const int k = (int)(e / n);
       const bool pres = a.bm[(int64_t)k * a.N + t] && a.q[k] > 0;
       a.colexp[(int64_t)k * a.colexp_ld + n0 + e % n] = (int16_t)(pres ? a.eB[(int64_t)k * a.N + t] - em : 0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- kernel 1b': line scales
+// Row/column scaling: one thread per row m of A (per column n of B): Emax = the largest
+// exponent of that line over its stored tiles (all-zero lines excluded; 0 when none), and
+// rowexp[k][m] = e(m, k) - Emax (colexp likewise), 0 where there is no tile or the line is
+// zero there (its slices are zero).
+__global__ void __launch_bounds__(256) split_scale_lines_kernel(SplitArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < a.Mtot) {
+    const int64_t m = t;
+    const int i = a.row_tile[m];
+    int em = INT_MIN;
+    for (int k = 0; k < a.K; k++) {
+      const int e = a.eArow[(int64_t)k * a.Mtot + m];
+      if (a.am[(int64_t)i * a.K + k] && a.q[k] > 0 && e != kZeroLine) em = max(em, e);
+    }
+    if (em == INT_MIN) em = 0;
+    a.eAmaxr[m] = em;
+    for (int k = 0; k < a.K; k++) {
+      const int e = a.eArow[(int64_t)k * a.Mtot + m];
+      const bool pres = a.am[(int64_t)i * a.K + k] && a.q[k] > 0 && e != kZeroLine;
+      a.rowexp[(int64_t)k * a.Mtot + m] = (int16_t)(pres ? e - em : 0);
+    }
+  } else if (t < a.Mtot + a.Ntot) {
+    const int64_t n = t - a.Mtot;
+    const int j = a.col_tile[n];
+    int em = INT_MIN;
+    for (int k = 0; k < a.K; k++) {
+      const int e = a.eBcol[(int64_t)k * a.Ntot + n];
+      if (a.bm[(int64_t)k * a.N + j] && a.q[k] > 0 && e != kZeroLine) em = max(em, e);
+    }
+    if (em == INT_MIN) em = 0;
+    a.eBmaxc[n] = em;
+    for (int k = 0; k < a.K; k++) {
+      const int e = a.eBcol[(int64_t)k * a.Ntot + n];
+      const bool pres = a.bm[(int64_t)k * a.N + j] && a.q[k] > 0 && e != kZeroLine;
+      a.colexp[(int64_t)k * a.colexp_ld + n] = (int16_t)(pres ? e - em : 0);
     }
   }
 }
@@ -467,7 +531,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
           atomicOr(a.err, kErrBadOffset);
           present = false;
         }
-        e = a.eA[(int64_t)i * a.K + kt];
+        e = a.rowscale ? a.eArow[(int64_t)kt * a.Mtot + m] : a.eA[(int64_t)i * a.K + kt];
       }
       const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
       const int64_t ri = m < a.Mtot ? a.r[i] : 0;
@@ -504,7 +568,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
           atomicOr(a.err, kErrBadOffset);
           present = false;
         }
-        e = a.eB[(int64_t)kt * a.N + j];
+        e = a.rowscale ? a.eBcol[(int64_t)kt * a.Ntot + n] : a.eB[(int64_t)kt * a.N + j];
       }
       const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
 #pragma unroll
@@ -1063,12 +1127,17 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       // stores whole rows, lane = column, so a store instruction writes one or two
       // contiguous row segments instead of 32 scattered elements.
       if (ok) {
-        const int Lrow = row_ok ? P.eAmax[P.row_tile[m]] - kSplitBeta * (S + 1) - kSplitGuard : 0;
+        // the accumulator's unit 2^L: per row block and column block of tiles, or per row and
+        // column with row/column scaling
+        const int Lrow =
+            row_ok ? (P.rowscale ? P.eAmaxr[m] : P.eAmax[P.row_tile[m]]) - kSplitBeta * (S + 1) - kSplitGuard : 0;
         double* srow = cstage + row * (TN + 1) + half * TH;
 #pragma unroll
         for (int c = 0; c < TH; c++) {
           const int64_t n = n0 + c;
-          srow[c] = (row_ok && n < P.Ntot) ? acc_to_double(acc[c], Lrow + P.eBmax[P.col_tile[n]]) : 0.0;
+          srow[c] = (row_ok && n < P.Ntot)
+                        ? acc_to_double(acc[c], Lrow + (P.rowscale ? P.eBmaxc[n] : P.eBmax[P.col_tile[n]]))
+                        : 0.0;
         }
       }
       asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
@@ -1189,7 +1258,14 @@ int max_clusters_s(int cl, int stages) {
 
 cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k) {
   if (a.n_a_tiles + a.n_b_tiles > 0) split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
-  if (a.M + a.N > 0) split_scale_kernel<<<a.M + a.N, 256, 0, st>>>(a);
+  if (a.rowscale) {
+    // the per-tile maxima (eAmax/eBmax) are not used in this mode; the line kernel writes
+    // rowexp/colexp and the line maxima
+    const int64_t lines = a.Mtot + a.Ntot;
+    if (lines > 0) split_scale_lines_kernel<<<(unsigned)((lines + 255) / 256), 256, 0, st>>>(a);
+  } else if (a.M + a.N > 0) {
+    split_scale_kernel<<<a.M + a.N, 256, 0, st>>>(a);
+  }
   const int64_t ncls = (int64_t)a.K * (a.RB + a.CB);
   if (a.urow && ncls > 0) split_class_kernel<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[++*k], st);
