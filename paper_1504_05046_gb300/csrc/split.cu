@@ -534,12 +534,12 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
         e = a.rowscale ? a.eArow[(int64_t)kt * a.Mtot + m] : a.eA[(int64_t)i * a.K + kt];
       }
       const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
-      const int64_t ri = m < a.Mtot ? a.r[i] : 0;
+      // element (lr, k) of A_ik at line + k * step, stored transposed or not
+      const int64_t step = a.transa ? (m < a.Mtot ? a.r[i] : 0) : 1;
+      const double* line = a.A + off + (a.transa ? lr : lr * q);
+      const int k0 = kc * kSplitKC + ch * 8;
 #pragma unroll
-      for (int u = 0; u < 8; u++) {  // element (lr, k) of A_ik, stored transposed or not
-        const int k = kc * kSplitKC + ch * 8 + u;
-        x[u] = (present && k < q) ? __ldg(a.A + off + (a.transa ? (int64_t)k * ri + lr : lr * q + k)) : 0.0;
-      }
+      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : 0.0;
       slice_store8<T>(x, e, s, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
     }
   } else {
@@ -571,11 +571,12 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
         e = a.rowscale ? a.eBcol[(int64_t)kt * a.Ntot + n] : a.eB[(int64_t)kt * a.N + j];
       }
       const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
+      // element (k, lc) of B_kj at line + k * step, stored transposed or not
+      const int64_t step = a.transb ? 1 : cj;
+      const double* line = a.B + off + (a.transb ? lc * q : lc);
+      const int k0 = kc * kSplitKC + ch * 8;
 #pragma unroll
-      for (int u = 0; u < 8; u++) {  // element (k, lc) of B_kj, stored transposed or not
-        const int k = kc * kSplitKC + ch * 8 + u;
-        x[u] = (present && k < q) ? __ldg(a.B + off + (a.transb ? lc * q + k : (int64_t)k * cj + lc)) : 0.0;
-      }
+      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : 0.0;
       slice_store8<T>(x, e, s, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
     }
   }
