@@ -236,14 +236,11 @@ __device__ __forceinline__ uint32_t swz64(int row, int k) {
 
 
 // ---------------------------------------------------------------- kernel 1: exponents
-__global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
-  const int b = blockIdx.x;
-  const bool isA = b < a.n_a_tiles;
-  const int t = isA ? a.a_tiles[b] : a.b_tiles[b - a.n_a_tiles];
-  int rows, cols;
-  int64_t off;
-  if (isA) {  // (transposed storage indexes the caller's tables (k,i) / (j,k); the
-              // maximum does not depend on the element order inside a tile)
+// The caller's offset of stored tile t of A (isA) or B; transposed storage indexes the
+// tables (k,i) / (j,k) (the maximum does not depend on the element order in a tile).
+__device__ __forceinline__ void tile_geometry(const SplitArgs& a, bool isA, int t, int& rows, int& cols,
+                                              int64_t& off) {
+  if (isA) {
     const int i = t / a.K, k = t % a.K;
     rows = a.r[i];
     cols = a.q[k];
@@ -254,69 +251,102 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
     cols = a.c[j];
     off = a.transb ? a.b_off[(int64_t)j * a.K + k] : a.b_off[t];
   }
+}
+
+// Magnitude of a double as its bit pattern without the sign: for non-negative doubles the
+// bit patterns order like the values, so maxima are taken with integer instructions
+// (GB300's FP64 pipe is narrow). A pattern at or above kInfBits is an infinity or a NaN.
+constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+__device__ __forceinline__ unsigned long long mag_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & kAbsMask;
+}
+
+// Smallest e with m < 2^e for the magnitude bits m of a finite nonzero double
+// (m = f 2^e with f in [0.5, 1), as frexp gives; subnormals included).
+__device__ __forceinline__ int exponent_above(unsigned long long m) {
+  const int be = (int)(m >> 52);
+  if (be) return be - 1022;
+  return -1022 - (__clzll((long long)m) - 12);  // subnormal: leading one at bit 63 - clz
+}
+
+__global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
+  const int b = blockIdx.x;
+  const bool isA = b < a.n_a_tiles;
+  const int t = isA ? a.a_tiles[b] : a.b_tiles[b - a.n_a_tiles];
+  int rows, cols;
+  int64_t off;
+  tile_geometry(a, isA, t, rows, cols, off);
   const double* x = (isA ? a.A : a.B) + (off < 0 ? 0 : off);
   const int64_t n = (int64_t)rows * cols;
-  if (a.rowscale) {
-    // one exponent per row of an A tile / per column of a B tile (the tile-wide exponent
-    // below is still computed: it is not used for slicing in this mode)
-    const int i_or_k = isA ? t / a.K : t / a.N;
-    const int k_or_j = isA ? t % a.K : t % a.N;
-    const int nl = isA ? rows : cols;    // lines
-    const int len = isA ? cols : rows;   // elements per line
-    const bool tr = isA ? a.transa != 0 : a.transb != 0;
-    for (int l = threadIdx.x; l < nl && off >= 0; l += blockDim.x) {
-      double lm = 0.0;
-      for (int u = 0; u < len; u++) {
-        // element u of line l: A row l is (l, u), B column l is (u, l); stored transposed or not
-        const int64_t at = isA ? (tr ? (int64_t)u * rows + l : (int64_t)l * cols + u)
-                               : (tr ? (int64_t)l * rows + u : (int64_t)u * cols + l);
-        lm = fmax(lm, fabs(__ldg(x + at)));
-      }
-      int e = kZeroLine;
-      if (lm > 0.0 && lm <= 1.7976931348623157e308) frexp(lm, &e);
-      if (isA)
-        a.eArow[(int64_t)k_or_j * a.Mtot + a.ro[i_or_k] + l] = e;
-      else
-        a.eBcol[(int64_t)i_or_k * a.Ntot + a.co[k_or_j] + l] = e;
-    }
-  }
-  double mx = 0.0;
-  int bad = 0;
+  // the largest magnitude as bits: at or above kInfBits when a NaN or infinity is there
+  unsigned long long mx = 0;
   if (off >= 0) {
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const double v = fabs(__ldg(x + e));
-      if (!(v <= 1.7976931348623157e308)) bad = 1;  // NaN or infinity
-      mx = fmax(mx, v);
+    // tiles start 16-byte aligned (even offsets): pairs of doubles, four pairs in flight
+    const longlong2* x2 = reinterpret_cast<const longlong2*>(x);
+    const int64_t n2 = n >> 1;
+    const int64_t bd = blockDim.x;
+    for (int64_t e = threadIdx.x; e < n2; e += 4 * bd) {
+      longlong2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) v[u] = e + u * bd < n2 ? __ldg(x2 + e + u * bd) : make_longlong2(0, 0);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        mx = max(mx, (unsigned long long)v[u].x & kAbsMask);
+        mx = max(mx, (unsigned long long)v[u].y & kAbsMask);
+      }
     }
+    if ((n & 1) && threadIdx.x == 0) mx = max(mx, mag_bits(__ldg(x + n - 1)));
   }
-  __shared__ double red[8];
-  __shared__ int redbad[8];
-  for (int o = 16; o; o >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = mx;
-    redbad[threadIdx.x >> 5] = bad;
-  }
+  __shared__ unsigned long long red[8];
+  for (int o = 16; o; o >>= 1) mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    int bb = off < 0 ? 1 : 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-      m = fmax(m, red[w]);
-      bb |= redbad[w];
-    }
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = max(m, red[w]);
     int e = 0;
-    if (bb) {
+    if (off < 0 || m >= kInfBits) {
       atomicOr(a.err, off < 0 ? kErrBadOffset : kErrNonFinite);
-    } else if (m > 0.0) {
-      frexp(m, &e);  // m = f 2^e, f in [0.5, 1): smallest e with m < 2^e
+    } else if (m > 0) {
+      e = exponent_above(m);  // smallest e with max|x| < 2^e
     }
     if (isA)
       a.eA[t] = e;
     else
       a.eB[t] = e;
+  }
+}
+
+// Row/column scaling: one exponent per row of each stored A tile and per column of each
+// stored B tile (kZeroLine for an all-zero line); a non-finite value is reported by
+// split_exp_kernel. One block per tile, one thread per line.
+__global__ void __launch_bounds__(256) split_exp_lines_kernel(SplitArgs a) {
+  const int b = blockIdx.x;
+  const bool isA = b < a.n_a_tiles;
+  const int t = isA ? a.a_tiles[b] : a.b_tiles[b - a.n_a_tiles];
+  int rows, cols;
+  int64_t off;
+  tile_geometry(a, isA, t, rows, cols, off);
+  if (off < 0) return;
+  const double* x = (isA ? a.A : a.B) + off;
+  const int i_or_k = isA ? t / a.K : t / a.N;
+  const int k_or_j = isA ? t % a.K : t % a.N;
+  const int nl = isA ? rows : cols;   // lines
+  const int len = isA ? cols : rows;  // elements per line
+  const bool tr = isA ? a.transa != 0 : a.transb != 0;
+  // element u of line l: A row l is (l, u), B column l is (u, l); stored transposed or not
+  const int64_t lstep = isA ? (tr ? 1 : cols) : (tr ? rows : 1);
+  const int64_t ustep = isA ? (tr ? rows : 1) : (tr ? 1 : cols);
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    unsigned long long lm = 0;
+    const double* line = x + l * lstep;
+    for (int u = 0; u < len; u++) lm = max(lm, mag_bits(__ldg(line + u * ustep)));
+    const int e = (lm > 0 && lm < kInfBits) ? exponent_above(lm) : kZeroLine;
+    if (isA)
+      a.eArow[(int64_t)k_or_j * a.Mtot + a.ro[i_or_k] + l] = e;
+    else
+      a.eBcol[(int64_t)i_or_k * a.Ntot + a.co[k_or_j] + l] = e;
   }
 }
 
@@ -1258,7 +1288,10 @@ int max_clusters_s(int cl, int stages) {
 }  // namespace
 
 cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k) {
-  if (a.n_a_tiles + a.n_b_tiles > 0) split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
+  if (a.n_a_tiles + a.n_b_tiles > 0) {
+    split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
+    if (a.rowscale) split_exp_lines_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
+  }
   if (a.rowscale) {
     // the per-tile maxima (eAmax/eBmax) are not used in this mode; the line kernel writes
     // rowexp/colexp and the line maxima

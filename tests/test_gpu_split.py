@@ -296,3 +296,20 @@ def test_subnormal_results_match_split_oracle():
     w = struct_elements(prob, cs, off, want)
     assert np.all(np.abs(w) < 2.0 ** -1022) and np.any(w != 0)
     assert np.array_equal(got, w)
+
+
+@pytest.mark.parametrize("split_scale", [0, 1])
+def test_subnormal_inputs(split_scale):
+    """A tiles in the subnormal range (about 2^-1060) and B tiles near 2^1000: the tile and
+    line exponents of subnormal maxima follow frexp, as the oracle's do."""
+    from gpu_helpers import run_lib
+    prob = G.make_problem("nonuniform_dense", 14, 300, lo=40, hi=120)
+    prob.A = prob.A * 2.0 ** -1060
+    prob.B = prob.B * 2.0 ** 1000
+    assert np.any((np.abs(prob.A) < 2.0 ** -1022) & (prob.A != 0))
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, fill=0.0)
+    want = C0.copy()
+    OS.bsmm_split(prob, cs, want, off, 6, scaling="rows" if split_scale else "tile")
+    Cg, _ = run_lib(prob, cs, C0, off, mode=P.BSMM_SPLIT_BF16, nslices=6, split_scale=split_scale)
+    assert np.array_equal(struct_elements(prob, cs, off, Cg), struct_elements(prob, cs, off, want))
