@@ -677,12 +677,10 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
     }
   }
   const int biased = r + L + 52 + 1023;
-  double d;
-  if (biased >= 1 && biased <= 2046) {
-    d = __longlong_as_double((long long)(((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
-  } else {
-    d = scalbn((double)mant, r + L);  // subnormal or overflowing result
-  }
+  if (biased >= 1 && biased <= 2046)  // sign, exponent and significand assembled as bits
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
+                                            (mant & ((1ull << 52) - 1))));
+  const double d = scalbn((double)mant, r + L);  // subnormal or overflowing result
   return neg ? -d : d;
 }
 
