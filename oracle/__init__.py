@@ -34,9 +34,10 @@ def lib():
         L.oracle_klists.argtypes = [ctypes.c_int] * 3 + [P] * 4
         L.oracle_klists.restype = ctypes.c_int
         L.oracle_bsmm.argtypes = [ctypes.c_int] * 3 + [P] * 6 + [f64, P, P, P, P, f64, P, P, ctypes.c_int,
-                                                                   ctypes.c_int]
+                                                                   ctypes.c_int, ctypes.c_int]
         L.oracle_bsmm.restype = ctypes.c_int
-        L.oracle_bsmm_tile.argtypes = [ctypes.c_int] * 5 + [P] * 5 + [f64, P, P, P, P, f64, P, P, ctypes.c_int]
+        L.oracle_bsmm_tile.argtypes = [ctypes.c_int] * 5 + [P] * 5 + [f64, P, P, P, P, f64, P, P, ctypes.c_int,
+                                                                        ctypes.c_int]
         L.oracle_bsmm_tile.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = ctypes.c_int
@@ -94,8 +95,10 @@ def klists(prob):
     return ptr, kl[:cnt]
 
 
-def bsmm(prob, c_struct, C, c_off, nthreads: int = 0):
-    """FP64 product in place on the C arena (float64 numpy array)."""
+def bsmm(prob, c_struct, C, c_off, nthreads: int = 0, pieces: int = 1):
+    """FP64 product in place on the C arena (float64 numpy array). ``pieces`` > 1: every
+    tile's k-list is cut into that many pieces (split k, see oracle.c) whose partial sums
+    are added in piece order."""
     r, c, q, am, bm = _common(prob)
     M, N, K = len(r), len(c), len(q)
     A = _c(prob.A, np.float64)
@@ -104,13 +107,14 @@ def bsmm(prob, c_struct, C, c_off, nthreads: int = 0):
     _, ao, _, bo, trans = _std(prob)
     rc = lib().oracle_bsmm(M, N, K, _p(r), _p(c), _p(q), _p(am), _p(bm), _p(_c(c_struct, np.uint8)),
                            float(prob.alpha), _p(A), _p(ao), _p(B), _p(bo), float(prob.beta), _p(C),
-                           _p(_c(c_off, np.int64)), int(nthreads), trans)
+                           _p(_c(c_off, np.int64)), int(nthreads), trans, int(pieces))
     assert rc == 0, "oracle_bsmm failed"
     return C
 
 
-def bsmm_tile(prob, i, j, cin=None):
-    """One C tile (r_i x c_j) of the FP64 product; cin = its prior content."""
+def bsmm_tile(prob, i, j, cin=None, pieces: int = 1):
+    """One C tile (r_i x c_j) of the FP64 product; cin = its prior content; ``pieces`` as
+    for bsmm."""
     r, c, q, am, bm = _common(prob)
     M, N, K = len(r), len(c), len(q)
     out = np.zeros((int(r[i]), int(c[j])), np.float64)
@@ -120,7 +124,7 @@ def bsmm_tile(prob, i, j, cin=None):
     _, ao, _, bo, trans = _std(prob)
     rc = lib().oracle_bsmm_tile(i, j, M, N, K, _p(r), _p(c), _p(q), _p(am), _p(bm), float(prob.alpha),
                                 _p(_c(prob.A, np.float64)), _p(ao), _p(_c(prob.B, np.float64)), _p(bo),
-                                float(prob.beta), _p(cin_a), _p(out), trans)
+                                float(prob.beta), _p(cin_a), _p(out), trans, int(pieces))
     assert rc == 0
     return out
 

@@ -32,6 +32,16 @@
  * transpose (c_j x q_k). Masks and offset tables keep the (i,k) and (k,j) indexing
  * here; only the element addressing inside a tile changes, so the arithmetic, its
  * order and its rounding are the same as for untransposed storage.
+ *
+ * Split k (Sec. 3.2, Fig. 2: a rank-k update becomes a multiply task that forms the
+ * product C^(k) = A_ik B_kj into a temporary and a task that adds the temporary into
+ * C_ij, so updates of one C tile need not run one after the other). With pieces = n > 1
+ * the k-list of tile (i,j), of length L, is cut into n' = min(n, L) consecutive pieces,
+ * piece p taking the list positions [floor(p L / n'), floor((p+1) L / n')). Each piece
+ * forms its partial sum P_p from zero with the same fused multiply-adds as acc above,
+ * and the partials are reduced in piece order, acc = (...((P_0 + P_1) + P_2) + ...),
+ * every addition rounded to FP64; the epilogue is unchanged. pieces <= 1 is the plain
+ * definition.
  */
 #include <math.h>
 #include <stdint.h>
@@ -87,17 +97,19 @@ int oracle_klists(int M, int N, int K, const uint8_t* a_mask, const uint8_t* b_m
   return OR_OK;
 }
 
-/* One C tile: out (r_i x c_j, row-major) = alpha*acc + beta*cin, cin may be NULL
- * when beta == 0. */
-static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t* c, const int32_t* q,
-                     const uint8_t* a_mask, const uint8_t* b_mask, double alpha, const double* A,
-                     const int64_t* a_off, const double* B, const int64_t* b_off, double beta,
-                     const double* cin, double* out, double* acc, int trans) {
+/* acc (r_i x c_j) = sum of A_ik B_kj over the k-list positions [lo, hi) of tile
+ * (i,j), from zero, one fma per scalar update (ascending k, then ascending kk). */
+static void tile_sum(int i, int j, int K, int N, const int32_t* r, const int32_t* c, const int32_t* q,
+                     const uint8_t* a_mask, const uint8_t* b_mask, const double* A, const int64_t* a_off,
+                     const double* B, const int64_t* b_off, int64_t lo, int64_t hi, double* acc, int trans) {
   const int ri = r[i], cj = c[j];
   const int64_t nel = (int64_t)ri * cj;
   for (int64_t e = 0; e < nel; e++) acc[e] = 0.0;
+  int64_t pos = -1; /* position of k in the tile's k-list */
   for (int k = 0; k < K; k++) {
     if (!(a_mask[(int64_t)i * K + k] && b_mask[(int64_t)k * N + j])) continue;
+    pos++;
+    if (pos < lo || pos >= hi) continue;
     const int qk = q[k];
     const double* At = A + a_off[(int64_t)i * K + k];
     const double* Bt = B + b_off[(int64_t)k * N + j];
@@ -111,6 +123,29 @@ static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t
           arow[jj] = fma(a, b, arow[jj]);
         }
       }
+    }
+  }
+}
+
+/* One C tile: out (r_i x c_j, row-major) = alpha*acc + beta*cin, cin may be NULL
+ * when beta == 0; acc and part are scratch of r_i x c_j (part is used when pieces > 1). */
+static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t* c, const int32_t* q,
+                     const uint8_t* a_mask, const uint8_t* b_mask, double alpha, const double* A,
+                     const int64_t* a_off, const double* B, const int64_t* b_off, double beta,
+                     const double* cin, double* out, double* acc, double* part, int trans, int pieces) {
+  const int ri = r[i], cj = c[j];
+  const int64_t nel = (int64_t)ri * cj;
+  int64_t L = 0;
+  for (int k = 0; k < K; k++) L += (a_mask[(int64_t)i * K + k] && b_mask[(int64_t)k * N + j]) ? 1 : 0;
+  const int64_t np = pieces > 1 ? (pieces < L ? pieces : L) : 1;
+  if (np <= 1) {
+    tile_sum(i, j, K, N, r, c, q, a_mask, b_mask, A, a_off, B, b_off, 0, L, acc, trans);
+  } else {
+    for (int64_t p = 0; p < np; p++) {
+      const int64_t lo = p * L / np, hi = (p + 1) * L / np;
+      tile_sum(i, j, K, N, r, c, q, a_mask, b_mask, A, a_off, B, b_off, lo, hi, p ? part : acc, trans);
+      if (p)
+        for (int64_t e = 0; e < nel; e++) acc[e] = acc[e] + part[e];
     }
   }
   for (int64_t e = 0; e < nel; e++) {
@@ -129,7 +164,8 @@ static void one_tile(int i, int j, int K, int N, const int32_t* r, const int32_t
 int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const int32_t* q,
                 const uint8_t* a_mask, const uint8_t* b_mask, const uint8_t* c_struct,
                 double alpha, const double* A, const int64_t* a_off, const double* B,
-                const int64_t* b_off, double beta, double* C, const int64_t* c_off, int nthreads, int trans) {
+                const int64_t* b_off, double beta, double* C, const int64_t* c_off, int nthreads, int trans,
+                int pieces) {
   int64_t maxel = 1;
   for (int i = 0; i < M; i++)
     for (int j = 0; j < N; j++) {
@@ -145,7 +181,8 @@ int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const i
   {
     double* acc = (double*)malloc(sizeof(double) * (size_t)maxel);
     double* tmp = (double*)malloc(sizeof(double) * (size_t)maxel);
-    if (!acc || !tmp) {
+    double* part = (double*)malloc(sizeof(double) * (size_t)maxel);
+    if (!acc || !tmp || !part) {
 #pragma omp atomic write
       err = 1;
     } else {
@@ -160,12 +197,14 @@ int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const i
           continue;
         }
         double* Ct = C + co;
-        one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, Ct, tmp, acc, trans);
+        one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, Ct, tmp, acc, part, trans,
+                 pieces);
         memcpy(Ct, tmp, sizeof(double) * (size_t)((int64_t)r[i] * c[j]));
       }
     }
     free(acc);
     free(tmp);
+    free(part);
   }
   return err ? OR_ERR : OR_OK;
 }
@@ -175,14 +214,20 @@ int oracle_bsmm(int M, int N, int K, const int32_t* r, const int32_t* c, const i
 int oracle_bsmm_tile(int i, int j, int M, int N, int K, const int32_t* r, const int32_t* c,
                      const int32_t* q, const uint8_t* a_mask, const uint8_t* b_mask, double alpha,
                      const double* A, const int64_t* a_off, const double* B, const int64_t* b_off,
-                     double beta, const double* cin, double* out, int trans) {
+                     double beta, const double* cin, double* out, int trans, int pieces) {
   if (i < 0 || i >= M || j < 0 || j >= N) return OR_ERR;
   int64_t nel = (int64_t)r[i] * c[j];
   double* acc = (double*)malloc(sizeof(double) * (size_t)(nel > 0 ? nel : 1));
-  if (!acc) return OR_ERR;
-  one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, cin, out, acc, trans);
+  double* part = (double*)malloc(sizeof(double) * (size_t)(nel > 0 ? nel : 1));
+  int rc = OR_ERR;
+  if (acc && part) {
+    one_tile(i, j, K, N, r, c, q, a_mask, b_mask, alpha, A, a_off, B, b_off, beta, cin, out, acc, part, trans,
+             pieces);
+    rc = OR_OK;
+  }
   free(acc);
-  return OR_OK;
+  free(part);
+  return rc;
 }
 
 int oracle_num_threads(void) {
