@@ -35,7 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "useful TFLOP/s (nonzero-tile flops) & % of peak; split vs FP64 at <=1e-11 rel err"
 PROFILE_FILE = os.path.join(ROOT, "profiles", "split_mma_kernel_nonuniform_dense.txt")
 # exponents, scales, scale classes, slices, contraction
-SPLIT_KERNELS_PER_EXECUTE = 5
+def kernels_per_execute(P, plan, mode, split_scale=0):
+    """Kernels one bsmm_execute launches: FP64 the tile kernel; split modes the exponent
+    (and line exponent), scale, class, pack and contraction kernels; plus the split-k
+    reduction when the plan cut a k-list."""
+    red = int(P.bsmm_plan_ksplit(plan)["n_regions"] > 0)
+    return (1 if mode == P.BSMM_FP64 else 5 + int(split_scale)) + red
 
 
 def parse():
@@ -54,12 +59,16 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="dense", choices=["dense", "batch", "uniform", "banded", "banded_wide",
-                                                                "clustered"],
+                                                                "clustered", "thin"],
                     help="dense: the 16384 nonuniform dense product (headline); batch: 256 independent products of "
                          "uneven size, separate launches vs one graph-replayed batch launch, before and after "
                          "autotuning; uniform: N=2048, blocks 128, Bernoulli(0.5) masks (FP64 path); banded / "
                          "banded_wide: N=32768 band |i-j|<=6 with distance-decaying values (FP64 vs split-fp16); "
-                         "clustered: M=N=24576, K=49152 clustered masks, learned vs flop-count schedule")
+                         "clustered: M=N=24576, K=49152 clustered masks, learned vs flop-count schedule; thin: "
+                         "M=N=512, K=524288 dense (few C tiles, long inner sums), split k against uncut k-lists")
+    ap.add_argument("--ksplit", type=int, default=0,
+                    help="split k for every plan: 0 = the library's automatic choice (split modes only), "
+                         "-1 = automatic in FP64 mode too, 1 = never, n = n pieces")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--split-scale", default="tile", choices=["tile", "rows"],
                     help="split modes: one power-of-two scale per tile, or per row of A and column of B")
@@ -287,7 +296,7 @@ def run_batch(args, rank, world):
     F = 0.0
     for p in probs:
         pl = P.bsmm_plan(p.row_sizes, p.col_sizes, p.inner_sizes, p.a_mask, p.b_mask, mode=P.BSMM_SPLIT_BF16,
-                         nslices=s)
+                         nslices=s, ksplit=args.ksplit)
         q = P.bsmm_plan_query(pl)
         F += q["useful_flops"]
         off, tot = G.layout_arena(q["c_mask"], p.row_sizes, p.col_sizes)
@@ -350,7 +359,7 @@ def run_batch(args, rank, world):
     P.bsmm_batch_status_device(batch)
     space = P.bsmm_tune_space(P.BSMM_SPLIT_BF16, s)
     tf = lambda ms: F / (ms * 1e-3) / 1e12
-    launches_per_step = 4 * len(plans) + 1
+    launches_per_step = P.bsmm_batch_kernels(batch)
     line = {"metric": METRIC, "value": tf(ms_tuned), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_tuned, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -363,7 +372,7 @@ def run_batch(args, rank, world):
                                                         for c, m in zip(space, tune_ms)}},
             "batch_graph_default": {"value": tf(ms_batch), "ms_per_step": ms_batch, "bins": default_bins},
             "separate_launches": {"value": tf(ms_sep), "ms_per_step": ms_sep, "launches_per_step":
-                                  SPLIT_KERNELS_PER_EXECUTE * len(plans)},
+                                  sum(kernels_per_execute(P, pl, P.BSMM_SPLIT_BF16) for pl in plans)},
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
@@ -380,7 +389,13 @@ SINGLE = {
     "clustered": dict(recipe="clustered", n=24576, kw=dict(lo=16, hi=512, nclusters=40, cluster_density=0.10),
                       mode="BSMM_SPLIT_BF16", head="split",
                       desc="clustered M=N=24576 K=49152, log-uniform blocks [16,512], 40 clusters at 10%, U[-1,1]"),
+    "thin": dict(recipe="thin_dense", n=512, kw=dict(lo=64, hi=256, k_factor=1024), mode="BSMM_SPLIT_BF16",
+                 head="split", desc="thin_dense M=N=512 K=524288, blocks U-int[64,256], dense, U[-1,1] "
+                                    "(few C tiles, long inner sums)"),
 }
+
+# position of the contraction kernel in bsmm_plan_kernel_ms (the reduction, if any, follows)
+CONTRACTION_INDEX = {"split": 2, "fp64": 0}
 
 
 def run_single(args, rank, world):
@@ -400,6 +415,7 @@ def run_single(args, rank, world):
     def setup(seed, mode, **opt):
         if mode != P.BSMM_FP64:
             opt.setdefault("split_scale", int(args.split_scale == "rows"))
+        opt.setdefault("ksplit", args.ksplit)
         prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,
                            nslices=s, profile=1, **opt)
@@ -454,8 +470,9 @@ def run_single(args, rank, world):
         feats, flops = P.bsmm_plan_features(plan)
         y = torch.zeros(len(feats), dtype=torch.float32, device=dev)
         P.bsmm_mlp_predict(mlp, torch.from_numpy(feats).to(dev), y)
+        ci = CONTRACTION_INDEX["split"]
         extra["learned_schedule"] = {
-            "makespan_ms_flop_count": k_flops[-1], "makespan_ms_mlp": k_split[-1], "step_ms_flop_count": ms_flops,
+            "makespan_ms_flop_count": k_flops[ci], "makespan_ms_mlp": k_split[ci], "step_ms_flop_count": ms_flops,
             "step_ms_mlp": ms_split, "bits_identical": same, "train_loss": loss,
             "log_rms_err_flop_count": CM.prediction_error(plan, times, np.maximum(flops, 1.0)),
             "log_rms_err_mlp": CM.prediction_error(plan, times, np.exp(y.cpu().numpy().astype(np.float64))),
@@ -468,8 +485,28 @@ def run_single(args, rank, world):
         ms_split, k_split = timed(plan, run, args.steps)
         clocks = clk.stop()
     Csplit = t["C"].clone()
-    prob64, plan64, _, t64, run64 = setup(seed, P.BSMM_FP64)
+    # FP64 takes automatic cuts only when asked (they change its rounding): the thin
+    # workload asks, to show split k on both paths
+    prob64, plan64, _, t64, run64 = setup(seed, P.BSMM_FP64,
+                                          **({"ksplit": -1} if args.workload == "thin" and args.ksplit == 0 else {}))
     ms64, k64 = timed(plan64, run64, args.steps if w["head"] == "fp64" else max(1, args.fp64_steps))
+    if args.workload == "thin":
+        # split k (Sec. 3.2, Fig. 2) against uncut k-lists on the same inputs, both paths
+        def uncut(mode, steps, ref, cut_plan, cut_ms):
+            _, plan1, _, t1, run1 = setup(seed, mode, ksplit=1)
+            ms1, k1 = timed(plan1, run1, steps)
+            ks = P.bsmm_plan_ksplit(cut_plan)
+            d = {"cut_ms": cut_ms, "uncut_ms": ms1, "speedup": ms1 / cut_ms, "regions_cut": ks["n_regions"],
+                 "pieces": ks["n_pieces"], "units_cut": int(len(ks["pieces"])),
+                 "units_uncut": int(P.bsmm_plan_query(plan1)["n_units"]), "uncut_kernel_ms": k1}
+            if mode == P.BSMM_FP64:
+                d["rel_diff_cut_vs_uncut"] = float(torch.linalg.norm(t1["C"] - ref) / torch.linalg.norm(t1["C"]))
+            else:
+                d["bits_identical_cut_vs_uncut"] = bool((t1["C"] == ref).all())
+            del plan1, t1
+            return d
+        extra["split_k"] = {"split_path": uncut(mode, args.steps, Csplit, plan, ms_split),
+                            "fp64_path": uncut(P.BSMM_FP64, max(1, args.fp64_steps), t64["C"], plan64, ms64)}
     ms_split, _ = aggregate(ms_split, 0.0, dev)
     ms64, F = aggregate(ms64, q["useful_flops"], dev)
     c64 = t64["C"]
@@ -477,18 +514,19 @@ def run_single(args, rank, world):
     tf = lambda ms: F / (ms * 1e-3) / 1e12
     pk, pk_src = peaks()
     head_split = w["head"] == "split"
+    cis, cif = CONTRACTION_INDEX["split"], CONTRACTION_INDEX["fp64"]
     split = {"value": tf(ms_split), "ms_per_step": ms_split, "kernel_ms": k_split,
              "mode": f"{w['mode'][5:].lower()} s={s}" + (", scale per row/column" if args.split_scale == "rows" else ""),
              "rel_err_vs_fp64": err}
     fp64 = {"value": tf(ms64), "ms_per_step": ms64, "kernel_ms": k64}
     pair = s * (s + 1) / 2 * F
     if head_split:
-        roof = {"bound": "tensor", "kernel": "split_mma_kernel", "achieved": pair / (k_split[-1] * 1e-3) / 1e12,
+        roof = {"bound": "tensor", "kernel": "split_mma_kernel", "achieved": pair / (k_split[cis] * 1e-3) / 1e12,
                 "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"}
     else:
         fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "fp64_tile_kernel", "achieved": F / (k64[-1] * 1e-3) / 1e12,
+        roof = {"bound": "alu", "kernel": "fp64_tile_kernel", "achieved": F / (k64[cif] * 1e-3) / 1e12,
                 "peak": fp64_peak, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -500,7 +538,8 @@ def run_single(args, rank, world):
             "config": {"workload": w["desc"], "useful_flops_per_step": F, "seed": seed,
                        "headline_path": "split" if head_split else "fp64"},
             "split_path": split, "fp64_path": fp64, "roofline": roof, "gpu_launches":
-                (SPLIT_KERNELS_PER_EXECUTE if head_split else 1) * args.steps, "clocks": clocks}
+                (kernels_per_execute(P, plan, mode, args.split_scale == "rows") if head_split
+                 else kernels_per_execute(P, plan64, P.BSMM_FP64)) * args.steps, "clocks": clocks}
     line.update(extra)
     if rank == 0:
         print(json.dumps(line))
@@ -550,7 +589,8 @@ def run_dense(args, rank, world, local):
     sc = dict(split_scale=int(args.split_scale == "rows"))
     s = args.slices
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
-                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster, **tr, **sc)
+                       mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster, ksplit=args.ksplit, **tr,
+                       **sc)
     q = P.bsmm_plan_query(plan)
     F = q["useful_flops"]
     cs = q["c_mask"]
@@ -583,7 +623,7 @@ def run_dense(args, rank, world, local):
         P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
         ks = P.bsmm_plan_kernel_ms(plan)
         kms.append(ks)
-        launches += SPLIT_KERNELS_PER_EXECUTE
+        launches += kernels_per_execute(P, plan, P.BSMM_SPLIT_BF16, sc["split_scale"])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()

@@ -286,6 +286,8 @@ RECIPES = {
     "banded_decay_wide": "as banded_decay with exp(-2.3|i-j|) (about 10^-|i-j|, six orders over the band)",
     "clustered": "M=N=n, K=2n, block sizes round(log-uniform[16,512]), 40 dense clusters at ~10% density, U[-1,1]",
     "paper_nonuniform": "square n, the paper's Sec. 4.1 generator with mean block 256, dense, U[-1,1]",
+    "thin_dense": "M=N=n, K=k_factor*n, block sizes U-int[64,256] on rows, cols and inner, dense, U[-1,1] "
+                  "(few C tiles, long inner sums)",
 }
 
 
@@ -319,6 +321,13 @@ def make_problem(recipe: str, seed: int, n: int, *, values: Optional[str] = None
         am = mask_clusters(len(r), len(q), nclusters, cluster_density, rm)
         bm = mask_clusters(len(q), len(c), nclusters, cluster_density, rm)
         return _assemble(f"{recipe}_n{n}_s{seed}", r, c, q, am, bm, rv, values or "uniform", recipe, alpha, beta)
+    if recipe == "thin_dense":
+        r = tiling_uniform_int(n, lo or 64, hi or 256, rt)
+        q = tiling_uniform_int(k_factor * n, lo or 64, hi or 256, rt)
+        am = mask_dense(len(r), len(q))
+        bm = mask_dense(len(q), len(r))
+        return _assemble(f"{recipe}_n{n}_k{k_factor * n}_s{seed}", r, r, q, am, bm, rv, values or "uniform", recipe,
+                         alpha, beta)
     if recipe == "paper_nonuniform":
         nb = max(1, n // block)
         r = tiling_paper(n, nb, rt)

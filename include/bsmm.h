@@ -99,6 +99,29 @@ typedef struct {
                               tiles whose rows or columns span many binades (an all-zero row
                               or column takes no part in the maxima that set the accumulator's
                               unit) */
+  int32_t ksplit;          /* split k (Sec. 3.2, Fig. 2: the rank-k updates of one C region
+                              run as multiply tasks on consecutive pieces of its k-list, each
+                              into a partial sum, then one reduction task adds the partials in
+                              piece order and applies the epilogue):
+                              0 = automatic in the split modes, whose results do not depend on
+                                  the cut: a region is cut when the persistent grid would
+                                  otherwise idle (few regions, or a region costlier than a
+                                  fraction of a CTA's share of the work); no cut in FP64 mode,
+                                  so that its rounding stays the plain definition's;
+                             -1 = automatic in every mode (FP64 results then depend on the
+                                  cut chosen for the machine, within the FP64 error bound);
+                              1 = never;
+                              n >= 2 = every region's k-list of length L is cut into
+                                  n' = min(n, L) pieces, piece p taking list positions
+                                  [floor(p L / n'), floor((p+1) L / n')).
+                              The split modes' partial sums are exact integers, so their
+                              results do not depend on the cut. In FP64 mode the partials
+                              are FP64 sums added in piece order (each addition rounded), so
+                              a cut region equals the plain result up to that rounding.
+                              A region is a work unit's C region: an FP64 sub-tile of one C
+                              tile, whose k-list is the tile's; or a split-mode 128-row block
+                              times a group of `cluster` 32-column blocks, whose k-list is the
+                              inner blocks where both have a stored tile. */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */
@@ -135,6 +158,16 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
  */
 bsmm_status bsmm_plan_query(bsmm_plan_t plan, int64_t* n_ctiles, int64_t* n_triples,
                             double* useful_flops, uint8_t* c_mask_out, int64_t* n_units);
+
+/*
+ * Split k of a plan (see bsmm_options.ksplit; host outputs, any pointer may be NULL):
+ *   n_regions   regions whose k-list was cut into pieces (each reduced by the extra
+ *               reduction kernel that bsmm_execute then launches after the contraction)
+ *   n_pieces    work units that are pieces of those regions (their sum over the regions)
+ *   pieces      n_units entries: for each work unit, the number of pieces of its region
+ *               (1 for a unit that finishes its region)
+ */
+bsmm_status bsmm_plan_ksplit(bsmm_plan_t plan, int64_t* n_regions, int64_t* n_pieces, int32_t* pieces);
 
 /*
  * Per-unit cost features for the learned cost model (host output, row-major
@@ -208,6 +241,11 @@ bsmm_status bsmm_batch_set_args(bsmm_batch_t batch, const double* alpha, const d
                                 const int64_t* const* c_off);
 bsmm_status bsmm_batch_execute(bsmm_batch_t batch, void* stream);
 bsmm_status bsmm_batch_query(bsmm_batch_t batch, int64_t* n_units, double* useful_flops, int32_t* bins);
+
+/* Number of kernels the batch's most recent bsmm_batch_execute launched (0 before the
+ * first): per wave the products' slicing kernels and one contraction launch, plus one
+ * split-k reduction per product that cut a k-list (FP64: one contraction launch). */
+bsmm_status bsmm_batch_kernels(bsmm_batch_t batch, int32_t* kernels);
 bsmm_status bsmm_batch_set_costs(bsmm_batch_t batch, const double* costs);
 bsmm_status bsmm_batch_status_device(bsmm_batch_t batch, void* stream);
 void bsmm_batch_destroy(bsmm_batch_t batch);

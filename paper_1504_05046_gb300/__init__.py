@@ -21,9 +21,10 @@ from . import build as _build
 __all__ = [
     "BsmmError", "lib", "library_path", "BSMM_FP64", "BSMM_SPLIT_BF16", "BSMM_SPLIT_FP16",
     "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
-    "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
-    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
-    "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy", "EXPORTED",
+    "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features",
+    "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device",
+    "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy",
+    "EXPORTED",
 ]
 
 BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
@@ -34,10 +35,10 @@ STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_
 
 # every symbol include/bsmm.h declares
 EXPORTED = [
-    "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_features", "bsmm_plan_set_costs",
+    "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features", "bsmm_plan_set_costs",
     "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
     "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_batch_create", "bsmm_batch_set_args",
-    "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_set_costs", "bsmm_batch_status_device",
+    "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_kernels", "bsmm_batch_set_costs", "bsmm_batch_status_device",
     "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
     "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_last_error", "bsmm_destroy",
@@ -55,7 +56,7 @@ class Options(ctypes.Structure):
                 ("max_ctas", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("transa", ctypes.c_int32),
-                ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32)]
+                ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32), ("ksplit", ctypes.c_int32)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ def lib():
         L.bsmm_plan.argtypes = [ctypes.POINTER(P), i32, P, i32, P, i32, P, P, P, P, ctypes.POINTER(Options)]
         L.bsmm_plan_query.argtypes = [P, P, P, P, P, P]
         L.bsmm_plan_features.argtypes = [P, P, P]
+        L.bsmm_plan_ksplit.argtypes = [P, P, P, P]
         L.bsmm_plan_set_costs.argtypes = [P, P]
         L.bsmm_plan_set_ctas.argtypes = [P, i32]
         L.bsmm_execute.argtypes = [P, f64, P, P, P, P, f64, P, P, P]
@@ -89,6 +91,7 @@ def lib():
         L.bsmm_batch_set_args.argtypes = [P, P, P, P, P, P, P, P, P]
         L.bsmm_batch_execute.argtypes = [P, P]
         L.bsmm_batch_query.argtypes = [P, P, P, P]
+        L.bsmm_batch_kernels.argtypes = [P, P]
         L.bsmm_batch_set_costs.argtypes = [P, P]
         L.bsmm_batch_status_device.argtypes = [P, P]
         L.bsmm_batch_destroy.argtypes = [P]
@@ -182,7 +185,8 @@ class Plan:
 def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *, mode: int = BSMM_FP64,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
               record_timings: int = 0, profile: int = 0, cluster: int = 0, fp64_tile: int = 0,
-              stages: int = 0, transa: int = 0, transb: int = 0, split_scale: int = 0) -> Plan:
+              stages: int = 0, transa: int = 0, transb: int = 0, split_scale: int = 0,
+              ksplit: int = 0) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -197,6 +201,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     o.transa = transa
     o.transb = transb
     o.split_scale = split_scale
+    o.ksplit = ksplit
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))
@@ -211,6 +216,16 @@ def bsmm_plan_query(plan: Plan) -> dict:
                                  _ptr(cs), ctypes.addressof(nun)))
     return {"n_ctiles": nct.value, "n_triples": ntr.value, "useful_flops": fl.value, "c_mask": cs,
             "n_units": nun.value}
+
+
+def bsmm_plan_ksplit(plan: Plan) -> dict:
+    """Split k of a plan: regions cut into pieces, their total piece count, and per work
+    unit the number of pieces of its region."""
+    nr, npc = ctypes.c_int64(), ctypes.c_int64()
+    n = bsmm_plan_query(plan)["n_units"]
+    pieces = np.zeros(max(n, 1), np.int32)
+    _check(lib().bsmm_plan_ksplit(plan.handle, ctypes.addressof(nr), ctypes.addressof(npc), _ptr(pieces)))
+    return {"n_regions": nr.value, "n_pieces": npc.value, "pieces": pieces[:n]}
 
 
 def bsmm_plan_features(plan: Plan):
@@ -315,6 +330,13 @@ def bsmm_batch_query(batch: Batch) -> dict:
     nu, fl, bins = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
     _check(lib().bsmm_batch_query(batch.handle, ctypes.byref(nu), ctypes.byref(fl), ctypes.byref(bins)))
     return {"n_units": nu.value, "useful_flops": fl.value, "bins": bins.value}
+
+
+def bsmm_batch_kernels(batch: Batch) -> int:
+    """Kernels the batch's most recent bsmm_batch_execute launched."""
+    n = ctypes.c_int32()
+    _check(lib().bsmm_batch_kernels(batch.handle, ctypes.byref(n)))
+    return n.value
 
 
 def bsmm_batch_set_costs(batch: Batch, costs):

@@ -9,6 +9,8 @@
 // into waves whose slice workspaces fit in half of L2: a wave issues its products'
 // exponent and slicing kernels and then its contraction launch, which finds the slices
 // still in L2 (a product larger than that is a wave of its own). FP64 is one wave.
+// Products whose plans split a k-list (bsmm_options.ksplit) get their reduction kernels
+// after the contraction launch of their wave.
 // bsmm_batch_execute issues kernels only, so a stream capture of it records a CUDA
 // graph that replays the whole batch with one graph launch.
 #include <algorithm>
@@ -41,6 +43,7 @@ struct bsmm_batch_s {
   std::vector<Fp64Args> fargs;
   std::vector<SplitArgs> sargs;
   bool args_set = false;
+  int32_t launches = 0;  // kernels the last bsmm_batch_execute launched
   DevBuf d_prods, d_unit_prod, d_unit_local, d_sched_ptr, d_sched_units, d_err;
   std::vector<bsmm_plan_t> owned;  // plans made by bsmm_batch_autotune, destroyed with the batch
 };
@@ -270,6 +273,7 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
   if (b->n_units == 0) return BSMM_OK;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
+  int32_t n = 0;
   for (size_t w = 0; w + 1 < b->wave_prod.size() && e == cudaSuccess; w++) {
     if (b->prod_begin[b->wave_prod[w + 1]] == b->prod_begin[b->wave_prod[w]]) continue;  // no units
     const int32_t* sp = (const int32_t*)b->d_sched_ptr.p + b->wave_ptr[w];
@@ -282,10 +286,18 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
       a.unit_local = (const int32_t*)b->d_unit_local.p;
       a.err = (int32_t*)b->d_err.p;
       e = launch_fp64(a, b->wave_bins[w], st, nullptr, nullptr);
+      n++;
+      // split k: the reductions of the products that cut a k-list
+      for (size_t i = 0; i < b->fargs.size() && e == cudaSuccess; i++)
+        if (b->fargs[i].n_red > 0) {
+          e = launch_fp64_reduce(b->fargs[i], st);
+          n++;
+        }
     } else {
       for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1] && e == cudaSuccess; i++) {
         int k = 0;
         e = launch_split_prep(b->sargs[i], st, nullptr, &k);
+        n += split_prep_kernels(b->sargs[i]);
       }
       if (e != cudaSuccess) break;
       SplitArgs a = b->sargs[0];
@@ -296,9 +308,22 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
       a.unit_local = (const int32_t*)b->d_unit_local.p;
       a.err = (int32_t*)b->d_err.p;
       e = launch_split_mma(a, b->wave_bins[w], st);
+      n++;
+      for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1] && e == cudaSuccess; i++)
+        if (b->sargs[i].n_red > 0) {
+          e = launch_split_reduce(b->sargs[i], st);
+          n++;
+        }
     }
   }
   if (e != cudaSuccess) return set_error(std::string("batch launch: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  b->launches = n;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_batch_kernels(bsmm_batch_t b, int32_t* kernels) {
+  if (!b || !kernels) return set_error("NULL argument"), BSMM_ERR_INVALID;
+  *kernels = b->launches;
   return BSMM_OK;
 }
 

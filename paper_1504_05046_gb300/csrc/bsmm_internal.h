@@ -52,12 +52,31 @@ struct DevBuf {
   bool borrowed = false;  // memory of another plan: not freed with this one
 };
 
-struct Fp64Unit {  // one C sub-tile of one C tile
+// Work units. A unit covers a region of C over a range of its k-list: the whole list,
+// or one piece of it when the planner splits k (Sec. 3.2, Fig. 2: multiply tasks on
+// parts of the k-list, then a reduction task). A piece writes its partial sum to the
+// plan's partial workspace at `slot` instead of finishing the region; a reduction unit
+// then adds the region's partials in slot order and applies the epilogue.
+struct Fp64Unit {  // one sub-tile of one C tile, k-list positions [t0, t1)
   int32_t i, j, r0, c0;
+  int64_t t0, t1;
+  int32_t slot;  // -1: the unit finishes its region
+  int32_t pad;
 };
 
-struct SplitUnit {  // one (128-row block, TN-column block)
+struct SplitUnit {  // one (128-row block, group of cl TN-column blocks), inner blocks [k0, k1)
   int32_t rb, cb;
+  int32_t k0, k1;
+  int32_t slot;  // -1: the unit finishes its region; else the partial-sum slot of this piece
+  int32_t pad;
+};
+
+struct Fp64Red {  // a region whose k-list was split: partial slots [slot0, slot0 + n)
+  int32_t i, j, r0, c0, slot0, n;
+};
+
+struct SplitRed {  // a (row block, column-block group) whose k-list was split
+  int32_t rb, cb, slot0, n;
 };
 
 // Arguments of the FP64 tile-task kernel.
@@ -85,6 +104,9 @@ struct Fp64Args {
   int32_t debug;
   int32_t tile;            // sub-tile edge of the units (64 or 32)
   int32_t transa, transb;  // transposed operand storage (bsmm_options)
+  double* part;            // split k: tile x tile partial sums per slot (row-major)
+  const Fp64Red* red;      // split k: the regions to reduce
+  int32_t n_red;
   // batch: per-product arguments in device memory; the schedule then lists batch-wide
   // unit ids, each mapped to (product, unit of that product)
   const Fp64Args* prods;
@@ -158,6 +180,11 @@ struct SplitArgs {
   int32_t* unit_cta;
   int32_t* err;
   int32_t debug;
+  // split k: exact 128-bit partial sums, per slot and cluster rank a TN x 128 array
+  // (column-major: element (row, col) at col * 128 + row), and the regions to reduce
+  uint4* part;
+  const SplitRed* red;
+  int32_t n_red;
   // batch (see Fp64Args)
   const SplitArgs* prods;
   const int32_t* unit_prod;
@@ -172,7 +199,11 @@ cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEven
 // the two halves of launch_split: per-product exponents, scales and slices; the
 // persistent contraction over the schedule in `a` (clusters of a.cl CTAs)
 cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k);
+int split_prep_kernels(const SplitArgs& a);  // how many kernels launch_split_prep launches
 cudaError_t launch_split_mma(const SplitArgs& a, int clusters, cudaStream_t st);
+// split k: the reductions of the regions whose k-list was split (no launch when none)
+cudaError_t launch_split_reduce(const SplitArgs& a, cudaStream_t st);
+cudaError_t launch_fp64_reduce(const Fp64Args& a, cudaStream_t st);
 
 // Longest-processing-time packing of n units with `cost` onto `bins` persistent CTAs
 // (or clusters); natural = round robin in unit order. CSR output.
@@ -185,6 +216,12 @@ void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, 
 void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
                      const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
 int default_bins(const bsmm_plan_s* p);
+// Persistent CTAs (FP64) or clusters (split modes) of the machine, capped by max_ctas but
+// not by the unit count.
+int machine_bins(const bsmm_plan_s* p);
+// Split k: pieces per unit from the units' costs, k-list lengths and the bin count.
+std::vector<int32_t> choose_pieces(const std::vector<double>& cost, const std::vector<int64_t>& len, int bins,
+                                   double overhead, int ksplit);
 int fp64_ctas_per_sm(int tile);
 
 void set_error(const std::string& msg);
@@ -216,6 +253,11 @@ struct bsmm_plan_s {
   std::vector<int64_t> kptr;   // FP64: CSR over M*N tiles
   std::vector<int32_t> klist;
   int64_t n_units = 0;
+  // split k: regions cut into pieces and their partial slots
+  std::vector<bsmm::Fp64Red> f64_red;
+  std::vector<bsmm::SplitRed> sp_red;
+  std::vector<int32_t> unit_pieces;  // per unit: pieces of its region (1: not split)
+  int64_t n_slots = 0;
   std::vector<double> flop_cost, cost;
   std::vector<float> features;  // n_units x BSMM_NFEATURES
   int ctas = 0;
@@ -231,7 +273,7 @@ struct bsmm_plan_s {
   bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_presBg, d_apk_off, d_bpk_off, d_apk, d_bpk;
   bsmm::DevBuf d_eArow, d_eBcol, d_eAmaxr, d_eBmaxc;
   bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_urow, d_ucol, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
-  bsmm::DevBuf d_err, d_timings, d_unit_cta;
+  bsmm::DevBuf d_err, d_timings, d_unit_cta, d_part, d_red;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;
 
   // per-kernel profiling events (profile option)

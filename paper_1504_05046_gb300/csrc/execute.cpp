@@ -37,6 +37,9 @@ void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, 
   a.tile = p->f64_tile;
   a.transa = p->opt.transa;
   a.transb = p->opt.transb;
+  a.part = (double*)p->d_part.p;
+  a.red = (const Fp64Red*)p->d_red.p;
+  a.n_red = (int32_t)p->f64_red.size();
   a.prods = nullptr;
   a.unit_prod = a.unit_local = nullptr;
 }
@@ -114,6 +117,9 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
   a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
   a.err = (int32_t*)p->d_err.p;
   a.debug = p->opt.debug_checks;
+  a.part = (uint4*)p->d_part.p;
+  a.red = (const SplitRed*)p->d_red.p;
+  a.n_red = (int32_t)p->sp_red.size();
   a.prods = nullptr;
   a.unit_prod = a.unit_local = nullptr;
 }

@@ -20,6 +20,10 @@
 // ascending kk; the epilogue rounds alpha*acc and beta*C separately before
 // adding. The result bits therefore do not depend on the schedule, the CTA count
 // or the unit order.
+//
+// Split k (Sec. 3.2, Fig. 2): when the planner cuts a region's k-list into pieces, each
+// piece is a unit that sums its positions from zero and stores the partial sum; the
+// reduction kernel adds the partials in piece order and applies the epilogue.
 #include <cstdint>
 
 #include "bsmm_internal.h"
@@ -115,9 +119,9 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
 #pragma unroll
       for (int y = 0; y < 4; y++) acc[x][y] = 0.0;
 
-    ChunkIter it;
-    it.t = P.kptr[tile];
-    it.t_end = P.kptr[tile + 1];
+    ChunkIter it;  // the unit's positions in the tile's k-list (a piece of it under split k)
+    it.t = un.t0;
+    it.t_end = un.t1;
     it.kk0 = 0;
     it.k = it.t < it.t_end ? P.klist[it.t] : 0;
     it.qk = it.t < it.t_end ? P.q[it.k] : 0;
@@ -236,9 +240,22 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
       __syncthreads();
     }
 
-    // epilogue: C_ij = alpha*acc + beta*C_ij on the valid part of the region
+    // epilogue: C_ij = alpha*acc + beta*C_ij on the valid part of the region; a piece of a
+    // split k-list stores its partial sum for the reduction instead
     const int64_t co = P.c_off[tile];
-    if (co < 0) {
+    if (un.slot >= 0) {
+      double* dst = P.part + (int64_t)un.slot * (BM * BN);
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int row = ty + TX * x;
+        if (row >= rows) continue;
+#pragma unroll
+        for (int y = 0; y < 4; y++) {
+          const int col = tx + TX * y;
+          if (col < cols) dst[row * BN + col] = acc[x][y];
+        }
+      }
+    } else if (co < 0) {
       if (tid == 0) atomicOr(a.err, kErrBadOffset);
     } else {
       double* Ct = P.C + co + (int64_t)un.r0 * cj + un.c0;
@@ -267,6 +284,35 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
   }
 }
 
+// Split k: the reduction task of a region whose k-list was cut into pieces (Sec. 3.2,
+// Fig. 2). The pieces' partial sums are added in piece order, each addition rounded to
+// FP64, then C = alpha*sum + beta*C as in the tile kernel. One CTA per region.
+__global__ void __launch_bounds__(256) fp64_reduce_kernel(const __grid_constant__ Fp64Args a) {
+  const Fp64Red rd = a.red[blockIdx.x];
+  const int T = a.tile;
+  const int ri = a.r[rd.i], cj = a.c[rd.j];
+  const int rows = min(T, ri - rd.r0), cols = min(T, cj - rd.c0);
+  const int64_t tile = (int64_t)rd.i * a.N + rd.j;
+  const int64_t co = a.c_off[tile];
+  if (co < 0) {
+    if (threadIdx.x == 0) atomicOr(a.err, kErrBadOffset);
+    return;
+  }
+  double* Ct = a.C + co + (int64_t)rd.r0 * cj + rd.c0;
+  const int64_t stride = (int64_t)T * T;
+  const double* src = a.part + (int64_t)rd.slot0 * stride;
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    const int row = e / T, col = e % T;
+    if (row >= rows || col >= cols) continue;
+    double v = src[e];
+    for (int p = 1; p < rd.n; p++) v = __dadd_rn(v, src[p * stride + e]);
+    double* dst = Ct + (int64_t)row * cj + col;
+    double out = __dmul_rn(a.alpha, v);
+    if (a.beta != 0.0) out = __dadd_rn(out, __dmul_rn(a.beta, *dst));
+    *dst = out;
+  }
+}
+
 }  // namespace
 
 int fp64_ctas_per_sm(int tile) {
@@ -278,6 +324,7 @@ int fp64_ctas_per_sm(int tile) {
   return n;
 }
 
+// One product's launch (a batch launches its products' reductions itself).
 cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
   if (ev) cudaEventRecord(ev[0], st);
   if (a.tile == 32)
@@ -285,7 +332,19 @@ cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_
   else
     fp64_tile_kernel<64><<<ctas, 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[1], st);
-  if (nk) *nk = 1;
+  int k = 1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !a.prods && a.n_red > 0) {
+    e = launch_fp64_reduce(a, st);
+    if (ev) cudaEventRecord(ev[++k], st);
+  }
+  if (nk) *nk = k;
+  return e;
+}
+
+cudaError_t launch_fp64_reduce(const Fp64Args& a, cudaStream_t st) {
+  if (a.n_red <= 0) return cudaSuccess;
+  fp64_reduce_kernel<<<a.n_red, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -103,7 +103,7 @@ __global__ void noalloc_setup_kernel(uint8_t* base, int m, int n, int k, int s, 
     int u = 0;
     for (int rb = 0; rb < RB; rb++)
       for (int cb = 0; cb < CB; cb++) {
-        t->units[u] = SplitUnit{rb, cb};
+        t->units[u] = SplitUnit{rb, cb, 0, 1, -1, 0};  // the one inner block, whole
         t->sched_ptr[u] = u;
         t->sched_units[u] = u;
         u++;
@@ -225,6 +225,9 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
   a.unit_cta = nullptr;
   a.err = t->err;
   a.debug = 0;
+  a.part = nullptr;  // no split k: one inner block
+  a.red = nullptr;
+  a.n_red = 0;
   e = launch_split(a, RB * CB, st, nullptr, nullptr);
   if (e != cudaSuccess) return set_error(std::string("noalloc launch: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   return BSMM_OK;

@@ -110,15 +110,85 @@ void wave_segments(int64_t u0, int64_t u1, int bins, std::vector<int64_t>& seg) 
 }
 
 // FP64: persistent CTAs; split modes: persistent clusters of p->cl CTAs.
-int default_bins(const bsmm_plan_s* p) {
+int machine_bins(const bsmm_plan_s* p) {
   int64_t c;
   if (p->opt.mode == BSMM_FP64)
     c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm(p->f64_tile));
   else
     c = std::max(1, split_max_clusters(p->s, p->cl, p->stages));
   if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
-  c = std::min<int64_t>(c, std::max<int64_t>(1, p->n_units));
   return (int)std::max<int64_t>(1, c);
+}
+
+int default_bins(const bsmm_plan_s* p) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(machine_bins(p), std::max<int64_t>(1, p->n_units)));
+}
+
+// Split k (Sec. 3.2, Fig. 2). The paper cuts the dependency between the rank-k updates
+// of one C tile by running each update as a multiply task into a temporary and adding
+// the temporaries in a separate task. Here a region's k-list is cut into a few
+// consecutive pieces only when that lets the persistent grid fill: a piece costs its
+// share of the region's work plus a fixed overhead (pipeline start and drain, the
+// partial sum's store and its reduction), and the longest-processing-time packing of
+// the pieces is simulated for several granularities.
+static double lpt_makespan(const std::vector<double>& cost, const std::vector<int32_t>& n, int bins, double overhead) {
+  std::vector<double> pc;
+  for (size_t u = 0; u < cost.size(); u++)
+    for (int32_t k = 0; k < n[u]; k++) pc.push_back(cost[u] / n[u] + (n[u] > 1 ? overhead : 0.0));
+  std::sort(pc.begin(), pc.end(), std::greater<double>());
+  std::priority_queue<double, std::vector<double>, std::greater<double>> heap;
+  for (int b = 0; b < bins; b++) heap.push(0.0);
+  double mk = 0.0;
+  for (double c : pc) {
+    double l = heap.top() + c;
+    heap.pop();
+    mk = std::max(mk, l);
+    heap.push(l);
+  }
+  return mk;
+}
+
+// Pieces per unit. Forced (ksplit >= 2): min(ksplit, len) for every unit. Automatic
+// (ksplit == 0): target piece costs total / (bins * g) for g in kGran give every unit
+// clamp(ceil(cost / target), 1, len) pieces; the candidate with the shortest simulated
+// makespan is taken if it is at least 10% shorter than the unsplit one.
+std::vector<int32_t> choose_pieces(const std::vector<double>& cost, const std::vector<int64_t>& len, int bins,
+                                   double overhead, int ksplit) {
+  const size_t n = cost.size();
+  std::vector<int32_t> one(n, 1);
+  if (ksplit == 1 || n == 0) return one;
+  if (ksplit >= 2) {
+    for (size_t u = 0; u < n; u++) one[u] = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ksplit, len[u]));
+    return one;
+  }
+  constexpr int kGran[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  double total = 0.0, mx = 0.0;
+  for (size_t u = 0; u < n; u++) {
+    total += cost[u];
+    mx = std::max(mx, cost[u]);
+  }
+  const double avg = total / std::max(1, bins);
+  if (mx <= avg / kGran[sizeof(kGran) / sizeof(kGran[0]) - 1]) return one;  // no candidate cuts a unit
+  double best = 0.9 * lpt_makespan(cost, one, bins, overhead);
+  std::vector<int32_t> pick = one;
+  for (int g : kGran) {
+    const double target = avg / g;
+    std::vector<int32_t> nn(n, 1);
+    bool any = false;
+    for (size_t u = 0; u < n; u++) {
+      const int64_t k = std::min<int64_t>(std::max<int64_t>(1, (int64_t)std::ceil(cost[u] / target)),
+                                          std::max<int64_t>(1, len[u]));
+      nn[u] = (int32_t)std::min<int64_t>(k, 1 << 20);
+      any |= nn[u] > 1;
+    }
+    if (!any) continue;
+    const double mk = lpt_makespan(cost, nn, bins, overhead);
+    if (mk < best) {
+      best = mk;
+      pick = nn;
+    }
+  }
+  return pick;
 }
 
 }  // namespace bsmm
@@ -190,37 +260,80 @@ bsmm_status upload_schedule(bsmm_plan_s* p) {
 // FP64 mode: units are 64x64 sub-tiles of the C tiles of S_C; each runs the tile's
 // ascending k-list.
 // ------------------------------------------------------------------------------------
+// Cost charged per piece when simulating a split k-list, in useful flops: about 3 us of
+// one FP64 CTA (pipeline start, the partial's store and its share of the reduction).
+constexpr double kF64PieceOverhead = 4096.0;
+
 bsmm_status plan_fp64(bsmm_plan_s* p) {
-  const int M = p->M, N = p->N, K = p->K;
+  const int M = p->M, N = p->N;
   // Sub-tile edge: 32 by default. The kernel skips the register-tile rows, columns and
   // inner steps a ragged sub-tile lacks, so padding costs little at either edge; 32-wide
   // units are four times as many, which balances the persistent CTAs better, and measured
   // as fast or faster than 64 on every workload shape here (64 stays an option).
   p->f64_tile = p->opt.fp64_tile ? p->opt.fp64_tile : 32;
   const int T = p->f64_tile;
+  // regions (sub-tiles of the C tiles of S_C), each with its tile's k-list
+  std::vector<Fp64Unit> base;
+  std::vector<double> bcost;
+  std::vector<int64_t> blen;
   for (int i = 0; i < M; i++)
     for (int j = 0; j < N; j++) {
-      if (!p->cs[(int64_t)i * N + j]) continue;
+      const int64_t t = (int64_t)i * N + j;
+      if (!p->cs[t]) continue;
       const int ri = p->r[i], cj = p->c[j];
       if (ri == 0 || cj == 0) continue;
-      int64_t kq = 0, kg = 0, nk = 0;
-      for (int64_t t = p->kptr[(int64_t)i * N + j]; t < p->kptr[(int64_t)i * N + j + 1]; t++) {
-        const int qk = p->q[p->klist[t]];
-        kq += qk;
-        kg += log2i_ceil_div(qk, kF64BK);
-        nk++;
-      }
+      int64_t kq = 0;
+      for (int64_t e = p->kptr[t]; e < p->kptr[t + 1]; e++) kq += p->q[p->klist[e]];
       for (int r0 = 0; r0 < ri; r0 += T)
         for (int c0 = 0; c0 < cj; c0 += T) {
           const int rows = std::min(T, ri - r0), cols = std::min(T, cj - c0);
-          p->f64_units.push_back({i, j, r0, c0});
-          const double fl = 2.0 * rows * cols * (double)kq;
-          p->flop_cost.push_back(std::max(fl, 1.0));
-          float f[BSMM_NFEATURES] = {lg(rows), lg(cols), lg((double)nk), lg((double)kq), lg((double)kg),
-                                     lg(fl), (float)(fl / std::max(1.0, 2.0 * T * T * kF64BK * (double)kg)),
-                                     0.0f, 0.0f, 0.0f, 0.0f, lg((double)kg)};
-          p->features.insert(p->features.end(), f, f + BSMM_NFEATURES);
+          base.push_back({i, j, r0, c0, p->kptr[t], p->kptr[t + 1], -1, 0});
+          bcost.push_back(std::max(2.0 * rows * cols * (double)kq, 1.0));
+          blen.push_back(p->kptr[t + 1] - p->kptr[t]);
         }
+    }
+  // automatic cuts change FP64 rounding, so FP64 takes them only when asked (ksplit = -1)
+  const int ks = p->opt.ksplit == 0 ? 1 : p->opt.ksplit == -1 ? 0 : p->opt.ksplit;
+  const std::vector<int32_t> np = choose_pieces(bcost, blen, machine_bins(p), kF64PieceOverhead, ks);
+  std::vector<int32_t> slot0(base.size(), -1);
+  int32_t maxp = 1;
+  p->n_slots = 0;
+  for (size_t u = 0; u < base.size(); u++) {
+    maxp = std::max(maxp, np[u]);
+    if (np[u] < 2) continue;
+    slot0[u] = (int32_t)p->n_slots;
+    p->f64_red.push_back({base[u].i, base[u].j, base[u].r0, base[u].c0, slot0[u], np[u]});
+    p->n_slots += np[u];
+  }
+  // units piece by piece (every region's piece 0, then every piece 1, ...): the pieces
+  // that run at the same time then read the same part of the k range
+  for (int32_t pc = 0; pc < maxp; pc++)
+    for (size_t u = 0; u < base.size(); u++) {
+      const int32_t n = np[u];
+      if (pc >= n) continue;
+      Fp64Unit un = base[u];
+      const int64_t L = un.t1 - un.t0;
+      if (n > 1) {
+        un.t1 = base[u].t0 + (int64_t)(pc + 1) * L / n;
+        un.t0 = base[u].t0 + (int64_t)pc * L / n;
+        un.slot = slot0[u] + pc;
+      }
+      const int rows = std::min(T, p->r[un.i] - un.r0), cols = std::min(T, p->c[un.j] - un.c0);
+      int64_t kq = 0, kg = 0;
+      for (int64_t e = un.t0; e < un.t1; e++) {
+        const int qk = p->q[p->klist[e]];
+        kq += qk;
+        kg += log2i_ceil_div(qk, kF64BK);
+      }
+      const int64_t nk = un.t1 - un.t0;
+      p->f64_units.push_back(un);
+      p->unit_pieces.push_back(n);
+      const double fl = 2.0 * rows * cols * (double)kq;
+      p->flop_cost.push_back(std::max(fl, 1.0));
+      float f[BSMM_NFEATURES] = {lg(rows), lg(cols), lg((double)nk), lg((double)kq), lg((double)kg),
+                                 lg(fl), (float)(fl / std::max(1.0, 2.0 * T * T * kF64BK * (double)kg)),
+                                 0.0f, 0.0f, 0.0f, 0.0f, lg((double)kg)};
+      p->features.insert(p->features.end(), f, f + BSMM_NFEATURES);
     }
   p->n_units = (int64_t)p->f64_units.size();
   return BSMM_OK;
@@ -231,6 +344,10 @@ bsmm_status plan_fp64(bsmm_plan_s* p) {
 // column index spaces; a unit's k order is the ascending set of inner blocks for which
 // both its packed A row block and packed B column block are present.
 // ------------------------------------------------------------------------------------
+// Cost charged per piece when simulating a split k-list, in useful flops: about 4 us of
+// one cluster (pipeline start and drain, the 128-bit partial's store and its reduction).
+constexpr double kSplitPieceOverhead = 4.0e6;
+
 bsmm_status plan_split(bsmm_plan_s* p) {
   const int M = p->M, N = p->N, K = p->K;
   const int s = p->s, tn = p->tn;
@@ -322,39 +439,105 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   // then work concurrently on a few A row panels and a few B column panels at a time,
   // so both stay in L2 while the CTAs stream through k.
   constexpr int kRasterRows = 8;
+  std::vector<SplitUnit> base;
+  std::vector<double> bcost;
+  std::vector<int64_t> blen, bk_ptr{0};
+  std::vector<int32_t> bk;  // each region's k-list (CSR)
   for (int rb0 = 0; rb0 < RB; rb0 += kRasterRows)
     for (int cb = 0; cb < CBG; cb++)  // cb indexes column-block groups here
       for (int rb = rb0; rb < std::min(RB, rb0 + kRasterRows); rb++) {
-      if (!umark[(size_t)rb * CBG + cb]) continue;
-      p->sp_units.push_back({rb, cb});
+        if (!umark[(size_t)rb * CBG + cb]) continue;
+        base.push_back({rb, cb, 0, K, -1, 0});
+        for (int wd = 0; wd < KW; wd++) {
+          uint64_t bits = presA[(size_t)rb * KW + wd] & presBg[(size_t)cb * KW + wd];
+          while (bits) {
+            bk.push_back(wd * 64 + __builtin_ctzll(bits));
+            bits &= bits - 1;
+          }
+        }
+        bk_ptr.push_back((int64_t)bk.size());
+        blen.push_back(bk_ptr.back() - bk_ptr[bk_ptr.size() - 2]);
+        bcost.push_back(0.0);  // set below
+      }
+  // useful flops of a region over inner blocks [k0, k1): its C tiles' overlap with the
+  // region times 2 q_k summed over their k-lists within the range
+  auto region_flops = [&](int rb, int cb, int k0, int k1, int& nrt, int& nct) {
+    const int64_t m0 = (int64_t)rb * kSplitBM, m1 = std::min<int64_t>(Mtot, m0 + kSplitBM);
+    const int64_t n0 = (int64_t)cb * CL * tn, n1 = std::min<int64_t>(Ntot, n0 + (int64_t)CL * tn);
+    const bool whole = k0 == 0 && k1 == K;
+    double fl = 0.0;
+    nrt = 0;
+    nct = 0;
+    for (int i = row_tile[m0]; i < M && p->ro[i] < m1; i++) {
+      const int64_t ov_r = std::min(m1, p->ro[i + 1]) - std::max(m0, p->ro[i]);
+      if (ov_r <= 0) continue;
+      nrt++;
+      for (int j = col_tile[n0]; j < N && p->co[j] < n1; j++) {
+        const int64_t ov_c = std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]);
+        if (ov_c <= 0) continue;
+        const int64_t t = (int64_t)i * N + j;
+        double wt = w[t];
+        if (!whole) {
+          wt = 0.0;
+          const int32_t* b = p->klist.data() + p->kptr[t];
+          const int32_t* e = p->klist.data() + p->kptr[t + 1];
+          for (const int32_t* x = std::lower_bound(b, e, k0); x != e && *x < k1; x++) wt += 2.0 * p->q[*x];
+        }
+        fl += (double)ov_r * (double)ov_c * wt;
+      }
+    }
+    for (int j = col_tile[n0]; j < N && p->co[j] < n1; j++)
+      if (std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]) > 0) nct++;
+    return fl;
+  };
+  for (size_t u = 0; u < base.size(); u++) {
+    int nrt, nct;
+    bcost[u] = std::max(region_flops(base[u].rb, base[u].cb, 0, K, nrt, nct), 1.0);
+  }
+  const std::vector<int32_t> np =
+      choose_pieces(bcost, blen, machine_bins(p), kSplitPieceOverhead, p->opt.ksplit == -1 ? 0 : p->opt.ksplit);
+  std::vector<int32_t> slot0(base.size(), -1);
+  int32_t maxp = 1;
+  p->n_slots = 0;
+  for (size_t u = 0; u < base.size(); u++) {
+    maxp = std::max(maxp, np[u]);
+    if (np[u] < 2) continue;
+    slot0[u] = (int32_t)p->n_slots;
+    p->sp_red.push_back({base[u].rb, base[u].cb, slot0[u], np[u]});
+    p->n_slots += np[u];
+  }
+  // units piece by piece (every region's piece 0, then every piece 1, ...), so the pieces
+  // that run at the same time read the same part of the k range
+  for (int32_t pc = 0; pc < maxp; pc++)
+    for (size_t u = 0; u < base.size(); u++) {
+      const int32_t n = np[u];
+      if (pc >= n) continue;
+      SplitUnit un = base[u];
+      const int32_t* ks = bk.data() + bk_ptr[u];
+      const int64_t L = blen[u];
+      int64_t lo = 0, hi = L;
+      if (n > 1) {
+        lo = (int64_t)pc * L / n;
+        hi = (int64_t)(pc + 1) * L / n;
+        un.k0 = ks[lo];
+        un.k1 = hi < L ? ks[hi] : K;
+        un.slot = slot0[u] + pc;
+      }
+      p->sp_units.push_back(un);
+      p->unit_pieces.push_back(n);
+      const int rb = un.rb, cb = un.cb;
       const int64_t m0 = (int64_t)rb * kSplitBM, m1 = std::min<int64_t>(Mtot, m0 + kSplitBM);
       const int64_t n0 = (int64_t)cb * CL * tn, n1 = std::min<int64_t>(Ntot, n0 + (int64_t)CL * tn);
-      double fl = 0.0;
-      int nrt = 0, nct = 0;
-      for (int i = row_tile[m0]; i < M && p->ro[i] < m1; i++) {
-        const int64_t ov_r = std::min(m1, p->ro[i + 1]) - std::max(m0, p->ro[i]);
-        if (ov_r <= 0) continue;
-        nrt++;
-        for (int j = col_tile[n0]; j < N && p->co[j] < n1; j++) {
-          const int64_t ov_c = std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]);
-          if (ov_c <= 0) continue;
-          fl += (double)ov_r * (double)ov_c * w[(int64_t)i * N + j];
-        }
+      int nrt, nct;
+      const double fl = region_flops(rb, cb, un.k0, un.k1, nrt, nct);
+      int64_t kq = 0, kg = 0, kc = 0;
+      for (int64_t x = lo; x < hi; x++) {
+        const int k = ks[x];
+        kq += p->q[k];
+        kg += log2i_ceil_div(p->q[k], 16);
+        kc += log2i_ceil_div(p->q[k], kSplitKC);
       }
-      for (int j = col_tile[n0]; j < N && p->co[j] < n1; j++)
-        if (std::min(n1, p->co[j + 1]) - std::max(n0, p->co[j]) > 0) nct++;
-      int64_t nk = 0, kq = 0, kg = 0, kc = 0;
-      for (int wd = 0; wd < KW; wd++) {
-        uint64_t bits = presA[(size_t)rb * KW + wd] & presBg[(size_t)cb * KW + wd];
-        while (bits) {
-          const int k = wd * 64 + __builtin_ctzll(bits);
-          bits &= bits - 1;
-          nk++;
-          kq += p->q[k];
-          kg += log2i_ceil_div(p->q[k], 16);
-          kc += log2i_ceil_div(p->q[k], kSplitKC);
-        }
-      }
+      const int64_t nk = hi - lo;
       p->flop_cost.push_back(std::max(fl, 1.0));
       const double padded = 2.0 * kSplitBM * tn * CL * 16.0 * (double)kg;
       float f[BSMM_NFEATURES] = {lg((double)(m1 - m0)), lg((double)(n1 - n0)), lg((double)nk), lg((double)kq),
@@ -380,6 +563,8 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   if ((st = upload(p->d_a_blocks, a_blocks)) != BSMM_OK) return st;
   if ((st = upload(p->d_b_blocks, b_blocks)) != BSMM_OK) return st;
   if ((st = upload(p->d_units, p->sp_units)) != BSMM_OK) return st;
+  if ((st = upload(p->d_red, p->sp_red)) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_part, (size_t)p->n_slots * CL * kSplitBM * tn * 16)) != BSMM_OK) return st;
   if ((st = upload(p->d_am, p->am)) != BSMM_OK) return st;
   if ((st = upload(p->d_bm, p->bm)) != BSMM_OK) return st;
   p->n_a_tiles = (int32_t)a_tiles.size();
@@ -435,6 +620,7 @@ bsmm_status validate_options(const bsmm_options& o) {
   if ((o.transa != 0 && o.transa != 1) || (o.transb != 0 && o.transb != 1))
     return set_error("transa and transb must be 0 or 1"), BSMM_ERR_INVALID;
   if (o.split_scale != 0 && o.split_scale != 1) return set_error("split_scale must be 0 or 1"), BSMM_ERR_INVALID;
+  if (o.ksplit < -1 || o.ksplit > 65536) return set_error("ksplit must be in -1..65536"), BSMM_ERR_INVALID;
   return BSMM_OK;
 }
 
@@ -462,7 +648,7 @@ void bsmm_destroy(bsmm_plan_t p) {
                     &p->d_presA, &p->d_presB, &p->d_presBg, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
                     &p->d_eArow, &p->d_eBcol, &p->d_eAmaxr, &p->d_eBmaxc,
                     &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_urow, &p->d_ucol, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
-                    &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta,
+                    &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta, &p->d_part, &p->d_red,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
   for (DevBuf* b : bufs) dev_free(*b);
   for (cudaEvent_t& e : p->ev)
@@ -598,7 +784,9 @@ bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, in
     bsmm_destroy(p);
     return st;
   }
-  if (o.mode == BSMM_FP64 && (st = upload(p->d_units, p->f64_units)) != BSMM_OK) {
+  if (o.mode == BSMM_FP64 &&
+      ((st = upload(p->d_units, p->f64_units)) != BSMM_OK || (st = upload(p->d_red, p->f64_red)) != BSMM_OK ||
+       (st = dev_alloc(p->d_part, sizeof(double) * (size_t)p->n_slots * p->f64_tile * p->f64_tile)) != BSMM_OK)) {
     bsmm_destroy(p);
     return st;
   }
@@ -641,6 +829,15 @@ bsmm_status bsmm_plan_query(bsmm_plan_t p, int64_t* n_ctiles, int64_t* n_triples
   if (useful_flops) *useful_flops = p->useful_flops;
   if (c_mask_out && !p->cs.empty()) std::memcpy(c_mask_out, p->cs.data(), p->cs.size());
   if (n_units) *n_units = p->n_units;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_plan_ksplit(bsmm_plan_t p, int64_t* n_regions, int64_t* n_pieces, int32_t* pieces) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  if (n_regions) *n_regions = (int64_t)(p->opt.mode == BSMM_FP64 ? p->f64_red.size() : p->sp_red.size());
+  if (n_pieces) *n_pieces = p->n_slots;
+  if (pieces && !p->unit_pieces.empty())
+    std::memcpy(pieces, p->unit_pieces.data(), sizeof(int32_t) * p->unit_pieces.size());
   return BSMM_OK;
 }
 

@@ -684,23 +684,89 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   return neg ? -d : d;
 }
 
+// w += v, 128-bit two's complement
+__device__ __forceinline__ void add128(uint32_t (&w)[4], const uint4& v) {
+  asm("add.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.cc.u32 %2, %2, %6;\n\t"
+      "addc.u32 %3, %3, %7;"
+      : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
+      : "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+}
+
+// True when v is true in every thread of the kEpiThreads epilogue threads (named barrier 1
+// with an AND reduction; all of them must call it).
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(kEpiThreads)
+      : "memory");
+  return r != 0;
+}
+
+// C = alpha*v + beta*C for a 128 x TN region staged in shared memory (row stride TN + 1),
+// on the elements that lie in S_C tiles. Warp w of NW stores rows w*(128/NW) .. with
+// lane = column (TN == 32), so a store instruction writes one or two contiguous row
+// segments; lanes below 128/NW fetch the rows' tile and row-in-tile, shuffles hand them out.
+template <int TN, int NW>
+__device__ __forceinline__ void store_region(const SplitArgs& P, const double* cstage, int rb, int cb, int w, int lane,
+                                             int32_t* err) {
+  static_assert(TN == 32, "one column per lane");
+  constexpr int kRowsPerWarp = kSplitBM / NW;
+  const int64_t nl = (int64_t)cb * TN + lane;
+  const bool col_ok = nl < P.Ntot;
+  const int jl = col_ok ? P.col_tile[nl] : 0;
+  const int64_t lcl = col_ok ? nl - P.co[jl] : 0;
+  const int64_t cjl = col_ok ? P.c[jl] : 0;
+  const int64_t mr = (int64_t)rb * kSplitBM + w * kRowsPerWarp + (lane % kRowsPerWarp);
+  const int ir = mr < P.Mtot ? P.row_tile[mr] : 0;
+  const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
+  const double alpha = P.alpha, beta = P.beta;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerWarp; rr++) {
+    const int r2 = w * kRowsPerWarp + rr;
+    const int64_t m2 = (int64_t)rb * kSplitBM + r2;
+    const int i2 = __shfl_sync(0xffffffffu, ir, rr);
+    const int lr2 = __shfl_sync(0xffffffffu, lrr, rr);
+    if (m2 < P.Mtot && col_ok) {
+      const int64_t tile = (int64_t)i2 * P.N + jl;
+      const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
+      if (off == -1) atomicOr(err, kErrBadOffset);
+      if (off >= 0) {
+        double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
+        double vv = cstage[r2 * (TN + 1) + lane];
+        if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
+        if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
+        *dst = vv;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernel 3: contraction
 // Ascending k blocks of one unit (a 128-row block times a group of cl column blocks):
-// presA[rb] & presBg[group]. Every CTA of the cluster walks the same list, because they
+// presA[rb] & presBg[group], within the unit's inner-block range [k0, k1) (all of it, or
+// one piece under split k). Every CTA of the cluster walks the same list, because they
 // share the A stream; own_b() tells whether the CTA's own column block has that k block.
 struct UnitIter {
   const uint64_t* pa;
   const uint64_t* pb;
   const uint64_t* po;  // this CTA's own column block (null: beyond the last one)
-  int kwords, wd;
+  int kwords, wd, kend;
   uint64_t bits;
-  __device__ void init(const SplitArgs& a, int rb, int grp, int cb) {
-    pa = a.presA + (size_t)rb * a.kwords;
-    pb = a.presBg + (size_t)grp * a.kwords;
+  __device__ void init(const SplitArgs& a, const SplitUnit& un, int cb) {
+    pa = a.presA + (size_t)un.rb * a.kwords;
+    pb = a.presBg + (size_t)un.cb * a.kwords;
     po = cb < a.CB ? a.presB + (size_t)cb * a.kwords : nullptr;
     kwords = a.kwords;
-    wd = 0;
-    bits = pa[0] & pb[0];
+    kend = un.k1;
+    wd = un.k0 >> 6;
+    bits = wd < kwords ? (pa[wd] & pb[wd]) & (~0ull << (un.k0 & 63)) : 0ull;
   }
   __device__ bool own_b(int k) const { return po && ((po[k >> 6] >> (k & 63)) & 1); }
   __device__ int next_own() {  // next k block that also has a B tile in this CTA's column block
@@ -714,6 +780,11 @@ struct UnitIter {
       bits = pa[wd] & pb[wd];
     }
     const int k = wd * 64 + __ffsll((long long)bits) - 1;
+    if (k >= kend) {  // past the unit's range
+      bits = 0;
+      wd = kwords;
+      return -1;
+    }
     bits &= bits - 1;
     return k;
   }
@@ -726,10 +797,14 @@ struct UnitIter {
 // to the same list, so they agree on where the accumulator is drained.
 // The scale class of k block k for the unit's row block rb and column block cb: true
 // and the binary offset sig of its products when both classes are uniform.
+// A class more than kSplitGuard binades below the unit's largest scale is not uniform
+// either: its products enter the accumulator rounded down (floor) to its unit, and the
+// floor of a sum is not the sum of the floors, so such k blocks are drained one by one,
+// each product taking its own floor as the exact sum's definition states.
 __device__ __forceinline__ bool scale_class(const SplitArgs& P, int k, int rb, int cb, int& sig) {
   if (!P.urow) return false;
   const int u = P.urow[(size_t)k * P.RB + rb], v = P.ucol[(size_t)k * P.CB + cb];
-  if (u == kNonUniform || v == kNonUniform) return false;
+  if (u == kNonUniform || v == kNonUniform || u + v < -kSplitGuard) return false;
   sig = u + v;
   return true;
 }
@@ -808,7 +883,7 @@ struct ChunkCursor {
       const SplitUnit un = P->units[g];
       rb = un.rb;
       cb = un.cb * cl + rank;
-      it.init(*P, un.rb, un.cb, cb);
+      it.init(*P, un, cb);
       in_unit = true;
     }
   }
@@ -949,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         const SplitUnit un = P.units[g];
         const int cb = un.cb * CL + rank;
         UnitIter it;
-        it.init(P, un.rb, un.cb, cb);
+        it.init(P, un, cb);
         GroupRule grp;
         bool in_group = false;
         uint32_t buf = 0;
@@ -1067,7 +1142,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
 #pragma unroll
       for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
       UnitIter it;
-      it.init(P, un.rb, un.cb, cb);
+      it.init(P, un, cb);
       int kt = it.next_own();
       while (kt >= 0) {
         // the accumulation group starting at kt, and the binary position of its integers:
@@ -1148,61 +1223,39 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         if (lane == 0) mbar_arrive(&tempty[buf]);
         tcount++;
       }
-      // (a warp whose wait gave up still passes the two barriers below, so that no other
+      // (a warp whose wait gave up still passes the barriers below, so that no other
       // epilogue warp waits at them for it; every wait before them is bounded and sees the
-      // abort flag, so all eight warps reach them)
-      // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles.
-      // Each thread rounds its row's sums to doubles into shared memory; then every warp
-      // stores whole rows, lane = column, so a store instruction writes one or two
-      // contiguous row segments instead of 32 scattered elements.
-      if (ok) {
-        // the accumulator's unit 2^L: per row block and column block of tiles, or per row and
-        // column with row/column scaling
-        const int Lrow =
-            row_ok ? (P.rowscale ? P.eAmaxr[m] : P.eAmax[P.row_tile[m]]) - kSplitBeta * (S + 1) - kSplitGuard : 0;
-        double* srow = cstage + row * (TN + 1) + half * TH;
+      // abort flag, so all eight warps reach them, and the last one agrees on the outcome,
+      // so all eight leave the unit loop together)
+      if (un.slot < 0) {
+        // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles.
+        // Each thread rounds its row's sums to doubles into shared memory; then every warp
+        // stores whole rows, lane = column, so a store instruction writes one or two
+        // contiguous row segments instead of 32 scattered elements.
+        if (ok) {
+          // the accumulator's unit 2^L: per row block and column block of tiles, or per row
+          // and column with row/column scaling
+          const int Lrow =
+              row_ok ? (P.rowscale ? P.eAmaxr[m] : P.eAmax[P.row_tile[m]]) - kSplitBeta * (S + 1) - kSplitGuard : 0;
+          double* srow = cstage + row * (TN + 1) + half * TH;
 #pragma unroll
-        for (int c = 0; c < TH; c++) {
-          const int64_t n = n0 + c;
-          srow[c] = (row_ok && n < P.Ntot)
-                        ? acc_to_double(acc[c], Lrow + (P.rowscale ? P.eBmaxc[n] : P.eBmax[P.col_tile[n]]))
-                        : 0.0;
-        }
-      }
-      asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
-      if (ok && !*abort_flag) {
-        const int64_t nl = (int64_t)cb * TN + lane;  // TN == 32: one column per lane
-        const bool col_ok = nl < P.Ntot;
-        const int jl = col_ok ? P.col_tile[nl] : 0;
-        const int64_t lcl = col_ok ? nl - P.co[jl] : 0;
-        const int64_t cjl = col_ok ? P.c[jl] : 0;
-        constexpr int kRowsPerWarp = kSplitBM / kSplitEpiWarps;
-        // lane r < kRowsPerWarp fetches row r's tile and row-in-tile; shuffles hand them out
-        const int64_t mr = (int64_t)un.rb * kSplitBM + ew * kRowsPerWarp + (lane % kRowsPerWarp);
-        const int ir = mr < P.Mtot ? P.row_tile[mr] : 0;
-        const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
-        const double alpha = P.alpha, beta = P.beta;
-#pragma unroll
-        for (int rr = 0; rr < kRowsPerWarp; rr++) {
-          const int r2 = ew * kRowsPerWarp + rr;
-          const int64_t m2 = (int64_t)un.rb * kSplitBM + r2;
-          const int i2 = __shfl_sync(0xffffffffu, ir, rr);
-          const int lr2 = __shfl_sync(0xffffffffu, lrr, rr);
-          if (m2 < P.Mtot && col_ok) {
-            const int64_t tile = (int64_t)i2 * P.N + jl;
-            const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
-            if (off == -1) atomicOr(a.err, kErrBadOffset);
-            if (off >= 0) {
-              double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
-              double vv = cstage[r2 * (TN + 1) + lane];
-              if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
-              if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
-              *dst = vv;
-            }
+          for (int c = 0; c < TH; c++) {
+            const int64_t n = n0 + c;
+            srow[c] = (row_ok && n < P.Ntot)
+                          ? acc_to_double(acc[c], Lrow + (P.rowscale ? P.eBmaxc[n] : P.eBmax[P.col_tile[n]]))
+                          : 0.0;
           }
         }
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+        if (ok && !*abort_flag) store_region<TN, kSplitEpiWarps>(P, cstage, un.rb, cb, ew, lane, a.err);
+      } else if (ok) {
+        // a piece of a split k-list: its exact partial sums go to the workspace (column-
+        // major, so the 32 rows of a warp write 512 contiguous bytes per column)
+        uint4* dst = P.part + ((size_t)un.slot * CL + rank) * (TN * kSplitBM) + (size_t)half * TH * kSplitBM + row;
+#pragma unroll
+        for (int c = 0; c < TH; c++) dst[(size_t)c * kSplitBM] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
       }
-      asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");  // cstage is free again
+      ok = epi_all(ok);  // cstage is free again; every epilogue warp has the same outcome
       if (!ok) break;
       if (a.timings && rank == 0) {
         if (ew == 0 && lane == 0) {
@@ -1218,6 +1271,39 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   if constexpr (CL > 1) cluster_sync();  // no peer multicasts into or signals this CTA any more
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, kTmemCols);
+}
+
+// ---------------------------------------------------------------- kernel 4: split-k reduction
+// The reduction task of a region whose k-list was cut into pieces (Sec. 3.2, Fig. 2).
+// The pieces' partial sums are exact 128-bit integers in the same unit 2^L, so adding
+// them is exact in any order and the rounded result equals the unsplit one bit for bit;
+// it is rounded once and stored like the contraction's epilogue. One CTA of 256 threads
+// per (region, column block of the region's group); thread = (row, half of the columns).
+template <int TN>
+__global__ void __launch_bounds__(256) split_reduce_kernel(const __grid_constant__ SplitArgs a) {
+  constexpr int TH = TN / 2;
+  __shared__ double cstage[kSplitBM * (TN + 1)];
+  const SplitRed rd = a.red[blockIdx.x / a.cl];
+  const int rank = blockIdx.x % a.cl;
+  const int cb = rd.cb * a.cl + rank;
+  if (cb >= a.CB) return;
+  const int row = threadIdx.x % kSplitBM, half = threadIdx.x / kSplitBM;
+  const int64_t m = (int64_t)rd.rb * kSplitBM + row;
+  const bool row_ok = m < a.Mtot;
+  const int Lrow =
+      row_ok ? (a.rowscale ? a.eAmaxr[m] : a.eAmax[a.row_tile[m]]) - kSplitBeta * (a.s + 1) - kSplitGuard : 0;
+  const int64_t n0 = (int64_t)cb * TN + half * TH;
+  const size_t piece_stride = (size_t)a.cl * TN * kSplitBM;
+  const uint4* src = a.part + ((size_t)rd.slot0 * a.cl + rank) * (TN * kSplitBM) + (size_t)half * TH * kSplitBM + row;
+  for (int c = 0; c < TH; c++) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (int p = 0; p < rd.n; p++) add128(w, src[p * piece_stride + (size_t)c * kSplitBM]);
+    const int64_t n = n0 + c;
+    cstage[row * (TN + 1) + half * TH + c] =
+        (row_ok && n < a.Ntot) ? acc_to_double(w, Lrow + (a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]])) : 0.0;
+  }
+  __syncthreads();
+  store_region<TN, 8>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
 }
 
 template <int S, int TN, int CL>
@@ -1285,6 +1371,15 @@ int max_clusters_s(int cl, int stages) {
 
 }  // namespace
 
+int split_prep_kernels(const SplitArgs& a) {  // the kernels launch_split_prep launches
+  int n = 0;
+  if (a.n_a_tiles + a.n_b_tiles > 0) n += a.rowscale ? 2 : 1;
+  if (a.rowscale ? a.Mtot + a.Ntot > 0 : a.M + a.N > 0) n++;
+  if (a.urow && (int64_t)a.K * (a.RB + a.CB) > 0) n++;
+  if (a.n_a_blocks + a.n_b_blocks > 0) n++;
+  return n;
+}
+
 cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* ev, int* k) {
   if (a.n_a_tiles + a.n_b_tiles > 0) {
     split_exp_kernel<<<a.n_a_tiles + a.n_b_tiles, 256, 0, st>>>(a);
@@ -1320,8 +1415,18 @@ cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEven
   if (e != cudaSuccess) return e;
   e = launch_split_mma(a, ctas, st);
   if (ev) cudaEventRecord(ev[++k], st);
+  if (e == cudaSuccess && !a.prods && a.n_red > 0) {  // a batch launches its products' reductions
+    e = launch_split_reduce(a, st);
+    if (ev) cudaEventRecord(ev[++k], st);
+  }
   if (nk) *nk = k;
   return e;
+}
+
+cudaError_t launch_split_reduce(const SplitArgs& a, cudaStream_t st) {
+  if (a.n_red <= 0) return cudaSuccess;
+  split_reduce_kernel<32><<<(unsigned)(a.n_red * a.cl), 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_mma(const SplitArgs& a, int ctas, cudaStream_t st) {

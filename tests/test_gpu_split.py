@@ -132,6 +132,28 @@ def test_exponent_span_beyond_guard_bits():
     check(prob, 3)
 
 
+def test_deep_uniform_classes_are_not_merged():
+    """Two consecutive k blocks with the same scale class 60 binades below the row block's
+    largest tile (a stored A tile whose B partner is absent): their products enter the
+    accumulator floored to its unit, block by block as the oracle states, so they must not
+    share one TMEM accumulation (the floor of a sum is not the sum of the floors)."""
+    rng = np.random.default_rng(9)
+    r = np.array([128], np.int32)
+    q = np.array([16, 16, 16, 16], np.int32)
+    c = np.array([32], np.int32)
+    am = np.ones((1, 4), np.uint8)
+    bm = np.array([[0], [1], [1], [1]], np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    A = rng.uniform(-1, 1, at)
+    B = rng.uniform(-1, 1, bt)
+    for k in (1, 2, 3):
+        A[a_off[0, k]:a_off[0, k] + 128 * 16] *= 2.0 ** -60
+    prob = G.Problem("deep_classes", r, c, q, am, bm, a_off, b_off, A, B, 1.0, 0.0)
+    for s in (6, 3):
+        check(prob, s)
+
+
 def test_too_deep_inner_block_is_rejected():
     with pytest.raises(P.BsmmError) as ei:
         P.bsmm_plan([8], [8], [513], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6)
