@@ -16,9 +16,10 @@
 // the result is fixed bit for bit, independent of schedule, unit order and k order.
 //
 // Kernels, in launch order:
-//   1. split_exp_kernel   per stored tile: the exponent e (FP64 max reduction);
-//      split_scale_kernel per row / column block: the largest tile exponent and the
-//                         per-row / per-column offsets from it.
+//   1. split_exp_kernel   per stored tile: the exponent e (integer max reduction);
+//      split_emax_kernel  per row / column block: the largest tile exponent;
+//      split_class_kernel per (k block, row block / column block): the per-row /
+//                         per-column offsets from it and the scale classes.
 //   2. split_pack_kernel  per (128-row block, k block) of A and (k block, tn-column
 //                         block) of B: the s slices, stored as bf16/fp16 in the
 //                         exact shared-memory image the tensor core reads (K-major,
@@ -350,50 +351,37 @@ __global__ void __launch_bounds__(256) split_exp_lines_kernel(SplitArgs a) {
   }
 }
 
-// ---------------------------------------------------------------- kernel 1b: relative scales
-// Per row block i: Emax_A(i) = largest exponent of its stored A tiles, and for every
-// k and every row of the block rowexp[k][m] = e_A(i,k) - Emax_A(i) (0 for an absent
-// tile); the same per column block for B. The contraction adds each tile pair's exact
-// integer at the binary position GUARD + rowexp + colexp of a 128-bit accumulator whose
-// unit is 2^(Emax_A(i) + Emax_B(j) - 7(s+1) - GUARD).
-__global__ void __launch_bounds__(256) split_scale_kernel(SplitArgs a) {
+// ---------------------------------------------------------------- kernel 1b: largest exponents
+// Per row block i: Emax_A(i) = the largest exponent of its stored A tiles (0 when none);
+// the same per column block for B. One block per row or column block, its threads
+// spread over the K inner blocks. The contraction adds each tile pair's exact integer at
+// the binary position GUARD + rowexp + colexp of a 128-bit accumulator whose unit is
+// 2^(Emax_A(i) + Emax_B(j) - 7(s+1) - GUARD); the class kernel writes rowexp and colexp.
+__global__ void __launch_bounds__(256) split_emax_kernel(SplitArgs a) {
   const bool isA = (int)blockIdx.x < a.M;
   const int t = isA ? blockIdx.x : blockIdx.x - a.M;
-  __shared__ int emax_sh;
-  if (threadIdx.x == 0) {
-    int em = INT_MIN;
-    if (isA) {
-      if (a.r[t] > 0)
-        for (int k = 0; k < a.K; k++)
-          if (a.am[(int64_t)t * a.K + k] && a.q[k] > 0) em = max(em, a.eA[(int64_t)t * a.K + k]);
-    } else {
-      if (a.c[t] > 0)
-        for (int k = 0; k < a.K; k++)
-          if (a.bm[(int64_t)k * a.N + t] && a.q[k] > 0) em = max(em, a.eB[(int64_t)k * a.N + t]);
+  int em = INT_MIN;
+  if (isA ? a.r[t] > 0 : a.c[t] > 0) {
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+      if (a.q[k] <= 0) continue;
+      if (isA) {
+        if (a.am[(int64_t)t * a.K + k]) em = max(em, a.eA[(int64_t)t * a.K + k]);
+      } else {
+        if (a.bm[(int64_t)k * a.N + t]) em = max(em, a.eB[(int64_t)k * a.N + t]);
+      }
     }
+  }
+  __shared__ int red[8];
+  for (int o = 16; o; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = em;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) em = max(em, red[w]);
     if (em == INT_MIN) em = 0;
-    emax_sh = em;
     if (isA)
       a.eAmax[t] = em;
     else
       a.eBmax[t] = em;
-  }
-  __syncthreads();
-  const int em = emax_sh;
-  if (isA) {
-    const int64_t m0 = a.ro[t], n = a.ro[t + 1] - m0;
-    for (int64_t e = threadIdx.x; e < n * a.K; e += blockDim.x) {
-      const int k = (int)(e / n);
-      const bool pres = a.am[(int64_t)t * a.K + k] && a.q[k] > 0;
-      a.rowexp[(int64_t)k * a.Mtot + m0 + e % n] = (int16_t)(pres ? a.eA[(int64_t)t * a.K + k] - em : 0);
-    }
-  } else {
-    const int64_t n0 = a.co[t], n = a.co[t + 1] - n0;
-    for (int64_t e = threadIdx.x; e < n * a.K; e += blockDim.x) {
-      const int k = (int)(e / n);
-      const bool pres = a.bm[(int64_t)k * a.N + t] && a.q[k] > 0;
-      a.colexp[(int64_t)k * a.colexp_ld + n0 + e % n] = (int16_t)(pres ? a.eB[(int64_t)k * a.N + t] - em : 0);
-    }
   }
 }
 
@@ -437,41 +425,58 @@ __global__ void __launch_bounds__(256) split_scale_lines_kernel(SplitArgs a) {
   }
 }
 
-// ---------------------------------------------------------------- kernel 1c: scale classes
-// One thread per (k block, row block) and per (k block, column block): the common
-// rowexp (colexp) of the rows (columns) whose tile is present, or kNonUniform. Two k
-// blocks whose row and column classes add up to the same value put every product of a
-// unit at the same binary position, so the contraction may accumulate them together.
+// ---------------------------------------------------------------- kernel 1c: offsets and scale classes
+// One thread per (k block, row block) and per (k block, column block). With one scale per
+// tile it first writes the offsets of its rows, rowexp[k][m] = e_A(i,k) - Emax_A(i) for a
+// stored tile (0 for an absent one), or of its columns (colexp); with one scale per row
+// and column the line kernel wrote them. Then the scale class: the common offset of the
+// rows (columns) whose tile is present, or kNonUniform. Two k blocks whose row and column
+// classes add up to the same value put every product of a unit at the same binary
+// position, so the contraction may accumulate them together.
 __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nr = (int64_t)a.K * a.RB, nc = (int64_t)a.K * a.CB;
   if (t < nr) {
     const int k = (int)(t / a.RB), rb = (int)(t % a.RB);
     int lo = INT_MAX, hi = INT_MIN;
-    if (a.q[k] > 0) {
-      const int64_t m1 = (int64_t)(rb + 1) * kSplitBM < a.Mtot ? (int64_t)(rb + 1) * kSplitBM : a.Mtot;
-      for (int64_t m = (int64_t)rb * kSplitBM; m < m1; m++) {
-        if (!a.am[(int64_t)a.row_tile[m] * a.K + k]) continue;
-        const int v = a.rowexp[(int64_t)k * a.Mtot + m];
+    const int64_t m1 = (int64_t)(rb + 1) * kSplitBM < a.Mtot ? (int64_t)(rb + 1) * kSplitBM : a.Mtot;
+    for (int64_t m = (int64_t)rb * kSplitBM; m < m1; m++) {
+      const int i = a.row_tile[m];
+      const bool pres = a.q[k] > 0 && a.am[(int64_t)i * a.K + k];
+      int v;
+      if (!a.rowscale) {
+        v = pres ? a.eA[(int64_t)i * a.K + k] - a.eAmax[i] : 0;
+        a.rowexp[(int64_t)k * a.Mtot + m] = (int16_t)v;
+      } else {
+        v = a.rowexp[(int64_t)k * a.Mtot + m];
+      }
+      if (pres) {
         lo = min(lo, v);
         hi = max(hi, v);
       }
     }
-    a.urow[t] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
+    if (a.urow) a.urow[t] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
   } else if (t < nr + nc) {
     const int64_t u = t - nr;
     const int k = (int)(u / a.CB), cb = (int)(u % a.CB);
     int lo = INT_MAX, hi = INT_MIN;
-    if (a.q[k] > 0) {
-      const int64_t n1 = (int64_t)(cb + 1) * a.tn < a.Ntot ? (int64_t)(cb + 1) * a.tn : a.Ntot;
-      for (int64_t n = (int64_t)cb * a.tn; n < n1; n++) {
-        if (!a.bm[(int64_t)k * a.N + a.col_tile[n]]) continue;
-        const int v = a.colexp[(int64_t)k * a.colexp_ld + n];
+    const int64_t n1 = (int64_t)(cb + 1) * a.tn < a.Ntot ? (int64_t)(cb + 1) * a.tn : a.Ntot;
+    for (int64_t n = (int64_t)cb * a.tn; n < n1; n++) {
+      const int j = a.col_tile[n];
+      const bool pres = a.q[k] > 0 && a.bm[(int64_t)k * a.N + j];
+      int v;
+      if (!a.rowscale) {
+        v = pres ? a.eB[(int64_t)k * a.N + j] - a.eBmax[j] : 0;
+        a.colexp[(int64_t)k * a.colexp_ld + n] = (int16_t)v;
+      } else {
+        v = a.colexp[(int64_t)k * a.colexp_ld + n];
+      }
+      if (pres) {
         lo = min(lo, v);
         hi = max(hi, v);
       }
     }
-    a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
+    if (a.ucol) a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
   }
 }
 
@@ -483,17 +488,44 @@ __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
 // subtracted 128 Z_{t-1} is even, so round-half-even commutes with it), hence
 // N_t = Z_t - 128 Z_{t-1}. Each Z_t is computed exactly from the mantissa with integer
 // shifts and a round-half-even step; no floating-point operation is involved.
-__device__ __forceinline__ long long rint_scaled(long long m, int sh) {  // rint(m 2^sh), m >= 0
-  // finite inputs always have sh < 0 (|x 2^-e| < 1); a non-finite one (already reported
-  // by the exponent kernel) must still not shift by the register width or more
-  if (sh >= 0) return sh >= 63 ? 0 : m << sh;
-  const int k = -sh;
-  if (k >= 63) return 0;  // m < 2^53 <= 2^(k-1): below one half
-  const long long q = m >> k;
-  const long long rem = m & ((1ll << k) - 1);
-  const long long half = 1ll << (k - 1);
-  return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-}
+// All Z_t of one element come from one window of its significand: x 2^-e = +-m 2^ex with
+// an integer m < 2^53; at the finest level t = S the window is W = floor(m 2^-k),
+// k = -(ex + 7S), with the round bit R (bit k-1 of m) and the sticky flag (any lower bit
+// set); level t < S drops a = 7(S-t) more bits of W, rounding with bit a-1 of W and the
+// bits below it (the finest level's fraction included). The window's shifts are
+// compile-time constants. Only the low 32 bits of Z_t are kept: N_t is small, so
+// Z_t - 128 Z_(t-1) is exact in 32-bit wrap-around arithmetic.
+struct SliceWindow {
+  unsigned long long W;  // floor(m 2^-k)
+  bool R, T, F;          // round bit and sticky bits at the finest level; F = any bit below W
+  __device__ __forceinline__ void init(unsigned long long m, int k) {
+    if (k <= 0) {  // exact (a subnormal tile's elements, or a non-finite input already reported)
+      W = -k >= 63 ? 0ull : m << -k;
+      R = T = F = false;
+    } else if (k >= 64) {
+      W = 0ull;
+      R = false;
+      T = F = m != 0ull;
+    } else {
+      W = m >> k;
+      R = (m >> (k - 1)) & 1ull;
+      T = (m & ((1ull << (k - 1)) - 1ull)) != 0ull;
+      F = R || T;
+    }
+  }
+  // low 32 bits of Z at the level a bits coarser than the finest
+  template <int A>
+  __device__ __forceinline__ uint32_t z() const {
+    if constexpr (A == 0) {
+      return (uint32_t)W + ((R && (T || (W & 1ull))) ? 1u : 0u);
+    } else {
+      const unsigned long long tr = W >> A;
+      const bool r = (W >> (A - 1)) & 1ull;
+      const bool t = F || (W & ((1ull << (A - 1)) - 1ull)) != 0ull;
+      return (uint32_t)tr + ((r && (t || (tr & 1ull))) ? 1u : 0u);
+    }
+  }
+};
 
 template <typename T>
 __device__ __forceinline__ uint16_t small_int_bits(int n) {  // |n| <= 256, exact in bf16/fp16
@@ -505,39 +537,46 @@ __device__ __forceinline__ uint16_t small_int_bits(int n) {  // |n| <= 256, exac
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void slice_store8(const double (&x)[8], int e, int s, uint8_t* base, int slice_stride,
+template <typename T, int S, int t>
+__device__ __forceinline__ void slice_level(const SliceWindow (&w)[8], const bool (&neg)[8], uint32_t (&zp)[8],
+                                            uint8_t* base, int slice_stride, uint32_t soff) {
+  if constexpr (t <= S) {
+    uint16_t h[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      uint32_t zt = w[u].template z<kSplitBeta * (S - t)>();
+      if (neg[u]) zt = 0u - zt;
+      h[u] = small_int_bits<T>((int)(zt - (zp[u] << kSplitBeta)));
+      zp[u] = zt;
+    }
+    *reinterpret_cast<uint4*>(base + (size_t)(t - 1) * slice_stride + soff) = *reinterpret_cast<uint4*>(h);
+    slice_level<T, S, t + 1>(w, neg, zp, base, slice_stride, soff);
+  }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void slice_store8(const double (&x)[8], int e, uint8_t* base, int slice_stride,
                                              uint32_t soff) {
-  long long m[8], z[8];
-  int ex[8];
+  SliceWindow w[8];
   bool neg[8];
+  uint32_t zp[8];
 #pragma unroll
   for (int u = 0; u < 8; u++) {
     const long long b = __double_as_longlong(x[u]);
     neg[u] = b < 0;
     const int be = (int)((b >> 52) & 0x7FF);
-    const long long frac = b & ((1ll << 52) - 1);
-    m[u] = be ? (frac | (1ll << 52)) : frac;
-    ex[u] = (be ? be : 1) - 1075 - e;  // x 2^-e = +-m 2^ex
-    z[u] = 0;
+    const unsigned long long frac = (unsigned long long)b & ((1ull << 52) - 1ull);
+    const unsigned long long m = be ? (frac | (1ull << 52)) : frac;
+    const int ex = (be ? be : 1) - 1075 - e;  // x 2^-e = +-m 2^ex
+    w[u].init(m, -(ex + kSplitBeta * S));
+    zp[u] = 0u;
   }
-  for (int t = 1; t <= s; t++) {
-    uint16_t h[8];
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      long long zt = rint_scaled(m[u], ex[u] + kSplitBeta * t);
-      if (neg[u]) zt = -zt;
-      const int n = (int)(zt - (z[u] << kSplitBeta));
-      z[u] = zt;
-      h[u] = small_int_bits<T>(n);
-    }
-    *reinterpret_cast<uint4*>(base + (size_t)(t - 1) * slice_stride + soff) = *reinterpret_cast<uint4*>(h);
-  }
+  slice_level<T, S, 1>(w, neg, zp, base, slice_stride, soff);
 }
 
-template <typename T>
+template <typename T, int S>
 __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
-  const int s = a.s;
+  constexpr int s = S;
   if ((int)blockIdx.x < a.n_a_blocks) {
     // A block (rb, kt): chunks of 128 rows x 32 inner elements
     const int blk = a.a_blocks[blockIdx.x];
@@ -570,7 +609,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int k0 = kc * kSplitKC + ch * 8;
 #pragma unroll
       for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : 0.0;
-      slice_store8<T>(x, e, s, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
+      slice_store8<T, S>(x, e, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
     }
   } else {
     // B block (kt, cb): chunks of tn rows (columns of B) x 32 inner elements, transposed
@@ -607,7 +646,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int k0 = kc * kSplitKC + ch * 8;
 #pragma unroll
       for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : 0.0;
-      slice_store8<T>(x, e, s, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
+      slice_store8<T, S>(x, e, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
     }
   }
 }
@@ -1375,7 +1414,7 @@ int split_prep_kernels(const SplitArgs& a) {  // the kernels launch_split_prep l
   int n = 0;
   if (a.n_a_tiles + a.n_b_tiles > 0) n += a.rowscale ? 2 : 1;
   if (a.rowscale ? a.Mtot + a.Ntot > 0 : a.M + a.N > 0) n++;
-  if (a.urow && (int64_t)a.K * (a.RB + a.CB) > 0) n++;
+  if ((a.urow || !a.rowscale) && (int64_t)a.K * (a.RB + a.CB) > 0) n++;
   if (a.n_a_blocks + a.n_b_blocks > 0) n++;
   return n;
 }
@@ -1391,18 +1430,31 @@ cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* 
     const int64_t lines = a.Mtot + a.Ntot;
     if (lines > 0) split_scale_lines_kernel<<<(unsigned)((lines + 255) / 256), 256, 0, st>>>(a);
   } else if (a.M + a.N > 0) {
-    split_scale_kernel<<<a.M + a.N, 256, 0, st>>>(a);
+    split_emax_kernel<<<a.M + a.N, 256, 0, st>>>(a);
   }
+  // tile scaling: the offsets rowexp/colexp; both: the scale classes (when kept)
   const int64_t ncls = (int64_t)a.K * (a.RB + a.CB);
-  if (a.urow && ncls > 0) split_class_kernel<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(a);
+  if ((a.urow || !a.rowscale) && ncls > 0) split_class_kernel<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[++*k], st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.n_a_blocks + a.n_b_blocks > 0) {
-    if (a.fp16)
-      split_pack_kernel<__half><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
-    else
-      split_pack_kernel<__nv_bfloat16><<<a.n_a_blocks + a.n_b_blocks, 256, 0, st>>>(a);
+    const unsigned g = (unsigned)(a.n_a_blocks + a.n_b_blocks);
+    switch (a.s * 2 + (a.fp16 ? 1 : 0)) {
+      case 2: split_pack_kernel<__nv_bfloat16, 1><<<g, 256, 0, st>>>(a); break;
+      case 3: split_pack_kernel<__half, 1><<<g, 256, 0, st>>>(a); break;
+      case 4: split_pack_kernel<__nv_bfloat16, 2><<<g, 256, 0, st>>>(a); break;
+      case 5: split_pack_kernel<__half, 2><<<g, 256, 0, st>>>(a); break;
+      case 6: split_pack_kernel<__nv_bfloat16, 3><<<g, 256, 0, st>>>(a); break;
+      case 7: split_pack_kernel<__half, 3><<<g, 256, 0, st>>>(a); break;
+      case 8: split_pack_kernel<__nv_bfloat16, 4><<<g, 256, 0, st>>>(a); break;
+      case 9: split_pack_kernel<__half, 4><<<g, 256, 0, st>>>(a); break;
+      case 10: split_pack_kernel<__nv_bfloat16, 5><<<g, 256, 0, st>>>(a); break;
+      case 11: split_pack_kernel<__half, 5><<<g, 256, 0, st>>>(a); break;
+      case 12: split_pack_kernel<__nv_bfloat16, 6><<<g, 256, 0, st>>>(a); break;
+      case 13: split_pack_kernel<__half, 6><<<g, 256, 0, st>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   if (ev) cudaEventRecord(ev[++*k], st);
   return cudaGetLastError();
