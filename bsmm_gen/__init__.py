@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Problem", "tiling_uniform", "tiling_uniform_int", "tiling_log_uniform", "tiling_paper",
     "mask_bernoulli", "mask_dense", "mask_band", "mask_clusters", "layout_arena",
-    "fill_uniform", "fill_band_decay", "fill_integers", "make_problem", "make_batch",
+    "fill_uniform", "fill_band_decay", "fill_integers", "make_problem", "make_batch", "as_float32",
     "tile_view", "densify", "RECIPES",
 ]
 
@@ -153,15 +153,16 @@ def mask_clusters(m: int, n: int, nclusters: int, density: float, rng: np.random
 # arenas
 # --------------------------------------------------------------------------------------
 
-def layout_arena(mask: np.ndarray, row_sizes: np.ndarray, col_sizes: np.ndarray):
+def layout_arena(mask: np.ndarray, row_sizes: np.ndarray, col_sizes: np.ndarray, align: int = 2):
     """Offsets (int64, -1 = absent) of the stored tiles of ``mask`` in row-major tile
     order, each tile row-major with ld = its column-block size, each start rounded up
-    to an even element (16 bytes). Returns (offsets, total_elements)."""
+    to a multiple of ``align`` elements (2 float64 or 4 float32 elements = 16 bytes).
+    Returns (offsets, total_elements)."""
     mask = np.asarray(mask, np.uint8)
     r = np.asarray(row_sizes, np.int64)
     c = np.asarray(col_sizes, np.int64)
     sizes = r[:, None] * c[None, :]
-    sizes = np.where(mask != 0, sizes + (sizes & 1), 0)
+    sizes = np.where(mask != 0, (sizes + align - 1) // align * align, 0)
     flat = sizes.reshape(-1)
     starts = np.concatenate([[0], np.cumsum(flat)[:-1]]) if flat.size else np.zeros(0, np.int64)
     off = np.where(mask.reshape(-1) != 0, starts, -1).reshape(mask.shape).astype(np.int64)
@@ -361,6 +362,23 @@ def transposed_storage(prob: Problem, transa: bool, transb: bool) -> Problem:
     return Problem(prob.name + f"_t{int(transa)}{int(transb)}", prob.row_sizes, prob.col_sizes, prob.inner_sizes,
                    am, bm, ao, bo, A, B, prob.alpha, prob.beta, prob.c_mask, prob.recipe, bool(transa),
                    bool(transb))
+
+
+def as_float32(prob: Problem) -> Problem:
+    """The same product with float32 arenas: every stored value rounded to float32 (ties
+    to even), the tiles laid out again with starts on multiples of 4 elements (16 bytes)."""
+    def move(mask, off, arena, rows, cols):
+        new_off, tot = layout_arena(mask, rows, cols, align=4)
+        out = np.zeros(tot, np.float32)
+        for u, v in zip(*np.nonzero(mask)):
+            n = int(rows[u]) * int(cols[v])
+            out[new_off[u, v]:new_off[u, v] + n] = arena[off[u, v]:off[u, v] + n].astype(np.float32)
+        return new_off, out
+    ar, ac = (prob.inner_sizes, prob.row_sizes) if prob.transa else (prob.row_sizes, prob.inner_sizes)
+    br, bc = (prob.col_sizes, prob.inner_sizes) if prob.transb else (prob.inner_sizes, prob.col_sizes)
+    ao, A = move(prob.a_mask, prob.a_off, prob.A, ar, ac)
+    bo, B = move(prob.b_mask, prob.b_off, prob.B, br, bc)
+    return dataclasses.replace(prob, name=prob.name + "_f32", a_off=ao, b_off=bo, A=A, B=B)
 
 
 def make_batch(count: int, seed: int, n_lo: int = 512, n_hi: int = 8192, b_lo: int = 32,

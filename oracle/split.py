@@ -45,6 +45,12 @@ accumulator unit is per element: L[ii,jj] = Emax_A(row ii) + Emax_B(col jj) - be
 - GUARD_BITS, with Emax_A(row) the largest exponent of that row over its stored tiles
 (0 when none) and Emax_B(col) likewise.
 
+Float32 elements (a float32 C arena; A and B may be float32 as well): the slicing and the
+exact sum are the same (float32 values are exact in float64); the sum is rounded once to
+a 24-bit significand (ties to even) and scaled by 2^L into float32, and the epilogue runs
+in float32: C = fl32(fl32(alpha*acc) + fl32(beta*C)). With float64 C the sum is rounded to
+a 53-bit significand and scaled into float64 (math.ldexp), the epilogue in float64.
+
 All integer matrix products below go through a float64 matmul: every entry is an
 integer of magnitude below 2^53, so the library routine returns it exactly in
 any summation order.
@@ -117,6 +123,37 @@ def pair_integer(na, nb, s: int, beta: int = BETA_BITS) -> np.ndarray:
     return T
 
 
+def round_significand(v: int, bits: int) -> int:
+    """The integer v rounded to ``bits`` significant bits, ties to even."""
+    if v == 0:
+        return 0
+    a = abs(v)
+    n = a.bit_length()
+    if n <= bits:
+        return v
+    sh = n - bits
+    q, rem, half = a >> sh, a & ((1 << sh) - 1), 1 << (sh - 1)
+    if rem > half or (rem == half and (q & 1)):
+        q += 1
+    return (q << sh) if v > 0 else -(q << sh)
+
+
+def _finish(exact, L, ct, alpha: float, bet: float):
+    """ct (a C tile, float64 or float32) = alpha*acc + beta*ct, acc = the exact integers
+    times 2^L rounded once to ct's precision (L a scalar or per element)."""
+    Ls = np.broadcast_to(np.asarray(L, dtype=object), exact.shape)
+    if ct.dtype == np.float32:
+        acc = np.array([np.float32(math.ldexp(float(round_significand(int(v), 24)), int(l)))
+                        for v, l in zip(exact.reshape(-1), Ls.reshape(-1))], np.float32).reshape(exact.shape)
+        u = np.float32(alpha) * acc
+        ct[...] = (u + np.float32(bet) * ct) if bet != 0.0 else u
+    else:
+        acc = np.array([math.ldexp(float(v), int(l)) for v, l in zip(exact.reshape(-1), Ls.reshape(-1))],
+                       np.float64).reshape(exact.shape)
+        u = alpha * acc
+        ct[...] = (u + bet * ct) if bet != 0.0 else u
+
+
 def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, tiles=None, scaling: str = "tile"):
     """Split-mode product in place on the C arena (numpy arrays). ``prob_like``
     carries row_sizes, col_sizes, inner_sizes, a_mask, b_mask, a_off, b_off, A, B,
@@ -178,14 +215,8 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
             T = pair_integer(na, nb, s, beta).astype(object)
             sh = eA + eB - beta * (s + 1) - L
             exact = exact + (T * (1 << sh) if sh >= 0 else T // (1 << -sh))  # floor below 2^L
-        acc = np.array([math.ldexp(float(v), L) for v in exact.reshape(-1)], np.float64).reshape(r[i], c[j])
         o = int(c_off[i, j])
-        ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
-        u = alpha * acc
-        if bet != 0.0:
-            ct[...] = u + bet * ct
-        else:
-            ct[...] = u
+        _finish(exact, L, C[o:o + r[i] * c[j]].reshape(r[i], c[j]), alpha, bet)
     return C
 
 
@@ -248,13 +279,6 @@ def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
             sh = eA[:, None] + eB[None, :] - beta * (s + 1) - L
             if T.size:
                 exact = exact + shift(T, sh)
-        acc = np.array([math.ldexp(float(v), int(l)) for v, l in zip(exact.reshape(-1), L.reshape(-1))],
-                       np.float64).reshape(r[i], c[j])
         o = int(c_off[i, j])
-        ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
-        u = alpha * acc
-        if bet != 0.0:
-            ct[...] = u + bet * ct
-        else:
-            ct[...] = u
+        _finish(exact, L, C[o:o + r[i] * c[j]].reshape(r[i], c[j]), alpha, bet)
     return C
