@@ -76,6 +76,9 @@ def parse():
                     help="dense workload: supply A and/or B as the transposed block matrix (C = A'^T B, A B'^T)")
     ap.add_argument("--other-slices", type=int, nargs="*", default=[3, 4, 5],
                     help="slice counts also timed on the dense workload, each with its error against FP64")
+    ap.add_argument("--f32-slices", type=int, nargs="*", default=[4, 6],
+                    help="dense workload: slice counts timed with float32 elements (the same values rounded "
+                         "to float32), each with its error against the FP64 result")
     return ap.parse_args()
 
 
@@ -699,6 +702,35 @@ def run_dense(args, rank, world, local):
                                 "rel_err_vs_fp64": e2, "bar": {3: 1e-5}.get(s2)}
             del plan2, C2
         extra["split_modes"] = modes
+        # float32 elements (the same values rounded to float32): throughput and error against FP64
+        if args.f32_slices and not (ta or tb):
+            p32 = G.as_float32(prob)
+            A32, B32 = torch.from_numpy(p32.A).to(dev), torch.from_numpy(p32.B).to(dev)
+            ao32, bo32 = torch.from_numpy(p32.a_off).to(dev), torch.from_numpy(p32.b_off).to(dev)
+            C32 = torch.zeros(c_tot, dtype=torch.float32, device=dev)
+            f32 = {}
+            for s2 in args.f32_slices:
+                plan2 = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                                    mode=P.BSMM_SPLIT_BF16, nslices=s2, cluster=args.cluster, elem=P.BSMM_F32,
+                                    profile=1, **sc)
+                for _ in range(2):
+                    P.bsmm_execute_f32(plan2, 1.0, A32, ao32, B32, bo32, 0.0, C32, co)
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                for _ in range(3):
+                    P.bsmm_execute_f32(plan2, 1.0, A32, ao32, B32, bo32, 0.0, C32, co)
+                g1.record(stream)
+                torch.cuda.synchronize()
+                P.bsmm_status_device(plan2)
+                ms2 = g0.elapsed_time(g1) / 3
+                e2 = float(np.linalg.norm(C32.cpu().numpy().astype(np.float64) - c64) / np.linalg.norm(c64))
+                f32[f"s={s2}"] = {"value": F / (ms2 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms2,
+                                  "rel_err_vs_fp64": e2, "kernel_ms": P.bsmm_plan_kernel_ms(plan2)}
+                del plan2
+            extra["float32_elements"] = {"modes": f32, "inputs": "the float64 inputs rounded to float32; error "
+                                         "against the FP64 product of the float64 inputs"}
+            del A32, B32, C32
         del plan64, C64
 
     # end to end through the public C ABI with host buffers (pinned)

@@ -68,6 +68,11 @@ typedef enum {
 } bsmm_mode;
 
 typedef enum {
+  BSMM_F64 = 0,  /* float64 arenas (every mode) */
+  BSMM_F32 = 1   /* float32 arenas (split modes; bsmm_execute_f32) */
+} bsmm_elem;
+
+typedef enum {
   BSMM_SCHED_FLOPS = 0,   /* order and pack work units by useful flop count */
   BSMM_SCHED_COSTS = 1,   /* by costs given through bsmm_plan_set_costs (e.g. the MLP) */
   BSMM_SCHED_NATURAL = 2  /* no reordering: units in row-major order, dealt round robin */
@@ -122,6 +127,16 @@ typedef struct {
                               tile, whose k-list is the tile's; or a split-mode 128-row block
                               times a group of `cluster` 32-column blocks, whose k-list is the
                               inner blocks where both have a stored tile. */
+  int32_t elem;            /* bsmm_elem (default BSMM_F64). BSMM_F32 (split modes only; the
+                              paper's tile kernel serves single- as well as double-precision
+                              types, Sec. 4.3): A, B and C are float32 arenas, offsets count
+                              float elements, and A and B tiles start on multiples of 4 (16
+                              bytes; a misaligned tile is reported by the device status). The slices
+                              and the exact sum are those of the float64 path (float32 values
+                              are exact doubles); the sum is rounded once to float32 (ties to
+                              even) and the epilogue runs in float32,
+                              C = fl32(fl32(alpha*acc) + fl32(beta*C)). Execute with
+                              bsmm_execute_f32; batches and bsmm_execute_host take float64. */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */
@@ -198,6 +213,16 @@ bsmm_status bsmm_plan_set_ctas(bsmm_plan_t plan, int32_t ctas);
 bsmm_status bsmm_execute(bsmm_plan_t plan, double alpha, const double* A, const int64_t* a_off,
                          const double* B, const int64_t* b_off, double beta, double* C,
                          const int64_t* c_off, void* stream);
+
+/*
+ * bsmm_execute for a plan built with elem = BSMM_F32: float32 arenas (offsets in float
+ * elements; A and B tiles on multiples of 4), alpha and beta in float32. Same ownership, stream and error
+ * behaviour as bsmm_execute; a plan built for float64 elements returns BSMM_ERR_INVALID,
+ * and bsmm_execute returns BSMM_ERR_INVALID for a float32 plan.
+ */
+bsmm_status bsmm_execute_f32(bsmm_plan_t plan, float alpha, const float* A, const int64_t* a_off,
+                             const float* B, const int64_t* b_off, float beta, float* C,
+                             const int64_t* c_off, void* stream);
 
 /*
  * Same as bsmm_execute with HOST buffers: copies A, B (and C when beta != 0) and

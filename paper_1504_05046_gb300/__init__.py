@@ -22,13 +22,15 @@ __all__ = [
     "BsmmError", "lib", "library_path", "BSMM_FP64", "BSMM_SPLIT_BF16", "BSMM_SPLIT_FP16",
     "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features",
-    "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device",
+    "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
+    "bsmm_status_device", "BSMM_F64", "BSMM_F32",
     "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy",
     "EXPORTED",
 ]
 
 BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
 BSMM_SCHED_FLOPS, BSMM_SCHED_COSTS, BSMM_SCHED_NATURAL = 0, 1, 2
+BSMM_F64, BSMM_F32 = 0, 1
 BSMM_NFEATURES = 12
 STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_NOMEM",
           4: "BSMM_ERR_TIMEOUT", 5: "BSMM_ERR_UNSUPPORTED", 6: "BSMM_ERR_DEVICE"}
@@ -36,7 +38,8 @@ STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_
 # every symbol include/bsmm.h declares
 EXPORTED = [
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features", "bsmm_plan_set_costs",
-    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_host", "bsmm_status_device", "bsmm_plan_timings",
+    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host", "bsmm_status_device",
+    "bsmm_plan_timings",
     "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_batch_create", "bsmm_batch_set_args",
     "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_kernels", "bsmm_batch_set_costs", "bsmm_batch_status_device",
     "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
@@ -56,7 +59,8 @@ class Options(ctypes.Structure):
                 ("max_ctas", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("transa", ctypes.c_int32),
-                ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32), ("ksplit", ctypes.c_int32)]
+                ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32), ("ksplit", ctypes.c_int32),
+                ("elem", ctypes.c_int32)]
 
 
 _lib = None
@@ -82,6 +86,7 @@ def lib():
         L.bsmm_plan_set_costs.argtypes = [P, P]
         L.bsmm_plan_set_ctas.argtypes = [P, i32]
         L.bsmm_execute.argtypes = [P, f64, P, P, P, P, f64, P, P, P]
+        L.bsmm_execute_f32.argtypes = [P, ctypes.c_float, P, P, P, P, ctypes.c_float, P, P, P]
         L.bsmm_execute_host.argtypes = [P, f64, P, i64, P, P, i64, P, f64, P, i64, P, P]
         L.bsmm_status_device.argtypes = [P, P]
         L.bsmm_plan_timings.argtypes = [P, P, P, P]
@@ -186,7 +191,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
               record_timings: int = 0, profile: int = 0, cluster: int = 0, fp64_tile: int = 0,
               stages: int = 0, transa: int = 0, transb: int = 0, split_scale: int = 0,
-              ksplit: int = 0) -> Plan:
+              ksplit: int = 0, elem: int = BSMM_F64) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -202,6 +207,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     o.transb = transb
     o.split_scale = split_scale
     o.ksplit = ksplit
+    o.elem = elem
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))
@@ -249,6 +255,13 @@ def bsmm_execute(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=N
     """Device tensors (torch, CUDA): A, B, C float64 arenas; a_off, b_off, c_off int64 tables."""
     _check(lib().bsmm_execute(plan.handle, float(alpha), _ptr(A), _ptr(a_off), _ptr(B), _ptr(b_off), float(beta),
                               _ptr(C), _ptr(c_off), _stream(stream)))
+
+
+def bsmm_execute_f32(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=None):
+    """Device tensors for a plan with float32 elements: A, B, C float32 arenas (offsets in
+    float elements, multiples of 4); a_off, b_off, c_off int64 tables."""
+    _check(lib().bsmm_execute_f32(plan.handle, float(alpha), _ptr(A), _ptr(a_off), _ptr(B), _ptr(b_off),
+                                  float(beta), _ptr(C), _ptr(c_off), _stream(stream)))
 
 
 def bsmm_execute_host(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=None):

@@ -175,7 +175,9 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
       return set_error("all FP64 plans of a batch need the same sub-tile edge (set bsmm_options.fp64_tile)"),
              BSMM_ERR_INVALID;
     if (p->device != p0->device) return set_error("all plans of a batch need the same device"), BSMM_ERR_INVALID;
+    if (p->opt.elem != BSMM_F64) return set_error("batches take float64 elements"), BSMM_ERR_UNSUPPORTED;
   }
+  if (p0->opt.elem != BSMM_F64) return set_error("batches take float64 elements"), BSMM_ERR_UNSUPPORTED;
   bsmm_batch_s* b = new (std::nothrow) bsmm_batch_s();
   if (!b) return set_error("out of host memory"), BSMM_ERR_NOMEM;
   b->plans.assign(plans, plans + count);

@@ -146,6 +146,10 @@ struct SplitArgs {
   // differ); null: every k block is drained on its own.
   int16_t* urow;
   int16_t* ucol;
+  // the row's and the column's part of a merged group's binary position (Mtot; padded like
+  // a colexp row): the largest Emax of the row block (column block) minus the line's Emax
+  int16_t* rowadj;
+  int16_t* coladj;
   int32_t kdepth;           // deepest exact FP32 accumulation (inner elements) for s slices
   int32_t transa, transb;   // transposed operand storage (bsmm_options)
   // per-row / per-column scaling (split_scale = 1): exponents of every row of every A tile
@@ -180,6 +184,12 @@ struct SplitArgs {
   int32_t* unit_cta;
   int32_t* err;
   int32_t debug;
+  // float32 elements (bsmm_options.elem): A, B and C are the float arrays below instead
+  // of the double ones; offsets count float elements
+  int32_t f32;
+  const float* Af;
+  const float* Bf;
+  float* Cf;
   // split k: exact 128-bit partial sums, per slot and cluster rank a TN x 128 array
   // (column-major: element (row, col) at col * 128 + row), and the regions to reduce
   uint4* part;
@@ -213,8 +223,9 @@ void wave_segments(int64_t u0, int64_t u1, int bins, std::vector<int64_t>& seg);
 // Kernel arguments of one product (device pointers from the caller).
 void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, const int64_t* a_off,
                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
-void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
-                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off);
+// (A, B, C are double arrays, or float arrays for a plan with float32 elements)
+void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const void* A, const int64_t* a_off,
+                     const void* B, const int64_t* b_off, double beta, void* C, const int64_t* c_off);
 int default_bins(const bsmm_plan_s* p);
 // Persistent CTAs (FP64) or clusters (split modes) of the machine, capped by max_ctas but
 // not by the unit count.
@@ -272,6 +283,7 @@ struct bsmm_plan_s {
   bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
   bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_presBg, d_apk_off, d_bpk_off, d_apk, d_bpk;
   bsmm::DevBuf d_eArow, d_eBcol, d_eAmaxr, d_eBmaxc;
+  bsmm::DevBuf d_rowadj, d_coladj;
   bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_urow, d_ucol, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
   bsmm::DevBuf d_err, d_timings, d_unit_cta, d_part, d_red;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;

@@ -44,8 +44,8 @@ void fill_fp64_args(bsmm_plan_s* p, Fp64Args& a, double alpha, const double* A, 
   a.unit_prod = a.unit_local = nullptr;
 }
 
-void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A, const int64_t* a_off,
-                     const double* B, const int64_t* b_off, double beta, double* C, const int64_t* c_off) {
+void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const void* A, const int64_t* a_off,
+                     const void* B, const int64_t* b_off, double beta, void* C, const int64_t* c_off) {
   a.M = p->M;
   a.N = p->N;
   a.K = p->K;
@@ -82,6 +82,8 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
   a.colexp_ld = p->colexp_ld;
   a.urow = (int16_t*)p->d_urow.p;
   a.ucol = (int16_t*)p->d_ucol.p;
+  a.rowadj = (int16_t*)p->d_rowadj.p;
+  a.coladj = (int16_t*)p->d_coladj.p;
   a.kdepth = split_max_depth(p->s);
   a.transa = p->opt.transa;
   a.transb = p->opt.transb;
@@ -107,11 +109,15 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
   a.sched_units = (const int32_t*)p->d_sched_units.p;
   a.alpha = alpha;
   a.beta = beta;
-  a.A = A;
+  a.f32 = p->opt.elem == BSMM_F32;
+  a.A = a.f32 ? nullptr : (const double*)A;
+  a.B = a.f32 ? nullptr : (const double*)B;
+  a.C = a.f32 ? nullptr : (double*)C;
+  a.Af = a.f32 ? (const float*)A : nullptr;
+  a.Bf = a.f32 ? (const float*)B : nullptr;
+  a.Cf = a.f32 ? (float*)C : nullptr;
   a.a_off = a_off;
-  a.B = B;
   a.b_off = b_off;
-  a.C = C;
   a.c_off = c_off;
   a.timings = p->opt.record_timings ? (int64_t*)p->d_timings.p : nullptr;
   a.unit_cta = p->opt.record_timings ? (int32_t*)p->d_unit_cta.p : nullptr;
@@ -128,8 +134,8 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const double* A
 
 namespace {
 
-bsmm_status check_ptrs(bsmm_plan_s* p, const double* A, const int64_t* a_off, const double* B,
-                       const int64_t* b_off, double* C, const int64_t* c_off) {
+bsmm_status check_ptrs(bsmm_plan_s* p, const void* A, const int64_t* a_off, const void* B,
+                       const int64_t* b_off, void* C, const int64_t* c_off) {
   if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
   if ((int64_t)p->M * p->K && !a_off) return set_error("a_off is NULL"), BSMM_ERR_INVALID;
   if ((int64_t)p->K * p->N && !b_off) return set_error("b_off is NULL"), BSMM_ERR_INVALID;
@@ -138,8 +144,8 @@ bsmm_status check_ptrs(bsmm_plan_s* p, const double* A, const int64_t* a_off, co
   return BSMM_OK;
 }
 
-bsmm_status run(bsmm_plan_s* p, double alpha, const double* A, const int64_t* a_off, const double* B,
-                const int64_t* b_off, double beta, double* C, const int64_t* c_off, cudaStream_t st) {
+bsmm_status run(bsmm_plan_s* p, double alpha, const void* A, const int64_t* a_off, const void* B,
+                const int64_t* b_off, double beta, void* C, const int64_t* c_off, cudaStream_t st) {
   if (p->n_units == 0) return BSMM_OK;
   cudaError_t e;
   cudaEvent_t* ev = nullptr;
@@ -151,7 +157,7 @@ bsmm_status run(bsmm_plan_s* p, double alpha, const double* A, const int64_t* a_
   }
   if (p->opt.mode == BSMM_FP64) {
     Fp64Args a{};
-    fill_fp64_args(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
+    fill_fp64_args(p, a, alpha, (const double*)A, a_off, (const double*)B, b_off, beta, (double*)C, c_off);
     e = launch_fp64(a, p->ctas, st, ev, &p->ev_count);
   } else {
     SplitArgs a{};
@@ -189,6 +195,15 @@ bsmm_status bsmm_execute(bsmm_plan_t p, double alpha, const double* A, const int
                          const int64_t* b_off, double beta, double* C, const int64_t* c_off, void* stream) {
   bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
   if (s != BSMM_OK) return s;
+  if (p->opt.elem != BSMM_F64) return set_error("plan has float32 elements: use bsmm_execute_f32"), BSMM_ERR_INVALID;
+  return run(p, alpha, A, a_off, B, b_off, beta, C, c_off, (cudaStream_t)stream);
+}
+
+bsmm_status bsmm_execute_f32(bsmm_plan_t p, float alpha, const float* A, const int64_t* a_off, const float* B,
+                             const int64_t* b_off, float beta, float* C, const int64_t* c_off, void* stream) {
+  bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
+  if (s != BSMM_OK) return s;
+  if (p->opt.elem != BSMM_F32) return set_error("plan has float64 elements: use bsmm_execute"), BSMM_ERR_INVALID;
   return run(p, alpha, A, a_off, B, b_off, beta, C, c_off, (cudaStream_t)stream);
 }
 
@@ -197,6 +212,7 @@ bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const double* A, int6
                               double beta, double* C, int64_t c_elems, const int64_t* c_off, void* stream) {
   bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
   if (s != BSMM_OK) return s;
+  if (p->opt.elem != BSMM_F64) return set_error("bsmm_execute_host takes float64 elements"), BSMM_ERR_INVALID;
   if (a_elems < 0 || b_elems < 0 || c_elems < 0) return set_error("negative arena length"), BSMM_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t na = (size_t)p->M * p->K, nb = (size_t)p->K * p->N, nc = (size_t)p->M * p->N;

@@ -271,6 +271,14 @@ __device__ __forceinline__ int exponent_above(unsigned long long m) {
   return -1022 - (__clzll((long long)m) - 12);  // subnormal: leading one at bit 63 - clz
 }
 
+// The same for the magnitude bits of a finite nonzero float (subnormals included).
+constexpr uint32_t kInfBits32 = 0x7F800000u;
+__device__ __forceinline__ int exponent_above32(uint32_t m) {
+  const int be = (int)(m >> 23);
+  if (be) return be - 126;
+  return -126 - (__clz((int)m) - 8);  // subnormal: leading one at bit 31 - clz
+}
+
 __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
   const int b = blockIdx.x;
   const bool isA = b < a.n_a_tiles;
@@ -282,7 +290,35 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
   const int64_t n = (int64_t)rows * cols;
   // the largest magnitude as bits: at or above kInfBits when a NaN or infinity is there
   unsigned long long mx = 0;
-  if (off >= 0) {
+  if (a.f32 && off >= 0) {
+    // float32 tiles start 16-byte aligned (offsets multiples of 4): four floats per load;
+    // the float maximum's bits are turned into a double's (both order like the values)
+    const float* xf = (isA ? a.Af : a.Bf) + off;
+    uint32_t m32 = 0;
+    if (off & 3) {
+      if (threadIdx.x == 0) atomicOr(a.err, kErrBadOffset);
+    } else {
+      const uint4* x4 = reinterpret_cast<const uint4*>(xf);
+      const int64_t n4 = n >> 2;
+      const int64_t bd = blockDim.x;
+      for (int64_t e = threadIdx.x; e < n4; e += 4 * bd) {  // four loads in flight
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = e + u * bd < n4 ? __ldg(x4 + e + u * bd) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          m32 = max(m32, max(max(v[u].x & 0x7FFFFFFFu, v[u].y & 0x7FFFFFFFu),
+                             max(v[u].z & 0x7FFFFFFFu, v[u].w & 0x7FFFFFFFu)));
+      }
+      for (int64_t e = (n4 << 2) + threadIdx.x; e < n; e += blockDim.x)
+        m32 = max(m32, __float_as_uint(__ldg(xf + e)) & 0x7FFFFFFFu);
+    }
+    // as a double's magnitude bits: equal exponent of the top bit, so exponent_above agrees
+    if (m32 >= kInfBits32)
+      mx = kInfBits;
+    else if (m32)
+      mx = (unsigned long long)(exponent_above32(m32) + 1022) << 52;
+  } else if (off >= 0) {
     // tiles start 16-byte aligned (even offsets): pairs of doubles, four pairs in flight
     const longlong2* x2 = reinterpret_cast<const longlong2*>(x);
     const int64_t n2 = n >> 1;
@@ -340,10 +376,18 @@ __global__ void __launch_bounds__(256) split_exp_lines_kernel(SplitArgs a) {
   const int64_t lstep = isA ? (tr ? 1 : cols) : (tr ? rows : 1);
   const int64_t ustep = isA ? (tr ? rows : 1) : (tr ? 1 : cols);
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    unsigned long long lm = 0;
-    const double* line = x + l * lstep;
-    for (int u = 0; u < len; u++) lm = max(lm, mag_bits(__ldg(line + u * ustep)));
-    const int e = (lm > 0 && lm < kInfBits) ? exponent_above(lm) : kZeroLine;
+    int e = kZeroLine;
+    if (a.f32) {
+      uint32_t lm = 0;
+      const float* line = (isA ? a.Af : a.Bf) + off + l * lstep;
+      for (int u = 0; u < len; u++) lm = max(lm, __float_as_uint(__ldg(line + u * ustep)) & 0x7FFFFFFFu);
+      if (lm > 0 && lm < kInfBits32) e = exponent_above32(lm);
+    } else {
+      unsigned long long lm = 0;
+      const double* line = x + l * lstep;
+      for (int u = 0; u < len; u++) lm = max(lm, mag_bits(__ldg(line + u * ustep)));
+      if (lm > 0 && lm < kInfBits) e = exponent_above(lm);
+    }
     if (isA)
       a.eArow[(int64_t)k_or_j * a.Mtot + a.ro[i_or_k] + l] = e;
     else
@@ -429,54 +473,80 @@ __global__ void __launch_bounds__(256) split_scale_lines_kernel(SplitArgs a) {
 // One thread per (k block, row block) and per (k block, column block). With one scale per
 // tile it first writes the offsets of its rows, rowexp[k][m] = e_A(i,k) - Emax_A(i) for a
 // stored tile (0 for an absent one), or of its columns (colexp); with one scale per row
-// and column the line kernel wrote them. Then the scale class: the common offset of the
-// rows (columns) whose tile is present, or kNonUniform. Two k blocks whose row and column
-// classes add up to the same value put every product of a unit at the same binary
-// position, so the contraction may accumulate them together.
+// and column the line kernel wrote them.
+// Then the scale class. The products of k block k land at element (m, n) at the binary
+// position e_A(m,k) + e_B(n,k) - Emax_A(m) - Emax_B(n) (exponents of the row's and the
+// column's tile, or line, at k, and their maxima). When the rows of the row block that
+// have a tile at k share one exponent e_A(k) (the columns likewise e_B(k)), that position
+// is e_A(k) + e_B(k) plus a part that depends only on the row and the column, not on k:
+//   urow[k][rb] = e_A(k) - maxE_A(rb),  rowadj[m] = maxE_A(rb) - Emax_A(m) >= 0
+// (maxE_A(rb) = the largest Emax_A over the block's rows; the same for columns), so two
+// k blocks whose urow + ucol agree may share one TMEM accumulation, drained at
+// guard + urow + ucol + rowadj[m] + coladj[n]. kNonUniform marks a k block whose rows (or
+// columns) at k have different exponents; rows without a tile (or all-zero lines) there
+// take no part.
 __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nr = (int64_t)a.K * a.RB, nc = (int64_t)a.K * a.CB;
   if (t < nr) {
     const int k = (int)(t / a.RB), rb = (int)(t % a.RB);
-    int lo = INT_MAX, hi = INT_MIN;
-    const int64_t m1 = (int64_t)(rb + 1) * kSplitBM < a.Mtot ? (int64_t)(rb + 1) * kSplitBM : a.Mtot;
-    for (int64_t m = (int64_t)rb * kSplitBM; m < m1; m++) {
+    const int64_t m0 = (int64_t)rb * kSplitBM;
+    const int64_t m1 = m0 + kSplitBM < a.Mtot ? m0 + kSplitBM : a.Mtot;
+    int lo = INT_MAX, hi = INT_MIN, emx = INT_MIN;
+    for (int64_t m = m0; m < m1; m++) {
       const int i = a.row_tile[m];
-      const bool pres = a.q[k] > 0 && a.am[(int64_t)i * a.K + k];
-      int v;
+      const int emax_m = a.rowscale ? a.eAmaxr[m] : a.eAmax[i];
+      emx = max(emx, emax_m);
+      bool pres = a.q[k] > 0 && a.am[(int64_t)i * a.K + k];
+      int eabs = 0;
       if (!a.rowscale) {
-        v = pres ? a.eA[(int64_t)i * a.K + k] - a.eAmax[i] : 0;
-        a.rowexp[(int64_t)k * a.Mtot + m] = (int16_t)v;
-      } else {
-        v = a.rowexp[(int64_t)k * a.Mtot + m];
+        eabs = pres ? a.eA[(int64_t)i * a.K + k] : 0;
+        a.rowexp[(int64_t)k * a.Mtot + m] = (int16_t)(pres ? eabs - emax_m : 0);
+      } else if (pres) {
+        eabs = a.eArow[(int64_t)k * a.Mtot + m];
+        pres = eabs != kZeroLine;
       }
       if (pres) {
-        lo = min(lo, v);
-        hi = max(hi, v);
+        lo = min(lo, eabs);
+        hi = max(hi, eabs);
       }
     }
-    if (a.urow) a.urow[t] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
+    if (a.urow) {
+      a.urow[t] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
+      if (k == 0)
+        for (int64_t m = m0; m < m1; m++)
+          a.rowadj[m] = (int16_t)(emx - (a.rowscale ? a.eAmaxr[m] : a.eAmax[a.row_tile[m]]));
+    }
   } else if (t < nr + nc) {
     const int64_t u = t - nr;
     const int k = (int)(u / a.CB), cb = (int)(u % a.CB);
-    int lo = INT_MAX, hi = INT_MIN;
-    const int64_t n1 = (int64_t)(cb + 1) * a.tn < a.Ntot ? (int64_t)(cb + 1) * a.tn : a.Ntot;
-    for (int64_t n = (int64_t)cb * a.tn; n < n1; n++) {
+    const int64_t n0 = (int64_t)cb * a.tn;
+    const int64_t n1 = n0 + a.tn < a.Ntot ? n0 + a.tn : a.Ntot;
+    int lo = INT_MAX, hi = INT_MIN, emx = INT_MIN;
+    for (int64_t n = n0; n < n1; n++) {
       const int j = a.col_tile[n];
-      const bool pres = a.q[k] > 0 && a.bm[(int64_t)k * a.N + j];
-      int v;
+      const int emax_n = a.rowscale ? a.eBmaxc[n] : a.eBmax[j];
+      emx = max(emx, emax_n);
+      bool pres = a.q[k] > 0 && a.bm[(int64_t)k * a.N + j];
+      int eabs = 0;
       if (!a.rowscale) {
-        v = pres ? a.eB[(int64_t)k * a.N + j] - a.eBmax[j] : 0;
-        a.colexp[(int64_t)k * a.colexp_ld + n] = (int16_t)v;
-      } else {
-        v = a.colexp[(int64_t)k * a.colexp_ld + n];
+        eabs = pres ? a.eB[(int64_t)k * a.N + j] : 0;
+        a.colexp[(int64_t)k * a.colexp_ld + n] = (int16_t)(pres ? eabs - emax_n : 0);
+      } else if (pres) {
+        eabs = a.eBcol[(int64_t)k * a.Ntot + n];
+        pres = eabs != kZeroLine;
       }
       if (pres) {
-        lo = min(lo, v);
-        hi = max(hi, v);
+        lo = min(lo, eabs);
+        hi = max(hi, eabs);
       }
     }
-    if (a.ucol) a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo : kNonUniform);
+    if (a.ucol) {
+      a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
+      if (k == 0)
+        for (int64_t n = n0; n < n1; n++)
+          a.coladj[n] = (int16_t)(emx - (a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]]));
+    }
   }
 }
 
@@ -554,29 +624,45 @@ __device__ __forceinline__ void slice_level(const SliceWindow (&w)[8], const boo
   }
 }
 
-template <typename T, int S>
-__device__ __forceinline__ void slice_store8(const double (&x)[8], int e, uint8_t* base, int slice_stride,
-                                             uint32_t soff) {
+// x 2^-e = +-m 2^ex with an integer significand m, from the bits of a double or a float
+__device__ __forceinline__ void decode(double x, int e, bool& neg, unsigned long long& m, int& ex) {
+  const long long b = __double_as_longlong(x);
+  neg = b < 0;
+  const int be = (int)((b >> 52) & 0x7FF);
+  const unsigned long long frac = (unsigned long long)b & ((1ull << 52) - 1ull);
+  m = be ? (frac | (1ull << 52)) : frac;
+  ex = (be ? be : 1) - 1075 - e;
+}
+__device__ __forceinline__ void decode(float x, int e, bool& neg, unsigned long long& m, int& ex) {
+  const uint32_t b = __float_as_uint(x);
+  neg = (b >> 31) != 0;
+  const int be = (int)((b >> 23) & 0xFF);
+  const uint32_t frac = b & 0x7FFFFFu;
+  m = be ? (frac | 0x800000u) : frac;
+  ex = (be ? be : 1) - 150 - e;
+}
+
+template <typename T, int S, typename E>
+__device__ __forceinline__ void slice_store8(const E (&x)[8], int e, uint8_t* base, int slice_stride, uint32_t soff) {
   SliceWindow w[8];
   bool neg[8];
   uint32_t zp[8];
 #pragma unroll
   for (int u = 0; u < 8; u++) {
-    const long long b = __double_as_longlong(x[u]);
-    neg[u] = b < 0;
-    const int be = (int)((b >> 52) & 0x7FF);
-    const unsigned long long frac = (unsigned long long)b & ((1ull << 52) - 1ull);
-    const unsigned long long m = be ? (frac | (1ull << 52)) : frac;
-    const int ex = (be ? be : 1) - 1075 - e;  // x 2^-e = +-m 2^ex
+    unsigned long long m;
+    int ex;
+    decode(x[u], e, neg[u], m, ex);
     w[u].init(m, -(ex + kSplitBeta * S));
     zp[u] = 0u;
   }
   slice_level<T, S, 1>(w, neg, zp, base, slice_stride, soff);
 }
 
-template <typename T, int S>
+template <typename T, int S, typename E>
 __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
   constexpr int s = S;
+  const E* Ae = reinterpret_cast<const E*>(std::is_same<E, float>::value ? (const void*)a.Af : (const void*)a.A);
+  const E* Be = reinterpret_cast<const E*>(std::is_same<E, float>::value ? (const void*)a.Bf : (const void*)a.B);
   if ((int)blockIdx.x < a.n_a_blocks) {
     // A block (rb, kt): chunks of 128 rows x 32 inner elements
     const int blk = a.a_blocks[blockIdx.x];
@@ -587,7 +673,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
     for (int item = threadIdx.x; item < nkc * kSplitBM * 4; item += blockDim.x) {
       const int ch = item & 3, rr = (item >> 2) % kSplitBM, kc = (item >> 2) / kSplitBM;
       const int64_t m = (int64_t)rb * kSplitBM + rr;
-      double x[8];
+      E x[8];
       int e = 0;
       bool present = false;
       int64_t off = -1;
@@ -605,10 +691,10 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
       // element (lr, k) of A_ik at line + k * step, stored transposed or not
       const int64_t step = a.transa ? (m < a.Mtot ? a.r[i] : 0) : 1;
-      const double* line = a.A + off + (a.transa ? lr : lr * q);
+      const E* line = Ae + off + (a.transa ? lr : lr * q);
       const int k0 = kc * kSplitKC + ch * 8;
 #pragma unroll
-      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : 0.0;
+      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : E(0);
       slice_store8<T, S>(x, e, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
     }
   } else {
@@ -623,7 +709,7 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
     for (int item = threadIdx.x; item < nkc * tn * 4; item += blockDim.x) {
       const int nn = item % tn, ch = (item / tn) & 3, kc = (item / tn) >> 2;
       const int64_t n = (int64_t)cb * tn + nn;
-      double x[8];
+      E x[8];
       int e = 0;
       bool present = false;
       int64_t off = -1;
@@ -642,10 +728,10 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
       // element (k, lc) of B_kj at line + k * step, stored transposed or not
       const int64_t step = a.transb ? 1 : cj;
-      const double* line = a.B + off + (a.transb ? lc * q : lc);
+      const E* line = Be + off + (a.transb ? lc * q : lc);
       const int k0 = kc * kSplitKC + ch * 8;
 #pragma unroll
-      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : 0.0;
+      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : E(0);
       slice_store8<T, S>(x, e, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
     }
   }
@@ -678,25 +764,22 @@ __device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsi
   return hi >> (r - 64);
 }
 
-// Round the 128-bit two's-complement integer w to the nearest double (ties to even) and
-// scale by 2^L, in integer arithmetic: the rounded 53-bit significand and the exponent are
-// assembled into the double's bit pattern (GB300's FP64 pipe is narrow, so no FP64
-// instruction is spent per element). Only a result outside the normal range takes the
-// library scaling.
-__device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
+// |w| of the 128-bit two's-complement integer w rounded to P significant bits (ties to
+// even): |w| ~ mant 2^r with mant in [2^(P-1), 2^P), in integer arithmetic. False for w = 0.
+template <int P>
+__device__ __forceinline__ bool acc_round(const uint32_t (&w)[4], bool& neg, unsigned long long& mant, int& r) {
   unsigned long long lo = ((unsigned long long)w[1] << 32) | w[0];
   unsigned long long hi = ((unsigned long long)w[3] << 32) | w[2];
-  const bool neg = (long long)hi < 0;
+  neg = (long long)hi < 0;
   if (neg) {
     lo = ~lo;
     hi = ~hi;
     lo += 1;
     if (lo == 0) hi += 1;
   }
-  if (hi == 0 && lo == 0) return 0.0;
+  if (hi == 0 && lo == 0) return false;
   const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  unsigned long long mant;
-  int r = msb - 52;  // value = mant * 2^(r + L), mant in [2^52, 2^53) after rounding
+  r = msb - (P - 1);
   if (r <= 0) {
     mant = lo << (-r);  // exact
   } else {
@@ -709,12 +792,24 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
       sticky = lo != 0 || (hi & ((1ull << (r - 1 - 64)) - 1)) != 0;
     if (round && (sticky || (mant & 1))) {
       mant += 1;
-      if (mant >> 53) {
+      if (mant >> P) {
         mant >>= 1;
         r += 1;
       }
     }
   }
+  return true;
+}
+
+// The integer w times 2^L rounded to the nearest double: the 53-bit significand and the
+// exponent are assembled into the double's bit pattern (GB300's FP64 pipe is narrow, so
+// no FP64 instruction is spent per element). Only a result outside the normal range takes
+// the library scaling (the 53-bit significand scaled, as the definition states).
+__device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
+  bool neg;
+  unsigned long long mant;
+  int r;
+  if (!acc_round<53>(w, neg, mant, r)) return 0.0;
   const int biased = r + L + 52 + 1023;
   if (biased >= 1 && biased <= 2046)  // sign, exponent and significand assembled as bits
     return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
@@ -722,6 +817,23 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   const double d = scalbn((double)mant, r + L);  // subnormal or overflowing result
   return neg ? -d : d;
 }
+
+// The same rounded once to float32 (24-bit significand), for float32 elements.
+__device__ __forceinline__ float acc_to_float(const uint32_t (&w)[4], int L) {
+  bool neg;
+  unsigned long long mant;
+  int r;
+  if (!acc_round<24>(w, neg, mant, r)) return 0.0f;
+  const int biased = r + L + 23 + 127;
+  if (biased >= 1 && biased <= 254)
+    return __uint_as_float(((uint32_t)neg << 31) | ((uint32_t)biased << 23) | ((uint32_t)mant & 0x7FFFFFu));
+  const float f = scalbnf((float)(uint32_t)mant, r + L);  // subnormal or overflowing result
+  return neg ? -f : f;
+}
+
+// A float32 result travels through the double staging buffer as its bit pattern.
+__device__ __forceinline__ double f32_slot(float f) { return __longlong_as_double((long long)__float_as_uint(f)); }
+__device__ __forceinline__ float f32_of_slot(double d) { return __uint_as_float((uint32_t)__double_as_longlong(d)); }
 
 // w += v, 128-bit two's complement
 __device__ __forceinline__ void add128(uint32_t (&w)[4], const uint4& v) {
@@ -752,7 +864,7 @@ __device__ __forceinline__ bool epi_all(bool v) {
 // on the elements that lie in S_C tiles. Warp w of NW stores rows w*(128/NW) .. with
 // lane = column (TN == 32), so a store instruction writes one or two contiguous row
 // segments; lanes below 128/NW fetch the rows' tile and row-in-tile, shuffles hand them out.
-template <int TN, int NW>
+template <int TN, int NW, bool F32>
 __device__ __forceinline__ void store_region(const SplitArgs& P, const double* cstage, int rb, int cb, int w, int lane,
                                              int32_t* err) {
   static_assert(TN == 32, "one column per lane");
@@ -766,6 +878,7 @@ __device__ __forceinline__ void store_region(const SplitArgs& P, const double* c
   const int ir = mr < P.Mtot ? P.row_tile[mr] : 0;
   const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
   const double alpha = P.alpha, beta = P.beta;
+  const float alpha32 = (float)alpha, beta32 = (float)beta;  // float32 elements: exact (given as floats)
 #pragma unroll
   for (int rr = 0; rr < kRowsPerWarp; rr++) {
     const int r2 = w * kRowsPerWarp + rr;
@@ -777,13 +890,41 @@ __device__ __forceinline__ void store_region(const SplitArgs& P, const double* c
       const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
       if (off == -1) atomicOr(err, kErrBadOffset);
       if (off >= 0) {
-        double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
-        double vv = cstage[r2 * (TN + 1) + lane];
-        if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
-        if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
-        *dst = vv;
+        if constexpr (F32) {
+          float* dst = P.Cf + off + (int64_t)lr2 * cjl + lcl;
+          float vv = f32_of_slot(cstage[r2 * (TN + 1) + lane]);
+          if (alpha32 != 1.0f) vv = __fmul_rn(alpha32, vv);
+          if (beta32 != 0.0f) vv = __fadd_rn(vv, __fmul_rn(beta32, *dst));
+          *dst = vv;
+        } else {
+          double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
+          double vv = cstage[r2 * (TN + 1) + lane];
+          if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
+          if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
+          *dst = vv;
+        }
       }
     }
+  }
+}
+
+// One thread's row of a unit's sums rounded into the staging buffer: doubles, or float32
+// bit patterns for float32 elements (zero outside the product).
+template <int TH, bool F32>
+__device__ __forceinline__ void round_row(const uint32_t (&acc)[TH][4], double* srow, const SplitArgs& P, bool row_ok,
+                                          int64_t n0, int Lrow) {
+#pragma unroll
+  for (int c = 0; c < TH; c++) {
+    const int64_t n = n0 + c;
+    double v = 0.0;
+    if (row_ok && n < P.Ntot) {
+      const int L = Lrow + (P.rowscale ? P.eBmaxc[n] : P.eBmax[P.col_tile[n]]);
+      if constexpr (F32)
+        v = f32_slot(acc_to_float(acc[c], L));
+      else
+        v = acc_to_double(acc[c], L);
+    }
+    srow[c] = v;
   }
 }
 
@@ -1200,10 +1341,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         }
         int shr = kSplitGuard;
         uint4 cx[TH / 8];
-        if (grp.uni) {
-          shr += grp.sig;
+        if (grp.uni) {  // the group's common class plus the row's and the columns' parts
+          shr += grp.sig + (row_ok ? (int)P.rowadj[m] : 0);
+          const uint4* src = reinterpret_cast<const uint4*>(P.coladj + n0);
 #pragma unroll
-          for (int w = 0; w < TH / 8; w++) cx[w] = make_uint4(0u, 0u, 0u, 0u);
+          for (int w = 0; w < TH / 8; w++) cx[w] = __ldg(src + w);
         } else {
           shr += row_ok ? (int)P.rowexp[(int64_t)kt * P.Mtot + m] : 0;
           const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)kt * P.colexp_ld + n0);
@@ -1277,16 +1419,18 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           const int Lrow =
               row_ok ? (P.rowscale ? P.eAmaxr[m] : P.eAmax[P.row_tile[m]]) - kSplitBeta * (S + 1) - kSplitGuard : 0;
           double* srow = cstage + row * (TN + 1) + half * TH;
-#pragma unroll
-          for (int c = 0; c < TH; c++) {
-            const int64_t n = n0 + c;
-            srow[c] = (row_ok && n < P.Ntot)
-                          ? acc_to_double(acc[c], Lrow + (P.rowscale ? P.eBmaxc[n] : P.eBmax[P.col_tile[n]]))
-                          : 0.0;
-          }
+          if (P.f32)
+            round_row<TH, true>(acc, srow, P, row_ok, n0, Lrow);
+          else
+            round_row<TH, false>(acc, srow, P, row_ok, n0, Lrow);
         }
         asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
-        if (ok && !*abort_flag) store_region<TN, kSplitEpiWarps>(P, cstage, un.rb, cb, ew, lane, a.err);
+        if (ok && !*abort_flag) {
+          if (P.f32)
+            store_region<TN, kSplitEpiWarps, true>(P, cstage, un.rb, cb, ew, lane, a.err);
+          else
+            store_region<TN, kSplitEpiWarps, false>(P, cstage, un.rb, cb, ew, lane, a.err);
+        }
       } else if (ok) {
         // a piece of a split k-list: its exact partial sums go to the workspace (column-
         // major, so the 32 rows of a warp write 512 contiguous bytes per column)
@@ -1338,11 +1482,18 @@ __global__ void __launch_bounds__(256) split_reduce_kernel(const __grid_constant
     uint32_t w[4] = {0u, 0u, 0u, 0u};
     for (int p = 0; p < rd.n; p++) add128(w, src[p * piece_stride + (size_t)c * kSplitBM]);
     const int64_t n = n0 + c;
-    cstage[row * (TN + 1) + half * TH + c] =
-        (row_ok && n < a.Ntot) ? acc_to_double(w, Lrow + (a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]])) : 0.0;
+    double v = 0.0;
+    if (row_ok && n < a.Ntot) {
+      const int L = Lrow + (a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]]);
+      v = a.f32 ? f32_slot(acc_to_float(w, L)) : acc_to_double(w, L);
+    }
+    cstage[row * (TN + 1) + half * TH + c] = v;
   }
   __syncthreads();
-  store_region<TN, 8>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
+  if (a.f32)
+    store_region<TN, 8, true>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
+  else
+    store_region<TN, 8, false>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
 }
 
 template <int S, int TN, int CL>
@@ -1410,6 +1561,26 @@ int max_clusters_s(int cl, int stages) {
 
 }  // namespace
 
+template <typename E>
+cudaError_t launch_pack(const SplitArgs& a, unsigned g, cudaStream_t st) {
+  switch (a.s * 2 + (a.fp16 ? 1 : 0)) {
+    case 2: split_pack_kernel<__nv_bfloat16, 1, E><<<g, 256, 0, st>>>(a); break;
+    case 3: split_pack_kernel<__half, 1, E><<<g, 256, 0, st>>>(a); break;
+    case 4: split_pack_kernel<__nv_bfloat16, 2, E><<<g, 256, 0, st>>>(a); break;
+    case 5: split_pack_kernel<__half, 2, E><<<g, 256, 0, st>>>(a); break;
+    case 6: split_pack_kernel<__nv_bfloat16, 3, E><<<g, 256, 0, st>>>(a); break;
+    case 7: split_pack_kernel<__half, 3, E><<<g, 256, 0, st>>>(a); break;
+    case 8: split_pack_kernel<__nv_bfloat16, 4, E><<<g, 256, 0, st>>>(a); break;
+    case 9: split_pack_kernel<__half, 4, E><<<g, 256, 0, st>>>(a); break;
+    case 10: split_pack_kernel<__nv_bfloat16, 5, E><<<g, 256, 0, st>>>(a); break;
+    case 11: split_pack_kernel<__half, 5, E><<<g, 256, 0, st>>>(a); break;
+    case 12: split_pack_kernel<__nv_bfloat16, 6, E><<<g, 256, 0, st>>>(a); break;
+    case 13: split_pack_kernel<__half, 6, E><<<g, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 int split_prep_kernels(const SplitArgs& a) {  // the kernels launch_split_prep launches
   int n = 0;
   if (a.n_a_tiles + a.n_b_tiles > 0) n += a.rowscale ? 2 : 1;
@@ -1440,21 +1611,8 @@ cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* 
   if (e != cudaSuccess) return e;
   if (a.n_a_blocks + a.n_b_blocks > 0) {
     const unsigned g = (unsigned)(a.n_a_blocks + a.n_b_blocks);
-    switch (a.s * 2 + (a.fp16 ? 1 : 0)) {
-      case 2: split_pack_kernel<__nv_bfloat16, 1><<<g, 256, 0, st>>>(a); break;
-      case 3: split_pack_kernel<__half, 1><<<g, 256, 0, st>>>(a); break;
-      case 4: split_pack_kernel<__nv_bfloat16, 2><<<g, 256, 0, st>>>(a); break;
-      case 5: split_pack_kernel<__half, 2><<<g, 256, 0, st>>>(a); break;
-      case 6: split_pack_kernel<__nv_bfloat16, 3><<<g, 256, 0, st>>>(a); break;
-      case 7: split_pack_kernel<__half, 3><<<g, 256, 0, st>>>(a); break;
-      case 8: split_pack_kernel<__nv_bfloat16, 4><<<g, 256, 0, st>>>(a); break;
-      case 9: split_pack_kernel<__half, 4><<<g, 256, 0, st>>>(a); break;
-      case 10: split_pack_kernel<__nv_bfloat16, 5><<<g, 256, 0, st>>>(a); break;
-      case 11: split_pack_kernel<__half, 5><<<g, 256, 0, st>>>(a); break;
-      case 12: split_pack_kernel<__nv_bfloat16, 6><<<g, 256, 0, st>>>(a); break;
-      case 13: split_pack_kernel<__half, 6><<<g, 256, 0, st>>>(a); break;
-      default: return cudaErrorInvalidValue;
-    }
+    cudaError_t pe = a.f32 ? launch_pack<float>(a, g, st) : launch_pack<double>(a, g, st);
+    if (pe != cudaSuccess) return pe;
   }
   if (ev) cudaEventRecord(ev[++*k], st);
   return cudaGetLastError();

@@ -203,7 +203,8 @@ def _scaled_problem(seed, r, q, c, a_scale, b_scale):
     return G.Problem("scaled", r, c, q, am, bm, a_off, b_off, A, B, 1.0, 0.0)
 
 
-@pytest.mark.parametrize("case", ["same_position", "shifting_position", "row_tiles_differ", "col_tiles_differ"])
+@pytest.mark.parametrize("case", ["same_position", "shifting_position", "row_tiles_differ", "col_tiles_differ",
+                                  "emax_differs"])
 def test_merged_accumulation_groups(case):
     """k blocks whose products land at the same binary position share one TMEM
     accumulation (up to the exact depth); the others are drained one by one. Every
@@ -217,8 +218,11 @@ def test_merged_accumulation_groups(case):
         fa, fb = (lambda i, k: k % 3), (lambda k, j: 0)
     elif case == "row_tiles_differ":   # row blocks whose tiles have different exponents
         fa, fb = (lambda i, k: 3 * (i % 2) - k % 2), (lambda k, j: k % 2)
-    else:                              # column blocks straddling tiles of different exponents
+    elif case == "col_tiles_differ":   # column blocks straddling tiles of different exponents
         fa, fb = (lambda i, k: 0), (lambda k, j: 2 * (j % 2))
+    else:                              # one tile lifts its row tile's (column tile's) largest exponent:
+        # blocks straddling it share exponents at every other k, so they still merge there
+        fa, fb = (lambda i, k: 3 if (i, k) == (1, 2) else 0), (lambda k, j: 2 if (k, j) == (4, 0) else 0)
     prob = _scaled_problem(11, r, q, c, fa, fb)
     for cl in (1, 2):
         check(prob, 6, cluster=cl)
