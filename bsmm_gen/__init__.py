@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Problem", "tiling_uniform", "tiling_uniform_int", "tiling_log_uniform", "tiling_paper",
     "mask_bernoulli", "mask_dense", "mask_band", "mask_clusters", "layout_arena",
-    "fill_uniform", "fill_band_decay", "fill_integers", "make_problem", "make_batch", "as_float32",
+    "fill_uniform", "fill_band_decay", "fill_integers", "make_problem", "make_batch", "as_float32", "as_complex",
     "tile_view", "densify", "RECIPES",
 ]
 
@@ -379,6 +379,20 @@ def as_float32(prob: Problem) -> Problem:
     ao, A = move(prob.a_mask, prob.a_off, prob.A, ar, ac)
     bo, B = move(prob.b_mask, prob.b_off, prob.B, br, bc)
     return dataclasses.replace(prob, name=prob.name + "_f32", a_off=ao, b_off=bo, A=A, B=B)
+
+
+def as_complex(prob: Problem, seed: int) -> Problem:
+    """The same structure with complex128 arenas: the real parts are the problem's values,
+    the imaginary parts drawn alike (integers in [-8, 8] when the real parts are all
+    integers, else U[-1,1]) from a stream of ``seed``. Offsets count complex elements."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(1)[0])
+    def im(x):
+        if x.size and np.all(x == np.round(x)):
+            return fill_integers(x.size, rng)
+        return fill_uniform(x.size, rng)
+    A = (prob.A + 1j * im(prob.A)).astype(np.complex128)
+    B = (prob.B + 1j * im(prob.B)).astype(np.complex128)
+    return dataclasses.replace(prob, name=prob.name + "_c128", A=A, B=B)
 
 
 def make_batch(count: int, seed: int, n_lo: int = 512, n_hi: int = 8192, b_lo: int = 32,

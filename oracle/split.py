@@ -45,6 +45,12 @@ accumulator unit is per element: L[ii,jj] = Emax_A(row ii) + Emax_B(col jj) - be
 - GUARD_BITS, with Emax_A(row) the largest exponent of that row over its stored tiles
 (0 when none) and Emax_B(col) likewise.
 
+Complex elements (complex128 arenas, tile mode, real alpha and beta): one exponent per
+tile over the real and imaginary parts together; both parts sliced with it; per tile pair
+the exact integers T_re = T(Ar,Br) - T(Ai,Bi) and T_im = T(Ar,Bi) + T(Ai,Br) (the complex
+product's definition), accumulated and rounded like a real element, each part on its own;
+the epilogue applies alpha and beta to each part.
+
 Float32 elements (a float32 C arena; A and B may be float32 as well): the slicing and the
 exact sum are the same (float32 values are exact in float64); the sum is rounded once to
 a 24-bit significand (ties to even) and scaled by 2^L into float32, and the epilogue runs
@@ -76,10 +82,10 @@ def tile_exponent(x: np.ndarray) -> int:
     return int(e)
 
 
-def slice_tile(x: np.ndarray, s: int, beta: int = BETA_BITS):
-    """Error-free slicing of one tile. Returns (e, [N_1..N_s] as float64 integer
-    matrices, rho_s residual in units of 2^e)."""
-    e = tile_exponent(x)
+def slice_tile(x: np.ndarray, s: int, beta: int = BETA_BITS, e=None):
+    """Error-free slicing of one tile (with its own exponent, or the given one). Returns
+    (e, [N_1..N_s] as float64 integer matrices, rho_s residual in units of 2^e)."""
+    e = tile_exponent(x) if e is None else e
     rho = np.ldexp(np.asarray(x, np.float64), -e)
     slices = []
     for t in range(1, s + 1):
@@ -174,14 +180,22 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
     a_off = prob_like.a_off.T if ta else prob_like.a_off
     b_off = prob_like.b_off.T if tb else prob_like.b_off
     cacheA, cacheB = {}, {}
+    cplx = np.iscomplexobj(prob_like.A)
+    assert not (cplx and (ta or tb)), "complex elements are stored untransposed"
+
+    def sl(x):  # (e, slices) or, for complex tiles, (e, (slices of re, slices of im))
+        if not cplx:
+            e, sl_, _ = slice_tile(x, s, beta)
+            return e, sl_
+        e = tile_exponent(np.concatenate([x.real.ravel(), x.imag.ravel()]))
+        return e, (slice_tile(x.real, s, beta, e)[1], slice_tile(x.imag, s, beta, e)[1])
 
     def a_sl(i, k):
         if (i, k) not in cacheA:
             o = int(a_off[i, k])
             x = (prob_like.A[o:o + r[i] * q[k]].reshape(q[k], r[i]).T if ta
                  else prob_like.A[o:o + r[i] * q[k]].reshape(r[i], q[k]))
-            e, sl, _ = slice_tile(x, s, beta)
-            cacheA[(i, k)] = (e, sl)
+            cacheA[(i, k)] = sl(x)
         return cacheA[(i, k)]
 
     def b_sl(k, j):
@@ -189,8 +203,7 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
             o = int(b_off[k, j])
             x = (prob_like.B[o:o + q[k] * c[j]].reshape(c[j], q[k]).T if tb
                  else prob_like.B[o:o + q[k] * c[j]].reshape(q[k], c[j]))
-            e, sl, _ = slice_tile(x, s, beta)
-            cacheB[(k, j)] = (e, sl)
+            cacheB[(k, j)] = sl(x)
         return cacheB[(k, j)]
 
     def emax_a(i):
@@ -205,23 +218,36 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
     alpha, bet = float(prob_like.alpha), float(prob_like.beta)
     for (i, j) in todo:
         L = emax_a(i) + emax_b(j) - beta * (s + 1) - GUARD_BITS
-        exact = np.zeros((r[i], c[j]), dtype=object)
-        exact[...] = 0
+        parts = [np.zeros((r[i], c[j]), dtype=object) for _ in range(2 if cplx else 1)]
+        for ex in parts:
+            ex[...] = 0
         for k in range(K):
             if not (am[i, k] and bm[k, j]):
                 continue
             eA, na = a_sl(i, k)
             eB, nb = b_sl(k, j)
-            T = pair_integer(na, nb, s, beta).astype(object)
+            if cplx:
+                (ar, ai), (br, bi) = na, nb
+                Ts = [pair_integer(ar, br, s, beta).astype(object) - pair_integer(ai, bi, s, beta).astype(object),
+                      pair_integer(ar, bi, s, beta).astype(object) + pair_integer(ai, br, s, beta).astype(object)]
+            else:
+                Ts = [pair_integer(na, nb, s, beta).astype(object)]
             sh = eA + eB - beta * (s + 1) - L
-            exact = exact + (T * (1 << sh) if sh >= 0 else T // (1 << -sh))  # floor below 2^L
+            for t, T in enumerate(Ts):
+                parts[t] = parts[t] + (T * (1 << sh) if sh >= 0 else T // (1 << -sh))  # floor below 2^L
         o = int(c_off[i, j])
-        _finish(exact, L, C[o:o + r[i] * c[j]].reshape(r[i], c[j]), alpha, bet)
+        ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
+        if cplx:
+            _finish(parts[0], L, ct.real, alpha, bet)
+            _finish(parts[1], L, ct.imag, alpha, bet)
+        else:
+            _finish(parts[0], L, ct, alpha, bet)
     return C
 
 
 def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
     """bsmm_split with one exponent per row of A and per column of B."""
+    assert not np.iscomplexobj(prob_like.A), "complex elements take one exponent per tile"
     r = np.asarray(prob_like.row_sizes, np.int64)
     c = np.asarray(prob_like.col_sizes, np.int64)
     q = np.asarray(prob_like.inner_sizes, np.int64)
