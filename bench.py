@@ -76,6 +76,9 @@ def parse():
                     help="dense workload: supply A and/or B as the transposed block matrix (C = A'^T B, A B'^T)")
     ap.add_argument("--other-slices", type=int, nargs="*", default=[3, 4, 5],
                     help="slice counts also timed on the dense workload, each with its error against FP64")
+    ap.add_argument("--c128-slices", type=int, nargs="*", default=[6],
+                    help="dense workload: slice counts timed with complex elements on the N/2 nonuniform dense "
+                         "product (same flops per element pair x4), each with its error against cuBLAS ZGEMM")
     ap.add_argument("--f32-slices", type=int, nargs="*", default=[4, 6],
                     help="dense workload: slice counts timed with float32 elements (the same values rounded "
                          "to float32), each with its error against the FP64 result")
@@ -574,6 +577,53 @@ def main():
         dist.destroy_process_group()
 
 
+def complex_line(args, P, G, torch, dev, stream):
+    """Complex elements on the N/2 nonuniform dense product: split-mode throughput in
+    useful flops (8 r c q per triple) and the error against cuBLAS ZGEMM of the dense
+    operands (a library reference point, not part of the measured path)."""
+    n2 = args.n // 2
+    pc = G.as_complex(make_inputs(n2, args.seed + 7), args.seed + 7)
+    d = lambda x: torch.from_numpy(x).to(dev)
+    Ac, Bc, ao, bo = d(pc.A), d(pc.B), d(pc.a_off), d(pc.b_off)
+    cs = np.ones((pc.M, pc.N), np.uint8)
+    off, tot = G.layout_arena(cs, pc.row_sizes, pc.col_sizes)
+    co = d(off)
+    # dense reference: the arenas are tile by tile; gather them into dense matrices
+    def dense(arena_t, offs, rows, cols):
+        ro = np.concatenate([[0], np.cumsum(rows.astype(np.int64))])
+        cc = np.concatenate([[0], np.cumsum(cols.astype(np.int64))])
+        out = torch.zeros((int(ro[-1]), int(cc[-1])), dtype=torch.complex128, device=dev)
+        for u in range(len(rows)):
+            for v in range(len(cols)):
+                nn = int(rows[u]) * int(cols[v])
+                out[ro[u]:ro[u + 1], cc[v]:cc[v + 1]] = arena_t[offs[u, v]:offs[u, v] + nn].view(int(rows[u]), int(cols[v]))
+        return out
+    ref = dense(Ac, pc.a_off, pc.row_sizes, pc.inner_sizes) @ dense(Bc, pc.b_off, pc.inner_sizes, pc.col_sizes)
+    out = {"workload": f"nonuniform_dense N={n2} blocks U-int[64,256], complex128 entries (re and im U[-1,1])"}
+    for s2 in args.c128_slices:
+        plan = P.bsmm_plan(pc.row_sizes, pc.col_sizes, pc.inner_sizes, pc.a_mask, pc.b_mask,
+                           mode=P.BSMM_SPLIT_BF16, nslices=s2, elem=P.BSMM_C128, profile=1)
+        F = P.bsmm_plan_query(plan)["useful_flops"]
+        C = torch.zeros(tot, dtype=torch.complex128, device=dev)
+        for _ in range(2):
+            P.bsmm_execute(plan, 1.0, Ac, ao, Bc, bo, 0.0, C, co)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(3):
+            P.bsmm_execute(plan, 1.0, Ac, ao, Bc, bo, 0.0, C, co)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        P.bsmm_status_device(plan)
+        ms = g0.elapsed_time(g1) / 3
+        got = dense(C, off, pc.row_sizes, pc.col_sizes)
+        err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+        out[f"s={s2}"] = {"value": F / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+                          "useful_flops_per_step": F, "rel_err_vs_zgemm": err,
+                          "kernel_ms": P.bsmm_plan_kernel_ms(plan)}
+        del plan, C
+    return out
+
+
 def run_dense(args, rank, world, local):
     """The headline workload: the 16384 nonuniform dense product, 6-slice split-bf16."""
     import torch
@@ -731,6 +781,9 @@ def run_dense(args, rank, world, local):
             extra["float32_elements"] = {"modes": f32, "inputs": "the float64 inputs rounded to float32; error "
                                          "against the FP64 product of the float64 inputs"}
             del A32, B32, C32
+        # complex elements: the N/2 product of the same recipe with complex128 entries
+        if args.c128_slices and not (ta or tb):
+            extra["complex_elements"] = complex_line(args, P, G, torch, dev, stream)
         del plan64, C64
 
     # end to end through the public C ABI with host buffers (pinned)

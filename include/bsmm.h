@@ -69,7 +69,8 @@ typedef enum {
 
 typedef enum {
   BSMM_F64 = 0,  /* float64 arenas (every mode) */
-  BSMM_F32 = 1   /* float32 arenas (split modes; bsmm_execute_f32) */
+  BSMM_F32 = 1,  /* float32 arenas (split modes; bsmm_execute_f32) */
+  BSMM_C128 = 2  /* complex double arenas, (re, im) interleaved (split modes; bsmm_execute) */
 } bsmm_elem;
 
 typedef enum {
@@ -136,7 +137,17 @@ typedef struct {
                               are exact doubles); the sum is rounded once to float32 (ties to
                               even) and the epilogue runs in float32,
                               C = fl32(fl32(alpha*acc) + fl32(beta*C)). Execute with
-                              bsmm_execute_f32; batches and bsmm_execute_host take float64. */
+                              bsmm_execute_f32; batches and bsmm_execute_host take float64.
+                              BSMM_C128 (split modes, untransposed, one scale per tile): A, B
+                              and C are complex double arenas passed to bsmm_execute as double
+                              arrays of interleaved (re, im) pairs; offsets count complex
+                              elements. Each tile takes one exponent over both parts; the
+                              real and imaginary parts of the product are exact sums (of
+                              Ar Br - Ai Bi and Ar Bi + Ai Br) rounded once each; alpha and
+                              beta are real and scale each part. The tensor cores run the
+                              equivalent real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]], so
+                              an inner block may hold half the real depth (256 for 6 slices)
+                              and the useful flop count is 8 r c q per nonzero triple. */
 } bsmm_options;
 
 /* Fill *opt with the defaults above. */

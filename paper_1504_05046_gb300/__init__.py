@@ -23,14 +23,14 @@ __all__ = [
     "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features",
     "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
-    "bsmm_status_device", "BSMM_F64", "BSMM_F32",
+    "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
     "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy",
     "EXPORTED",
 ]
 
 BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
 BSMM_SCHED_FLOPS, BSMM_SCHED_COSTS, BSMM_SCHED_NATURAL = 0, 1, 2
-BSMM_F64, BSMM_F32 = 0, 1
+BSMM_F64, BSMM_F32, BSMM_C128 = 0, 1, 2
 BSMM_NFEATURES = 12
 STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_NOMEM",
           4: "BSMM_ERR_TIMEOUT", 5: "BSMM_ERR_UNSUPPORTED", 6: "BSMM_ERR_DEVICE"}
@@ -252,7 +252,8 @@ def bsmm_plan_set_ctas(plan: Plan, ctas: int):
 
 
 def bsmm_execute(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=None):
-    """Device tensors (torch, CUDA): A, B, C float64 arenas; a_off, b_off, c_off int64 tables."""
+    """Device tensors (torch, CUDA): A, B, C float64 arenas (complex128 for a plan with
+    complex elements; alpha and beta real); a_off, b_off, c_off int64 tables."""
     _check(lib().bsmm_execute(plan.handle, float(alpha), _ptr(A), _ptr(a_off), _ptr(B), _ptr(b_off), float(beta),
                               _ptr(C), _ptr(c_off), _stream(stream)))
 

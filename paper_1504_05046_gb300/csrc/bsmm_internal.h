@@ -187,6 +187,10 @@ struct SplitArgs {
   // float32 elements (bsmm_options.elem): A, B and C are the float arrays below instead
   // of the double ones; offsets count float elements
   int32_t f32;
+  // complex elements: A, B, C are interleaved (re, im) double arenas and offsets count
+  // complex elements; the plan's inner and column tilings are doubled (the real product
+  // [Ar, -Ai] x [[Br, Bi], [Bi, -Br]]), so the tiles' complex sizes are half of q and c
+  int32_t cplx;
   const float* Af;
   const float* Bf;
   float* Cf;

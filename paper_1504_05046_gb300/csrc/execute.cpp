@@ -110,6 +110,7 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const void* A, 
   a.alpha = alpha;
   a.beta = beta;
   a.f32 = p->opt.elem == BSMM_F32;
+  a.cplx = p->opt.elem == BSMM_C128;
   a.A = a.f32 ? nullptr : (const double*)A;
   a.B = a.f32 ? nullptr : (const double*)B;
   a.C = a.f32 ? nullptr : (double*)C;
@@ -195,7 +196,7 @@ bsmm_status bsmm_execute(bsmm_plan_t p, double alpha, const double* A, const int
                          const int64_t* b_off, double beta, double* C, const int64_t* c_off, void* stream) {
   bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
   if (s != BSMM_OK) return s;
-  if (p->opt.elem != BSMM_F64) return set_error("plan has float32 elements: use bsmm_execute_f32"), BSMM_ERR_INVALID;
+  if (p->opt.elem == BSMM_F32) return set_error("plan has float32 elements: use bsmm_execute_f32"), BSMM_ERR_INVALID;
   return run(p, alpha, A, a_off, B, b_off, beta, C, c_off, (cudaStream_t)stream);
 }
 

@@ -624,9 +624,12 @@ bsmm_status validate_options(const bsmm_options& o) {
     return set_error("transa and transb must be 0 or 1"), BSMM_ERR_INVALID;
   if (o.split_scale != 0 && o.split_scale != 1) return set_error("split_scale must be 0 or 1"), BSMM_ERR_INVALID;
   if (o.ksplit < -1 || o.ksplit > 65536) return set_error("ksplit must be in -1..65536"), BSMM_ERR_INVALID;
-  if (o.elem != BSMM_F64 && o.elem != BSMM_F32) return set_error("unknown element type"), BSMM_ERR_INVALID;
-  if (o.elem == BSMM_F32 && o.mode == BSMM_FP64)
-    return set_error("float32 elements take a split mode"), BSMM_ERR_UNSUPPORTED;
+  if (o.elem != BSMM_F64 && o.elem != BSMM_F32 && o.elem != BSMM_C128)
+    return set_error("unknown element type"), BSMM_ERR_INVALID;
+  if (o.elem != BSMM_F64 && o.mode == BSMM_FP64)
+    return set_error("float32 and complex elements take a split mode"), BSMM_ERR_UNSUPPORTED;
+  if (o.elem == BSMM_C128 && (o.transa || o.transb || o.split_scale))
+    return set_error("complex elements are stored untransposed with one scale per tile"), BSMM_ERR_UNSUPPORTED;
   return BSMM_OK;
 }
 
@@ -700,6 +703,12 @@ bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, in
   p->r.assign(row_sizes, row_sizes + M);
   p->c.assign(col_sizes, col_sizes + N);
   p->q.assign(inner_sizes, inner_sizes + K);
+  if (o.elem == BSMM_C128) {
+    // complex elements run as the real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]]: every
+    // inner and column block holds twice as many real lines
+    for (int32_t& x : p->q) x *= 2;
+    for (int32_t& x : p->c) x *= 2;
+  }
   p->ro.assign(M + 1, 0);
   p->co.assign(N + 1, 0);
   p->qo.assign(K + 1, 0);

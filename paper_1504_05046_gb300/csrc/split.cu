@@ -286,8 +286,10 @@ __global__ void __launch_bounds__(256) split_exp_kernel(SplitArgs a) {
   int rows, cols;
   int64_t off;
   tile_geometry(a, isA, t, rows, cols, off);
-  const double* x = (isA ? a.A : a.B) + (off < 0 ? 0 : off);
-  const int64_t n = (int64_t)rows * cols;
+  // complex elements: the tile's doubles (both parts) at twice its complex offset; an A
+  // tile holds r x q' doubles (q' = 2q), a B tile q' x c' / 2 (c' = 2c)
+  const double* x = (isA ? a.A : a.B) + (off < 0 ? 0 : (a.cplx ? 2 * off : off));
+  const int64_t n = (int64_t)rows * cols / (a.cplx && !isA ? 2 : 1);
   // the largest magnitude as bits: at or above kInfBits when a NaN or infinity is there
   unsigned long long mx = 0;
   if (a.f32 && off >= 0) {
@@ -658,7 +660,15 @@ __device__ __forceinline__ void slice_store8(const E (&x)[8], int e, uint8_t* ba
   slice_level<T, S, 1>(w, neg, zp, base, slice_stride, soff);
 }
 
-template <typename T, int S, typename E>
+// Complex elements (CPLX): the real product's A tile is [Ar, -Ai] (inner index kk' < q
+// takes the real part of column kk', kk' >= q the negated imaginary part of column kk' - q)
+// and its B tile [[Br, Bi], [Bi, -Br]] (row half and column half pick the part and the
+// sign); q and c below are the doubled sizes, the stored complex tile is q/2 and c/2 wide.
+__device__ __forceinline__ double neg_if(double v, bool n) {  // sign flip as bits (no FP64 op)
+  return n ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull) : v;
+}
+
+template <typename T, int S, typename E, bool CPLX = false>
 __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
   constexpr int s = S;
   const E* Ae = reinterpret_cast<const E*>(std::is_same<E, float>::value ? (const void*)a.Af : (const void*)a.A);
@@ -691,10 +701,20 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int64_t lr = m - (m < a.Mtot ? a.ro[i] : 0);
       // element (lr, k) of A_ik at line + k * step, stored transposed or not
       const int64_t step = a.transa ? (m < a.Mtot ? a.r[i] : 0) : 1;
-      const E* line = Ae + off + (a.transa ? lr : lr * q);
       const int k0 = kc * kSplitKC + ch * 8;
+      if constexpr (CPLX) {
+        const int qc = q >> 1;
+        const double* row = a.A + 2 * (off + lr * qc);
 #pragma unroll
-      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : E(0);
+        for (int u = 0; u < 8; u++) {
+          const int kk = k0 + u, part = kk >= qc;
+          x[u] = (present && kk < q) ? neg_if(__ldg(row + 2 * (kk - part * qc) + part), part) : 0.0;
+        }
+      } else {
+        const E* line = Ae + off + (a.transa ? lr : lr * q);
+#pragma unroll
+        for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : E(0);
+      }
       slice_store8<T, S>(x, e, out + (size_t)kc * s * kAChunk, kAChunk, swz64(rr, ch * 8));
     }
   } else {
@@ -728,10 +748,23 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int64_t lc = n - (n < a.Ntot ? a.co[j] : 0);
       // element (k, lc) of B_kj at line + k * step, stored transposed or not
       const int64_t step = a.transb ? 1 : cj;
-      const E* line = Be + off + (a.transb ? lc * q : lc);
       const int k0 = kc * kSplitKC + ch * 8;
+      if constexpr (CPLX) {
+        const int qc = q >> 1, cc = cj >> 1;
+        const int cpart = lc >= cc;
+        const double* col = a.B + 2 * (off + (lc - cpart * cc));
 #pragma unroll
-      for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : E(0);
+        for (int u = 0; u < 8; u++) {
+          const int kk = k0 + u, rpart = kk >= qc;
+          x[u] = (present && kk < q)
+                     ? neg_if(__ldg(col + 2 * (int64_t)(kk - rpart * qc) * cc + (rpart ^ cpart)), rpart & cpart)
+                     : 0.0;
+        }
+      } else {
+        const E* line = Be + off + (a.transb ? lc * q : lc);
+#pragma unroll
+        for (int u = 0; u < 8; u++) x[u] = (present && k0 + u < q) ? __ldg(line + (k0 + u) * step) : E(0);
+      }
       slice_store8<T, S>(x, e, out + (size_t)kc * s * bchunk, bchunk, swz64(nn, ch * 8));
     }
   }
@@ -864,7 +897,7 @@ __device__ __forceinline__ bool epi_all(bool v) {
 // on the elements that lie in S_C tiles. Warp w of NW stores rows w*(128/NW) .. with
 // lane = column (TN == 32), so a store instruction writes one or two contiguous row
 // segments; lanes below 128/NW fetch the rows' tile and row-in-tile, shuffles hand them out.
-template <int TN, int NW, bool F32>
+template <int TN, int NW, int ELEM>  // ELEM: 0 float64, 1 float32, 2 complex (one part per column)
 __device__ __forceinline__ void store_region(const SplitArgs& P, const double* cstage, int rb, int cb, int w, int lane,
                                              int32_t* err) {
   static_assert(TN == 32, "one column per lane");
@@ -890,7 +923,17 @@ __device__ __forceinline__ void store_region(const SplitArgs& P, const double* c
       const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
       if (off == -1) atomicOr(err, kErrBadOffset);
       if (off >= 0) {
-        if constexpr (F32) {
+        if constexpr (ELEM == 2) {
+          // column lcl of the doubled tile: the real part of complex column lcl, or the
+          // imaginary part of column lcl - c_j / 2
+          const int64_t cc = cjl >> 1;
+          const int64_t part = lcl >= cc;
+          double* dst = P.C + 2 * (off + (int64_t)lr2 * cc + lcl - part * cc) + part;
+          double vv = cstage[r2 * (TN + 1) + lane];
+          if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
+          if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
+          *dst = vv;
+        } else if constexpr (ELEM == 1) {
           float* dst = P.Cf + off + (int64_t)lr2 * cjl + lcl;
           float vv = f32_of_slot(cstage[r2 * (TN + 1) + lane]);
           if (alpha32 != 1.0f) vv = __fmul_rn(alpha32, vv);
@@ -1427,9 +1470,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
         if (ok && !*abort_flag) {
           if (P.f32)
-            store_region<TN, kSplitEpiWarps, true>(P, cstage, un.rb, cb, ew, lane, a.err);
+            store_region<TN, kSplitEpiWarps, 1>(P, cstage, un.rb, cb, ew, lane, a.err);
+          else if (P.cplx)
+            store_region<TN, kSplitEpiWarps, 2>(P, cstage, un.rb, cb, ew, lane, a.err);
           else
-            store_region<TN, kSplitEpiWarps, false>(P, cstage, un.rb, cb, ew, lane, a.err);
+            store_region<TN, kSplitEpiWarps, 0>(P, cstage, un.rb, cb, ew, lane, a.err);
         }
       } else if (ok) {
         // a piece of a split k-list: its exact partial sums go to the workspace (column-
@@ -1491,9 +1536,11 @@ __global__ void __launch_bounds__(256) split_reduce_kernel(const __grid_constant
   }
   __syncthreads();
   if (a.f32)
-    store_region<TN, 8, true>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
+    store_region<TN, 8, 1>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
+  else if (a.cplx)
+    store_region<TN, 8, 2>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
   else
-    store_region<TN, 8, false>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
+    store_region<TN, 8, 0>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
 }
 
 template <int S, int TN, int CL>
@@ -1561,21 +1608,21 @@ int max_clusters_s(int cl, int stages) {
 
 }  // namespace
 
-template <typename E>
+template <typename E, bool C = false>
 cudaError_t launch_pack(const SplitArgs& a, unsigned g, cudaStream_t st) {
   switch (a.s * 2 + (a.fp16 ? 1 : 0)) {
-    case 2: split_pack_kernel<__nv_bfloat16, 1, E><<<g, 256, 0, st>>>(a); break;
-    case 3: split_pack_kernel<__half, 1, E><<<g, 256, 0, st>>>(a); break;
-    case 4: split_pack_kernel<__nv_bfloat16, 2, E><<<g, 256, 0, st>>>(a); break;
-    case 5: split_pack_kernel<__half, 2, E><<<g, 256, 0, st>>>(a); break;
-    case 6: split_pack_kernel<__nv_bfloat16, 3, E><<<g, 256, 0, st>>>(a); break;
-    case 7: split_pack_kernel<__half, 3, E><<<g, 256, 0, st>>>(a); break;
-    case 8: split_pack_kernel<__nv_bfloat16, 4, E><<<g, 256, 0, st>>>(a); break;
-    case 9: split_pack_kernel<__half, 4, E><<<g, 256, 0, st>>>(a); break;
-    case 10: split_pack_kernel<__nv_bfloat16, 5, E><<<g, 256, 0, st>>>(a); break;
-    case 11: split_pack_kernel<__half, 5, E><<<g, 256, 0, st>>>(a); break;
-    case 12: split_pack_kernel<__nv_bfloat16, 6, E><<<g, 256, 0, st>>>(a); break;
-    case 13: split_pack_kernel<__half, 6, E><<<g, 256, 0, st>>>(a); break;
+    case 2: split_pack_kernel<__nv_bfloat16, 1, E, C><<<g, 256, 0, st>>>(a); break;
+    case 3: split_pack_kernel<__half, 1, E, C><<<g, 256, 0, st>>>(a); break;
+    case 4: split_pack_kernel<__nv_bfloat16, 2, E, C><<<g, 256, 0, st>>>(a); break;
+    case 5: split_pack_kernel<__half, 2, E, C><<<g, 256, 0, st>>>(a); break;
+    case 6: split_pack_kernel<__nv_bfloat16, 3, E, C><<<g, 256, 0, st>>>(a); break;
+    case 7: split_pack_kernel<__half, 3, E, C><<<g, 256, 0, st>>>(a); break;
+    case 8: split_pack_kernel<__nv_bfloat16, 4, E, C><<<g, 256, 0, st>>>(a); break;
+    case 9: split_pack_kernel<__half, 4, E, C><<<g, 256, 0, st>>>(a); break;
+    case 10: split_pack_kernel<__nv_bfloat16, 5, E, C><<<g, 256, 0, st>>>(a); break;
+    case 11: split_pack_kernel<__half, 5, E, C><<<g, 256, 0, st>>>(a); break;
+    case 12: split_pack_kernel<__nv_bfloat16, 6, E, C><<<g, 256, 0, st>>>(a); break;
+    case 13: split_pack_kernel<__half, 6, E, C><<<g, 256, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1611,7 +1658,8 @@ cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* 
   if (e != cudaSuccess) return e;
   if (a.n_a_blocks + a.n_b_blocks > 0) {
     const unsigned g = (unsigned)(a.n_a_blocks + a.n_b_blocks);
-    cudaError_t pe = a.f32 ? launch_pack<float>(a, g, st) : launch_pack<double>(a, g, st);
+    cudaError_t pe = a.f32 ? launch_pack<float>(a, g, st)
+                           : a.cplx ? launch_pack<double, true>(a, g, st) : launch_pack<double>(a, g, st);
     if (pe != cudaSuccess) return pe;
   }
   if (ev) cudaEventRecord(ev[++*k], st);

@@ -1,0 +1,115 @@
+"""GPU parity of complex elements in the split modes (bsmm_options.elem = BSMM_C128),
+through the C ABI: the split oracle with complex arenas fixes every bit (each part's exact
+sum rounded once), so the comparison is bit for bit; the error against numpy's complex
+FP64 product is asserted at the slice count's bar."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import bsmm_gen as G
+import oracle
+from oracle import split as OS
+import paper_1504_05046_gb300 as P
+from helpers import c_arena, struct_elements
+
+pytestmark = pytest.mark.gpu
+BARS = {3: 1e-5, 4: 1e-7, 6: 1e-11}
+
+
+def _dense(arena, off, rows, cols):
+    ro = np.concatenate([[0], np.cumsum(np.asarray(rows, np.int64))])
+    co = np.concatenate([[0], np.cumsum(np.asarray(cols, np.int64))])
+    out = np.zeros((ro[-1], co[-1]), np.complex128)
+    for u in range(len(rows)):
+        for v in range(len(cols)):
+            if off[u, v] >= 0:
+                n = int(rows[u]) * int(cols[v])
+                out[ro[u]:ro[u + 1], co[v]:co[v + 1]] = arena[off[u, v]:off[u, v] + n].reshape(rows[u], cols[v])
+    return out
+
+
+def run_c(prob, s=6, mode=P.BSMM_SPLIT_BF16, c_mask=None, **opt):
+    import torch
+    from gpu_helpers import to_dev
+    cs, _, _ = oracle.structure(prob, c_mask)
+    off, C64 = c_arena(prob, cs, rng=np.random.default_rng(0))
+    C0 = (C64 + 1j * np.random.default_rng(1).uniform(-1, 1, C64.size)).astype(np.complex128)
+    want = C0.copy()
+    OS.bsmm_split(prob, cs, want, off, s)
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, c_mask,
+                       mode=mode, nslices=s, elem=P.BSMM_C128, debug_checks=1, **opt)
+    dev = lambda x: to_dev(x if x.size else np.zeros(2, x.dtype))
+    C = dev(C0)
+    P.bsmm_execute(plan, prob.alpha, dev(prob.A), dev(prob.a_off.astype(np.int64)), dev(prob.B),
+                   dev(prob.b_off.astype(np.int64)), prob.beta, C, dev(off.astype(np.int64)))
+    torch.cuda.synchronize()
+    P.bsmm_status_device(plan)
+    got = C.cpu().numpy()[:C0.size]
+    g, w = struct_elements(prob, cs, off, got), struct_elements(prob, cs, off, want)
+    if not np.array_equal(g, w):
+        bad = np.flatnonzero(g != w)
+        raise AssertionError(f"{bad.size} of {g.size} differ; first {bad[:4]}: {g[bad[:4]]} vs {w[bad[:4]]}")
+    # against numpy's complex FP64 product
+    Pd = _dense(prob.A, prob.a_off, prob.row_sizes, prob.inner_sizes) @ \
+        _dense(prob.B, prob.b_off, prob.inner_sizes, prob.col_sizes)
+    ref = C0.copy()
+    ro = np.concatenate([[0], np.cumsum(prob.row_sizes.astype(np.int64))])
+    co = np.concatenate([[0], np.cumsum(prob.col_sizes.astype(np.int64))])
+    for i in range(prob.M):
+        for j in range(prob.N):
+            if cs[i, j]:
+                r, c = int(prob.row_sizes[i]), int(prob.col_sizes[j])
+                t = ref[off[i, j]:off[i, j] + r * c].reshape(r, c)
+                t[...] = prob.alpha * Pd[ro[i]:ro[i + 1], co[j]:co[j + 1]] + (prob.beta * t if prob.beta else 0)
+    r = struct_elements(prob, cs, off, ref)
+    den = float(np.linalg.norm(r))
+    return plan, float(np.linalg.norm(g - r)) / den if den > 0 else float(np.linalg.norm(g - r))
+
+
+@pytest.mark.parametrize("s,mode", [(6, P.BSMM_SPLIT_BF16), (4, P.BSMM_SPLIT_FP16), (3, P.BSMM_SPLIT_BF16)])
+@pytest.mark.parametrize("seed", range(5))
+def test_small_ragged(seed, s, mode):
+    prob = G.as_complex(G.random_small(seed, max_blocks=6, max_size=60), seed)
+    _, err = run_c(prob, s, mode)
+    assert err <= BARS[s], err
+
+
+def test_integer_inputs_exact():
+    prob = G.as_complex(G.random_small(11, max_blocks=5, max_size=40, values="integers"), 11)
+    _, err = run_c(prob, 1)
+    assert err == 0.0
+
+
+def test_nonuniform_dense_clusters():
+    prob = G.as_complex(G.make_problem("nonuniform_dense", 3, 700, lo=64, hi=200), 3)
+    for cl in (1, 2, 4):
+        _, err = run_c(prob, 6, cluster=cl)
+        assert err <= 1e-11, err
+
+
+def test_alpha_beta_c_mask_and_split_k():
+    prob = G.as_complex(G.make_problem("banded_decay", 5, 1000, lo=32, hi=200, band=3), 5)
+    prob.alpha, prob.beta = -0.75, 1.5
+    cm = (np.random.default_rng(2).random((prob.M, prob.N)) < 0.2).astype(np.uint8)
+    run_c(prob, 6, P.BSMM_SPLIT_FP16, c_mask=cm)
+    run_c(prob, 6, c_mask=cm, ksplit=3)
+
+
+def test_thin_automatic_split_k():
+    prob = G.as_complex(G.make_problem("thin_dense", 4, 260, hi=200, k_factor=40), 4)
+    plan, _ = run_c(prob, 6)
+    assert P.bsmm_plan_ksplit(plan)["n_regions"] > 0
+
+
+def test_unsupported_combinations_are_rejected():
+    prob = G.as_complex(G.random_small(1, max_blocks=3, max_size=30), 1)
+    args = (prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask)
+    for bad in (dict(mode=P.BSMM_FP64), dict(mode=P.BSMM_SPLIT_BF16, transa=1),
+                dict(mode=P.BSMM_SPLIT_BF16, split_scale=1)):
+        with pytest.raises(P.BsmmError):
+            P.bsmm_plan(*args, elem=P.BSMM_C128, **bad)
+    deep = np.array([300], np.int32)  # 2 x 300 real lines exceed the 6-slice exact depth
+    with pytest.raises(P.BsmmError):
+        P.bsmm_plan(np.array([10], np.int32), np.array([10], np.int32), deep, np.ones((1, 1), np.uint8),
+                    np.ones((1, 1), np.uint8), mode=P.BSMM_SPLIT_BF16, elem=P.BSMM_C128)
