@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) split_scale_lines_kernel(SplitArgs a) {
 }
 
 // ---------------------------------------------------------------- kernel 1c: offsets and scale classes
-// One thread per (k block, row block) and per (k block, column block). With one scale per
+// One warp per (k block, row block) and per (k block, column block). With one scale per
 // tile it first writes the offsets of its rows, rowexp[k][m] = e_A(i,k) - Emax_A(i) for a
 // stored tile (0 for an absent one), or of its columns (colexp); with one scale per row
 // and column the line kernel wrote them.
@@ -488,14 +488,16 @@ __global__ void __launch_bounds__(256) split_scale_lines_kernel(SplitArgs a) {
 // columns) at k have different exponents; rows without a tile (or all-zero lines) there
 // take no part.
 __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per (k block, row block) and per (k block, column block); lanes over the lines
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   const int64_t nr = (int64_t)a.K * a.RB, nc = (int64_t)a.K * a.CB;
-  if (t < nr) {
-    const int k = (int)(t / a.RB), rb = (int)(t % a.RB);
+  int lo = INT_MAX, hi = INT_MIN, emx = INT_MIN;
+  if (wid < nr) {
+    const int k = (int)(wid / a.RB), rb = (int)(wid % a.RB);
     const int64_t m0 = (int64_t)rb * kSplitBM;
     const int64_t m1 = m0 + kSplitBM < a.Mtot ? m0 + kSplitBM : a.Mtot;
-    int lo = INT_MAX, hi = INT_MIN, emx = INT_MIN;
-    for (int64_t m = m0; m < m1; m++) {
+    for (int64_t m = m0 + lane; m < m1; m += 32) {
       const int i = a.row_tile[m];
       const int emax_m = a.rowscale ? a.eAmaxr[m] : a.eAmax[i];
       emx = max(emx, emax_m);
@@ -513,19 +515,23 @@ __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
         hi = max(hi, eabs);
       }
     }
+    for (int o = 16; o; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+    }
     if (a.urow) {
-      a.urow[t] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
+      if (lane == 0) a.urow[wid] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
       if (k == 0)
-        for (int64_t m = m0; m < m1; m++)
+        for (int64_t m = m0 + lane; m < m1; m += 32)
           a.rowadj[m] = (int16_t)(emx - (a.rowscale ? a.eAmaxr[m] : a.eAmax[a.row_tile[m]]));
     }
-  } else if (t < nr + nc) {
-    const int64_t u = t - nr;
+  } else if (wid < nr + nc) {
+    const int64_t u = wid - nr;
     const int k = (int)(u / a.CB), cb = (int)(u % a.CB);
     const int64_t n0 = (int64_t)cb * a.tn;
     const int64_t n1 = n0 + a.tn < a.Ntot ? n0 + a.tn : a.Ntot;
-    int lo = INT_MAX, hi = INT_MIN, emx = INT_MIN;
-    for (int64_t n = n0; n < n1; n++) {
+    for (int64_t n = n0 + lane; n < n1; n += 32) {
       const int j = a.col_tile[n];
       const int emax_n = a.rowscale ? a.eBmaxc[n] : a.eBmax[j];
       emx = max(emx, emax_n);
@@ -543,10 +549,15 @@ __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
         hi = max(hi, eabs);
       }
     }
+    for (int o = 16; o; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
+    }
     if (a.ucol) {
-      a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
+      if (lane == 0) a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
       if (k == 0)
-        for (int64_t n = n0; n < n1; n++)
+        for (int64_t n = n0 + lane; n < n1; n += 32)
           a.coladj[n] = (int16_t)(emx - (a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]]));
     }
   }
@@ -585,16 +596,17 @@ struct SliceWindow {
       F = R || T;
     }
   }
-  // low 32 bits of Z at the level a bits coarser than the finest
+  // low 32 bits of Z at the level a bits coarser than the finest. For A > 0 the rounding
+  // is one addition: with h = 2^(A-1) and b = (bit A of W) | F, W + h - 1 + b carries into
+  // bit A exactly when the dropped part exceeds h, or equals h with an odd quotient or a
+  // nonzero fraction below W (round half to even).
   template <int A>
   __device__ __forceinline__ uint32_t z() const {
     if constexpr (A == 0) {
       return (uint32_t)W + ((R && (T || (W & 1ull))) ? 1u : 0u);
     } else {
-      const unsigned long long tr = W >> A;
-      const bool r = (W >> (A - 1)) & 1ull;
-      const bool t = F || (W & ((1ull << (A - 1)) - 1ull)) != 0ull;
-      return (uint32_t)tr + ((r && (t || (tr & 1ull))) ? 1u : 0u);
+      const unsigned long long b = ((W >> A) & 1ull) | (F ? 1ull : 0ull);
+      return (uint32_t)((W + ((1ull << (A - 1)) - 1ull) + b) >> A);
     }
   }
 };
@@ -1652,7 +1664,7 @@ cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* 
   }
   // tile scaling: the offsets rowexp/colexp; both: the scale classes (when kept)
   const int64_t ncls = (int64_t)a.K * (a.RB + a.CB);
-  if ((a.urow || !a.rowscale) && ncls > 0) split_class_kernel<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(a);
+  if ((a.urow || !a.rowscale) && ncls > 0) split_class_kernel<<<(unsigned)((ncls * 32 + 255) / 256), 256, 0, st>>>(a);
   if (ev) cudaEventRecord(ev[++*k], st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
