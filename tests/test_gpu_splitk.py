@@ -231,3 +231,18 @@ def test_options_validation():
     for bad in (-2, 65537):
         with pytest.raises(P.BsmmError):
             P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, ksplit=bad)
+
+
+def test_transposed_storage_with_cuts():
+    """Transposed A and B storage under forced cuts: FP64 matches the oracle's cut bit for
+    bit, the split path the split oracle."""
+    from gpu_helpers import run_lib
+    base = G.random_small(77, max_blocks=6, max_size=60)
+    prob = G.transposed_storage(base, True, True)
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, rng=np.random.default_rng(3))
+    want = C0.copy()
+    oracle.bsmm(prob, cs, want, off, pieces=3)
+    Cg, _ = run_lib(prob, cs, C0, off, ksplit=3)
+    assert np.array_equal(struct_elements(prob, cs, off, Cg), struct_elements(prob, cs, off, want))
+    _split_check(prob, 6, mode=P.BSMM_SPLIT_BF16, ksplit=4)
