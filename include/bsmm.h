@@ -370,6 +370,18 @@ void bsmm_mlp_destroy(bsmm_mlp_t mlp);
 bsmm_status bsmm_status_device(bsmm_plan_t plan, void* stream);
 
 /*
+ * Diagnostics for the kernels' bounded waits (no GPU fault, trap or hang): runs a one-block
+ * kernel whose waits can never be satisfied (mbarriers that no thread arrives at). One
+ * thread waits with a limit of limit_ns nanoseconds (1e6 .. 1e9), runs out, sets the error
+ * word and the abort flag; two warps waiting with a 20x longer limit leave as soon as they
+ * see the flag -- the timeout and abort protocol of the contraction kernel. Synchronises
+ * the stream. Returns BSMM_ERR_TIMEOUT when the waits ran out as designed (the device and
+ * the context stay usable), BSMM_OK if they did not, BSMM_ERR_INVALID for a limit out of
+ * range, BSMM_ERR_CUDA when a CUDA call failed.
+ */
+bsmm_status bsmm_selftest_wait(int64_t limit_ns, void* stream);
+
+/*
  * Per-unit timing records of the last execute with record_timings set:
  * start_ns[n_units], end_ns[n_units] (device %globaltimer, host outputs, either
  * may be NULL) and the CTA each unit ran on (cta[n_units], may be NULL).

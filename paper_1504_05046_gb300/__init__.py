@@ -24,8 +24,8 @@ __all__ = [
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features",
     "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
     "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
-    "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_last_error", "bsmm_destroy",
-    "EXPORTED",
+    "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_selftest_wait", "bsmm_last_error",
+    "bsmm_destroy", "EXPORTED",
 ]
 
 BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
@@ -44,7 +44,7 @@ EXPORTED = [
     "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_kernels", "bsmm_batch_set_costs", "bsmm_batch_status_device",
     "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
-    "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_selftest_wait", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -97,6 +97,7 @@ def lib():
         L.bsmm_batch_execute.argtypes = [P, P]
         L.bsmm_batch_query.argtypes = [P, P, P, P]
         L.bsmm_batch_kernels.argtypes = [P, P]
+        L.bsmm_selftest_wait.argtypes = [i64, P]
         L.bsmm_batch_set_costs.argtypes = [P, P]
         L.bsmm_batch_status_device.argtypes = [P, P]
         L.bsmm_batch_destroy.argtypes = [P]
@@ -344,6 +345,12 @@ def bsmm_batch_query(batch: Batch) -> dict:
     nu, fl, bins = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
     _check(lib().bsmm_batch_query(batch.handle, ctypes.byref(nu), ctypes.byref(fl), ctypes.byref(bins)))
     return {"n_units": nu.value, "useful_flops": fl.value, "bins": bins.value}
+
+
+def bsmm_selftest_wait(limit_ns: int, stream=None):
+    """Runs the bounded-wait self-test kernel; raises BsmmError with status BSMM_ERR_TIMEOUT
+    (4) when its waits ran out as designed."""
+    _check(lib().bsmm_selftest_wait(int(limit_ns), _stream(stream)))
 
 
 def bsmm_batch_kernels(batch: Batch) -> int:

@@ -217,6 +217,8 @@ int split_prep_kernels(const SplitArgs& a);  // how many kernels launch_split_pr
 cudaError_t launch_split_mma(const SplitArgs& a, int clusters, cudaStream_t st);
 // split k: the reductions of the regions whose k-list was split (no launch when none)
 cudaError_t launch_split_reduce(const SplitArgs& a, cudaStream_t st);
+// a kernel whose bounded waits can never be satisfied (see bsmm_selftest_wait)
+cudaError_t launch_wait_selftest(int32_t* err, int64_t limit_ns, cudaStream_t st);
 cudaError_t launch_fp64_reduce(const Fp64Args& a, cudaStream_t st);
 
 // Longest-processing-time packing of n units with `cost` onto `bins` persistent CTAs

@@ -262,6 +262,22 @@ bsmm_status bsmm_status_device(bsmm_plan_t p, void* stream) {
   return BSMM_OK;
 }
 
+bsmm_status bsmm_selftest_wait(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000000 || limit_ns > 1000000000) return set_error("limit_ns must be in 1e6..1e9"), BSMM_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* d = nullptr;
+  int32_t w = 0;
+  cudaError_t e = cudaMalloc(&d, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = launch_wait_selftest(d, limit_ns, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&w, d, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return set_error(std::string("self-test: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  if (w & kErrTimeout) return set_error("the self-test's waits ran out (as designed)"), BSMM_ERR_TIMEOUT;
+  return BSMM_OK;
+}
+
 bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t p, float* ms, int32_t max_n, int32_t* count) {
   if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
   if (!p->opt.profile || !p->ev[0]) return set_error("plan has no profile events (profile option, one execute)"), BSMM_ERR_INVALID;

@@ -91,13 +91,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Single-thread bounded wait. False on timeout (sets the error word and the abort
 // flag) or when another role aborted.
-__device__ bool wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err) {
+__device__ bool wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err,
+                      int64_t limit = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const int64_t t0 = gtimer();
   for (uint32_t spin = 1;; spin++) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if ((spin & 63) == 0 && gtimer() - t0 > kWaitNs) {
+    if ((spin & 63) == 0 && gtimer() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(err, kErrTimeout);
       return false;
@@ -106,14 +107,15 @@ __device__ bool wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag, 
 }
 
 // Warp-uniform bounded wait (every lane polls; the decision is taken by the warp).
-__device__ bool wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err) {
+__device__ bool wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err,
+                          int64_t limit = kWaitNs) {
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const int64_t t0 = gtimer();
   for (uint32_t spin = 1;; spin++) {
     const bool ok = mbar_try_wait(bar, parity);
     if (__all_sync(0xffffffffu, ok)) return true;
     int stop = *abort_flag;
-    if ((spin & 63) == 0 && gtimer() - t0 > kWaitNs) stop = 2;
+    if ((spin & 63) == 0 && gtimer() - t0 > limit) stop = 2;
     if (__any_sync(0xffffffffu, stop != 0)) {
       if (stop == 2 && (threadIdx.x & 31) == 0) {
         *abort_flag = 1;
@@ -1555,6 +1557,30 @@ __global__ void __launch_bounds__(256) split_reduce_kernel(const __grid_constant
     store_region<TN, 8, 0>(a, cstage, rd.rb, cb, threadIdx.x >> 5, threadIdx.x & 31, a.err);
 }
 
+// ---------------------------------------------------------------- bounded-wait self-test
+// Two mbarriers that no thread ever arrives at. Warp 0 (one thread) waits on the first
+// with the given limit, runs out, sets the error word and the abort flag; warps 1 and 2
+// wait on the second (warp-uniform waits, a 20x longer limit) and leave as soon as they
+// see the abort flag. The kernel then exits normally: the contraction's wait functions
+// and its abort protocol, exercised without a hang.
+__global__ void __launch_bounds__(96) wait_selftest_kernel(int32_t* err, int64_t limit_ns) {
+  __shared__ uint64_t bars[2];
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) wait1(&bars[0], 0, &abort_flag, err, limit_ns);
+  } else {
+    wait_warp(&bars[1], 0, &abort_flag, err, 20 * limit_ns);
+  }
+  __syncthreads();
+}
+
 template <int S, int TN, int CL>
 cudaError_t launch_mma(const SplitArgs& a, int clusters, cudaStream_t st) {
   const size_t smem = split_smem_bytes(S, TN, a.stages);
@@ -1691,6 +1717,11 @@ cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEven
   }
   if (nk) *nk = k;
   return e;
+}
+
+cudaError_t launch_wait_selftest(int32_t* err, int64_t limit_ns, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 96, 0, st>>>(err, limit_ns);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_reduce(const SplitArgs& a, cudaStream_t st) {

@@ -56,6 +56,9 @@ def test_invalid_arguments_return_status():
     assert L.bsmm_status_device(None, None) == 1
     L.bsmm_destroy(None)
     assert "NULL" in P.bsmm_last_error() or P.bsmm_last_error() != ""
+    # the wait self-test rejects a limit out of range before touching the device
+    assert L.bsmm_selftest_wait(10, None) == 1
+    assert L.bsmm_selftest_wait(10 ** 10, None) == 1
 
 
 def test_plan_without_gpu_reports_cuda_error():
