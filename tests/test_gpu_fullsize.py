@@ -11,6 +11,8 @@ the schedule).
       (sizes reduced to n <= 2048 so the test generates its inputs in seconds)
   C5  M=N=24576, K=49152, log-uniform blocks [16,512], 40 clusters at 10%: split under two
       schedules
+  thin  M=N=512, K=524288 dense: every region's k-list cut (split k)
+  C2 with float32 elements, and the 8192 dense product with complex elements
 """
 import numpy as np
 import pytest
@@ -203,3 +205,63 @@ def test_c5_clustered_two_schedules():
     run.C.zero_()
     run.execute()
     assert bool((run.C == first).all())
+
+
+# ---------------------------------------------------------------- split k, element types
+def test_thin_split_k_full_size():
+    """The thin workload (M = N = 512, K = 524288) in the benchmark's configuration: the
+    planner cuts every region's k-list; a sampled tile matches the split oracle bit for bit
+    and the FP64 oracle within the 6-slice bar."""
+    prob = G.make_problem("thin_dense", 2024, 512, lo=64, hi=256, k_factor=1024)
+    run = Run(prob, P.BSMM_SPLIT_BF16, 6).execute()
+    check_structure(prob, run)
+    assert P.bsmm_plan_ksplit(run.plan)["n_regions"] > 0
+    check_split_tiles(run, 6, [(0, 0)], [(0, 0)], 1e-11)
+
+
+def test_float32_elements_full_size():
+    """The 16384 dense workload with float32 elements: sampled tiles match the float32 split
+    oracle bit for bit."""
+    import torch
+    prob = G.as_float32(G.make_problem("nonuniform_dense", 2024, 16384, lo=64, hi=256))
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                       mode=P.BSMM_SPLIT_BF16, nslices=6, elem=P.BSMM_F32)
+    cs = P.bsmm_plan_query(plan)["c_mask"]
+    off, tot = G.layout_arena(cs, prob.row_sizes, prob.col_sizes)
+    C = torch.zeros(tot, dtype=torch.float32, device="cuda")
+    P.bsmm_execute_f32(plan, 1.0, _dev(prob.A), _dev(prob.a_off), _dev(prob.B), _dev(prob.b_off), 0.0, C, _dev(off))
+    torch.cuda.synchronize()
+    P.bsmm_status_device(plan)
+    for (i, j) in sample_tiles(cs, 2, 9):
+        r, c = int(prob.row_sizes[i]), int(prob.col_sizes[j])
+        o = int(off[i, j])
+        got = C[o:o + r * c].cpu().numpy()
+        want = np.zeros(r * c, np.float32)
+        offs = np.full((prob.M, prob.N), -1, np.int64)
+        offs[i, j] = 0
+        OS.bsmm_split(prob, None, want, offs, 6, tiles=[(i, j)])
+        assert np.array_equal(got, want), (i, j)
+
+
+def test_complex_elements_full_size():
+    """The 8192 dense product with complex entries (the benchmark's complex line): sampled
+    tiles match the complex split oracle bit for bit."""
+    import torch
+    prob = G.as_complex(G.make_problem("nonuniform_dense", 2031, 8192, lo=64, hi=256), 2031)
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                       mode=P.BSMM_SPLIT_BF16, nslices=6, elem=P.BSMM_C128)
+    cs = P.bsmm_plan_query(plan)["c_mask"]
+    off, tot = G.layout_arena(cs, prob.row_sizes, prob.col_sizes)
+    C = torch.zeros(tot, dtype=torch.complex128, device="cuda")
+    P.bsmm_execute(plan, 1.0, _dev(prob.A), _dev(prob.a_off), _dev(prob.B), _dev(prob.b_off), 0.0, C, _dev(off))
+    torch.cuda.synchronize()
+    P.bsmm_status_device(plan)
+    for (i, j) in sample_tiles(cs, 2, 10):
+        r, c = int(prob.row_sizes[i]), int(prob.col_sizes[j])
+        o = int(off[i, j])
+        got = C[o:o + r * c].cpu().numpy()
+        want = np.zeros(r * c, np.complex128)
+        offs = np.full((prob.M, prob.N), -1, np.int64)
+        offs[i, j] = 0
+        OS.bsmm_split(prob, None, want, offs, 6, tiles=[(i, j)])
+        assert np.array_equal(got, want), (i, j)
