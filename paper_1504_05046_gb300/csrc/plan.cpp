@@ -7,7 +7,8 @@
 // multiply and the reduction into C are fused, Sec. 3.2 last paragraphs), the
 // useful flop count, and a packing of the tasks onto persistent CTAs
 // (longest-processing-time first onto the least-loaded CTA) that replaces the
-// paper's process grid and task queue on one GPU.
+// paper's process grid and task queue on one GPU. Where the grid would idle, a
+// region's k-list is cut into pieces with a reduction task (split k, Sec. 3.2, Fig. 2).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -34,8 +34,13 @@
 //                         accumulators; warps 4..11 drain TMEM (zeroing it behind
 //                         them), recombine in integer arithmetic and store
 //                         C = alpha*fl(sum) + beta*C.
-// A work unit is a 128-row x tn-column block of the global C index space; the CTA
-// that owns it runs every inner block in ascending order.
+//   4. split_reduce_kernel only for a plan that cut k-lists (split k, Sec. 3.2, Fig. 2):
+//                         adds each cut region's exact partial sums and stores C.
+// A work unit is a 128-row x tn-column block of the global C index space over its
+// k-list (or one piece of it); the CTA that owns it runs its inner blocks in ascending
+// order. Float32 and complex elements use the same kernels: the exponent and pack
+// kernels read the element type, the epilogue rounds and stores it.
+// wait_selftest_kernel exercises the bounded waits and the abort protocol (diagnostics).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
