@@ -168,7 +168,9 @@ void bsmm_options_default(bsmm_options* opt);
  * Allocates device memory (task tables; slice arenas for the split modes).
  * Returns BSMM_ERR_INVALID for negative sizes or an unknown option value,
  * BSMM_ERR_UNSUPPORTED for a split mode whose inner block exceeds the exact
- * accumulation depth of the tensor-core path (see bsmm_plan_query).
+ * accumulation depth of the tensor-core path (512 for 6 slices, half that for complex
+ * elements), and for an element type the mode or storage does not take (float32 or
+ * complex elements in FP64 mode; complex elements transposed or with split_scale).
  */
 bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
                       const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,
@@ -178,7 +180,8 @@ bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int
 /*
  * Structure of a plan (host outputs; any pointer may be NULL):
  *   n_ctiles     |S_C|;  n_triples  number of nonzero (i,k,j) triples
- *   useful_flops sum over the triples of 2*r_i*c_j*q_k (padding and slices not counted)
+ *   useful_flops sum over the triples of 2*r_i*c_j*q_k (8*r_i*c_j*q_k for complex
+ *                elements; padding and slices not counted)
  *   c_mask_out   M*N bytes: S_C
  *   n_units      number of work units (each owned by one CTA, fixed k order)
  */
@@ -197,8 +200,12 @@ bsmm_status bsmm_plan_ksplit(bsmm_plan_t plan, int64_t* n_regions, int64_t* n_pi
 
 /*
  * Per-unit cost features for the learned cost model (host output, row-major
- * n_units x BSMM_NFEATURES floats, see bsmm_features in the source for the
- * order) and the unit's flop-count cost. Either pointer may be NULL.
+ * n_units x BSMM_NFEATURES floats) and the unit's flop-count cost. Either pointer may
+ * be NULL. With lg(x) = log2(1 + x), a unit's features are, in order: lg(rows),
+ * lg(columns), lg(inner blocks in its k-list), lg(inner depth), lg(16-deep steps),
+ * lg(useful flops), useful / padded flops, then for the split modes 1, s/6,
+ * lg(row tiles), lg(column tiles), lg(32-deep chunks); for FP64 0, 0, 0, 0,
+ * lg(16-deep steps). A piece of a cut k-list has the features of its own range.
  */
 #define BSMM_NFEATURES 12
 bsmm_status bsmm_plan_features(bsmm_plan_t plan, float* features, double* flop_costs);
@@ -215,7 +222,9 @@ bsmm_status bsmm_plan_set_ctas(bsmm_plan_t plan, int32_t ctas);
 
 /*
  * Run the product on `stream` (device pointers):
- *   A, B       device arenas of FP64 tiles; a_off (M*K), b_off (K*N) device int64
+ *   A, B       device arenas of FP64 tiles (for a plan with complex elements:
+ *              interleaved (re, im) pairs, offsets counting complex elements);
+ *              a_off (M*K), b_off (K*N) device int64
  *   C          device arena; c_off (M*N) device int64; every tile of S_C must be
  *              present in c_off (checked on the device when debug_checks is set)
  * Asynchronous; the plan's work buffers are reused, so two executes of the same
