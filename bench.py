@@ -702,11 +702,15 @@ def run_dense(args, rank, world, local):
     pair_flops = s * (s + 1) / 2 * F
     mma_tflops = pair_flops / t_mma / 1e12
     peak_tc = pk["bf16_tflops_sustained"]
+    traffic = profiled_traffic()
     roofline = {"bound": "tensor", "kernel": "split_mma_kernel", "achieved": mma_tflops, "peak": peak_tc,
-                "unit": "TFLOP/s", "frac": mma_tflops / peak_tc, "traffic": profiled_traffic(),
+                "unit": "TFLOP/s", "frac": mma_tflops / peak_tc, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
                 "achieved_def": f"{s * (s + 1) // 2} slice-pair products x useful flops per launch / mean launch time",
                 "kernel_ms": k_avg}
+    if traffic:  # the recorded DRAM bytes per launch over this run's launch time, against the copy peak
+        roofline["dram_gbs"] = traffic / t_mma / 1e9
+        roofline["dram_frac_of_measured_copy_peak"] = roofline["dram_gbs"] / pk["hbm_gbs"]
 
     extra = {}
     if rank == 0 and not args.no_fp64:
