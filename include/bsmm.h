@@ -328,6 +328,28 @@ typedef struct {
   int32_t reserved;   /* must be zero */
 } bsmm_tune_point;
 bsmm_status bsmm_tune_space(int32_t mode, int32_t nslices, bsmm_tune_point* out, int32_t cap, int32_t* count);
+
+/*
+ * Host scheduling utilities: the planner's own packing and split-k choice, on host arrays
+ * (no device needed).
+ *
+ * bsmm_schedule_lpt: longest-processing-time packing of n units with cost[n] (> 0) onto
+ *   `bins` persistent CTAs (Sec. 3.2's task scheduler made static): units by descending
+ *   cost (ties in unit order), each to the least-loaded bin (ties to the lowest bin); each
+ *   bin then lists its units in ascending unit order. Outputs in CSR form: ptr[bins + 1]
+ *   and units[n] (bin b runs units[ptr[b] .. ptr[b+1])), and, if makespan is not NULL,
+ *   the largest bin load.
+ * bsmm_schedule_pieces: how many pieces the planner cuts each of n units into (split k,
+ *   Sec. 3.2 Fig. 2) given its cost[n] (> 0), its k-list length len[n] (>= 0), the bin
+ *   count, the per-piece overhead charged in the simulation (in cost units) and the
+ *   ksplit option (0 automatic, 1 never, >= 2 forced; see bsmm_options.ksplit).
+ *   pieces[n] receives values in 1 .. max(1, len[i]).
+ * Both return BSMM_ERR_INVALID for NULL arrays, n < 0, bins < 1, or a cost <= 0.
+ */
+bsmm_status bsmm_schedule_lpt(int64_t n, const double* cost, int32_t bins, int32_t* ptr, int32_t* units,
+                              double* makespan);
+bsmm_status bsmm_schedule_pieces(int64_t n, const double* cost, const int64_t* len, int32_t bins,
+                                 double overhead, int32_t ksplit, int32_t* pieces);
 bsmm_status bsmm_batch_autotune(bsmm_batch_t batch, int32_t n, const bsmm_tune_point* candidates, int32_t reps,
                                 void* stream, int32_t* chosen, float* ms);
 

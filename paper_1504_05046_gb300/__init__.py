@@ -44,7 +44,8 @@ EXPORTED = [
     "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_kernels", "bsmm_batch_set_costs", "bsmm_batch_status_device",
     "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
-    "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_selftest_wait", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_selftest_wait", "bsmm_schedule_lpt",
+    "bsmm_schedule_pieces", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -98,6 +99,8 @@ def lib():
         L.bsmm_batch_query.argtypes = [P, P, P, P]
         L.bsmm_batch_kernels.argtypes = [P, P]
         L.bsmm_selftest_wait.argtypes = [i64, P]
+        L.bsmm_schedule_lpt.argtypes = [i64, P, i32, P, P, P]
+        L.bsmm_schedule_pieces.argtypes = [i64, P, P, i32, f64, i32, P]
         L.bsmm_batch_set_costs.argtypes = [P, P]
         L.bsmm_batch_status_device.argtypes = [P, P]
         L.bsmm_batch_destroy.argtypes = [P]
@@ -345,6 +348,25 @@ def bsmm_batch_query(batch: Batch) -> dict:
     nu, fl, bins = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
     _check(lib().bsmm_batch_query(batch.handle, ctypes.byref(nu), ctypes.byref(fl), ctypes.byref(bins)))
     return {"n_units": nu.value, "useful_flops": fl.value, "bins": bins.value}
+
+
+def bsmm_schedule_lpt(cost, bins: int):
+    """The planner's longest-processing-time packing on the host: (ptr, units, makespan)."""
+    c = _np(cost, np.float64)
+    ptr = np.zeros(bins + 1, np.int32)
+    units = np.zeros(max(len(c), 1), np.int32)
+    mk = ctypes.c_double()
+    _check(lib().bsmm_schedule_lpt(len(c), _ptr(c), int(bins), _ptr(ptr), _ptr(units), ctypes.byref(mk)))
+    return ptr, units[:len(c)], mk.value
+
+
+def bsmm_schedule_pieces(cost, length, bins: int, overhead: float, ksplit: int = 0):
+    """The planner's split-k choice on the host: pieces per unit."""
+    c = _np(cost, np.float64)
+    ln = _np(length, np.int64)
+    out = np.zeros(max(len(c), 1), np.int32)
+    _check(lib().bsmm_schedule_pieces(len(c), _ptr(c), _ptr(ln), int(bins), float(overhead), int(ksplit), _ptr(out)))
+    return out[:len(c)]
 
 
 def bsmm_selftest_wait(limit_ns: int, stream=None):

@@ -848,6 +848,44 @@ bsmm_status bsmm_plan_query(bsmm_plan_t p, int64_t* n_ctiles, int64_t* n_triples
   return BSMM_OK;
 }
 
+bsmm_status bsmm_schedule_lpt(int64_t n, const double* cost, int32_t bins, int32_t* ptr, int32_t* units,
+                              double* makespan) {
+  if (n < 0 || bins < 1 || (n > 0 && (!cost || !units)) || !ptr)
+    return set_error("schedule_lpt: NULL array, n < 0 or bins < 1"), BSMM_ERR_INVALID;
+  std::vector<double> c(cost, cost + n);
+  for (double x : c)
+    if (!(x > 0.0) || !std::isfinite(x)) return set_error("schedule_lpt: costs must be finite and > 0"), BSMM_ERR_INVALID;
+  std::vector<int32_t> p_, u_;
+  lpt_pack(c, bins, false, p_, u_);
+  std::copy(p_.begin(), p_.end(), ptr);
+  std::copy(u_.begin(), u_.end(), units);
+  if (makespan) {
+    double mk = 0.0;
+    for (int b = 0; b < bins; b++) {
+      double l = 0.0;
+      for (int32_t x = p_[b]; x < p_[b + 1]; x++) l += c[u_[x]];
+      mk = std::max(mk, l);
+    }
+    *makespan = mk;
+  }
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_schedule_pieces(int64_t n, const double* cost, const int64_t* len, int32_t bins, double overhead,
+                                 int32_t ksplit, int32_t* pieces) {
+  if (n < 0 || bins < 1 || (n > 0 && (!cost || !len || !pieces)))
+    return set_error("schedule_pieces: NULL array, n < 0 or bins < 1"), BSMM_ERR_INVALID;
+  if (ksplit < 0 || ksplit > 65536 || !(overhead >= 0.0)) return set_error("schedule_pieces: bad ksplit or overhead"), BSMM_ERR_INVALID;
+  std::vector<double> c(cost, cost + n);
+  std::vector<int64_t> l(len, len + n);
+  for (int64_t i = 0; i < n; i++)
+    if (!(c[i] > 0.0) || !std::isfinite(c[i]) || l[i] < 0)
+      return set_error("schedule_pieces: costs must be finite and > 0, lengths >= 0"), BSMM_ERR_INVALID;
+  const std::vector<int32_t> np = choose_pieces(c, l, bins, overhead, ksplit);
+  std::copy(np.begin(), np.end(), pieces);
+  return BSMM_OK;
+}
+
 bsmm_status bsmm_plan_ksplit(bsmm_plan_t p, int64_t* n_regions, int64_t* n_pieces, int32_t* pieces) {
   if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
   if (n_regions) *n_regions = (int64_t)(p->opt.mode == BSMM_FP64 ? p->f64_red.size() : p->sp_red.size());
