@@ -150,6 +150,10 @@ struct SplitArgs {
   // a colexp row): the largest Emax of the row block (column block) minus the line's Emax
   int16_t* rowadj;
   int16_t* coladj;
+  // every row's and column's largest exponent (Emax_A of the row, Emax_B of the column;
+  // Mtot, and padded like a colexp row), the parts of the accumulator unit 2^L
+  int32_t* emaxr;
+  int32_t* emaxc;
   int32_t kdepth;           // deepest exact FP32 accumulation (inner elements) for s slices
   int32_t transa, transb;   // transposed operand storage (bsmm_options)
   // per-row / per-column scaling (split_scale = 1): exponents of every row of every A tile
@@ -289,7 +293,7 @@ struct bsmm_plan_s {
   bsmm::DevBuf d_r, d_c, d_q, d_ro, d_co, d_kptr, d_klist, d_cs, d_units, d_sched_ptr, d_sched_units;
   bsmm::DevBuf d_row_tile, d_col_tile, d_presA, d_presB, d_presBg, d_apk_off, d_bpk_off, d_apk, d_bpk;
   bsmm::DevBuf d_eArow, d_eBcol, d_eAmaxr, d_eBmaxc;
-  bsmm::DevBuf d_rowadj, d_coladj;
+  bsmm::DevBuf d_rowadj, d_coladj, d_emaxr, d_emaxc;
   bsmm::DevBuf d_am, d_bm, d_rowexp, d_colexp, d_urow, d_ucol, d_eA, d_eB, d_eAmax, d_eBmax, d_a_tiles, d_b_tiles, d_a_blocks, d_b_blocks;
   bsmm::DevBuf d_err, d_timings, d_unit_cta, d_part, d_red;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;

@@ -84,6 +84,8 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const void* A, 
   a.ucol = (int16_t*)p->d_ucol.p;
   a.rowadj = (int16_t*)p->d_rowadj.p;
   a.coladj = (int16_t*)p->d_coladj.p;
+  a.emaxr = (int32_t*)p->d_emaxr.p;
+  a.emaxc = (int32_t*)p->d_emaxc.p;
   a.kdepth = split_max_depth(p->s);
   a.transa = p->opt.transa;
   a.transb = p->opt.transb;

@@ -57,6 +57,8 @@ struct NaTables {
   int64_t apk_off[kNaRB], bpk_off[kNaCB];
   alignas(16) int16_t rowexp[kNaMaxM + 64];
   alignas(16) int16_t colexp[kNaColLd + 64];
+  alignas(16) int32_t emaxr[kNaMaxM];
+  alignas(16) int32_t emaxc[kNaColLd + 64];
   int32_t eA[1], eB[1], eAmax[1], eBmax[1];
   int32_t a_tiles[1], b_tiles[1];
   int32_t a_blocks[kNaRB], b_blocks[kNaCB];
@@ -77,6 +79,8 @@ __global__ void noalloc_setup_kernel(uint8_t* base, int m, int n, int k, int s, 
   for (int i = tid; i < kNaMaxN; i += blockDim.x) t->col_tile[i] = 0;
   for (int i = tid; i < kNaMaxM + 64; i += blockDim.x) t->rowexp[i] = 0;
   for (int i = tid; i < kNaColLd + 64; i += blockDim.x) t->colexp[i] = 0;
+  for (int i = tid; i < kNaMaxM; i += blockDim.x) t->emaxr[i] = 0;
+  for (int i = tid; i < kNaColLd + 64; i += blockDim.x) t->emaxc[i] = 0;
   if (tid == 0) {
     t->r[0] = m;
     t->c[0] = n;
@@ -198,6 +202,8 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
   a.rowexp = t->rowexp;
   a.colexp = t->colexp;
   a.colexp_ld = kNaColLd;
+  a.emaxr = t->emaxr;
+  a.emaxc = t->emaxc;
   a.eA = t->eA;
   a.eB = t->eB;
   a.eAmax = t->eAmax;

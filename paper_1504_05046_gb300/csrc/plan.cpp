@@ -601,6 +601,9 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   if ((st = dev_alloc(p->d_rowadj, sizeof(int16_t) * std::max<int64_t>(1, Mtot))) != BSMM_OK) return st;
   if ((st = dev_alloc(p->d_coladj, sizeof(int16_t) * (p->colexp_ld + 64))) != BSMM_OK) return st;
   CUDA_TRY(cudaMemset(p->d_coladj.p, 0, p->d_coladj.bytes));  // padding columns read as 0
+  if ((st = dev_alloc(p->d_emaxr, sizeof(int32_t) * std::max<int64_t>(1, Mtot))) != BSMM_OK) return st;
+  if ((st = dev_alloc(p->d_emaxc, sizeof(int32_t) * (p->colexp_ld + 64))) != BSMM_OK) return st;
+  CUDA_TRY(cudaMemset(p->d_emaxc.p, 0, p->d_emaxc.bytes));
   // exponents of absent tiles stay 0 (their slices are zero, so the scale is never used)
   CUDA_TRY(cudaMemset(p->d_rowexp.p, 0, p->d_rowexp.bytes));
   CUDA_TRY(cudaMemset(p->d_colexp.p, 0, p->d_colexp.bytes));
@@ -657,7 +660,7 @@ void bsmm_destroy(bsmm_plan_t p) {
                     &p->d_units, &p->d_sched_ptr, &p->d_sched_units, &p->d_row_tile, &p->d_col_tile,
                     &p->d_presA, &p->d_presB, &p->d_presBg, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
                     &p->d_eArow, &p->d_eBcol, &p->d_eAmaxr, &p->d_eBmaxc,
-                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_urow, &p->d_ucol, &p->d_rowadj, &p->d_coladj, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
+                    &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_urow, &p->d_ucol, &p->d_rowadj, &p->d_coladj, &p->d_emaxr, &p->d_emaxc, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
                     &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta, &p->d_part, &p->d_red,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
   for (DevBuf* b : bufs) dev_free(*b);

@@ -527,12 +527,13 @@ __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
       hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
       emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
     }
-    if (a.urow) {
-      if (lane == 0) a.urow[wid] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
-      if (k == 0)
-        for (int64_t m = m0 + lane; m < m1; m += 32)
-          a.rowadj[m] = (int16_t)(emx - (a.rowscale ? a.eAmaxr[m] : a.eAmax[a.row_tile[m]]));
-    }
+    if (k == 0)
+      for (int64_t m = m0 + lane; m < m1; m += 32) {
+        const int e = a.rowscale ? a.eAmaxr[m] : a.eAmax[a.row_tile[m]];
+        a.emaxr[m] = e;
+        if (a.urow) a.rowadj[m] = (int16_t)(emx - e);
+      }
+    if (a.urow && lane == 0) a.urow[wid] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
   } else if (wid < nr + nc) {
     const int64_t u = wid - nr;
     const int k = (int)(u / a.CB), cb = (int)(u % a.CB);
@@ -561,12 +562,13 @@ __global__ void __launch_bounds__(256) split_class_kernel(SplitArgs a) {
       hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
       emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
     }
-    if (a.ucol) {
-      if (lane == 0) a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
-      if (k == 0)
-        for (int64_t n = n0 + lane; n < n1; n += 32)
-          a.coladj[n] = (int16_t)(emx - (a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]]));
-    }
+    if (k == 0)
+      for (int64_t n = n0 + lane; n < n1; n += 32) {
+        const int e = a.rowscale ? a.eBmaxc[n] : a.eBmax[a.col_tile[n]];
+        a.emaxc[n] = e;
+        if (a.ucol) a.coladj[n] = (int16_t)(emx - e);
+      }
+    if (a.ucol && lane == 0) a.ucol[u] = (int16_t)(lo > hi ? 0 : lo == hi ? lo - emx : kNonUniform);
   }
 }
 
@@ -853,6 +855,17 @@ __device__ __forceinline__ bool acc_round(const uint32_t (&w)[4], bool& neg, uns
   return true;
 }
 
+// Results outside the normal range (rare): the rounded significand scaled by the library,
+// kept out of line so that the common path carries no FP64 instruction.
+__device__ __noinline__ double scaled_slow(unsigned long long mant, int e, bool neg) {
+  const double d = scalbn((double)mant, e);
+  return neg ? -d : d;
+}
+__device__ __noinline__ float scaled_slow32(uint32_t mant, int e, bool neg) {
+  const float f = scalbnf((float)mant, e);
+  return neg ? -f : f;
+}
+
 // The integer w times 2^L rounded to the nearest double: the 53-bit significand and the
 // exponent are assembled into the double's bit pattern (GB300's FP64 pipe is narrow, so
 // no FP64 instruction is spent per element). Only a result outside the normal range takes
@@ -866,8 +879,7 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   if (biased >= 1 && biased <= 2046)  // sign, exponent and significand assembled as bits
     return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
                                             (mant & ((1ull << 52) - 1))));
-  const double d = scalbn((double)mant, r + L);  // subnormal or overflowing result
-  return neg ? -d : d;
+  return scaled_slow(mant, r + L, neg);  // subnormal or overflowing result
 }
 
 // The same rounded once to float32 (24-bit significand), for float32 elements.
@@ -879,8 +891,7 @@ __device__ __forceinline__ float acc_to_float(const uint32_t (&w)[4], int L) {
   const int biased = r + L + 23 + 127;
   if (biased >= 1 && biased <= 254)
     return __uint_as_float(((uint32_t)neg << 31) | ((uint32_t)biased << 23) | ((uint32_t)mant & 0x7FFFFFu));
-  const float f = scalbnf((float)(uint32_t)mant, r + L);  // subnormal or overflowing result
-  return neg ? -f : f;
+  return scaled_slow32((uint32_t)mant, r + L, neg);  // subnormal or overflowing result
 }
 
 // A float32 result travels through the double staging buffer as its bit pattern.
@@ -931,15 +942,26 @@ __device__ __forceinline__ void store_region(const SplitArgs& P, const double* c
   const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
   const double alpha = P.alpha, beta = P.beta;
   const float alpha32 = (float)alpha, beta32 = (float)beta;  // float32 elements: exact (given as floats)
+  // every row's C tile offset first (independent loads, all in flight), then the stores
+  int64_t offs[kRowsPerWarp];
+  int lr2s[kRowsPerWarp];
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerWarp; rr++) {
+    const int64_t m2 = (int64_t)rb * kSplitBM + w * kRowsPerWarp + rr;
+    const int i2 = __shfl_sync(0xffffffffu, ir, rr);
+    lr2s[rr] = __shfl_sync(0xffffffffu, lrr, rr);
+    offs[rr] = -2;
+    if (m2 < P.Mtot && col_ok) {
+      const int64_t tile = (int64_t)i2 * P.N + jl;
+      offs[rr] = P.cs[tile] ? P.c_off[tile] : -2;
+    }
+  }
 #pragma unroll
   for (int rr = 0; rr < kRowsPerWarp; rr++) {
     const int r2 = w * kRowsPerWarp + rr;
-    const int64_t m2 = (int64_t)rb * kSplitBM + r2;
-    const int i2 = __shfl_sync(0xffffffffu, ir, rr);
-    const int lr2 = __shfl_sync(0xffffffffu, lrr, rr);
-    if (m2 < P.Mtot && col_ok) {
-      const int64_t tile = (int64_t)i2 * P.N + jl;
-      const int64_t off = P.cs[tile] ? P.c_off[tile] : -2;
+    const int lr2 = lr2s[rr];
+    {
+      const int64_t off = offs[rr];
       if (off == -1) atomicOr(err, kErrBadOffset);
       if (off >= 0) {
         if constexpr (ELEM == 2) {
@@ -975,12 +997,22 @@ __device__ __forceinline__ void store_region(const SplitArgs& P, const double* c
 template <int TH, bool F32>
 __device__ __forceinline__ void round_row(const uint32_t (&acc)[TH][4], double* srow, const SplitArgs& P, bool row_ok,
                                           int64_t n0, int Lrow) {
+  // the TH columns' maxima with a few 16-byte loads (n0 is a multiple of TH)
+  int emc[TH];
+#pragma unroll
+  for (int w = 0; w < TH / 4; w++) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(P.emaxc + n0) + w);
+    emc[4 * w] = v.x;
+    emc[4 * w + 1] = v.y;
+    emc[4 * w + 2] = v.z;
+    emc[4 * w + 3] = v.w;
+  }
 #pragma unroll
   for (int c = 0; c < TH; c++) {
     const int64_t n = n0 + c;
     double v = 0.0;
     if (row_ok && n < P.Ntot) {
-      const int L = Lrow + (P.rowscale ? P.eBmaxc[n] : P.eBmax[P.col_tile[n]]);
+      const int L = Lrow + emc[c];
       if constexpr (F32)
         v = f32_slot(acc_to_float(acc[c], L));
       else
@@ -1478,8 +1510,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         if (ok) {
           // the accumulator's unit 2^L: per row block and column block of tiles, or per row
           // and column with row/column scaling
-          const int Lrow =
-              row_ok ? (P.rowscale ? P.eAmaxr[m] : P.eAmax[P.row_tile[m]]) - kSplitBeta * (S + 1) - kSplitGuard : 0;
+          const int Lrow = row_ok ? P.emaxr[m] - kSplitBeta * (S + 1) - kSplitGuard : 0;
           double* srow = cstage + row * (TN + 1) + half * TH;
           if (P.f32)
             round_row<TH, true>(acc, srow, P, row_ok, n0, Lrow);
