@@ -75,3 +75,22 @@ def test_batch():
     for p in probs:
         assert 300 <= int(p.row_sizes.sum()) <= 900
         assert p.row_sizes.min() >= 32
+
+
+def test_float32_and_complex_arenas():
+    prob = G.make_problem("nonuniform_dense", 3, 300, lo=32, hi=90)
+    p32 = G.as_float32(prob)
+    assert p32.A.dtype == np.float32 and p32.B.dtype == np.float32
+    for mask, off, src_off, src, dst, rows, cols in ((prob.a_mask, p32.a_off, prob.a_off, prob.A, p32.A,
+                                                      prob.row_sizes, prob.inner_sizes),
+                                                     (prob.b_mask, p32.b_off, prob.b_off, prob.B, p32.B,
+                                                      prob.inner_sizes, prob.col_sizes)):
+        assert (off[mask != 0] % 4 == 0).all() and (off[mask == 0] == -1).all()
+        for u, v in zip(*np.nonzero(mask)):
+            n = int(rows[u]) * int(cols[v])
+            assert np.array_equal(dst[off[u, v]:off[u, v] + n], src[src_off[u, v]:src_off[u, v] + n].astype(np.float32))
+    pc = G.as_complex(prob, 7)
+    assert pc.A.dtype == np.complex128 and np.array_equal(pc.A.real, prob.A)
+    assert np.array_equal(pc.a_off, prob.a_off)
+    assert np.abs(pc.A.imag).max() <= 1.0 and pc.A.imag.std() > 0.5  # U[-1,1]: std 0.577
+    assert np.array_equal(G.as_complex(prob, 7).B, pc.B)  # a pure function of the seed

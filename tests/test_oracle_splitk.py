@@ -113,3 +113,19 @@ def test_one_piece_per_block_is_blockwise_sum():
     for a, bb in zip(prob.A[prob.a_off[0, :]], b):
         acc = acc + float(a) * float(bb)
     assert C[0] == acc
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_transposed_storage_gives_the_same_cut(seed):
+    """Only the element addressing inside a tile changes with transposed storage, so every
+    cut gives the untransposed bits."""
+    base = G.random_small(seed + 40, max_blocks=5, max_size=14)
+    cs, _, _ = oracle.structure(base)
+    off, C0 = c_arena(base, cs, fill=0.5)
+    for n in (2, 5):
+        want = C0.copy()
+        oracle.bsmm(base, cs, want, off, pieces=n)
+        for ta, tb in ((True, False), (False, True), (True, True)):
+            got = C0.copy()
+            oracle.bsmm(G.transposed_storage(base, ta, tb), cs, got, off, pieces=n)
+            assert np.array_equal(got, want), (n, ta, tb)
