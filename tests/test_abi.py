@@ -56,6 +56,11 @@ def test_invalid_arguments_return_status():
     assert L.bsmm_status_device(None, None) == 1
     L.bsmm_destroy(None)
     assert "NULL" in P.bsmm_last_error() or P.bsmm_last_error() != ""
+    # the entry points added for split k, element types and batches reject NULL handles
+    assert L.bsmm_execute_f32(None, 1.0, None, None, None, None, 0.0, None, None, None) == 1
+    assert L.bsmm_plan_ksplit(None, None, None, None) == 1
+    n = ctypes.c_int32()
+    assert L.bsmm_batch_kernels(None, ctypes.byref(n)) == 1
     # the wait self-test rejects a limit out of range before touching the device
     assert L.bsmm_selftest_wait(10, None) == 1
     assert L.bsmm_selftest_wait(10 ** 10, None) == 1
