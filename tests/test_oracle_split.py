@@ -243,3 +243,17 @@ def test_split_alpha_beta_epilogue():
     S.bsmm_split(prob2, cs, Cp, off, 6)
     want = -0.75 * struct_elements(prob, cs, off, Cp) + 2.0 * struct_elements(prob, cs, off, C0)
     assert np.array_equal(struct_elements(prob, cs, off, C1), want)
+
+
+def test_hand_worked_slices_with_ties():
+    """A hand-worked tile (tests/golden/split_slices_hand.txt): the exponent rule and the
+    ties-to-even rounding of each slice, including a negative tie."""
+    from helpers import read_golden
+    g = read_golden("split_slices_hand.txt")
+    x = np.array([float.fromhex(v) for v in g["tile"].split()])
+    e, sl, rho = S.slice_tile(x.reshape(1, -1), 3)
+    assert e == int(g["exponent"])
+    for u in range(x.size):
+        want = [int(v) for v in g[f"slices_{u}"].split()]
+        assert [int(sl[t][0, u]) for t in range(3)] == want, u
+    assert not rho.any()
