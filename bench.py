@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=16384, help="matrix order")
     ap.add_argument("--slices", type=int, default=6)
-    ap.add_argument("--cluster", type=int, default=0, help="CTAs sharing the A stream (0 = library default)")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="split modes: CTAs per column-block group (0 = library default)")
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -427,6 +428,7 @@ def run_single(args, rank, world):
     def setup(seed, mode, **opt):
         if mode != P.BSMM_FP64:
             opt.setdefault("split_scale", int(args.split_scale == "rows"))
+            opt.setdefault("cluster", args.cluster)
         opt.setdefault("ksplit", args.ksplit)
         prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,

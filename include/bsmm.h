@@ -87,8 +87,10 @@ typedef struct {
   int32_t debug_checks;    /* 1 = kernels validate offsets against the plan */
   int32_t record_timings;  /* 1 = record per-unit start/end times (bsmm_plan_timings) */
   int32_t profile;         /* 1 = time each internal kernel with CUDA events (bsmm_plan_kernel_ms) */
-  int32_t cluster;         /* split modes: CTAs per thread-block cluster sharing the A stream
-                              by multicast, 1, 2 or 4 (0 = default) */
+  int32_t cluster;         /* split modes: CTAs per column-block group, 1, 2 or 4 (0 = default):
+                              the group's CTAs take the same 128-row block at the same time,
+                              one 32-column block each, and share its A panel through L2
+                              (each CTA loads its own operands) */
   int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = 32) */
   int32_t stages;          /* split modes: depth of the shared-memory ring of 32-deep k chunks
                               (k panels in flight), 2..8 and within the 227 KB shared memory of
@@ -300,7 +302,7 @@ void bsmm_batch_destroy(bsmm_batch_t batch);
  * is a library DGEMM); these pick, by measurement, the knobs that set the contraction's
  * work-unit shape and pipeline depth.
  *
- * bsmm_tune_point: one candidate. Split modes: `cluster` CTAs per thread-block cluster
+ * bsmm_tune_point: one candidate. Split modes: `cluster` CTAs per column-block group
  *   (a work unit is 128 rows x 32*cluster columns) and `stages`, the depth of the
  *   shared-memory ring (k panels in flight). FP64 mode: `fp64_tile`, the sub-tile edge
  *   of a work unit (32 or 64). Fields that do not apply to the mode must be 0.

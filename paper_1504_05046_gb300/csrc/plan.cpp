@@ -110,7 +110,7 @@ void wave_segments(int64_t u0, int64_t u1, int bins, std::vector<int64_t>& seg) 
   if (u1 > u0) seg.push_back(u1);
 }
 
-// FP64: persistent CTAs; split modes: persistent clusters of p->cl CTAs.
+// FP64: persistent CTAs; split modes: persistent groups of p->cl CTAs.
 int machine_bins(const bsmm_plan_s* p) {
   int64_t c;
   if (p->opt.mode == BSMM_FP64)
@@ -420,8 +420,9 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   for (int64_t t = 0; t < (int64_t)M * N; t++)
     for (int64_t e = p->kptr[t]; e < p->kptr[t + 1]; e++) w[t] += 2.0 * p->q[p->klist[e]];
 
-  // A work unit is one cluster's task: a 128-row block times CL consecutive column
-  // blocks (CL * tn columns); the CL CTAs of the cluster share the A stream by multicast.
+  // A work unit is one group's task: a 128-row block times CL consecutive column blocks
+  // (CL * tn columns), one column block per CTA of the group; the CL CTAs read the same
+  // A panel at about the same time, so L2 serves it once from DRAM.
   const int CL = p->cl;
   const int CBG = (CB + CL - 1) / CL;
   p->CBG = CBG;

@@ -140,27 +140,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Same copy delivered to the same shared-memory offset of every CTA in `mask` (cluster
-// multicast within this GPU's memory); each destination's mbarrier at `bar`'s offset
-// receives the byte count.
-__device__ __forceinline__ void bulk_g2s_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                            uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 // ---------------------------------------------------------------- tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -189,15 +168,6 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-// arrive on the mbarrier at `bar`'s offset in every CTA of `mask` once this thread's
-// earlier tcgen05 operations have completed
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -1025,8 +995,8 @@ __device__ __forceinline__ void round_row(const uint32_t (&acc)[TH][4], double* 
 // ---------------------------------------------------------------- kernel 3: contraction
 // Ascending k blocks of one unit (a 128-row block times a group of cl column blocks):
 // presA[rb] & presBg[group], within the unit's inner-block range [k0, k1) (all of it, or
-// one piece under split k). Every CTA of the cluster walks the same list, because they
-// share the A stream; own_b() tells whether the CTA's own column block has that k block.
+// one piece under split k). Each CTA of the group takes from it, with next_own(), the k
+// blocks where its own column block has a B tile.
 struct UnitIter {
   const uint64_t* pa;
   const uint64_t* pb;
@@ -1099,33 +1069,32 @@ struct GroupRule {
   }
 };
 
-// The values of one k block of a unit's list that the MMA warps need, loaded ahead.
+// The values of one own k block of a unit's list that the MMA warps need, loaded ahead.
 struct KAhead {
   int k, q;
-  bool own, uni;
+  bool uni;
   int sig;
-  __device__ void load(const SplitArgs& P, const UnitIter& it, int k_, int rb, int cb) {
+  __device__ void load(const SplitArgs& P, int k_, int rb, int cb) {  // k_: an own k block, or -1
     k = k_;
     q = 0;
-    own = false;
     uni = false;
     sig = 0;
     if (k < 0) return;
     q = P.q[k];
-    own = it.own_b(k);
-    if (own) uni = scale_class(P, k, rb, cb, sig);
+    uni = scale_class(P, k, rb, cb, sig);
   }
 };
 
 // The chunks of one CTA's unit list in order: unit by unit, k block by k block
-// (ascending), 32-deep chunk by chunk.
+// (ascending; only the k blocks where the CTA's own column block has a B tile), 32-deep
+// chunk by chunk.
 struct ChunkCursor {
   const SplitArgs* P;  // the product of the current unit (the batch-wide args for one product)
   int idx, uend;
   int rb, cb;  // this CTA's row block and column block
   UnitIter it;
   int kt, kc, nkc;
-  bool ownb, in_unit;
+  bool in_unit;
   const uint8_t* asrc;
   const uint8_t* bsrc;
   __device__ void start(int beg, int end) {
@@ -1139,13 +1108,12 @@ struct ChunkCursor {
     if (++kc < nkc) return true;
     for (;;) {
       if (in_unit) {
-        kt = it.next();
+        kt = it.next_own();
         if (kt >= 0) {
           nkc = (P->q[kt] + kSplitKC - 1) / kSplitKC;  // >= 1: blocks with q = 0 are never present
           kc = 0;
-          ownb = it.own_b(kt);
           asrc = P->apk + P->apk_off[(size_t)rb * P->K + kt];
-          bsrc = ownb ? P->bpk + P->bpk_off[(size_t)kt * P->CB + cb] : nullptr;
+          bsrc = P->bpk + P->bpk_off[(size_t)kt * P->CB + cb];
           return true;
         }
         in_unit = false;
@@ -1163,17 +1131,19 @@ struct ChunkCursor {
   }
 };
 
+// CL consecutive CTAs form a column-block group: they take the same units (a 128-row
+// block times CL column blocks), each its own column block, at about the same time, so
+// the A panel they all read is served from L2. Every CTA loads its own operands; no CTA
+// reads or signals another's shared memory.
 template <int S, int TN, int CL>
 __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_constant__ SplitArgs a) {
   constexpr int TH = TN / 2;                    // columns per epilogue thread
   constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
-  constexpr int A_SLICE = A_STAGE / CL;         // bytes of A each cluster CTA loads and multicasts
   constexpr int B_STAGE = S * TN * kSplitKC * 2;
   constexpr int STAGE = A_STAGE + B_STAGE;
   constexpr int BUF_COLS = S * TN;              // TMEM columns per accumulator buffer
-  constexpr uint16_t MASK = (uint16_t)((1u << CL) - 1);
   constexpr int W = S < kMmaWarps ? S : kMmaWarps;  // MMA warps with work: warp 1+w issues slices p = w+1, w+1+W, ...
-  static_assert(A_SLICE % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(A_STAGE % 16 == 0 && B_STAGE % 16 == 0, "bulk copies move multiples of 16 bytes");
   static_assert(TN == 32, "the coalesced C store maps one column to each lane");
 
   extern __shared__ uint8_t smem_raw[];
@@ -1191,14 +1161,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   double* cstage = (double*)(smem + (size_t)stages * STAGE + kSplitBarBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cta = blockIdx.x / CL;  // the cluster: schedules are per cluster
-  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
+  const int cta = blockIdx.x / CL;   // the group: schedules are per group
+  const int rank = blockIdx.x % CL;  // this CTA's column block within the group's units
   const int ubeg = a.sched_ptr[cta], uend = a.sched_ptr[cta + 1];
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < stages; st++) {
       mbar_init(&full[st], 1);
-      mbar_init(&empty[st], CL * W);  // released by every MMA warp of every CTA of the cluster
+      mbar_init(&empty[st], W);  // released by every MMA warp
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(&tfull[b], W);
@@ -1214,7 +1184,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL > 1) cluster_sync();  // peers' barriers exist before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -1229,19 +1198,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       ChunkCursor cur;
       cur.start(ubeg, uend);
       while (ok && cur.advance(a, CL, rank)) {
-        // the slot is free in every CTA of the cluster (the multicast writes all of them)
         if (!wait1(&empty[stage], phase ^ 1, abort_flag, a.err)) {
           ok = false;
           break;
         }
         uint8_t* sa = smem + (size_t)stage * STAGE;
-        mbar_arrive_expect_tx(&full[stage], A_STAGE + (cur.ownb ? B_STAGE : 0));
-        const uint8_t* asrc = cur.asrc + (size_t)cur.kc * A_STAGE;
-        if constexpr (CL > 1)
-          bulk_g2s_mc(sa + rank * A_SLICE, asrc + rank * A_SLICE, A_SLICE, &full[stage], MASK);
-        else
-          bulk_g2s(sa, asrc, A_STAGE, &full[stage]);
-        if (cur.ownb) bulk_g2s(sa + A_STAGE, cur.bsrc + (size_t)cur.kc * B_STAGE, B_STAGE, &full[stage]);
+        mbar_arrive_expect_tx(&full[stage], STAGE);
+        bulk_g2s(sa, cur.asrc + (size_t)cur.kc * A_STAGE, A_STAGE, &full[stage]);
+        bulk_g2s(sa + A_STAGE, cur.bsrc + (size_t)cur.kc * B_STAGE, B_STAGE, &full[stage]);
         issued |= 1u << stage;
         issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
         if (++stage == stages) {
@@ -1305,14 +1269,13 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         // per-k values are loaded one k block ahead, so their latency hides behind the
         // current block's MMAs; a group is closed when the next own k block does not join
         KAhead cur, nxt;
-        cur.load(P, it, it.next(), un.rb, cb);
+        cur.load(P, it.next_own(), un.rb, cb);
         while (cur.k >= 0 && ok) {
-          nxt.load(P, it, it.next(), un.rb, cb);
+          nxt.load(P, it.next_own(), un.rb, cb);
           const int kt = cur.k;
           const int q = cur.q;
           const int nkc = (q + kSplitKC - 1) / kSplitKC;
-          const bool ownb = cur.own;
-          if (ownb && !(in_group && grp.joins(cur.uni, cur.sig, cur.q))) {
+          if (!(in_group && grp.joins(cur.uni, cur.sig, cur.q))) {
             if (in_group) {  // the previous group is complete
               umma_commit(&tfull[buf]);
               tcount++;
@@ -1336,7 +1299,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
               break;
             }
             tc_fence_after();
-            if (ownb) {
+            {
               const uint64_t soff = (uint64_t)((stage * STAGE) >> 4);
               const uint64_t ad = adesc0 + soff, bd = bdesc0 + soff;
               const bool two = q - kc * kSplitKC > 16;  // second 16-deep step of the 32-deep chunk
@@ -1347,11 +1310,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
                 if (two) umma_f16(dbase + dcol[j], ad + aoff[j] + 2, bd + 2, idp[j], 1u);
               }
             }
-            // release the stage in every CTA of the cluster once these MMAs finished
-            if constexpr (CL > 1)
-              umma_commit_mc(&empty[stage], MASK);
-            else
-              umma_commit(&empty[stage]);
+            umma_commit(&empty[stage]);  // the stage is free once these MMAs have finished
             any = true;
             if (++stage == stages) {
               stage = 0;
@@ -1407,7 +1366,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       if (a.prods) u = a.unit_local[u];
       const SplitUnit un = P.units[u];
       const int cb = un.cb * CL + rank;
-      if (cb >= P.CB) continue;  // this CTA only helps stream the cluster's A panel
+      if (cb >= P.CB) continue;  // a group's CTA past the last column block has no work
       if (a.timings && rank == 0 && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = gtimer();
       const int64_t m = (int64_t)un.rb * kSplitBM + row;
       const bool row_ok = m < P.Mtot;
@@ -1546,7 +1505,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
 
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL > 1) cluster_sync();  // no peer multicasts into or signals this CTA any more
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, kTmemCols);
 }
@@ -1618,24 +1576,13 @@ __global__ void __launch_bounds__(96) wait_selftest_kernel(int32_t* err, int64_t
 }
 
 template <int S, int TN, int CL>
-cudaError_t launch_mma(const SplitArgs& a, int clusters, cudaStream_t st) {
+cudaError_t launch_mma(const SplitArgs& a, int groups, cudaStream_t st) {
   const size_t smem = split_smem_bytes(S, TN, a.stages);
   cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(clusters * CL), 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, split_mma_kernel<S, TN, CL>, a);
+  split_mma_kernel<S, TN, CL><<<(unsigned)(groups * CL), kThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <int S>
@@ -1648,26 +1595,21 @@ cudaError_t launch_mma_cl(const SplitArgs& a, int clusters, cudaStream_t st) {
   }
 }
 
+// Groups of CL CTAs that are resident at once: the persistent grid (one CTA per SM at
+// this shared-memory size) divided into groups.
 template <int S, int CL>
 int max_clusters_for(int stages) {
   const size_t smem = split_smem_bytes(S, 32, stages);
   if (cudaFuncSetAttribute(split_mma_kernel<S, 32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL, 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, split_mma_kernel<S, 32, CL>, &cfg) != cudaSuccess) return 0;
-  return n;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, CL>, kThreads, smem) !=
+      cudaSuccess)
+    return 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return per_sm * sms / CL;
 }
 
 template <int S>

@@ -162,10 +162,10 @@ def test_too_deep_inner_block_is_rejected():
 
 @pytest.mark.parametrize("cluster", [1, 2, 4])
 @pytest.mark.parametrize("recipe", ["nonuniform_dense", "clustered", "ragged"])
-def test_cluster_multicast_sizes(cluster, recipe):
-    """The A stream shared by multicast across 1, 2 or 4 CTAs: same bits, including
-    column-block groups whose last members fall beyond the matrix and CTAs whose own
-    column block has no B tile at some k block."""
+def test_column_block_group_sizes(cluster, recipe):
+    """Units of 1, 2 or 4 column blocks, one per CTA of a group: same bits, including
+    groups whose last members fall beyond the matrix and CTAs whose own column block has
+    no B tile at some k block of the group's list."""
     if recipe == "nonuniform_dense":
         prob = G.make_problem("nonuniform_dense", 31, 777, lo=40, hi=200)
     elif recipe == "clustered":
