@@ -25,25 +25,20 @@ power-of-two scale per tile:
   accumulation, exact, then one rounding:
     each C element of tile (i, j) is the exact sum over its k blocks of
       T_k * 2^(E_k),  E_k = e_A(i,k) + e_B(k,j) - beta*(s+1),
-    held as an integer multiple of 2^L with
-      L = Emax_A(i) + Emax_B(j) - beta*(s+1) - GUARD_BITS,
-    where Emax_A(i) is the largest exponent of the stored A tiles of row block i
-    (Emax_B(j) likewise for column block j; 0 when there is none). A term with
-    E_k < L enters as floor(T_k 2^(E_k - L)) (never for exponent spans up to
-    GUARD_BITS binades); the sum is then rounded once to FP64 (round to nearest
-    even) and scaled by 2^L, and the epilogue is C_ij = fl(alpha*acc) + fl(beta*C_ij)
-    as in the FP64 oracle.
+    formed here as one Python integer in units of 2^(min_k E_k) (every term enters
+    with its full value: nothing below any unit is dropped); that exact value is
+    rounded once to the output format (round to nearest, ties to even, subnormal
+    results rounded directly on the subnormal grid) and the epilogue is
+    C_ij = fl(alpha*acc) + fl(beta*C_ij) as in the FP64 oracle.
 
 Because the sum is exact before its single rounding, the value does not depend on
 the order in which tile pairs, slice pairs or k blocks are added.
 
 Row/column scaling (scaling="rows"): the same slicing with one exponent per row of an
 A tile and per column of a B tile (e_A(i,k)[ii], e_B(k,j)[jj]); an all-zero row or
-column has zero slices and takes no part in the maxima below. The contribution of a
-tile pair to element (ii, jj) is T[ii,jj] * 2^(e_A[ii] + e_B[jj] - beta*(s+1)), and the
-accumulator unit is per element: L[ii,jj] = Emax_A(row ii) + Emax_B(col jj) - beta*(s+1)
-- GUARD_BITS, with Emax_A(row) the largest exponent of that row over its stored tiles
-(0 when none) and Emax_B(col) likewise.
+column has exponent 0 and zero slices. The contribution of a tile pair to element
+(ii, jj) is T[ii,jj] * 2^(e_A[ii] + e_B[jj] - beta*(s+1)); the exact sum and its single
+rounding are as above.
 
 Complex elements (complex128 arenas, tile mode, real alpha and beta): one exponent per
 tile over the real and imaginary parts together; both parts sliced with it; per tile pair
@@ -53,9 +48,10 @@ the epilogue applies alpha and beta to each part.
 
 Float32 elements (a float32 C arena; A and B may be float32 as well): the slicing and the
 exact sum are the same (float32 values are exact in float64); the sum is rounded once to
-a 24-bit significand (ties to even) and scaled by 2^L into float32, and the epilogue runs
-in float32: C = fl32(fl32(alpha*acc) + fl32(beta*C)). With float64 C the sum is rounded to
-a 53-bit significand and scaled into float64 (math.ldexp), the epilogue in float64.
+binary32 (24-bit significand, subnormals on their own grid, ties to even) and the epilogue
+runs in float32: C = fl32(fl32(alpha*acc) + fl32(beta*C)). With float64 C the exact sum is
+rounded once to binary64 by Python's correctly rounded integer division, the epilogue in
+float64.
 
 All integer matrix products below go through a float64 matmul: every entry is an
 integer of magnitude below 2^53, so the library routine returns it exactly in
@@ -68,7 +64,6 @@ import math
 import numpy as np
 
 BETA_BITS = 7
-GUARD_BITS = 55
 
 
 def tile_exponent(x: np.ndarray) -> int:
@@ -144,17 +139,48 @@ def round_significand(v: int, bits: int) -> int:
     return (q << sh) if v > 0 else -(q << sh)
 
 
+def round_binary32(v: int, L: int) -> np.float32:
+    """v * 2^L rounded once to binary32: the last place of a normal result is 2^(E-23) for
+    a value in [2^E, 2^(E+1)), of a subnormal one 2^-149; ties to even; overflow to inf."""
+    if v == 0:
+        return np.float32(0.0)
+    a = abs(v)
+    E = a.bit_length() - 1 + L
+    Q = max(E - 23, -149)              # exponent of the last place
+    sh = Q - L
+    if sh <= 0:
+        m = a << (-sh)
+    else:
+        m, rem, half = a >> sh, a & ((1 << sh) - 1), 1 << (sh - 1)
+        if rem > half or (rem == half and (m & 1)):
+            m += 1
+    if m.bit_length() + Q > 128:       # |result| >= 2^128
+        out = math.inf
+    else:
+        out = math.ldexp(float(m), Q)  # m <= 2^24: exact
+    return np.float32(out if v > 0 else -out)
+
+
+def round_binary64(v: int, L: int) -> float:
+    """v * 2^L rounded once to binary64 (Python's int-to-float conversion and int / int
+    division are correctly rounded, ties to even, subnormals included); overflow to inf."""
+    try:
+        return float(v << L) if L >= 0 else v / (1 << -L)
+    except OverflowError:
+        return math.copysign(math.inf, v)
+
+
 def _finish(exact, L, ct, alpha: float, bet: float):
     """ct (a C tile, float64 or float32) = alpha*acc + beta*ct, acc = the exact integers
-    times 2^L rounded once to ct's precision (L a scalar or per element)."""
+    times 2^L (L a scalar or per element) rounded once to ct's precision."""
     Ls = np.broadcast_to(np.asarray(L, dtype=object), exact.shape)
     if ct.dtype == np.float32:
-        acc = np.array([np.float32(math.ldexp(float(round_significand(int(v), 24)), int(l)))
-                        for v, l in zip(exact.reshape(-1), Ls.reshape(-1))], np.float32).reshape(exact.shape)
+        acc = np.array([round_binary32(int(v), int(l)) for v, l in zip(exact.reshape(-1), Ls.reshape(-1))],
+                       np.float32).reshape(exact.shape)
         u = np.float32(alpha) * acc
         ct[...] = (u + np.float32(bet) * ct) if bet != 0.0 else u
     else:
-        acc = np.array([math.ldexp(float(v), int(l)) for v, l in zip(exact.reshape(-1), Ls.reshape(-1))],
+        acc = np.array([round_binary64(int(v), int(l)) for v, l in zip(exact.reshape(-1), Ls.reshape(-1))],
                        np.float64).reshape(exact.shape)
         u = alpha * acc
         ct[...] = (u + bet * ct) if bet != 0.0 else u
@@ -206,21 +232,11 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
             cacheB[(k, j)] = sl(x)
         return cacheB[(k, j)]
 
-    def emax_a(i):
-        ks = [k for k in range(K) if am[i, k] and r[i] > 0 and q[k] > 0]
-        return max((a_sl(i, k)[0] for k in ks), default=0)
-
-    def emax_b(j):
-        ks = [k for k in range(K) if bm[k, j] and c[j] > 0 and q[k] > 0]
-        return max((b_sl(k, j)[0] for k in ks), default=0)
-
     todo = tiles if tiles is not None else [(i, j) for i in range(M) for j in range(N) if c_struct[i, j]]
     alpha, bet = float(prob_like.alpha), float(prob_like.beta)
     for (i, j) in todo:
-        L = emax_a(i) + emax_b(j) - beta * (s + 1) - GUARD_BITS
-        parts = [np.zeros((r[i], c[j]), dtype=object) for _ in range(2 if cplx else 1)]
-        for ex in parts:
-            ex[...] = 0
+        # every term of the exact sum: (T per part, its binary position E_k)
+        terms = []
         for k in range(K):
             if not (am[i, k] and bm[k, j]):
                 continue
@@ -232,9 +248,14 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
                       pair_integer(ar, bi, s, beta).astype(object) + pair_integer(ai, br, s, beta).astype(object)]
             else:
                 Ts = [pair_integer(na, nb, s, beta).astype(object)]
-            sh = eA + eB - beta * (s + 1) - L
+            terms.append((Ts, eA + eB - beta * (s + 1)))
+        L = min((E for _, E in terms), default=0)  # the unit of the exact sum: every shift below is >= 0
+        parts = [np.zeros((r[i], c[j]), dtype=object) for _ in range(2 if cplx else 1)]
+        for ex in parts:
+            ex[...] = 0
+        for Ts, E in terms:
             for t, T in enumerate(Ts):
-                parts[t] = parts[t] + (T * (1 << sh) if sh >= 0 else T // (1 << -sh))  # floor below 2^L
+                parts[t] = parts[t] + T * (1 << (E - L))
         o = int(c_off[i, j])
         ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
         if cplx:
@@ -277,34 +298,26 @@ def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
             cacheB[(k, j)] = (e, nz, [t.T for t in sl])
         return cacheB[(k, j)]
 
-    def emax(vals, n):  # largest exponent of nonzero rows, per row (0 when none)
-        out = np.full(n, -(1 << 40), np.int64)
-        for e, nz in vals:
-            out = np.where(nz, np.maximum(out, e), out)
-        return np.where(out == -(1 << 40), 0, out)
-
-    def emax_a(i):
-        return emax([a_sl(i, k)[:2] for k in range(K) if am[i, k] and r[i] > 0 and q[k] > 0], int(r[i]))
-
-    def emax_b(j):
-        return emax([b_sl(k, j)[:2] for k in range(K) if bm[k, j] and c[j] > 0 and q[k] > 0], int(c[j]))
-
-    shift = np.vectorize(lambda t, h: t << h if h >= 0 else t >> (-h), otypes=[object])  # floor below 2^L
     todo = tiles if tiles is not None else [(i, j) for i in range(M) for j in range(N) if c_struct[i, j]]
     alpha, bet = float(prob_like.alpha), float(prob_like.beta)
     for (i, j) in todo:
-        L = emax_a(i)[:, None] + emax_b(j)[None, :] - beta * (s + 1) - GUARD_BITS
-        exact = np.zeros((r[i], c[j]), dtype=object)
-        exact[...] = 0
+        terms = []  # (T, per-element binary position E_k[ii, jj])
         for k in range(K):
             if not (am[i, k] and bm[k, j]):
                 continue
             eA, _, na = a_sl(i, k)
             eB, _, nb = b_sl(k, j)
-            T = pair_integer(na, nb, s, beta).astype(object)
-            sh = eA[:, None] + eB[None, :] - beta * (s + 1) - L
+            terms.append((pair_integer(na, nb, s, beta).astype(object),
+                          eA[:, None] + eB[None, :] - beta * (s + 1)))
+        # per element, the unit of the exact sum: the lowest position of its terms
+        L = np.zeros((r[i], c[j]), np.int64)
+        if terms:
+            L = np.minimum.reduce([E for _, E in terms])
+        exact = np.zeros((r[i], c[j]), dtype=object)
+        exact[...] = 0
+        for T, E in terms:
             if T.size:
-                exact = exact + shift(T, sh)
+                exact = exact + T * np.left_shift(np.ones_like(E, dtype=object), (E - L).astype(object))
         o = int(c_off[i, j])
         _finish(exact, L, C[o:o + r[i] * c[j]].reshape(r[i], c[j]), alpha, bet)
     return C

@@ -103,14 +103,31 @@ def test_pair_integer_brute_force(s):
             assert int(T[i, j]) == tot
 
 
+def _span_tiles(prob, seed, binades):
+    """Scale every A tile of inner block k by 2^(-binades * k / K): the k blocks of one C
+    element then contribute at positions up to ``binades`` binades apart."""
+    rng = np.random.default_rng(seed)
+    for i in range(prob.M):
+        for k in range(prob.K):
+            if prob.a_mask[i, k]:
+                o = prob.a_off[i, k]
+                n = int(prob.row_sizes[i]) * int(prob.inner_sizes[k])
+                prob.A[o:o + n] *= 2.0 ** (-(binades * k) // max(prob.K, 1) - int(rng.integers(0, 3)))
+    return prob
+
+
+@pytest.mark.parametrize("span", [0, 120])
 @pytest.mark.parametrize("s", [2, 3, 6])
 @pytest.mark.parametrize("seed", range(3))
-def test_split_result_is_exact_sum_rounded_once(s, seed):
+def test_split_result_is_exact_sum_rounded_once(s, seed, span):
     """Independent route: the exact rational sum over k blocks, kept slice pairs and
     inner indices of N^A_p N^B_q 2^(eA+eB-7(p+q)), rounded once (Fraction -> float is
-    correctly rounded). The oracle's value must equal it bit for bit."""
+    correctly rounded). The oracle's value must equal it bit for bit, also when the k
+    blocks' products lie up to 120 binades apart."""
     prob = G.random_small(seed + 500, max_blocks=4, max_size=9)
     prob.alpha, prob.beta = 1.0, 0.0
+    if span:
+        prob = _span_tiles(prob, seed, span)
     cs, _, _ = oracle.structure(prob)
     off, C = c_arena(prob, cs, fill=0.0)
     S.bsmm_split(prob, cs, C, off, s)
@@ -257,3 +274,64 @@ def test_hand_worked_slices_with_ties():
         want = [int(v) for v in g[f"slices_{u}"].split()]
         assert [int(sl[t][0, u]) for t in range(3)] == want, u
     assert not rho.any()
+
+
+def _one_by_one(a_vals, b_vals):
+    """A 1 x 1 C tile whose k-th term is a_vals[k] * b_vals[k] (1 x 1 tiles, K = len)."""
+    one = np.ones(1, np.int32)
+    q = np.ones(len(a_vals), np.int32)
+    am, bm = np.ones((1, len(a_vals)), np.uint8), np.ones((len(a_vals), 1), np.uint8)
+    a_off, at = G.layout_arena(am, one, q)
+    b_off, bt = G.layout_arena(bm, q, one)
+    A, B = np.zeros(at), np.zeros(bt)
+    A[a_off[0, :]] = a_vals
+    B[b_off[:, 0]] = b_vals
+    prob = G.Problem("terms", one, one, q, am, bm, a_off, b_off, A, B, 1.0, 0.0)
+    cs = np.ones((1, 1), np.uint8)
+    off, _ = G.layout_arena(cs, one, one)
+    return prob, cs, off
+
+
+@pytest.mark.parametrize("s", [1, 6])
+def test_far_term_decides_a_tie(s):
+    """Terms 1, 2^-53 and 2^-150 (each a power of two, sliced exactly): 1 + 2^-53 is a tie
+    between 1 and 1 + 2^-52, and the term 97 binades further down puts the exact sum above
+    it, so the one rounding gives 1 + 2^-52. An accumulation that dropped bits far below
+    the largest term (a fixed-width window, say 55 bits under it) would see the tie and
+    round to 1."""
+    prob, cs, off = _one_by_one([1.0, 2.0 ** -53, 2.0 ** -150], [1.0, 1.0, 1.0])
+    C = np.zeros(1)
+    S.bsmm_split(prob, cs, C, off, s)
+    assert C[0] == 1.0 + 2.0 ** -52
+    prob2, cs2, off2 = _one_by_one([1.0, 2.0 ** -53, -2.0 ** -150], [1.0, 1.0, 1.0])
+    S.bsmm_split(prob2, cs2, C, off2, s)
+    assert C[0] == 1.0  # just below the tie
+
+
+def test_subnormal_result_rounded_once():
+    """Terms 1.5 * 2^-1074 and -2^-1144 (products of powers of two and 1.5): the exact sum
+    (1.5 - 2^-70) 2^-1074 lies just below the midpoint of the two smallest subnormals, so
+    it rounds to 2^-1074. Rounding to a 53-bit significand first (1.5 * 2^-1074, a tie)
+    and then to the subnormal grid would give 2^-1073."""
+    prob, cs, off = _one_by_one([1.5 * 2.0 ** -600, -2.0 ** -572], [2.0 ** -474, 2.0 ** -572])
+    for s in (1, 6):
+        C = np.zeros(1)
+        S.bsmm_split(prob, cs, C, off, s)
+        assert C[0] == 2.0 ** -1074, (s, C[0])
+        assert C[0] == float(Fraction(3, 2) * Fraction(2) ** -1074 - Fraction(2) ** -1144)
+    C32 = np.zeros(1, np.float32)
+    prob32, _, _ = _one_by_one([1.5 * 2.0 ** -80, -2.0 ** -95], [2.0 ** -69, 2.0 ** -94])
+    S.bsmm_split(prob32, cs, C32, off, 6)
+    assert C32[0] == np.float32(2.0 ** -149)  # (1.5 - 2^-40) 2^-149: below the tie
+
+
+def test_overflowing_sum_rounds_to_infinity():
+    """Two terms of 2^1023 each: the exact sum 2^1024 is beyond binary64, so the result is
+    +inf (round to nearest); with opposite signs it is 0."""
+    prob, cs, off = _one_by_one([2.0 ** 600, 2.0 ** 600], [2.0 ** 423, 2.0 ** 423])
+    C = np.zeros(1)
+    S.bsmm_split(prob, cs, C, off, 6)
+    assert C[0] == math.inf
+    prob2, _, _ = _one_by_one([2.0 ** 600, -2.0 ** 600], [2.0 ** 423, 2.0 ** 423])
+    S.bsmm_split(prob2, cs, C, off, 6)
+    assert C[0] == 0.0

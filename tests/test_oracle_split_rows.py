@@ -65,8 +65,8 @@ def _scaled_integers(seed, zero_segments=False):
     integer sum, and every row (column) fits one 7-bit slice of its own exponent."""
     p = G.make_problem("nonuniform_dense", seed, 180, lo=20, hi=60, values="integers")
     rng = np.random.default_rng(seed)
-    # rows 2^-70 .. 2^-110: more than the 55 guard bits below 2^0, so an all-zero row segment
-    # (exponent 0) that took part in the row maximum would floor the row's real terms
+    # rows 2^-70 .. 2^-110: far below an all-zero row segment's exponent 0, so a rule that
+    # let such a segment set the row's scale would lose the row's real terms
     ra = np.ldexp(1.0, -70 - 10 * rng.integers(0, 5, int(p.row_sizes.sum())))
     cb = np.ldexp(1.0, -10 * rng.integers(0, 5, int(p.col_sizes.sum())))
     ro = np.concatenate([[0], np.cumsum(p.row_sizes)])
