@@ -43,6 +43,7 @@
 // wait_selftest_kernel exercises the bounded waits and the abort protocol (diagnostics).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <math_constants.h>
 
 #include <climits>
 #include <cstdint>
@@ -825,21 +826,46 @@ __device__ __forceinline__ bool acc_round(const uint32_t (&w)[4], bool& neg, uns
   return true;
 }
 
-// Results outside the normal range (rare): the rounded significand scaled by the library,
-// kept out of line so that the common path carries no FP64 instruction.
-__device__ __noinline__ double scaled_slow(unsigned long long mant, int e, bool neg) {
-  const double d = scalbn((double)mant, e);
-  return neg ? -d : d;
+// Bit b of the 128-bit magnitude (hi, lo), and whether any of its bits below b is set.
+__device__ __forceinline__ bool bit128(unsigned long long hi, unsigned long long lo, int b) {
+  return b < 64 ? (lo >> b) & 1 : (hi >> (b - 64)) & 1;
 }
-__device__ __noinline__ float scaled_slow32(uint32_t mant, int e, bool neg) {
-  const float f = scalbnf((float)mant, e);
-  return neg ? -f : f;
+__device__ __forceinline__ bool low128(unsigned long long hi, unsigned long long lo, int b) {  // bits [0, b)
+  if (b <= 0) return false;
+  if (b <= 64) return (b == 64 ? lo : lo & ((1ull << b) - 1)) != 0;
+  if (b >= 128) return (lo | hi) != 0;
+  return lo != 0 || (hi & ((1ull << (b - 64)) - 1)) != 0;
+}
+
+// A result below the smallest normal number (rare): w * 2^L rounded once, ties to even,
+// to a multiple of the format's smallest subnormal 2^emin_sub, returned as that multiple
+// (at most 2^P-1: the next normal number's pattern when it rounds up). Callers pass only
+// values below the smallest normal, so |w| < 2^(emin_sub - L + P - 1).
+template <int P>
+__device__ __noinline__ unsigned long long acc_round_subnormal(const uint32_t (&w)[4], int L, int emin_sub,
+                                                               bool& neg) {
+  unsigned long long lo = ((unsigned long long)w[1] << 32) | w[0];
+  unsigned long long hi = ((unsigned long long)w[3] << 32) | w[2];
+  neg = (long long)hi < 0;
+  if (neg) {
+    lo = ~lo;
+    hi = ~hi;
+    lo += 1;
+    if (lo == 0) hi += 1;
+  }
+  const int sh = emin_sub - L;  // the grid step in units of w
+  if (sh <= 0) return lo << (-sh);  // exact (then |w| < 2^(P-1+sh), so hi = 0)
+  if (sh > 128) return 0;           // |w| < 2^128 <= half a step
+  unsigned long long q = sh < 128 ? shr128(hi, lo, sh) : 0ull;
+  const bool round = bit128(hi, lo, sh - 1);
+  if (round && (low128(hi, lo, sh - 1) || (q & 1))) q += 1;
+  return q;
 }
 
 // The integer w times 2^L rounded to the nearest double: the 53-bit significand and the
 // exponent are assembled into the double's bit pattern (GB300's FP64 pipe is narrow, so
-// no FP64 instruction is spent per element). Only a result outside the normal range takes
-// the library scaling (the 53-bit significand scaled, as the definition states).
+// no FP64 instruction is spent per element). A result below the normal range is rounded
+// once on the subnormal grid (not first to 53 bits); one beyond it is an infinity.
 __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   bool neg;
   unsigned long long mant;
@@ -849,7 +875,9 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
   if (biased >= 1 && biased <= 2046)  // sign, exponent and significand assembled as bits
     return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
                                             (mant & ((1ull << 52) - 1))));
-  return scaled_slow(mant, r + L, neg);  // subnormal or overflowing result
+  if (biased > 2046) return neg ? -CUDART_INF : CUDART_INF;
+  const unsigned long long q = acc_round_subnormal<53>(w, L, -1074, neg);
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) | q));
 }
 
 // The same rounded once to float32 (24-bit significand), for float32 elements.
@@ -861,7 +889,9 @@ __device__ __forceinline__ float acc_to_float(const uint32_t (&w)[4], int L) {
   const int biased = r + L + 23 + 127;
   if (biased >= 1 && biased <= 254)
     return __uint_as_float(((uint32_t)neg << 31) | ((uint32_t)biased << 23) | ((uint32_t)mant & 0x7FFFFFu));
-  return scaled_slow32((uint32_t)mant, r + L, neg);  // subnormal or overflowing result
+  if (biased > 254) return neg ? -CUDART_INF_F : CUDART_INF_F;
+  const unsigned long long q = acc_round_subnormal<24>(w, L, -149, neg);
+  return __uint_as_float(((uint32_t)neg << 31) | (uint32_t)q);
 }
 
 // A float32 result travels through the double staging buffer as its bit pattern.
