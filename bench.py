@@ -446,16 +446,16 @@ def run_single(args, rank, world):
         for _ in range(args.warmup):
             run()
         torch.cuda.synchronize()
+        P.bsmm_plan_kernel_ms(plan)  # the per-kernel means below cover the timed steps only
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ks = []
         e0.record(stream)
         for _ in range(steps):
             run()
-            ks.append(P.bsmm_plan_kernel_ms(plan))
         e1.record(stream)
         torch.cuda.synchronize()
+        ks = P.bsmm_plan_kernel_ms(plan)  # mean per kernel over the timed steps
         P.bsmm_status_device(plan)
-        return e0.elapsed_time(e1) / steps, np.mean(np.array(ks), axis=0).tolist()
+        return e0.elapsed_time(e1) / steps, ks
 
     extra = {}
     seed = args.seed + rank
@@ -539,10 +539,11 @@ def run_single(args, rank, world):
                 "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"}
     else:
-        fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        rates = P.bsmm_measure_rates()
         roof = {"bound": "alu", "kernel": "fp64_tile_kernel", "achieved": F / (k64[cif] * 1e-3) / 1e12,
-                "peak": fp64_peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}
+                "peak": rates["dfma"], "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "measured in this run (bsmm_measure_rates): DFMA on every SM",
+                "dmma_tflops": rates["dmma"], "frac_of_dmma": F / (k64[cif] * 1e-3) / 1e12 / rates["dmma"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
     head = split if head_split else fp64
     line = {"metric": METRIC, "value": head["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -615,6 +616,7 @@ def complex_line(args, P, G, torch, dev, stream):
         C = torch.zeros(tot, dtype=torch.complex128, device=dev)
         for _ in range(2):
             P.bsmm_execute(plan, 1.0, Ac, ao, Bc, bo, 0.0, C, co)
+        P.bsmm_plan_kernel_ms(plan)  # kernel means over the timed executes only
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         for _ in range(3):
@@ -675,20 +677,22 @@ def run_dense(args, rank, world, local):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
+    P.bsmm_plan_kernel_ms(plan)  # start the per-kernel means at the first timed step
+    per_step = kernels_per_execute(P, plan, P.BSMM_SPLIT_BF16, sc["split_scale"])
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    kms = []
     launches = 0
     e0.record(stream)
     for _ in range(args.steps):
         P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
-        ks = P.bsmm_plan_kernel_ms(plan)
-        kms.append(ks)
-        launches += kernels_per_execute(P, plan, P.BSMM_SPLIT_BF16, sc["split_scale"])
+        launches += per_step
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
+    # each kernel's mean device time over the timed steps, from the events the library
+    # recorded around its launches on this stream (read once, after the timed region)
+    kms = [P.bsmm_plan_kernel_ms(plan)]
     ms = e0.elapsed_time(e1) / args.steps
     ms_max, F_all = aggregate(ms, F, dev)
     value = F_all / (ms_max * 1e-3) / 1e12
@@ -733,11 +737,15 @@ def run_dense(args, rank, world, local):
         c64 = C64.cpu().numpy()
         d = Csplit - c64
         err = float(np.linalg.norm(d) / np.linalg.norm(c64))
-        fp64_peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        extra["fp64_path"] = {"value": F / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
-                              "roofline": {"bound": "alu", "peak": fp64_peak, "unit": "TFLOP/s",
-                                           "frac": F / (ms64 * 1e-3) / 1e12 / fp64_peak,
-                                           "peak_def": "152 SMs x 2 DFMA/clk x 2 flop x max SM clock"}}
+        rates = P.bsmm_measure_rates()  # this GPU's FP64 rates, measured now (DFMA; FP64 mma.sync)
+        v64 = F / (ms64 * 1e-3) / 1e12
+        extra["fp64_path"] = {"value": v64, "unit": "TFLOP/s", "ms_per_step": ms64,
+                              "roofline": {"bound": "alu", "peak": rates["dfma"], "unit": "TFLOP/s",
+                                           "frac": v64 / rates["dfma"], "dmma_tflops": rates["dmma"],
+                                           "frac_of_dmma": v64 / rates["dmma"],
+                                           "int8_mma_sync_tops": rates["imma"],
+                                           "peak_def": "measured in this run (bsmm_measure_rates): DFMA chains on "
+                                                       "every SM; dmma = FP64 mma.sync m8n8k4 on every SM"}}
         extra["split_rel_err_vs_fp64"] = err
         extra["split_speedup_vs_fp64"] = ms64 / ms_max
         # the other slice counts on the same inputs: throughput and error against the FP64 result
@@ -777,6 +785,7 @@ def run_dense(args, rank, world, local):
                                     profile=1, **sc)
                 for _ in range(2):
                     P.bsmm_execute_f32(plan2, 1.0, A32, ao32, B32, bo32, 0.0, C32, co)
+                P.bsmm_plan_kernel_ms(plan2)  # kernel means over the timed executes only
                 g0 = torch.cuda.Event(enable_timing=True)
                 g1 = torch.cuda.Event(enable_timing=True)
                 g0.record(stream)

@@ -150,7 +150,21 @@ typedef struct {
                               equivalent real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]], so
                               an inner block may hold half the real depth (256 for 6 slices)
                               and the useful flop count is 8 r c q per nonzero triple. */
+  const char* model_path;  /* NULL or "" = no model. Otherwise the path of a cost-model file
+                              written by bsmm_mlp_save: bsmm_plan loads it, predicts every work
+                              unit's time with it on the GPU and packs the units by those
+                              costs (schedule BSMM_SCHED_COSTS). A file that is missing,
+                              unreadable, corrupt (checksum), or of another format or feature
+                              version leaves the flop-count costs in place (the fallback);
+                              bsmm_plan_cost_source tells which was used. The string is read
+                              during bsmm_plan only. Results never depend on the schedule. */
 } bsmm_options;
+
+typedef enum {
+  BSMM_COSTS_FLOPS = 0,  /* useful flop counts (the default, and the model file's fallback) */
+  BSMM_COSTS_MODEL = 1,  /* predicted by the cost-model file of bsmm_options.model_path */
+  BSMM_COSTS_GIVEN = 2   /* set by bsmm_plan_set_costs or bsmm_plan_predict_costs */
+} bsmm_cost_source;
 
 /* Fill *opt with the defaults above. */
 void bsmm_options_default(bsmm_options* opt);
@@ -298,6 +312,24 @@ bsmm_status bsmm_batch_status_device(bsmm_batch_t batch, void* stream);
 void bsmm_batch_destroy(bsmm_batch_t batch);
 
 /*
+ * The whole batch in one call (the same work as bsmm_batch_create, bsmm_batch_set_args
+ * and bsmm_batch_execute): `count` plans (same rules as bsmm_batch_create) with their
+ * per-product arguments as in bsmm_batch_set_args, launched on `stream`. The library
+ * keeps the batch objects of its last 4 plan lists (keyed by the plans, never by
+ * addresses that a later plan could reuse) with the arguments last uploaded to each:
+ * the first call for a plan list creates the batch (allocation, synchronous uploads),
+ * a call with new arguments uploads them after synchronising `stream` (the previous
+ * launch's argument table is then no longer read), and a call with the plans and
+ * arguments of the previous one only enqueues kernels, so such calls can be captured
+ * into a CUDA graph once one call has set the batch up. Calls that overlap on
+ * different streams with the same plan list race. The plans must outlive the calls;
+ * a destroyed plan's entry is released when it becomes the least recently used.
+ */
+bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const double* alpha, const double* const* A,
+                               const int64_t* const* a_off, const double* const* B, const int64_t* const* b_off,
+                               const double* beta, double* const* C, const int64_t* const* c_off, void* stream);
+
+/*
  * Autotuning of a batch's launch shape. The paper has no counterpart (its tile kernel
  * is a library DGEMM); these pick, by measurement, the knobs that set the contraction's
  * work-unit shape and pipeline depth.
@@ -394,6 +426,22 @@ bsmm_status bsmm_mlp_fit(bsmm_mlp_t mlp, const float* X, const float* t, int64_t
                          float* final_loss, void* stream);
 bsmm_status bsmm_mlp_predict(bsmm_mlp_t mlp, const float* X, int64_t n, float* y, void* stream);
 bsmm_status bsmm_plan_predict_costs(bsmm_plan_t plan, bsmm_mlp_t mlp, void* stream);
+/*
+ * Cost-model files (the learned schedule's checkpoint). bsmm_mlp_save writes the
+ * parameters and the standardisation of `mlp` to `path` (created or replaced); the
+ * file is binary, little-endian: the 8 bytes "BSMMMLP\0", uint32 format version (1),
+ * uint32 feature version (BSMM_FEATURE_VERSION: the order and meaning of the
+ * bsmm_plan_features columns), uint32 F, uint32 hidden width, uint32 parameter count,
+ * the float32 parameters, x means[F], x deviations[F], y mean, y deviation, then a
+ * uint64 FNV-1a checksum of every byte before it. bsmm_mlp_load creates a model from
+ * such a file (BSMM_ERR_INVALID for a missing or unreadable file, a bad checksum, or
+ * another format, feature version or shape). Adam state is not saved.
+ */
+#define BSMM_FEATURE_VERSION 1
+bsmm_status bsmm_mlp_save(bsmm_mlp_t mlp, const char* path);
+bsmm_status bsmm_mlp_load(bsmm_mlp_t* out, const char* path);
+/* Where the plan's current unit costs came from (bsmm_cost_source). */
+bsmm_status bsmm_plan_cost_source(bsmm_plan_t plan, int32_t* source);
 void bsmm_mlp_destroy(bsmm_mlp_t mlp);
 
 /*
@@ -423,13 +471,30 @@ bsmm_status bsmm_selftest_wait(int64_t limit_ns, void* stream);
 bsmm_status bsmm_plan_timings(bsmm_plan_t plan, int64_t* start_ns, int64_t* end_ns, int32_t* cta);
 
 /*
- * Device time of each internal kernel of the last execute of a plan built with
- * profile = 1, measured with CUDA events recorded on the execute's stream around
- * every launch. ms[max_n] host output (kernel order: split modes = exponents,
- * slicing, contraction; FP64 = contraction); *count = kernels recorded.
- * Synchronises on the last event.
+ * Device time of each internal kernel of a plan built with profile = 1, measured with
+ * CUDA events recorded on the execute's stream around every launch: the mean over the
+ * executes since the previous call of this function (the plan keeps the events of its
+ * last 64 executes; with no execute since the previous call, the last execute's times
+ * again). So a caller can run many executes without any synchronisation and read their
+ * mean once afterwards. ms[max_n] host output (kernel order: split modes = exponents,
+ * slicing, contraction[, split-k reduction]; FP64 = contraction[, reduction]);
+ * *count = kernels per execute. Synchronises on the last event. BSMM_ERR_INVALID when
+ * the averaged executes launched different kernel counts.
  */
 bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t plan, float* ms, int32_t max_n, int32_t* count);
+
+/*
+ * Diagnostics: arithmetic rates of the current GPU, measured. The FP64 ones are the
+ * denominators of the FP64 path's roofline (the paper's tile kernel is an FP64 DGEMM,
+ * Sec. 4.1); the INT8 one is the rate an integer variant of the split method could use.
+ * Runs three kernels on every SM, three times each, on `stream` (the fastest pass
+ * counts) and synchronises it. rates[3] host output: rates[0] = FP64 fused multiply-adds on the FP64
+ * units, TFLOP/s (16 independent chains per thread); rates[1] = the FP64 tensor-core
+ * instruction mma.sync m8n8k4, TFLOP/s; rates[2] = the INT8 tensor-core instruction
+ * mma.sync m16n8k32 (s8 x s8 -> s32), TOP/s (sm_103a has no INT8 kind of tcgen05.mma).
+ * Allocates and frees a small scratch buffer.
+ */
+bsmm_status bsmm_measure_rates(double* rates, void* stream);
 
 /*
  * One dense tile task without any allocation (the paper has no counterpart: it is
@@ -440,18 +505,23 @@ bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t plan, float* ms, int32_t max_n, int3
  * Computes C = alpha * A*B + beta * C for one m x k tile A, k x n tile B and m x n
  * tile C (row-major, contiguous, device pointers, 16-byte aligned) with the 6-or-
  * fewer-slice split-bfloat16 method of bsmm_execute: the same bits as a plan of the
- * 1 x 1 x 1 tiling (m), (n), (k) in BSMM_SPLIT_BF16 mode. beta == 0 does not read C.
- * Limits: m, n <= 256, k <= 512, nslices in 1..6; larger sizes return
- * BSMM_ERR_INVALID before anything runs.
+ * 1 x 1 x 1 tiling (m), (n), (k) in BSMM_SPLIT_BF16 mode. beta == 0 does not read C;
+ * k == 0 gives C = beta * C (A and B may then be NULL).
+ * Limits: 0 <= m, n <= 256, 0 <= k <= 512, nslices in 1..6; anything else returns
+ * BSMM_ERR_INVALID before anything runs (every k up to 512 is within the exact
+ * accumulation depth of every slice count, so no depth is refused beyond that).
  *
  * Scratch: a file-scope device array of about 3.2 MB inside the library, held by
  * every GPU that loads the library until the process exits; no cudaMalloc,
- * cudaFree or other allocating call is made. The first call on a device (with
- * that device current) looks up the array's address and should come before any
- * stream capture. All calls share the array and leave their contents in it, so
- * calls that overlap on the GPU (several streams or host threads) race: the
- * caller must serialise them. Asynchronous on `stream`; no device error word is
- * reported for this entry point.
+ * cudaFree or other allocating call is made. Each call looks up the array's address
+ * on the current device (cudaGetSymbolAddress); the first call on a device loads the
+ * library's code there and should come before any stream capture. All calls share
+ * the array and leave their contents in it, so calls that overlap on the GPU
+ * (several streams or host threads) race: the caller must serialise them.
+ * The call enqueues its kernels on `stream`, reads the device error word back from
+ * the array on that stream and returns once the product is complete:
+ * BSMM_ERR_DEVICE for a non-finite input element, BSMM_ERR_TIMEOUT when a kernel
+ * wait ran out (C is then incomplete), BSMM_ERR_CUDA for a failed CUDA call.
  */
 bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, int32_t nslices, double alpha,
                                     const double* A, const double* B, double beta, double* C, void* stream);

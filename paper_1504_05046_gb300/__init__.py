@@ -25,6 +25,7 @@ __all__ = [
     "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
     "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
     "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_selftest_wait", "bsmm_last_error",
+    "bsmm_measure_rates",
     "bsmm_destroy", "EXPORTED",
 ]
 
@@ -45,7 +46,8 @@ EXPORTED = [
     "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
     "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_selftest_wait", "bsmm_schedule_lpt",
-    "bsmm_schedule_pieces", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_schedule_pieces", "bsmm_measure_rates", "bsmm_mlp_save", "bsmm_mlp_load", "bsmm_plan_cost_source",
+    "bsmm_execute_batch", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -61,7 +63,7 @@ class Options(ctypes.Structure):
                 ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("transa", ctypes.c_int32),
                 ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32), ("ksplit", ctypes.c_int32),
-                ("elem", ctypes.c_int32)]
+                ("elem", ctypes.c_int32), ("model_path", ctypes.c_char_p)]
 
 
 _lib = None
@@ -93,6 +95,7 @@ def lib():
         L.bsmm_plan_timings.argtypes = [P, P, P, P]
         L.bsmm_plan_kernel_ms.argtypes = [P, P, i32, P]
         L.bsmm_split_tile_noalloc.argtypes = [i32, i32, i32, i32, f64, P, P, f64, P, P]
+        L.bsmm_measure_rates.argtypes = [P, P]
         L.bsmm_batch_create.argtypes = [ctypes.POINTER(P), i32, P]
         L.bsmm_batch_set_args.argtypes = [P, P, P, P, P, P, P, P, P]
         L.bsmm_batch_execute.argtypes = [P, P]
@@ -117,6 +120,10 @@ def lib():
         L.bsmm_mlp_fit.argtypes = [P, P, P, i64, i32, ctypes.c_float, P, P]
         L.bsmm_mlp_predict.argtypes = [P, P, i64, P, P]
         L.bsmm_plan_predict_costs.argtypes = [P, P, P]
+        L.bsmm_mlp_save.argtypes = [P, ctypes.c_char_p]
+        L.bsmm_execute_batch.argtypes = [i32, P, P, P, P, P, P, P, P, P, P]
+        L.bsmm_mlp_load.argtypes = [ctypes.POINTER(P), ctypes.c_char_p]
+        L.bsmm_plan_cost_source.argtypes = [P, P]
         L.bsmm_mlp_destroy.argtypes = [P]
         L.bsmm_mlp_destroy.restype = None
         L.bsmm_last_error.argtypes = []
@@ -195,7 +202,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
               record_timings: int = 0, profile: int = 0, cluster: int = 0, fp64_tile: int = 0,
               stages: int = 0, transa: int = 0, transb: int = 0, split_scale: int = 0,
-              ksplit: int = 0, elem: int = BSMM_F64) -> Plan:
+              ksplit: int = 0, elem: int = BSMM_F64, model_path=None) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -212,6 +219,8 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     o.split_scale = split_scale
     o.ksplit = ksplit
     o.elem = elem
+    path = None if model_path is None else os.fsencode(model_path)
+    o.model_path = path  # read by bsmm_plan only; `path` keeps the bytes alive until it returns
     h = ctypes.c_void_p()
     _check(lib().bsmm_plan(ctypes.byref(h), len(r), _ptr(r), len(c), _ptr(c), len(q), _ptr(q), _ptr(am),
                            _ptr(bm), _ptr(cm), ctypes.byref(o)))
@@ -298,12 +307,34 @@ def bsmm_plan_kernel_ms(plan: Plan):
     return [float(ms[i]) for i in range(n.value)]
 
 
+def bsmm_measure_rates(stream=None):
+    """Measured rates of the current GPU: {"dfma": TFLOP/s of FP64 fused multiply-adds,
+    "dmma": TFLOP/s of the FP64 tensor-core mma.sync, "imma": TOP/s of the INT8 one}."""
+    r = (ctypes.c_double * 3)()
+    _check(lib().bsmm_measure_rates(r, _stream(stream)))
+    return {"dfma": r[0], "dmma": r[1], "imma": r[2]}
+
+
 def bsmm_split_tile_noalloc(m, n, k, nslices, alpha, A, B, beta, C, stream=None):
     """One dense split-precision tile task with no device allocation (device tensors:
     A m x k, B k x n, C m x n, row-major float64). For callers that cannot allocate
-    device memory at the point of the call; see include/bsmm.h for the limits and the
-    shared-scratch rules (calls overlapping on the GPU race)."""
-    _check(lib().bsmm_split_tile_noalloc(int(m), int(n), int(k), int(nslices), float(alpha), _ptr(A), _ptr(B),
+    device memory at the point of the call (an allocator that is locked or forbids
+    allocation on their hot path, or device memory reserved up front); see
+    include/bsmm.h for the limits and the shared-scratch rules (calls overlapping on
+    the GPU race). Returns once the product is complete; raises BsmmError with the
+    library's status otherwise."""
+    m, n, k = int(m), int(n), int(k)
+    for name, t, need in (("A", A, m * k), ("B", B, k * n), ("C", C, m * n)):
+        if need == 0 and t is None:
+            continue
+        if t is None or str(getattr(t, "dtype", "")) != "torch.float64" or not getattr(t, "is_cuda", False) \
+                or not t.is_contiguous():
+            raise BsmmError(1, f"bsmm_split_tile_noalloc: {name} must be a contiguous float64 "
+                                              f"CUDA tensor")
+        if t.numel() < need:
+            raise BsmmError(1, f"bsmm_split_tile_noalloc: {name} holds {t.numel()} elements, "
+                                              f"needs {need}")
+    _check(lib().bsmm_split_tile_noalloc(m, n, k, int(nslices), float(alpha), _ptr(A), _ptr(B),
                                          float(beta), _ptr(C), _stream(stream)))
 
 
@@ -319,6 +350,18 @@ class Batch:
             bsmm_batch_destroy(self)
         except Exception:
             pass
+
+
+def bsmm_execute_batch(plans, alphas, As, a_offs, Bs, b_offs, betas, Cs, c_offs, stream=None):
+    """The whole batch in one library call (device tensors per product; see
+    include/bsmm.h: the library caches the batch object of the plan list)."""
+    n = len(plans)
+    keep = list(plans)  # the plans stay referenced for the duration of the call
+    ptrs = lambda xs: (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    _check(lib().bsmm_execute_batch(n, (ctypes.c_void_p * n)(*[p.handle for p in keep]),
+                                    (ctypes.c_double * n)(*[float(a) for a in alphas]), ptrs(As), ptrs(a_offs),
+                                    ptrs(Bs), ptrs(b_offs), (ctypes.c_double * n)(*[float(b) for b in betas]),
+                                    ptrs(Cs), ptrs(c_offs), _stream(stream)))
 
 
 def bsmm_batch_create(plans) -> Batch:
@@ -492,6 +535,28 @@ def bsmm_mlp_fit(mlp: Mlp, X, t, steps: int, lr: float, stream=None) -> float:
 
 def bsmm_mlp_predict(mlp: Mlp, X, y, stream=None):
     _check(lib().bsmm_mlp_predict(mlp.handle, _ptr(X), int(y.numel()), _ptr(y), _stream(stream)))
+
+
+def bsmm_mlp_save(mlp: Mlp, path) -> None:
+    """Write the model to a versioned, checksummed cost-model file (see include/bsmm.h)."""
+    _check(lib().bsmm_mlp_save(mlp.handle, os.fsencode(path)))
+
+
+def bsmm_mlp_load(path) -> Mlp:
+    """A model read from a cost-model file written by bsmm_mlp_save."""
+    h = ctypes.c_void_p()
+    _check(lib().bsmm_mlp_load(ctypes.byref(h), os.fsencode(path)))
+    return Mlp(h.value)
+
+
+BSMM_COSTS_FLOPS, BSMM_COSTS_MODEL, BSMM_COSTS_GIVEN = 0, 1, 2
+
+
+def bsmm_plan_cost_source(plan: Plan) -> int:
+    """Where the plan's unit costs came from: BSMM_COSTS_FLOPS, _MODEL or _GIVEN."""
+    v = ctypes.c_int32()
+    _check(lib().bsmm_plan_cost_source(plan.handle, ctypes.byref(v)))
+    return v.value
 
 
 def bsmm_plan_predict_costs(plan: Plan, mlp: Mlp, stream=None):

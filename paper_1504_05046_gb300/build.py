@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -58,6 +59,30 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if verbose:
         print(LIB)
     return LIB
+
+
+_KIND_PROBE = r"""
+#include <cstdint>
+__global__ void probe(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::KIND [%0], %1, %2, %3, p;\n\t}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+"""
+
+
+def tcgen05_kind_supported(kind: str):
+    """Whether the toolchain accepts one tcgen05.mma of the given kind (f16, tf32, f8f6f4,
+    i8, ...) for sm_103a: compiles a one-instruction kernel. Returns (accepted, message)."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "probe.cu")
+        with open(src, "w") as f:
+            f.write(_KIND_PROBE.replace("KIND", kind))
+        r = subprocess.run([nvcc(), *ARCH, "-c", src, "-o", os.path.join(d, "probe.o")], capture_output=True,
+                           text=True)
+        msg = " ".join(m.group(1) for m in re.finditer(r"error\s*:\s*(.*)", r.stderr))
+        return r.returncode == 0, msg
 
 
 if __name__ == "__main__":

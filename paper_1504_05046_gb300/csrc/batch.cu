@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
 
 #include "bsmm_internal.h"
 
@@ -321,6 +322,87 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
   if (e != cudaSuccess) return set_error(std::string("batch launch: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   b->launches = n;
   return BSMM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// bsmm_execute_batch keeps the batch objects of its last few plan lists: keyed by the
+// plans' unique ids (a destroyed plan's id never comes back, so a stale entry never
+// matches), with the arguments last uploaded to each.
+struct OneCall {
+  std::vector<uint64_t> uids;
+  bsmm_batch_t batch = nullptr;
+  std::vector<double> alpha, beta;
+  std::vector<const void*> ptrs;  // A, a_off, B, b_off, C, c_off of every product
+  uint64_t used = 0;
+};
+constexpr size_t kOneCallEntries = 4;
+std::mutex g_one_mu;
+std::vector<OneCall>* g_one = new std::vector<OneCall>();  // never destroyed: no CUDA call at exit
+uint64_t g_one_clock = 0;
+
+}  // namespace
+
+extern "C" {
+
+bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const double* alpha, const double* const* A,
+                               const int64_t* const* a_off, const double* const* B, const int64_t* const* b_off,
+                               const double* beta, double* const* C, const int64_t* const* c_off, void* stream) {
+  if (count <= 0 || !plans || !alpha || !beta || !A || !a_off || !B || !b_off || !C || !c_off)
+    return set_error("bsmm_execute_batch: NULL argument or count <= 0"), BSMM_ERR_INVALID;
+  std::vector<uint64_t> uids(count);
+  for (int32_t i = 0; i < count; i++) {
+    if (!plans[i]) return set_error("bsmm_execute_batch: NULL plan"), BSMM_ERR_INVALID;
+    uids[i] = plans[i]->uid;
+  }
+  std::lock_guard<std::mutex> lk(g_one_mu);
+  std::vector<OneCall>& cache = *g_one;
+  OneCall* hit = nullptr;
+  for (OneCall& e : cache)
+    if (e.uids == uids) hit = &e;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!hit) {
+    bsmm_batch_t b = nullptr;
+    const bsmm_status s = bsmm_batch_create(&b, count, plans);
+    if (s != BSMM_OK) return s;
+    if (cache.size() >= kOneCallEntries) {  // the least recently used entry makes room
+      auto lru = std::min_element(cache.begin(), cache.end(),
+                                  [](const OneCall& x, const OneCall& y) { return x.used < y.used; });
+      if (cudaStreamSynchronize(st) != cudaSuccess) {
+        bsmm_batch_destroy(b);
+        return set_error("bsmm_execute_batch: stream synchronisation failed"), BSMM_ERR_CUDA;
+      }
+      bsmm_batch_destroy(lru->batch);
+      cache.erase(lru);
+    }
+    cache.push_back(OneCall{uids, b, {}, {}, {}, 0});
+    hit = &cache.back();
+  }
+  hit->used = ++g_one_clock;
+  std::vector<double> al(alpha, alpha + count), be(beta, beta + count);
+  std::vector<const void*> ptrs;
+  ptrs.reserve(6 * (size_t)count);
+  for (int32_t i = 0; i < count; i++)
+    for (const void* x : {(const void*)A[i], (const void*)a_off[i], (const void*)B[i], (const void*)b_off[i],
+                          (const void*)C[i], (const void*)c_off[i]})
+      ptrs.push_back(x);
+  if (al != hit->alpha || be != hit->beta || ptrs != hit->ptrs) {
+    // new arguments: the table the previous launch of this batch reads is replaced only
+    // after that launch (on this stream) has finished
+    if (!hit->ptrs.empty() && cudaStreamSynchronize(st) != cudaSuccess)
+      return set_error("bsmm_execute_batch: stream synchronisation failed"), BSMM_ERR_CUDA;
+    const bsmm_status s = bsmm_batch_set_args(hit->batch, alpha, A, a_off, B, b_off, beta, C, c_off);
+    if (s != BSMM_OK) {
+      hit->ptrs.clear();
+      return s;
+    }
+    hit->alpha = al;
+    hit->beta = be;
+    hit->ptrs = ptrs;
+  }
+  return bsmm_batch_execute(hit->batch, stream);
 }
 
 bsmm_status bsmm_batch_kernels(bsmm_batch_t b, int32_t* kernels) {

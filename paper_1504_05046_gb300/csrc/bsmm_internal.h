@@ -42,7 +42,7 @@ constexpr int16_t kNonUniform = 0x7FFF;         // scale-class sentinel (offsets
 constexpr int32_t kZeroLine = -(1 << 20);       // exponent of an all-zero row or column
 int split_max_depth(int s);
 constexpr int kSplitDefaultCluster = 2;
-// Largest number of clusters of `cl` contraction CTAs that can be resident at once.
+// Largest number of groups of `cl` contraction CTAs that can be resident at once.
 int split_max_clusters(int s, int cl, int stages);
 
 // Device arrays owned by a plan.
@@ -212,6 +212,7 @@ struct SplitArgs {
 // ev: null, or kMaxEvents events; ev[0] is recorded before the first kernel and
 // ev[i+1] after kernel i. *nk receives the number of kernels launched.
 constexpr int kMaxEvents = 8;
+constexpr int kProfileRing = 64;  // executes whose per-kernel times a plan keeps
 cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk);
 cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk);
 // the two halves of launch_split: per-product exponents, scales and slices; the
@@ -244,6 +245,9 @@ int machine_bins(const bsmm_plan_s* p);
 std::vector<int32_t> choose_pieces(const std::vector<double>& cost, const std::vector<int64_t>& len, int bins,
                                    double overhead, int ksplit);
 int fp64_ctas_per_sm(int tile);
+// measured rates of this GPU: rates[0] DFMA, rates[1] FP64 mma.sync (TFLOP/s), rates[2]
+// INT8 mma.sync (TOP/s); synchronises `st`
+cudaError_t unit_rates(double* rates, cudaStream_t st);
 
 void set_error(const std::string& msg);
 
@@ -298,12 +302,18 @@ struct bsmm_plan_s {
   bsmm::DevBuf d_err, d_timings, d_unit_cta, d_part, d_red;
   int32_t n_a_tiles = 0, n_b_tiles = 0, n_a_blocks = 0, n_b_blocks = 0;
 
-  // per-kernel profiling events (profile option)
-  cudaEvent_t ev[bsmm::kMaxEvents] = {};
-  int ev_count = 0;
+  // per-kernel profiling events (profile option): a ring of event sets, one set per
+  // execute; bsmm_plan_kernel_ms averages the sets recorded since its previous call
+  cudaEvent_t ev[bsmm::kProfileRing][bsmm::kMaxEvents] = {};
+  int ev_counts[bsmm::kProfileRing] = {};
+  int ev_next = 0;     // the set the next execute records into
+  int ev_pending = 0;  // sets recorded since the last bsmm_plan_kernel_ms (at most the ring)
+  int ev_last = -1;    // the set of the last execute
 
   // a plan whose slice workspace (d_apk, d_bpk) this one shares, or null
   const bsmm_plan_s* donor = nullptr;
+  int32_t cost_source = BSMM_COSTS_FLOPS;  // where `cost` came from (bsmm_cost_source)
+  uint64_t uid = 0;  // unique over the process's plans (never reused, unlike an address)
 
   // host-buffer execute staging (grown on demand)
   bsmm::DevBuf h_A, h_B, h_C, h_aoff, h_boff, h_coff;

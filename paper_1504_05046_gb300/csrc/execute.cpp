@@ -152,20 +152,30 @@ bsmm_status run(bsmm_plan_s* p, double alpha, const void* A, const int64_t* a_of
   if (p->n_units == 0) return BSMM_OK;
   cudaError_t e;
   cudaEvent_t* ev = nullptr;
+  int set = -1;
   if (p->opt.profile) {
-    if (!p->ev[0])
-      for (int i = 0; i < kMaxEvents; i++)
-        if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return set_error("cudaEventCreate failed"), BSMM_ERR_CUDA;
-    ev = p->ev;
+    if (!p->ev[0][0])
+      for (int r = 0; r < kProfileRing; r++)
+        for (int i = 0; i < kMaxEvents; i++)
+          if (cudaEventCreate(&p->ev[r][i]) != cudaSuccess) return set_error("cudaEventCreate failed"), BSMM_ERR_CUDA;
+    set = p->ev_next;
+    ev = p->ev[set];
   }
+  int nk = 0;
   if (p->opt.mode == BSMM_FP64) {
     Fp64Args a{};
     fill_fp64_args(p, a, alpha, (const double*)A, a_off, (const double*)B, b_off, beta, (double*)C, c_off);
-    e = launch_fp64(a, p->ctas, st, ev, &p->ev_count);
+    e = launch_fp64(a, p->ctas, st, ev, &nk);
   } else {
     SplitArgs a{};
     fill_split_args(p, a, alpha, A, a_off, B, b_off, beta, C, c_off);
-    e = launch_split(a, p->ctas, st, ev, &p->ev_count);
+    e = launch_split(a, p->ctas, st, ev, &nk);
+  }
+  if (set >= 0) {
+    p->ev_counts[set] = nk;
+    p->ev_last = set;
+    p->ev_next = (set + 1) % kProfileRing;
+    p->ev_pending = std::min(p->ev_pending + 1, kProfileRing);
   }
   if (e != cudaSuccess) {
     set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -264,6 +274,13 @@ bsmm_status bsmm_status_device(bsmm_plan_t p, void* stream) {
   return BSMM_OK;
 }
 
+bsmm_status bsmm_measure_rates(double* rates, void* stream) {
+  if (!rates) return set_error("rates is NULL"), BSMM_ERR_INVALID;
+  const cudaError_t e = unit_rates(rates, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(std::string("rates: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  return BSMM_OK;
+}
+
 bsmm_status bsmm_selftest_wait(int64_t limit_ns, void* stream) {
   if (limit_ns < 1000000 || limit_ns > 1000000000) return set_error("limit_ns must be in 1e6..1e9"), BSMM_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
@@ -282,13 +299,30 @@ bsmm_status bsmm_selftest_wait(int64_t limit_ns, void* stream) {
 
 bsmm_status bsmm_plan_kernel_ms(bsmm_plan_t p, float* ms, int32_t max_n, int32_t* count) {
   if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
-  if (!p->opt.profile || !p->ev[0]) return set_error("plan has no profile events (profile option, one execute)"), BSMM_ERR_INVALID;
-  const int n = std::min<int>(p->ev_count, max_n);
-  if (cudaEventSynchronize(p->ev[p->ev_count]) != cudaSuccess) return set_error("event sync failed"), BSMM_ERR_CUDA;
-  for (int i = 0; i < n; i++)
-    if (cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]) != cudaSuccess)
-      return set_error("cudaEventElapsedTime failed"), BSMM_ERR_CUDA;
-  if (count) *count = p->ev_count;
+  if (!p->opt.profile || p->ev_last < 0)
+    return set_error("plan has no profile events (profile option, one execute)"), BSMM_ERR_INVALID;
+  if (max_n < 0 || (max_n > 0 && !ms)) return set_error("ms is NULL"), BSMM_ERR_INVALID;
+  // the executes since the previous call (or, when there was none, the last one again)
+  const int sets = std::max(1, p->ev_pending);
+  const int nk = p->ev_counts[p->ev_last];
+  const int n = std::min<int>(nk, max_n);
+  const int last = p->ev_last;
+  if (cudaEventSynchronize(p->ev[last][p->ev_counts[last]]) != cudaSuccess)
+    return set_error("event sync failed"), BSMM_ERR_CUDA;
+  std::vector<double> sum(n, 0.0);
+  for (int b = 0; b < sets; b++) {
+    const int set = (last - b + kProfileRing) % kProfileRing;
+    if (p->ev_counts[set] != nk) return set_error("executes with different kernel counts"), BSMM_ERR_INVALID;
+    for (int i = 0; i < n; i++) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, p->ev[set][i], p->ev[set][i + 1]) != cudaSuccess)
+        return set_error("cudaEventElapsedTime failed"), BSMM_ERR_CUDA;
+      sum[i] += t;
+    }
+  }
+  for (int i = 0; i < n; i++) ms[i] = (float)(sum[i] / sets);
+  p->ev_pending = 0;
+  if (count) *count = nk;
   return BSMM_OK;
 }
 

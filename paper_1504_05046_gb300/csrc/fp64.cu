@@ -313,7 +313,123 @@ __global__ void __launch_bounds__(256) fp64_reduce_kernel(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------- rate diagnostics
+// Arithmetic paths of the SM, each kept busy on every SM: DFMA (16 independent fused
+// multiply-add chains per thread, so issue and not latency sets the rate), the FP64
+// tensor-core instruction mma.sync m8n8k4 (4 independent accumulators per warp; 512 flops
+// per instruction) and the INT8 one, mma.sync m16n8k32 s8 x s8 -> s32 (4 accumulators per
+// warp; 8192 operations per instruction; sm_103a has no INT8 kind of tcgen05.mma, so this
+// is the only INT8 tensor path). Every thread stores its accumulators' sum, so nothing is
+// eliminated.
+constexpr int kRateThreads = 256;
+constexpr int kRateBlocksPerSm = 8;
+
+__global__ void __launch_bounds__(kRateThreads) fp64_dfma_rate_kernel(double* out, int iters) {
+  const double b = 1.0 + 0x1p-40, c = 0x1p-60;
+  double x[16];
+#pragma unroll
+  for (int u = 0; u < 16; u++) x[u] = (threadIdx.x + u) * 0x1p-20;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int u = 0; u < 16; u++) x[u] = fma(x[u], b, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int u = 0; u < 16; u++) sum += x[u];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(kRateThreads) fp64_dmma_rate_kernel(double* out, int iters) {
+  const double a = 1.0 + threadIdx.x * 0x1p-30, b = 1.0 - 0x1p-40;
+  double d[4][2];
+#pragma unroll
+  for (int u = 0; u < 4; u++) d[u][0] = d[u][1] = u * 0x1p-50;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(d[u][0]), "+d"(d[u][1])
+                   : "d"(a), "d"(b));
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; u++) sum += d[u][0] + d[u][1];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(kRateThreads) imma_rate_kernel(double* out, int iters) {
+  const uint32_t a = 0x01020304u + threadIdx.x, b = 0x05060708u;
+  int32_t d[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) d[u][v] = u + v;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      asm volatile(
+          "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%0,%1,%2,%3};"
+          : "+r"(d[u][0]), "+r"(d[u][1]), "+r"(d[u][2]), "+r"(d[u][3])
+          : "r"(a), "r"(a), "r"(a), "r"(a), "r"(b), "r"(b));
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) sum += d[u][v];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 }  // namespace
+
+cudaError_t unit_rates(double* rates, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int blocks = sms * kRateBlocksPerSm;
+  double* out = nullptr;
+  e = cudaMalloc(&out, sizeof(double) * (size_t)blocks * kRateThreads);
+  if (e != cudaSuccess) return e;
+  constexpr int kReps = 3;  // timed passes of each kernel; the fastest counts
+  cudaEvent_t ev[3 * kReps + 1] = {};
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  const int it_fma = 8192, it_mma = 2048, it_imma = 8192;
+  if (e == cudaSuccess) {
+    // one untimed pass of each (clocks up, code loaded), then the timed passes
+    fp64_dfma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(out, it_fma / 4);
+    fp64_dmma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(out, it_mma / 4);
+    imma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(out, it_imma / 4);
+    cudaEventRecord(ev[0], st);
+    for (int r = 0; r < kReps; r++) {
+      fp64_dfma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(out, it_fma);
+      cudaEventRecord(ev[3 * r + 1], st);
+      fp64_dmma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(out, it_mma);
+      cudaEventRecord(ev[3 * r + 2], st);
+      imma_rate_kernel<<<blocks, kRateThreads, 0, st>>>(out, it_imma);
+      cudaEventRecord(ev[3 * r + 3], st);
+    }
+    e = cudaGetLastError();
+  }
+  float best[3] = {0.0f, 0.0f, 0.0f};
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[3 * kReps]);
+  for (int i = 0; i < 3 * kReps && e == cudaSuccess; i++) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+    if (best[i % 3] == 0.0f || t < best[i % 3]) best[i % 3] = t;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  cudaFree(out);
+  if (e != cudaSuccess) return e;
+  const double threads = (double)blocks * kRateThreads, warps = threads / 32.0;
+  rates[0] = threads * 16.0 * it_fma * 2.0 / (best[0] * 1e-3) / 1e12;
+  rates[1] = warps * 4.0 * it_mma * 512.0 / (best[1] * 1e-3) / 1e12;
+  rates[2] = warps * 4.0 * it_imma * 8192.0 / (best[2] * 1e-3) / 1e12;
+  return cudaSuccess;
+}
 
 int fp64_ctas_per_sm(int tile) {
   int n = 0;

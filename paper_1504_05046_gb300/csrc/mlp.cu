@@ -16,6 +16,7 @@
 // a fixed order (per-block partial sums, then a sum over blocks in block order), so
 // training is bit-for-bit reproducible.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -404,6 +405,113 @@ bsmm_status bsmm_plan_predict_costs(bsmm_plan_t plan, bsmm_mlp_t mlp, void* stre
   std::vector<double> cost(n);
   for (int64_t u = 0; u < n; u++) cost[u] = std::exp(std::min(60.0, std::max(-60.0, (double)y[u])));
   return bsmm_plan_set_costs(plan, cost.data());
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr char kMagic[8] = {'B', 'S', 'M', 'M', 'M', 'L', 'P', '\0'};
+constexpr uint32_t kFormatVersion = 1;
+
+// FNV-1a, 64 bits, over a byte string
+uint64_t fnv1a(const std::vector<unsigned char>& b) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : b) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+template <class T>
+void put_raw(std::vector<unsigned char>& b, const T* v, size_t n) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v);
+  b.insert(b.end(), p, p + sizeof(T) * n);
+}
+
+template <class T>
+bool get_raw(const std::vector<unsigned char>& b, size_t& pos, T* v, size_t n) {
+  if (pos + sizeof(T) * n > b.size()) return false;
+  std::memcpy(v, b.data() + pos, sizeof(T) * n);
+  pos += sizeof(T) * n;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+bsmm_status bsmm_mlp_save(bsmm_mlp_t mlp, const char* path) {
+  if (!mlp || !path || !*path) return set_error("NULL model or path"), BSMM_ERR_INVALID;
+  std::vector<float> prm(NP);
+  bsmm_status st = bsmm_mlp_get_params(mlp, prm.data(), NP);
+  if (st != BSMM_OK) return st;
+  std::vector<unsigned char> b;
+  put_raw(b, kMagic, 8);
+  const uint32_t hdr[5] = {kFormatVersion, (uint32_t)BSMM_FEATURE_VERSION, (uint32_t)F, (uint32_t)H, (uint32_t)NP};
+  put_raw(b, hdr, 5);
+  put_raw(b, prm.data(), NP);
+  put_raw(b, mlp->norm.xmu, F);
+  put_raw(b, mlp->norm.xsd, F);
+  put_raw(b, &mlp->norm.ymu, 1);
+  put_raw(b, &mlp->norm.ysd, 1);
+  const uint64_t sum = fnv1a(b);
+  put_raw(b, &sum, 1);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return set_error(std::string("cannot write ") + tmp), BSMM_ERR_INVALID;
+  const bool ok = std::fwrite(b.data(), 1, b.size(), f) == b.size();
+  if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return set_error(std::string("cannot write ") + path), BSMM_ERR_INVALID;
+  }
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_mlp_load(bsmm_mlp_t* out, const char* path) {
+  if (!out || !path || !*path) return set_error("NULL output or path"), BSMM_ERR_INVALID;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(std::string("cannot open ") + path), BSMM_ERR_INVALID;
+  std::vector<unsigned char> b;
+  unsigned char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) {
+    b.insert(b.end(), buf, buf + n);
+    if (b.size() > (1u << 20)) break;  // far larger than any model file
+  }
+  std::fclose(f);
+  if (b.size() < 8 + sizeof(uint64_t) || b.size() > (1u << 20))
+    return set_error(std::string("not a cost-model file: ") + path), BSMM_ERR_INVALID;
+  uint64_t sum = 0;
+  std::memcpy(&sum, b.data() + b.size() - sizeof(uint64_t), sizeof(uint64_t));
+  b.resize(b.size() - sizeof(uint64_t));
+  if (fnv1a(b) != sum) return set_error(std::string("cost-model file checksum mismatch: ") + path), BSMM_ERR_INVALID;
+  size_t pos = 0;
+  char magic[8];
+  uint32_t hdr[5];
+  if (!get_raw(b, pos, magic, 8) || std::memcmp(magic, kMagic, 8) != 0 || !get_raw(b, pos, hdr, 5))
+    return set_error(std::string("not a cost-model file: ") + path), BSMM_ERR_INVALID;
+  if (hdr[0] != kFormatVersion || hdr[1] != (uint32_t)BSMM_FEATURE_VERSION || hdr[2] != (uint32_t)F ||
+      hdr[3] != (uint32_t)H || hdr[4] != (uint32_t)NP)
+    return set_error(std::string("cost-model file of another format, feature version or shape: ") + path),
+           BSMM_ERR_INVALID;
+  std::vector<float> prm(NP);
+  Norm nm{};
+  if (!get_raw(b, pos, prm.data(), NP) || !get_raw(b, pos, nm.xmu, F) || !get_raw(b, pos, nm.xsd, F) ||
+      !get_raw(b, pos, &nm.ymu, 1) || !get_raw(b, pos, &nm.ysd, 1) || pos != b.size())
+    return set_error(std::string("truncated cost-model file: ") + path), BSMM_ERR_INVALID;
+  bsmm_mlp_t m = nullptr;
+  bsmm_status st = bsmm_mlp_create(&m, 0);
+  if (st == BSMM_OK) st = bsmm_mlp_set_params(m, prm.data(), NP);
+  if (st == BSMM_OK) st = bsmm_mlp_set_norm(m, nm.xmu, nm.xsd, nm.ymu, nm.ysd);
+  if (st != BSMM_OK) {
+    bsmm_mlp_destroy(m);
+    return st;
+  }
+  *out = m;
+  return BSMM_OK;
 }
 
 void bsmm_mlp_destroy(bsmm_mlp_t mlp) {

@@ -11,19 +11,25 @@
 // tables and the small task tables. It calls no cudaMalloc, cudaFree or other
 // allocating routine.
 //
-// Limits (checked before any launch): m, n <= 256, 1 <= k <= 512, 1 <= nslices <= 6.
+// Limits (checked before any launch; BSMM_ERR_INVALID otherwise): 0 <= m, n <= 256,
+// 0 <= k <= 512, 1 <= nslices <= 6. k = 512 is within the exact FP32 accumulation depth
+// of every slice count (split_max_depth(s) >= 512 for s <= 6), so no inner depth is
+// refused beyond that. k = 0 gives C = beta*C (alpha times an empty sum).
 // The scratch array is kNoallocScratchBytes (about 3.2 MB); every GPU that loads the
 // library holds it until the process exits.
 //
-// Set-up: the first call on a device, with that device current, looks up the
-// array's device address with cudaGetSymbolAddress and caches it; that first call
-// should come before any stream capture. Every call reuses the same array and
-// leaves the last call's contents in it (each call rewrites every entry it reads),
-// so calls that overlap on the GPU -- on different streams, or from several host
-// threads -- race and must be serialised by the caller.
+// Set-up: every call, with the target device current, looks up the array's device
+// address on that device with cudaGetSymbolAddress (the host-side name of the array is
+// not a device address); the first call on a device loads the library's module there
+// and should come before any stream capture. Every call reuses the same array and
+// leaves the last call's contents in it (the set-up kernel rewrites every entry the
+// product reads and clears the error word), so calls that overlap on the GPU -- on
+// different streams, or from several host threads -- race and must be serialised by
+// the caller. The call reads the error word back from the array on `stream` and
+// returns once the product is complete.
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "bsmm_internal.h"
 
@@ -118,11 +124,6 @@ __global__ void noalloc_setup_kernel(uint8_t* base, int m, int n, int k, int s, 
   }
 }
 
-// device address of the scratch array, per device (looked up on a device's first call)
-constexpr int kNaMaxDevices = 64;
-uint8_t* g_scratch_ptr[kNaMaxDevices] = {};
-std::mutex g_scratch_mu;
-
 }  // namespace
 
 }  // namespace bsmm
@@ -134,38 +135,28 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
                                                void* stream) {
   if (m < 0 || n < 0 || k < 0 || m > kNaMaxM || n > kNaMaxN || k > kNaMaxK || nslices < 1 ||
       nslices > kSplitMaxS)
-    return set_error("bsmm_split_tile_noalloc: sizes must satisfy m, n <= 256, k <= 512 and nslices in 1..6"),
+    return set_error("bsmm_split_tile_noalloc: sizes must satisfy 0 <= m, n <= 256, 0 <= k <= 512 and "
+                     "nslices in 1..6"),
            BSMM_ERR_INVALID;
-  if (k > split_max_depth(nslices))
-    return set_error("bsmm_split_tile_noalloc: k exceeds the exact accumulation depth"), BSMM_ERR_UNSUPPORTED;
   if (m == 0 || n == 0) return BSMM_OK;
   if (!C || (k > 0 && (!A || !B))) return set_error("bsmm_split_tile_noalloc: NULL operand"), BSMM_ERR_INVALID;
   if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15)
     return set_error("bsmm_split_tile_noalloc: operands must be 16-byte aligned"), BSMM_ERR_INVALID;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
-    return set_error("bsmm_split_tile_noalloc: no usable current device"), BSMM_ERR_CUDA;
-  uint8_t* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p)
-        return set_error(std::string("bsmm_split_tile_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e)),
-               BSMM_ERR_CUDA;
-      g_scratch_ptr[dev] = (uint8_t*)p;
-    }
-    base = g_scratch_ptr[dev];
-  }
+  // the array's address on the current device (the host-side symbol is only a handle)
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(std::string("bsmm_split_tile_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e)),
+           BSMM_ERR_CUDA;
+  uint8_t* base = (uint8_t*)p;
   cudaStream_t st = (cudaStream_t)stream;
   const int s = nslices;
   const int RB = (m + kSplitBM - 1) / kSplitBM;
   const int CB = (n + 31) / 32;
   const int nkc = (k + kSplitKC - 1) / kSplitKC;
   noalloc_setup_kernel<<<1, 256, 0, st>>>(base, m, n, k, s, RB, CB, nkc);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(std::string("noalloc setup: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
 
   NaTables* t = reinterpret_cast<NaTables*>(base + NaLayout::tables);
@@ -236,5 +227,15 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
   a.n_red = 0;
   e = launch_split(a, RB * CB, st, nullptr, nullptr);
   if (e != cudaSuccess) return set_error(std::string("noalloc launch: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  // the device error word, read back from the array itself (no buffer of the caller's)
+  int32_t w = 0;
+  e = cudaMemcpyFromSymbolAsync(&w, g_noalloc_scratch, sizeof(int32_t), NaLayout::tables + offsetof(NaTables, err),
+                                cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(std::string("noalloc status: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  if (w & kErrTimeout) return set_error("bsmm_split_tile_noalloc: a kernel wait timed out"), BSMM_ERR_TIMEOUT;
+  if (w & kErrNonFinite)
+    return set_error("bsmm_split_tile_noalloc: non-finite input element"), BSMM_ERR_DEVICE;
+  if (w) return set_error("bsmm_split_tile_noalloc: device error word set"), BSMM_ERR_DEVICE;
   return BSMM_OK;
 }

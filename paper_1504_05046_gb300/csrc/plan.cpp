@@ -10,6 +10,7 @@
 // paper's process grid and task queue on one GPU. Where the grid would idle, a
 // region's k-list is cut into pieces with a reduction task (split k, Sec. 3.2, Fig. 2).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -665,8 +666,9 @@ void bsmm_destroy(bsmm_plan_t p) {
                     &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta, &p->d_part, &p->d_red,
                     &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
   for (DevBuf* b : bufs) dev_free(*b);
-  for (cudaEvent_t& e : p->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto& set : p->ev)
+    for (cudaEvent_t& e : set)
+      if (e) cudaEventDestroy(e);
   delete p;
 }
 
@@ -704,7 +706,11 @@ bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, in
   p->N = N;
   p->K = K;
   p->opt = o;
+  const std::string model_path = o.model_path ? o.model_path : "";
+  p->opt.model_path = nullptr;  // the caller's string is read here only
   p->donor = donor;
+  static std::atomic<uint64_t> next_uid{1};
+  p->uid = next_uid++;
   p->r.assign(row_sizes, row_sizes + M);
   p->c.assign(col_sizes, col_sizes + N);
   p->q.assign(inner_sizes, inner_sizes + K);
@@ -826,6 +832,28 @@ bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, in
       return st;
     }
   }
+  // the learned costs of a cost-model file; a file that cannot be used leaves the
+  // flop-count costs (the fallback) and the plan is still built
+  if (!model_path.empty() && o.schedule != BSMM_SCHED_NATURAL && p->n_units > 0) {
+    const std::string keep = g_last_error;
+    bsmm_mlp_t mlp = nullptr;
+    if (bsmm_mlp_load(&mlp, model_path.c_str()) == BSMM_OK) {
+      if (bsmm_plan_predict_costs(p, mlp, nullptr) == BSMM_OK) {
+        p->cost_source = BSMM_COSTS_MODEL;
+      } else {  // back to the flop-count packing
+        p->cost = p->flop_cost;
+        p->opt.schedule = o.schedule;
+        pack_lpt(p);
+        if ((st = upload_schedule(p)) != BSMM_OK) {
+          bsmm_mlp_destroy(mlp);
+          bsmm_destroy(p);
+          return st;
+        }
+      }
+      bsmm_mlp_destroy(mlp);
+    }
+    if (p->cost_source != BSMM_COSTS_MODEL) g_last_error = keep;  // the fallback is not an error
+  }
   *out = p;
   return BSMM_OK;
 }
@@ -914,8 +942,15 @@ bsmm_status bsmm_plan_set_costs(bsmm_plan_t p, const double* costs) {
     if (!(costs[u] > 0.0) || !std::isfinite(costs[u])) return set_error("costs must be finite and > 0"), BSMM_ERR_INVALID;
   p->cost.assign(costs, costs + p->n_units);
   p->opt.schedule = BSMM_SCHED_COSTS;
+  p->cost_source = BSMM_COSTS_GIVEN;
   pack_lpt(p);
   return upload_schedule(p);
+}
+
+bsmm_status bsmm_plan_cost_source(bsmm_plan_t p, int32_t* source) {
+  if (!p || !source) return set_error("NULL argument"), BSMM_ERR_INVALID;
+  *source = p->cost_source;
+  return BSMM_OK;
 }
 
 bsmm_status bsmm_plan_set_ctas(bsmm_plan_t p, int32_t ctas) {

@@ -88,3 +88,55 @@ def test_tune_space_lists_fitting_candidates():
     assert [(c["cluster"], c["stages"]) for c in s3] == [(cl, st) for cl in (1, 2, 4) for st in range(2, 7)]
     with pytest.raises(P.BsmmError):
         P.bsmm_tune_space(P.BSMM_SPLIT_BF16, 7)
+
+
+def _model_file(path, version=1, feature_version=1, F=12, H=32, corrupt=False):
+    """A cost-model file laid out as include/bsmm.h states (written here byte by byte)."""
+    import struct
+    NP = H * F + H + H * H + H + H + 1
+    body = b"BSMMMLP\0" + struct.pack("<5I", version, feature_version, F, H, NP)
+    body += struct.pack(f"<{NP}f", *([0.01] * NP)) + struct.pack(f"<{F}f", *([0.0] * F))
+    body += struct.pack(f"<{F}f", *([1.0] * F)) + struct.pack("<2f", 0.0, 1.0)
+    h = 1469598103934665603
+    for c in body:
+        h = ((h ^ c) * 1099511628211) & (2 ** 64 - 1)
+    if corrupt:
+        h ^= 1
+    with open(path, "wb") as f:
+        f.write(body + struct.pack("<Q", h))
+
+
+def test_cost_model_file_checks_before_any_device_work(tmp_path):
+    """bsmm_mlp_load refuses a missing file, a bad checksum, another format or feature
+    version and another shape with BSMM_ERR_INVALID, before creating a model (no GPU
+    needed); a well-formed file passes the checks and only then needs the device."""
+    import torch
+    L = P.lib()
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_mlp_load(tmp_path / "missing.bin")
+    assert ei.value.status == 1
+    for kw in (dict(corrupt=True), dict(version=2), dict(feature_version=9), dict(H=16)):
+        _model_file(tmp_path / "m.bin", **kw)
+        with pytest.raises(P.BsmmError) as ei:
+            P.bsmm_mlp_load(tmp_path / "m.bin")
+        assert ei.value.status == 1, kw
+    (tmp_path / "short.bin").write_bytes(b"BSMMMLP\0")
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_mlp_load(tmp_path / "short.bin")
+    assert ei.value.status == 1
+    if not torch.cuda.is_available():
+        _model_file(tmp_path / "good.bin")
+        with pytest.raises(P.BsmmError) as ei:
+            P.bsmm_mlp_load(tmp_path / "good.bin")
+        assert ei.value.status == 2  # the file was accepted; creating the model needs a GPU
+    assert L.bsmm_mlp_save(None, b"x") == 1
+    assert L.bsmm_plan_cost_source(None, None) == 1
+
+
+def test_execute_batch_rejects_null_arguments():
+    L = P.lib()
+    assert L.bsmm_execute_batch(0, None, None, None, None, None, None, None, None, None, None) == 1
+    one = (ctypes.c_void_p * 1)(None)
+    d = (ctypes.c_double * 1)(1.0)
+    assert L.bsmm_execute_batch(1, one, d, one, one, one, one, d, one, one, None) == 1
+    assert L.bsmm_measure_rates(None, None) == 1

@@ -1,0 +1,147 @@
+"""The boundary's one-call batch (bsmm_execute_batch) and the learned schedule's
+checkpoint (bsmm_mlp_save / bsmm_mlp_load, bsmm_options.model_path), through the C ABI.
+Neither may change a single bit of any result: only the order of the work units does."""
+import numpy as np
+import pytest
+
+import bsmm_gen as G
+import oracle
+from oracle import split as OS
+import paper_1504_05046_gb300 as P
+from helpers import c_arena, struct_elements
+
+pytestmark = pytest.mark.gpu
+
+
+def _items(count=5, seed=11):
+    import torch
+    probs = G.make_batch(count, seed, n_lo=150, n_hi=700, b_lo=24, b_hi=140)
+    items = []
+    for i, prob in enumerate(probs):
+        prob.alpha, prob.beta = [1.0, -0.5, 2.0][i % 3], [0.0, 1.0, 0.5][i % 3]
+        cs, _, _ = oracle.structure(prob)
+        off, C0 = c_arena(prob, cs, rng=np.random.default_rng(i))
+        plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                           mode=P.BSMM_SPLIT_BF16, nslices=6, debug_checks=1)
+        d = lambda x: torch.from_numpy(np.ascontiguousarray(x if x.size else np.zeros(2, x.dtype))).cuda()
+        items.append(dict(prob=prob, cs=cs, off=off, C0=C0, plan=plan, A=d(prob.A), B=d(prob.B), ao=d(prob.a_off),
+                          bo=d(prob.b_off), co=d(off), C=d(C0)))
+    return items
+
+
+def _one_call(items, Cs=None):
+    P.bsmm_execute_batch([it["plan"] for it in items], [it["prob"].alpha for it in items], [it["A"] for it in items],
+                         [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                         [it["prob"].beta for it in items], Cs or [it["C"] for it in items],
+                         [it["co"] for it in items])
+
+
+def test_execute_batch_one_call_matches_the_oracle_repeatedly_and_in_a_graph():
+    import torch
+    items = _items()
+    wants = []
+    for it in items:
+        w = it["C0"].copy()
+        OS.bsmm_split(it["prob"], it["cs"], w, it["off"], 6)
+        wants.append(struct_elements(it["prob"], it["cs"], it["off"], w))
+
+    def check(Cs):
+        torch.cuda.synchronize()
+        for it, C, want in zip(items, Cs, wants):
+            got = struct_elements(it["prob"], it["cs"], it["off"], C.cpu().numpy())
+            assert np.array_equal(got, want)
+
+    _one_call(items)                       # first call: the batch is created and set up
+    check([it["C"] for it in items])
+    for it in items:                       # same arguments: kernels only
+        it["C"].copy_(torch.from_numpy(it["C0"] if it["C0"].size else np.zeros(2)))
+    _one_call(items)
+    check([it["C"] for it in items])
+    fresh = [torch.from_numpy(it["C0"].copy() if it["C0"].size else np.zeros(2)).cuda() for it in items]
+    _one_call(items, fresh)                # new C pointers: arguments re-uploaded
+    check(fresh)
+    # with the arguments of the previous call, the call only enqueues kernels: capture it
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        _one_call(items, fresh)
+    for C, it in zip(fresh, items):
+        C.copy_(torch.from_numpy(it["C0"] if it["C0"].size else np.zeros(2)))
+    g.replay()
+    check(fresh)
+    for it in items:
+        P.bsmm_status_device(it["plan"])
+
+
+def test_execute_batch_after_plans_are_replaced():
+    """A new plan list (even one reusing freed plans' memory) gets its own batch; results
+    stay exact."""
+    import torch
+    for seed in (21, 22, 23, 24, 25, 26):
+        items = _items(count=3, seed=seed)
+        _one_call(items)
+        torch.cuda.synchronize()
+        for it in items:
+            w = it["C0"].copy()
+            OS.bsmm_split(it["prob"], it["cs"], w, it["off"], 6)
+            got = struct_elements(it["prob"], it["cs"], it["off"], it["C"].cpu().numpy())
+            assert np.array_equal(got, struct_elements(it["prob"], it["cs"], it["off"], w))
+        del items
+
+
+def _clustered():
+    return G.make_problem("clustered", 41, 2000, lo=16, hi=200, nclusters=8, cluster_density=0.2)
+
+
+def test_mlp_file_round_trip(tmp_path):
+    m = P.bsmm_mlp_create(7)
+    n = P.bsmm_mlp_num_params()
+    prm = np.random.default_rng(1).normal(0, 0.3, n).astype(np.float32)
+    P.bsmm_mlp_set_params(m, prm)
+    xm = np.arange(12, dtype=np.float32)
+    xs = np.linspace(0.5, 2.0, 12).astype(np.float32)
+    P.bsmm_mlp_set_norm(m, xm, xs, 1.5, 0.25)
+    P.bsmm_mlp_save(m, tmp_path / "cost.bin")
+    m2 = P.bsmm_mlp_load(tmp_path / "cost.bin")
+    assert np.array_equal(P.bsmm_mlp_get_params(m2), prm)
+    nm = P.bsmm_mlp_get_norm(m2)
+    assert np.array_equal(nm[0], xm) and np.array_equal(nm[1], xs) and nm[2:] == (1.5, 0.25)
+
+
+def test_model_path_schedules_by_the_saved_model_with_the_same_bits(tmp_path):
+    """A plan built with model_path packs its units by the file's predictions, exactly as
+    bsmm_plan_predict_costs with the same model does; a missing or damaged file leaves the
+    flop-count schedule. Every variant gives the same bits."""
+    import torch
+    from gpu_helpers import run_lib
+    prob = _clustered()
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = c_arena(prob, cs, rng=np.random.default_rng(2))
+    m = P.bsmm_mlp_create(3)
+    P.bsmm_mlp_set_params(m, np.random.default_rng(4).normal(0, 0.5, P.bsmm_mlp_num_params()).astype(np.float32))
+    path = tmp_path / "cost.bin"
+    P.bsmm_mlp_save(m, path)
+    mk = lambda **kw: P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                                  mode=P.BSMM_SPLIT_BF16, nslices=6, **kw)
+    flops = mk()
+    assert P.bsmm_plan_cost_source(flops) == P.BSMM_COSTS_FLOPS
+    learned = mk(model_path=path)
+    assert P.bsmm_plan_cost_source(learned) == P.BSMM_COSTS_MODEL
+    given = mk()
+    P.bsmm_plan_predict_costs(given, m)
+    assert P.bsmm_plan_cost_source(given) == P.BSMM_COSTS_GIVEN
+    missing = mk(model_path=tmp_path / "none.bin")
+    assert P.bsmm_plan_cost_source(missing) == P.BSMM_COSTS_FLOPS
+    raw = bytearray(path.read_bytes())
+    raw[40] ^= 0xFF
+    (tmp_path / "bad.bin").write_bytes(bytes(raw))
+    damaged = mk(model_path=tmp_path / "bad.bin")
+    assert P.bsmm_plan_cost_source(damaged) == P.BSMM_COSTS_FLOPS
+    outs = [run_lib(prob, cs, C0, off, plan=pl)[0] for pl in (flops, learned, given, missing, damaged)]
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    want = C0.copy()
+    OS.bsmm_split(prob, cs, want, off, 6)
+    assert np.array_equal(struct_elements(prob, cs, off, outs[0]), struct_elements(prob, cs, off, want))
+    torch.cuda.synchronize()
