@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="dense workload: skip the learned-schedule comparison on the clustered workload")
     ap.add_argument("--workload", default="dense", choices=["dense", "batch", "uniform", "banded", "banded_wide",
                                                                 "clustered", "thin"],
                     help="dense: the 16384 nonuniform dense product (headline); batch: 256 independent products of "
@@ -411,19 +413,78 @@ SINGLE = {
 CONTRACTION_INDEX = {"split": 2, "fp64": 0}
 
 
-def run_single(args, rank, world):
-    """One of the other workloads: the split path (and, for the clustered one, the
-    learned schedule against the flop-count schedule) and the FP64 path on the same
-    inputs, each timed over the steps with CUDA events; the split result compared with
-    the FP64 result over the whole C."""
+def timed_steps(plan, run, steps, warmup):
+    """Mean step time (ms, CUDA events on the current stream) of `steps` runs after
+    `warmup` untimed ones, and each kernel's mean device time over the timed runs (read
+    once afterwards from the plan's events)."""
+    import torch
+    import paper_1504_05046_gb300 as P
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    P.bsmm_plan_kernel_ms(plan)  # the per-kernel means below cover the timed steps only
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ks = P.bsmm_plan_kernel_ms(plan)
+    P.bsmm_status_device(plan)
+    return e0.elapsed_time(e1) / steps, ks
+
+
+def learned_vs_flops(setup, seed, steps, warmup, dev):
+    """The learned schedule against the flop-count schedule on one product: the cost model
+    is trained on unit timings of three other inputs of the same recipe (3 timed runs
+    each, 2000 Adam steps on the GPU), then the product is timed under both schedules.
+    `setup(seed, **opt)` plans a product and returns (prob, plan, q, t, run). Returns the
+    record, the product's (plan, t, run) under the learned schedule, its timing and the
+    clocks sampled while it was timed."""
+    import torch
+    import paper_1504_05046_gb300 as P
+    from paper_1504_05046_gb300 import costmodel as CM
+    rows = []
+    for ts in (seed + 101, seed + 102, seed + 103):
+        _, tplan, _, _, trun = setup(ts, record_timings=1)
+        trun()
+        rows.append(CM.training_rows(tplan, CM.unit_times(tplan, trun, repeats=3)))
+        del tplan
+    mlp, loss = CM.fit(rows, steps=2000, lr=3e-3)
+    prob, plan, q, t, run = setup(seed, record_timings=1)
+    run()
+    times = CM.unit_times(plan, run, repeats=3)
+    CM.apply_flops(plan)
+    ms_flops, k_flops = timed_steps(plan, run, steps, warmup)
+    ref = t["C"].clone()
+    CM.apply(plan, mlp)
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    ms_mlp, k_mlp = timed_steps(plan, run, steps, warmup)
+    clocks = clk.stop()
+    same = bool((t["C"] == ref).all())
+    feats, flops = P.bsmm_plan_features(plan)
+    y = torch.zeros(len(feats), dtype=torch.float32, device=dev)
+    P.bsmm_mlp_predict(mlp, torch.from_numpy(feats).to(dev), y)
+    ci = CONTRACTION_INDEX["split"]
+    rec = {"makespan_ms_flop_count": k_flops[ci], "makespan_ms_mlp": k_mlp[ci], "step_ms_flop_count": ms_flops,
+           "step_ms_mlp": ms_mlp, "makespan_gain": 1.0 - k_mlp[ci] / k_flops[ci], "bits_identical": same,
+           "train_loss": loss,
+           "log_rms_err_flop_count": CM.prediction_error(plan, times, np.maximum(flops, 1.0)),
+           "log_rms_err_mlp": CM.prediction_error(plan, times, np.exp(y.cpu().numpy().astype(np.float64))),
+           "train_inputs": "3 other seeds of the same workload, 3 timed runs each",
+           "timing": f"mean of {steps} steps after {warmup} warm-up steps, per schedule"}
+    return rec, (prob, plan, q, t, run), (ms_mlp, k_mlp), clocks
+
+
+def single_setup(args, w, dev):
+    """setup(seed, mode, **opt) for one of the SINGLE workloads: the seeded product
+    planned (profile events on) with its device arenas; returns (prob, plan, q, t, run)."""
     import torch
     import bsmm_gen as G
     import paper_1504_05046_gb300 as P
-    from paper_1504_05046_gb300 import costmodel as CM
-    w = SINGLE[args.workload]
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    s = args.slices
-    mode = getattr(P, w["mode"])
 
     def setup(seed, mode, **opt):
         if mode != P.BSMM_FP64:
@@ -432,7 +493,7 @@ def run_single(args, rank, world):
         opt.setdefault("ksplit", args.ksplit)
         prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,
-                           nslices=s, profile=1, **opt)
+                           nslices=args.slices, profile=1, **opt)
         q = P.bsmm_plan_query(plan)
         off, tot = G.layout_arena(q["c_mask"], prob.row_sizes, prob.col_sizes)
         d = lambda x: torch.from_numpy(x if x.size else np.zeros(2, x.dtype)).to(dev)
@@ -440,57 +501,32 @@ def run_single(args, rank, world):
                  C=torch.zeros(max(tot, 1), dtype=torch.float64, device=dev))
         run = lambda: P.bsmm_execute(plan, 1.0, t["A"], t["ao"], t["B"], t["bo"], 0.0, t["C"], t["co"])
         return prob, plan, q, t, run
+    return setup
+
+
+def run_single(args, rank, world):
+    """One of the other workloads: the split path (and, for the clustered one, the
+    learned schedule against the flop-count schedule) and the FP64 path on the same
+    inputs, each timed over the steps with CUDA events; the split result compared with
+    the FP64 result over the whole C."""
+    import torch
+    import paper_1504_05046_gb300 as P
+    w = SINGLE[args.workload]
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    s = args.slices
+    mode = getattr(P, w["mode"])
+    setup = single_setup(args, w, dev)
 
     def timed(plan, run, steps):
-        stream = torch.cuda.current_stream()
-        for _ in range(args.warmup):
-            run()
-        torch.cuda.synchronize()
-        P.bsmm_plan_kernel_ms(plan)  # the per-kernel means below cover the timed steps only
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            run()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ks = P.bsmm_plan_kernel_ms(plan)  # mean per kernel over the timed steps
-        P.bsmm_status_device(plan)
-        return e0.elapsed_time(e1) / steps, ks
+        return timed_steps(plan, run, steps, args.warmup)
 
     extra = {}
     seed = args.seed + rank
     if args.workload == "clustered":
-        # learned schedule: train on unit timings of three other inputs of the same shape
-        rows = []
-        for ts in (seed + 101, seed + 102, seed + 103):
-            _, tplan, _, _, trun = setup(ts, mode, record_timings=1)
-            trun()
-            rows.append(CM.training_rows(tplan, CM.unit_times(tplan, trun, repeats=3)))
-            del tplan
-        mlp, loss = CM.fit(rows, steps=2000, lr=3e-3)
-        prob, plan, q, t, run = setup(seed, mode, record_timings=1)
-        run()
-        times = CM.unit_times(plan, run, repeats=3)
-        CM.apply_flops(plan)
-        ms_flops, k_flops = timed(plan, run, args.steps)
-        ref = t["C"].clone()
-        CM.apply(plan, mlp)
-        clk = ClockSampler(dev.index)
-        clk.start()
-        time.sleep(0.3)
-        ms_split, k_split = timed(plan, run, args.steps)
-        clocks = clk.stop()
-        same = bool((t["C"] == ref).all())
-        feats, flops = P.bsmm_plan_features(plan)
-        y = torch.zeros(len(feats), dtype=torch.float32, device=dev)
-        P.bsmm_mlp_predict(mlp, torch.from_numpy(feats).to(dev), y)
-        ci = CONTRACTION_INDEX["split"]
-        extra["learned_schedule"] = {
-            "makespan_ms_flop_count": k_flops[ci], "makespan_ms_mlp": k_split[ci], "step_ms_flop_count": ms_flops,
-            "step_ms_mlp": ms_split, "bits_identical": same, "train_loss": loss,
-            "log_rms_err_flop_count": CM.prediction_error(plan, times, np.maximum(flops, 1.0)),
-            "log_rms_err_mlp": CM.prediction_error(plan, times, np.exp(y.cpu().numpy().astype(np.float64))),
-            "train_inputs": "3 other seeds of the same workload, 3 timed runs each"}
+        # learned schedule against the flop-count schedule (the split path's headline)
+        rec, (prob, plan, q, t, run), (ms_split, k_split), clocks = learned_vs_flops(
+            lambda sd, **o: setup(sd, mode, **o), seed, args.steps, args.warmup, dev)
+        extra["learned_schedule"] = rec
     else:
         prob, plan, q, t, run = setup(seed, mode)
         clk = ClockSampler(dev.index)
@@ -806,6 +842,15 @@ def run_dense(args, rank, world, local):
         if args.c128_slices and not (ta or tb):
             extra["complex_elements"] = complex_line(args, P, G, torch, dev, stream)
         del plan64, C64
+        # the learned schedule against the flop-count schedule on the clustered workload
+        if not args.no_learned and not (ta or tb):
+            w = SINGLE["clustered"]
+            cl_setup = single_setup(args, w, dev)
+            rec, (cprob, cplan, cq, ct, crun), _, _ = learned_vs_flops(
+                lambda sd, **o: cl_setup(sd, P.BSMM_SPLIT_BF16, **o), args.seed, 5, args.warmup, dev)
+            rec["workload"] = w["desc"]
+            extra["learned_schedule_clustered"] = rec
+            del cplan, ct, crun
 
     # end to end through the public C ABI with host buffers (pinned)
     e2e = None

@@ -37,7 +37,7 @@ int split_tile_n(int s);          // work-unit width (32 or 64)
 int split_stages(int s, int tn);  // smem ring depth
 size_t split_smem_bytes(int s, int tn, int stages);
 constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory of one CTA
-constexpr size_t kSplitBarBytes = 256;          // mbarriers, TMEM slot and flags after the ring
+constexpr size_t kSplitBarBytes = 512;          // mbarriers, TMEM slot, flags and group descriptors after the ring
 constexpr int16_t kNonUniform = 0x7FFF;         // scale-class sentinel (offsets are <= 0)
 constexpr int32_t kZeroLine = -(1 << 20);       // exponent of an all-zero row or column
 int split_max_depth(int s);
@@ -68,7 +68,8 @@ struct SplitUnit {  // one (128-row block, group of cl TN-column blocks), inner 
   int32_t rb, cb;
   int32_t k0, k1;
   int32_t slot;  // -1: the unit finishes its region; else the partial-sum slot of this piece
-  int32_t pad;
+  int32_t own;   // bit r: the group's r-th column block has a B tile at some k of [k0, k1)
+                 // where the row block has an A tile (that CTA's list is not empty)
 };
 
 struct Fp64Red {  // a region whose k-list was split: partial slots [slot0, slot0 + n)

@@ -325,13 +325,16 @@ constexpr int kRateThreads = 256;
 constexpr int kRateBlocksPerSm = 8;
 
 __global__ void __launch_bounds__(kRateThreads) fp64_dfma_rate_kernel(double* out, int iters) {
-  const double b = 1.0 + 0x1p-40, c = 0x1p-60;
-  double x[16];
+  double x[16], b[16], c[16];  // every chain its own multiplier and addend
 #pragma unroll
-  for (int u = 0; u < 16; u++) x[u] = (threadIdx.x + u) * 0x1p-20;
+  for (int u = 0; u < 16; u++) {
+    x[u] = (threadIdx.x + u) * 0x1p-20;
+    b[u] = 1.0 + (u + 1) * 0x1p-40;
+    c[u] = (u + 1) * 0x1p-60;
+  }
   for (int i = 0; i < iters; i++) {
 #pragma unroll
-    for (int u = 0; u < 16; u++) x[u] = fma(x[u], b, c);
+    for (int u = 0; u < 16; u++) x[u] = fma(x[u], b[u], c[u]);
   }
   double sum = 0.0;
 #pragma unroll

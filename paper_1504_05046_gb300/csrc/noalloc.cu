@@ -113,7 +113,7 @@ __global__ void noalloc_setup_kernel(uint8_t* base, int m, int n, int k, int s, 
     int u = 0;
     for (int rb = 0; rb < RB; rb++)
       for (int cb = 0; cb < CB; cb++) {
-        t->units[u] = SplitUnit{rb, cb, 0, 1, -1, 0};  // the one inner block, whole
+        t->units[u] = SplitUnit{rb, cb, 0, 1, -1, k > 0 ? 1 : 0};  // the one inner block, whole
         t->sched_ptr[u] = u;
         t->sched_units[u] = u;
         u++;

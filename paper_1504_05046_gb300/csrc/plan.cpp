@@ -526,6 +526,16 @@ bsmm_status plan_split(bsmm_plan_s* p) {
         un.k1 = hi < L ? ks[hi] : K;
         un.slot = slot0[u] + pc;
       }
+      un.own = 0;
+      for (int r = 0; r < CL; r++) {
+        const int64_t cbr = (int64_t)un.cb * CL + r;
+        if (cbr >= CB) break;
+        for (int k = un.k0; k < un.k1; k++)  // presA & presB of the CTA's own column block
+          if ((presA[(size_t)un.rb * KW + k / 64] & presB[(size_t)cbr * KW + k / 64]) >> (k % 64) & 1) {
+            un.own |= 1 << r;
+            break;
+          }
+      }
       p->sp_units.push_back(un);
       p->unit_pieces.push_back(n);
       const int rb = un.rb, cb = un.cb;

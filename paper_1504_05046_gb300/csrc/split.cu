@@ -60,8 +60,20 @@ constexpr int kEpiThreads = kSplitEpiWarps * 32;
 // MMA issue: one thread issues tcgen05.mma instructions about one per 100 cycles, whatever
 // their N, so the slice products of a step are spread over kMmaWarps issuing warps.
 constexpr int kMmaWarps = 3;
-constexpr int kEpiWarp0 = 1 + kMmaWarps;                    // first epilogue warp
-constexpr int kThreads = 32 * kEpiWarp0 + kEpiThreads;     // producer + MMA warps + epilogue warps
+constexpr int kEpiWarp0 = 1 + kMmaWarps;                 // first epilogue warp (warpgroups 1 and 2)
+constexpr int kStoreWarps = 4;                           // C store warps (warpgroup 3)
+constexpr int kStoreWarp0 = kEpiWarp0 + kSplitEpiWarps;  // first store warp
+constexpr int kThreads = 32 * (kStoreWarp0 + kStoreWarps);
+// Register split with setmaxnreg: the CTA is launched with kThreads x kRegsLaunch registers
+// (the whole register file); the producer and MMA warps (warpgroup 0) and the store warps
+// (warpgroup 3) give registers back and the epilogue warps take them. The shares add up to
+// the launch's total exactly, so every setmaxnreg.inc is satisfiable.
+constexpr int kRegsLaunch = 65536 / kThreads;  // 128
+constexpr int kRegsCtl = 80, kRegsEpi = 168, kRegsStore = 96;
+static_assert(kEpiWarp0 % 4 == 0 && kStoreWarp0 % 4 == 0, "roles start on warpgroup boundaries");
+static_assert(4 * 32 * kRegsCtl + kSplitEpiWarps * 32 * kRegsEpi + kStoreWarps * 32 * kRegsStore ==
+                  kThreads * kRegsLaunch,
+              "the warpgroups' register shares must add up to the launch's registers");
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAChunk = kSplitBM * kSplitKC * 2;  // bytes of one slice of a 128x32 A chunk
 
@@ -112,12 +124,15 @@ __device__ bool wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag, 
   }
 }
 
-// Warp-uniform bounded wait (every lane polls; the decision is taken by the warp).
+// Warp-uniform bounded wait (every lane polls; the decision is taken by the warp). A warp
+// whose wait is not on the critical path passes sleep_ns > 0: it sleeps between polls,
+// leaving the issue slots to the warps that are.
 __device__ bool wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int32_t* err,
-                          int64_t limit = kWaitNs) {
+                          int64_t limit = kWaitNs, uint32_t sleep_ns = 0) {
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const int64_t t0 = gtimer();
   for (uint32_t spin = 1;; spin++) {
+    if (sleep_ns) __nanosleep(sleep_ns);
     const bool ok = mbar_try_wait(bar, parity);
     if (__all_sync(0xffffffffu, ok)) return true;
     int stop = *abort_flag;
@@ -840,13 +855,15 @@ __device__ __forceinline__ bool low128(unsigned long long hi, unsigned long long
 // A result below the smallest normal number (rare): w * 2^L rounded once, ties to even,
 // to a multiple of the format's smallest subnormal 2^emin_sub, returned as that multiple
 // (at most 2^P-1: the next normal number's pattern when it rounds up). Callers pass only
-// values below the smallest normal, so |w| < 2^(emin_sub - L + P - 1).
+// values below the smallest normal, so |w| < 2^(emin_sub - L + P - 1). Out of line, with
+// the words passed by value (no address of the caller's accumulators is taken). The sign
+// bit of the result's pattern is added by the caller.
 template <int P>
-__device__ __noinline__ unsigned long long acc_round_subnormal(const uint32_t (&w)[4], int L, int emin_sub,
-                                                               bool& neg) {
-  unsigned long long lo = ((unsigned long long)w[1] << 32) | w[0];
-  unsigned long long hi = ((unsigned long long)w[3] << 32) | w[2];
-  neg = (long long)hi < 0;
+__device__ __noinline__ unsigned long long acc_round_subnormal(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                                               int L, int emin_sub) {
+  unsigned long long lo = ((unsigned long long)w1 << 32) | w0;
+  unsigned long long hi = ((unsigned long long)w3 << 32) | w2;
+  const bool neg = (long long)hi < 0;
   if (neg) {
     lo = ~lo;
     hi = ~hi;
@@ -876,7 +893,7 @@ __device__ __forceinline__ double acc_to_double(const uint32_t (&w)[4], int L) {
     return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
                                             (mant & ((1ull << 52) - 1))));
   if (biased > 2046) return neg ? -CUDART_INF : CUDART_INF;
-  const unsigned long long q = acc_round_subnormal<53>(w, L, -1074, neg);
+  const unsigned long long q = acc_round_subnormal<53>(w[0], w[1], w[2], w[3], L, -1074);
   return __longlong_as_double((long long)(((unsigned long long)neg << 63) | q));
 }
 
@@ -890,7 +907,7 @@ __device__ __forceinline__ float acc_to_float(const uint32_t (&w)[4], int L) {
   if (biased >= 1 && biased <= 254)
     return __uint_as_float(((uint32_t)neg << 31) | ((uint32_t)biased << 23) | ((uint32_t)mant & 0x7FFFFFu));
   if (biased > 254) return neg ? -CUDART_INF_F : CUDART_INF_F;
-  const unsigned long long q = acc_round_subnormal<24>(w, L, -149, neg);
+  const unsigned long long q = acc_round_subnormal<24>(w[0], w[1], w[2], w[3], L, -149);
   return __uint_as_float(((uint32_t)neg << 31) | (uint32_t)q);
 }
 
@@ -906,6 +923,15 @@ __device__ __forceinline__ void add128(uint32_t (&w)[4], const uint4& v) {
       "addc.u32 %3, %3, %7;"
       : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
       : "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+}
+
+template <int R>
+__device__ __forceinline__ void regs_dec() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R));
+}
+template <int R>
+__device__ __forceinline__ void regs_inc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(R));
 }
 
 // True when v is true in every thread of the kEpiThreads epilogue threads (named barrier 1
@@ -926,67 +952,70 @@ __device__ __forceinline__ bool epi_all(bool v) {
 // C = alpha*v + beta*C for a 128 x TN region staged in shared memory (row stride TN + 1),
 // on the elements that lie in S_C tiles. Warp w of NW stores rows w*(128/NW) .. with
 // lane = column (TN == 32), so a store instruction writes one or two contiguous row
-// segments; lanes below 128/NW fetch the rows' tile and row-in-tile, shuffles hand them out.
+// segments; per pass of up to 16 rows, lanes fetch the rows' tile and row-in-tile and
+// shuffles hand them out.
 template <int TN, int NW, int ELEM>  // ELEM: 0 float64, 1 float32, 2 complex (one part per column)
 __device__ __forceinline__ void store_region(const SplitArgs& P, const double* cstage, int rb, int cb, int w, int lane,
                                              int32_t* err) {
   static_assert(TN == 32, "one column per lane");
   constexpr int kRowsPerWarp = kSplitBM / NW;
+  constexpr int kPass = kRowsPerWarp < 16 ? kRowsPerWarp : 16;  // rows whose offsets are in flight together
+  static_assert(kRowsPerWarp % kPass == 0, "whole passes");
   const int64_t nl = (int64_t)cb * TN + lane;
   const bool col_ok = nl < P.Ntot;
   const int jl = col_ok ? P.col_tile[nl] : 0;
   const int64_t lcl = col_ok ? nl - P.co[jl] : 0;
   const int64_t cjl = col_ok ? P.c[jl] : 0;
-  const int64_t mr = (int64_t)rb * kSplitBM + w * kRowsPerWarp + (lane % kRowsPerWarp);
-  const int ir = mr < P.Mtot ? P.row_tile[mr] : 0;
-  const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
   const double alpha = P.alpha, beta = P.beta;
   const float alpha32 = (float)alpha, beta32 = (float)beta;  // float32 elements: exact (given as floats)
-  // every row's C tile offset first (independent loads, all in flight), then the stores
-  int64_t offs[kRowsPerWarp];
-  int lr2s[kRowsPerWarp];
+#pragma unroll 1
+  for (int r0 = 0; r0 < kRowsPerWarp; r0 += kPass) {
+    const int64_t mr = (int64_t)rb * kSplitBM + w * kRowsPerWarp + r0 + (lane % kPass);
+    const int ir = mr < P.Mtot ? P.row_tile[mr] : 0;
+    const int lrr = mr < P.Mtot ? (int)(mr - P.ro[ir]) : 0;
+    // every row's C tile offset first (independent loads, all in flight), then the stores
+    int64_t offs[kPass];
+    int lr2s[kPass];
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerWarp; rr++) {
-    const int64_t m2 = (int64_t)rb * kSplitBM + w * kRowsPerWarp + rr;
-    const int i2 = __shfl_sync(0xffffffffu, ir, rr);
-    lr2s[rr] = __shfl_sync(0xffffffffu, lrr, rr);
-    offs[rr] = -2;
-    if (m2 < P.Mtot && col_ok) {
-      const int64_t tile = (int64_t)i2 * P.N + jl;
-      offs[rr] = P.cs[tile] ? P.c_off[tile] : -2;
+    for (int rr = 0; rr < kPass; rr++) {
+      const int64_t m2 = (int64_t)rb * kSplitBM + w * kRowsPerWarp + r0 + rr;
+      const int i2 = __shfl_sync(0xffffffffu, ir, rr);
+      lr2s[rr] = __shfl_sync(0xffffffffu, lrr, rr);
+      offs[rr] = -2;
+      if (m2 < P.Mtot && col_ok) {
+        const int64_t tile = (int64_t)i2 * P.N + jl;
+        offs[rr] = P.cs[tile] ? P.c_off[tile] : -2;
+      }
     }
-  }
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerWarp; rr++) {
-    const int r2 = w * kRowsPerWarp + rr;
-    const int lr2 = lr2s[rr];
-    {
+    for (int rr = 0; rr < kPass; rr++) {
+      const int r2 = w * kRowsPerWarp + r0 + rr;
+      const int lr2 = lr2s[rr];
       const int64_t off = offs[rr];
       if (off == -1) atomicOr(err, kErrBadOffset);
-      if (off >= 0) {
-        if constexpr (ELEM == 2) {
-          // column lcl of the doubled tile: the real part of complex column lcl, or the
-          // imaginary part of column lcl - c_j / 2
-          const int64_t cc = cjl >> 1;
-          const int64_t part = lcl >= cc;
-          double* dst = P.C + 2 * (off + (int64_t)lr2 * cc + lcl - part * cc) + part;
-          double vv = cstage[r2 * (TN + 1) + lane];
-          if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
-          if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
-          *dst = vv;
-        } else if constexpr (ELEM == 1) {
-          float* dst = P.Cf + off + (int64_t)lr2 * cjl + lcl;
-          float vv = f32_of_slot(cstage[r2 * (TN + 1) + lane]);
-          if (alpha32 != 1.0f) vv = __fmul_rn(alpha32, vv);
-          if (beta32 != 0.0f) vv = __fadd_rn(vv, __fmul_rn(beta32, *dst));
-          *dst = vv;
-        } else {
-          double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
-          double vv = cstage[r2 * (TN + 1) + lane];
-          if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
-          if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
-          *dst = vv;
-        }
+      if (off < 0) continue;
+      if constexpr (ELEM == 2) {
+        // column lcl of the doubled tile: the real part of complex column lcl, or the
+        // imaginary part of column lcl - c_j / 2
+        const int64_t cc = cjl >> 1;
+        const int64_t part = lcl >= cc;
+        double* dst = P.C + 2 * (off + (int64_t)lr2 * cc + lcl - part * cc) + part;
+        double vv = cstage[r2 * (TN + 1) + lane];
+        if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
+        if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
+        *dst = vv;
+      } else if constexpr (ELEM == 1) {
+        float* dst = P.Cf + off + (int64_t)lr2 * cjl + lcl;
+        float vv = f32_of_slot(cstage[r2 * (TN + 1) + lane]);
+        if (alpha32 != 1.0f) vv = __fmul_rn(alpha32, vv);
+        if (beta32 != 0.0f) vv = __fadd_rn(vv, __fmul_rn(beta32, *dst));
+        *dst = vv;
+      } else {
+        double* dst = P.C + off + (int64_t)lr2 * cjl + lcl;
+        double vv = cstage[r2 * (TN + 1) + lane];
+        if (alpha != 1.0) vv = __dmul_rn(alpha, vv);
+        if (beta != 0.0) vv = __dadd_rn(vv, __dmul_rn(beta, *dst));
+        *dst = vv;
       }
     }
   }
@@ -1099,6 +1128,17 @@ struct GroupRule {
   }
 };
 
+// A group is complete: its descriptor goes to the epilogue (from the first MMA warp),
+// then every MMA warp's commit marks the buffer full once its MMAs have finished.
+__device__ __forceinline__ void close_group(bool first, int4* gdesc, uint64_t* gready, uint64_t* tfull, uint32_t buf,
+                                            int gk0, const GroupRule& grp, bool last) {
+  if (first) {
+    gdesc[buf] = make_int4(gk0, grp.sig, (grp.uni ? 1 : 0) | (last ? 2 : 0), 0);
+    mbar_arrive(&gready[buf]);
+  }
+  umma_commit(&tfull[buf]);
+}
+
 // The values of one own k block of a unit's list that the MMA warps need, loaded ahead.
 struct KAhead {
   int k, q;
@@ -1184,9 +1224,16 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   uint64_t* empty = bars + stages;
   uint64_t* tfull = bars + 2 * stages;
   uint64_t* tempty = tfull + 2;
-  uint64_t* drain = tempty + 2;  // one per MMA warp
+  uint64_t* gready = tempty + 2;  // a group's descriptor is in gdesc[buf]
+  uint64_t* cready = gready + 2;  // the unit's rounded results are in cstage
+  uint64_t* cfree = cready + 1;   // the store warps are done with cstage
+  uint64_t* drain = cfree + 1;    // one per MMA warp
   uint32_t* tmem_slot = (uint32_t*)(drain + kMmaWarps);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // the accumulation group in TMEM buffer b: first k block, binary offset of a uniform
+  // group, flags (1: uniform scale class, 2: the unit's last group); written by the first
+  // MMA warp when it closes the group
+  int4* gdesc = (int4*)(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);
   // the unit's results on their way to C: 128 rows x (TN + 1) doubles (padded rows)
   double* cstage = (double*)(smem + (size_t)stages * STAGE + kSplitBarBytes);
 
@@ -1203,7 +1250,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
     for (int b = 0; b < 2; b++) {
       mbar_init(&tfull[b], W);
       mbar_init(&tempty[b], kSplitEpiWarps);
+      mbar_init(&gready[b], 1);
     }
+    mbar_init(cready, kEpiThreads);         // every epilogue thread, after its row
+    mbar_init(cfree, kStoreWarps * 32);     // every store thread, after its rows
     for (int w = 0; w < kMmaWarps; w++) mbar_init(&drain[w], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1217,6 +1267,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
+  // Roles by warpgroup; each warpgroup first takes its register share (every warp of the
+  // warpgroup executes the setmaxnreg, and it dominates the role's code).
+  if (warp < kEpiWarp0) {
+    regs_dec<kRegsCtl>();
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
@@ -1296,6 +1350,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         GroupRule grp;
         bool in_group = false;
         uint32_t buf = 0;
+        int gk0 = 0;  // the current group's first k block
         // per-k values are loaded one k block ahead, so their latency hides behind the
         // current block's MMAs; a group is closed when the next own k block does not join
         KAhead cur, nxt;
@@ -1307,7 +1362,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           const int nkc = (q + kSplitKC - 1) / kSplitKC;
           if (!(in_group && grp.joins(cur.uni, cur.sig, cur.q))) {
             if (in_group) {  // the previous group is complete
-              umma_commit(&tfull[buf]);
+              close_group(mw == 0, gdesc, gready, tfull, buf, gk0, grp, false);
               tcount++;
             }
             buf = tcount & 1;
@@ -1320,6 +1375,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
             }
             tc_fence_after();
             grp.start(cur.uni, cur.sig, cur.q, P.kdepth);
+            gk0 = kt;
             in_group = true;
           }
           const uint32_t dbase = tmem_base + buf * BUF_COLS;
@@ -1347,11 +1403,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
               phase ^= 1;
             }
           }
-          (void)kt;
           cur = nxt;
         }
         if (in_group && ok) {  // the unit's last group
-          umma_commit(&tfull[buf]);
+          close_group(mw == 0, gdesc, gready, tfull, buf, gk0, grp, true);
           tcount++;
         }
       }
@@ -1367,7 +1422,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         }
       }
     }
-  } else if (warp >= kEpiWarp0) {
+  }
+  } else if (warp < kStoreWarp0) {
+    regs_inc<kRegsEpi>();
     // ------------------------------------------------------------ epilogue warps
     const int ew = warp - kEpiWarp0;   // 0..7
     const int quad = warp & 3;         // TMEM lane quadrant this warp may access
@@ -1389,6 +1446,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       mbar_arrive(&tempty[1]);
     }
     uint32_t tcount = 0;
+    uint32_t ncs = 0;  // uses of cstage so far
     bool ok = true;
     for (int idx = ubeg; idx < uend && ok; idx++) {
       int u = a.sched_units[idx];
@@ -1404,39 +1462,33 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       uint32_t acc[TH][4];  // exact 128-bit two's-complement sums, unit 2^L per column
 #pragma unroll
       for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
-      UnitIter it;
-      it.init(P, un, cb);
-      int kt = it.next_own();
-      while (kt >= 0) {
-        // the accumulation group starting at kt, and the binary position of its integers:
-        // one shift for a uniform group, per-row and per-column offsets for a lone k block
-        GroupRule grp;
-        {
-          int sg = 0;
-          const bool uni = scale_class(P, kt, un.rb, cb, sg);
-          grp.start(uni, sg, P.q[kt], P.kdepth);
+      // The unit's accumulation groups as the MMA warps close them (none when this CTA's
+      // column block has no B tile in the unit's inner range: the planner's own mask).
+      bool more = (un.own >> rank) & 1;
+      while (more) {
+        const uint32_t buf = tcount & 1, use = tcount >> 1;
+        if (!wait_warp(&gready[buf], use & 1, abort_flag, a.err)) {
+          ok = false;
+          break;
         }
-        int kn = it.next_own();
-        for (; kn >= 0; kn = it.next_own()) {
-          int sg = 0;
-          const bool uni = scale_class(P, kn, un.rb, cb, sg);
-          if (!grp.joins(uni, sg, P.q[kn])) break;
-        }
+        const int4 gd = gdesc[buf];
+        more = (gd.z & 2) == 0;
+        // the binary position of the group's integers: one shift for a uniform group (its
+        // common class plus the row's and the columns' parts), per-row and per-column
+        // offsets for a lone k block; loaded while the tensor core finishes the group
         int shr = kSplitGuard;
         uint4 cx[TH / 8];
-        if (grp.uni) {  // the group's common class plus the row's and the columns' parts
-          shr += grp.sig + (row_ok ? (int)P.rowadj[m] : 0);
+        if (gd.z & 1) {
+          shr += gd.y + (row_ok ? (int)P.rowadj[m] : 0);
           const uint4* src = reinterpret_cast<const uint4*>(P.coladj + n0);
 #pragma unroll
           for (int w = 0; w < TH / 8; w++) cx[w] = __ldg(src + w);
         } else {
-          shr += row_ok ? (int)P.rowexp[(int64_t)kt * P.Mtot + m] : 0;
-          const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)kt * P.colexp_ld + n0);
+          shr += row_ok ? (int)P.rowexp[(int64_t)gd.x * P.Mtot + m] : 0;
+          const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)gd.x * P.colexp_ld + n0);
 #pragma unroll
           for (int w = 0; w < TH / 8; w++) cx[w] = __ldg(src + w);
         }
-        kt = kn;
-        const uint32_t buf = tcount & 1, use = tcount >> 1;
         if (!wait_warp(&tfull[buf], use & 1, abort_flag, a.err)) {
           ok = false;
           break;
@@ -1492,10 +1544,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       // abort flag, so all eight warps reach them, and the last one agrees on the outcome,
       // so all eight leave the unit loop together)
       if (un.slot < 0) {
-        // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles.
-        // Each thread rounds its row's sums to doubles into shared memory; then every warp
-        // stores whole rows, lane = column, so a store instruction writes one or two
-        // contiguous row segments instead of 32 scattered elements.
+        // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles: each
+        // thread rounds its row's sums to doubles into the staging buffer once the store
+        // warps are done with the previous unit's, and hands it to them; the C store then
+        // runs while this warp drains the next unit.
+        if (ok && !wait_warp(cfree, (ncs & 1) ^ 1, abort_flag, a.err)) ok = false;
         if (ok) {
           // the accumulator's unit 2^L: per row block and column block of tiles, or per row
           // and column with row/column scaling
@@ -1506,15 +1559,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           else
             round_row<TH, false>(acc, srow, P, row_ok, n0, Lrow);
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
-        if (ok && !*abort_flag) {
-          if (P.f32)
-            store_region<TN, kSplitEpiWarps, 1>(P, cstage, un.rb, cb, ew, lane, a.err);
-          else if (P.cplx)
-            store_region<TN, kSplitEpiWarps, 2>(P, cstage, un.rb, cb, ew, lane, a.err);
-          else
-            store_region<TN, kSplitEpiWarps, 0>(P, cstage, un.rb, cb, ew, lane, a.err);
-        }
+        mbar_arrive(cready);  // every thread: its row is in cstage (release)
+        ncs++;
       } else if (ok) {
         // a piece of a split k-list: its exact partial sums go to the workspace (column-
         // major, so the 32 rows of a warp write 512 contiguous bytes per column)
@@ -1522,7 +1568,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
 #pragma unroll
         for (int c = 0; c < TH; c++) dst[(size_t)c * kSplitBM] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
       }
-      ok = epi_all(ok);  // cstage is free again; every epilogue warp has the same outcome
+      ok = epi_all(ok);  // every epilogue warp has the same outcome
       if (!ok) break;
       if (a.timings && rank == 0) {
         if (ew == 0 && lane == 0) {
@@ -1530,6 +1576,32 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           a.unit_cta[u] = cta;
         }
       }
+    }
+  } else {
+    regs_dec<kRegsStore>();
+    // ------------------------------------------------------------ C store warps
+    // The units' rounded results from the staging buffer to C, in the epilogue's unit
+    // order, while the epilogue warps drain the next unit.
+    const int sw = warp - kStoreWarp0;
+    uint32_t ncs = 0;
+    for (int idx = ubeg; idx < uend; idx++) {
+      int u = a.sched_units[idx];
+      const SplitArgs& P = a.prods ? a.prods[a.unit_prod[u]] : a;
+      if (a.prods) u = a.unit_local[u];
+      const SplitUnit un = P.units[u];
+      const int cb = un.cb * CL + rank;
+      if (cb >= P.CB || un.slot >= 0) continue;  // units that do not use the staging buffer
+      if (!wait_warp(cready, ncs & 1, abort_flag, a.err, kWaitNs, 200)) break;
+      if (!*abort_flag) {
+        if (P.f32)
+          store_region<TN, kStoreWarps, 1>(P, cstage, un.rb, cb, sw, lane, a.err);
+        else if (P.cplx)
+          store_region<TN, kStoreWarps, 2>(P, cstage, un.rb, cb, sw, lane, a.err);
+        else
+          store_region<TN, kStoreWarps, 0>(P, cstage, un.rb, cb, sw, lane, a.err);
+      }
+      mbar_arrive(cfree);  // every thread: done reading cstage (release)
+      ncs++;
     }
   }
 
@@ -1611,6 +1683,12 @@ cudaError_t launch_mma(const SplitArgs& a, int groups, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  // the register split assumes exactly kRegsLaunch registers per thread at launch (a
+  // smaller allocation could not satisfy the epilogue's setmaxnreg.inc): refuse otherwise
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, CL>);
+  if (e != cudaSuccess) return e;
+  if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
   split_mma_kernel<S, TN, CL><<<(unsigned)(groups * CL), kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }

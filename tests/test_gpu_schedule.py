@@ -1,6 +1,8 @@
 """What the learned cost model gains: trained on unit timings of clustered products
 (irregular log-uniform blocks, dense clusters of tiles), evaluated on a held-out
-product against the flop-count schedule. The result bits are the same either way."""
+product against the flop-count schedule, at the clustered workload's full size (M = N =
+24576, K = 49152). The makespans are medians of 5 timed runs each; the learned schedule
+must be no slower than the flop-count one, and the result bits are the same either way."""
 import json
 import os
 
@@ -12,7 +14,7 @@ import paper_1504_05046_gb300 as P
 from paper_1504_05046_gb300 import costmodel as CM
 
 pytestmark = pytest.mark.gpu
-N = 12288
+N = 24576
 
 
 def _setup(seed):
@@ -45,10 +47,10 @@ def test_learned_schedule_vs_flop_count():
     times = CM.unit_times(plan, run, repeats=3)
     _, flops = P.bsmm_plan_features(plan)
     CM.apply_flops(plan)
-    t_flops = CM.makespan_ms(plan, run)
+    t_flops = CM.makespan_ms(plan, run, repeats=5)
     ref = C.cpu().numpy().copy()
     CM.apply(plan, mlp)
-    t_mlp = CM.makespan_ms(plan, run)
+    t_mlp = CM.makespan_ms(plan, run, repeats=5)
     assert np.array_equal(C.cpu().numpy(), ref), "the schedule changed result bits"
     # predicted costs as the plan now holds them
     import torch
@@ -66,4 +68,4 @@ def test_learned_schedule_vs_flop_count():
             json.dump(record, f, indent=1)
     print(record)
     assert err_mlp < err_flops
-    assert t_mlp <= 1.03 * t_flops
+    assert t_mlp <= t_flops
