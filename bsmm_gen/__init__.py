@@ -345,7 +345,7 @@ def transposed_storage(prob: Problem, transa: bool, transb: bool) -> Problem:
         # tile (u, v) of a rows[u] x cols[v] grid -> tile (v, u) of the transposed grid
         mt = np.ascontiguousarray(mask.T)
         new_off, tot = layout_arena(mt, cols, rows)
-        out = np.zeros(tot)
+        out = np.zeros(tot, arena.dtype)
         for u in range(mask.shape[0]):
             for v in range(mask.shape[1]):
                 if mask[u, v]:

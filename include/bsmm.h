@@ -139,7 +139,7 @@ typedef struct {
                               are exact doubles); the sum is rounded once to float32 (ties to
                               even) and the epilogue runs in float32,
                               C = fl32(fl32(alpha*acc) + fl32(beta*C)). Execute with
-                              bsmm_execute_f32; batches and bsmm_execute_host take float64.
+                              bsmm_execute_f32, bsmm_execute_host or in a batch.
                               BSMM_C128 (split modes, untransposed, one scale per tile): A, B
                               and C are complex double arenas passed to bsmm_execute as double
                               arrays of interleaved (re, im) pairs; offsets count complex
@@ -261,14 +261,17 @@ bsmm_status bsmm_execute_f32(bsmm_plan_t plan, float alpha, const float* A, cons
                              const int64_t* c_off, void* stream);
 
 /*
- * Same as bsmm_execute with HOST buffers: copies A, B (and C when beta != 0) and
- * the offset tables to device buffers the plan keeps, runs, copies C back and
- * synchronises `stream` before returning. a_elems, b_elems, c_elems = arena
- * lengths in elements. Pinned host memory makes the copies asynchronous.
+ * Same as bsmm_execute (bsmm_execute_f32 for float32 elements) with HOST buffers:
+ * copies A, B (and C when beta != 0) and the offset tables to device buffers the plan
+ * keeps, runs, copies C back and synchronises `stream` before returning. The arenas
+ * hold the plan's element type (bsmm_options.elem): float64, float32, or interleaved
+ * complex doubles; a_elems, b_elems, c_elems = arena lengths in those elements.
+ * alpha and beta are real (converted to float32 for float32 elements). Pinned host
+ * memory makes the copies asynchronous.
  */
-bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const double* A, int64_t a_elems,
-                              const int64_t* a_off, const double* B, int64_t b_elems,
-                              const int64_t* b_off, double beta, double* C, int64_t c_elems,
+bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const void* A, int64_t a_elems,
+                              const int64_t* a_off, const void* B, int64_t b_elems,
+                              const int64_t* b_off, double beta, void* C, int64_t c_elems,
                               const int64_t* c_off, void* stream);
 
 /*
@@ -279,9 +282,13 @@ bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const double* A, i
  *
  * bsmm_batch_create: `count` plans, all with the same mode, slice count and cluster
  *   size, on one device. The plans must outlive the batch. Allocates device memory.
+ *   In the split modes each plan may have its own element type (bsmm_options.elem).
  * bsmm_batch_set_args: per-product arguments as in bsmm_execute, given as host arrays
- *   of length `count` (alpha[i], beta[i], and DEVICE pointers A[i], a_off[i], ...).
- *   Copied to the device synchronously; call again when any of them changes.
+ *   of length `count` (alpha[i], beta[i], and DEVICE pointers A[i], a_off[i], ...). A[i],
+ *   B[i] and C[i] point to arenas of plan i's element type (float64, float32, or
+ *   interleaved complex doubles); alpha and beta are real (converted to float32 for
+ *   float32 elements). Copied to the device synchronously; call again when any of them
+ *   changes.
  * bsmm_batch_execute: issues the kernels of the whole batch on `stream`. FP64: one
  *   contraction launch. Split modes: the products are taken in waves whose slice
  *   workspaces fit in half of L2 (a larger product is a wave of its own); each wave
@@ -296,9 +303,9 @@ bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const double* A, i
  */
 typedef struct bsmm_batch_s* bsmm_batch_t;
 bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_t* plans);
-bsmm_status bsmm_batch_set_args(bsmm_batch_t batch, const double* alpha, const double* const* A,
-                                const int64_t* const* a_off, const double* const* B,
-                                const int64_t* const* b_off, const double* beta, double* const* C,
+bsmm_status bsmm_batch_set_args(bsmm_batch_t batch, const double* alpha, const void* const* A,
+                                const int64_t* const* a_off, const void* const* B,
+                                const int64_t* const* b_off, const double* beta, void* const* C,
                                 const int64_t* const* c_off);
 bsmm_status bsmm_batch_execute(bsmm_batch_t batch, void* stream);
 bsmm_status bsmm_batch_query(bsmm_batch_t batch, int64_t* n_units, double* useful_flops, int32_t* bins);
@@ -325,9 +332,9 @@ void bsmm_batch_destroy(bsmm_batch_t batch);
  * different streams with the same plan list race. The plans must outlive the calls;
  * a destroyed plan's entry is released when it becomes the least recently used.
  */
-bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const double* alpha, const double* const* A,
-                               const int64_t* const* a_off, const double* const* B, const int64_t* const* b_off,
-                               const double* beta, double* const* C, const int64_t* const* c_off, void* stream);
+bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const double* alpha, const void* const* A,
+                               const int64_t* const* a_off, const void* const* B, const int64_t* const* b_off,
+                               const double* beta, void* const* C, const int64_t* const* c_off, void* stream);
 
 /*
  * Autotuning of a batch's launch shape. The paper has no counterpart (its tile kernel

@@ -207,7 +207,6 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
     b_off = prob_like.b_off.T if tb else prob_like.b_off
     cacheA, cacheB = {}, {}
     cplx = np.iscomplexobj(prob_like.A)
-    assert not (cplx and (ta or tb)), "complex elements are stored untransposed"
 
     def sl(x):  # (e, slices) or, for complex tiles, (e, (slices of re, slices of im))
         if not cplx:

@@ -108,9 +108,9 @@ void free_batch(bsmm_batch_s* b) {
 // The caller's per-product arguments, as stored by bsmm_batch_set_args.
 struct BatchArgs {
   std::vector<double> alpha, beta;
-  std::vector<const double*> A, B;
+  std::vector<const void*> A, B;
   std::vector<const int64_t*> ao, bo, co;
-  std::vector<double*> C;
+  std::vector<void*> C;
   explicit BatchArgs(const bsmm_batch_s* b) {
     const size_t n = b->plans.size();
     alpha.resize(n), beta.resize(n), A.resize(n), B.resize(n), ao.resize(n), bo.resize(n), co.resize(n), C.resize(n);
@@ -121,12 +121,14 @@ struct BatchArgs {
         co[i] = a.c_off, C[i] = a.C;
       } else {
         const SplitArgs& a = b->sargs[i];
-        alpha[i] = a.alpha, beta[i] = a.beta, A[i] = a.A, B[i] = a.B, ao[i] = a.a_off, bo[i] = a.b_off;
-        co[i] = a.c_off, C[i] = a.C;
+        alpha[i] = a.alpha, beta[i] = a.beta, ao[i] = a.a_off, bo[i] = a.b_off, co[i] = a.c_off;
+        A[i] = a.f32 ? (const void*)a.Af : (const void*)a.A;
+        B[i] = a.f32 ? (const void*)a.Bf : (const void*)a.B;
+        C[i] = a.f32 ? (void*)a.Cf : (void*)a.C;
       }
     }
   }
-  bsmm_status set(bsmm_batch_t b, const std::vector<double*>& Cs) const;
+  bsmm_status set(bsmm_batch_t b, const std::vector<void*>& Cs) const;
 };
 
 // Plans of every product of `src` under options `o` (sharing the slice workspace of the
@@ -176,9 +178,7 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
       return set_error("all FP64 plans of a batch need the same sub-tile edge (set bsmm_options.fp64_tile)"),
              BSMM_ERR_INVALID;
     if (p->device != p0->device) return set_error("all plans of a batch need the same device"), BSMM_ERR_INVALID;
-    if (p->opt.elem != BSMM_F64) return set_error("batches take float64 elements"), BSMM_ERR_UNSUPPORTED;
   }
-  if (p0->opt.elem != BSMM_F64) return set_error("batches take float64 elements"), BSMM_ERR_UNSUPPORTED;
   bsmm_batch_s* b = new (std::nothrow) bsmm_batch_s();
   if (!b) return set_error("out of host memory"), BSMM_ERR_NOMEM;
   b->plans.assign(plans, plans + count);
@@ -241,16 +241,17 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   return BSMM_OK;
 }
 
-bsmm_status bsmm_batch_set_args(bsmm_batch_t b, const double* alpha, const double* const* A,
-                                const int64_t* const* a_off, const double* const* B, const int64_t* const* b_off,
-                                const double* beta, double* const* C, const int64_t* const* c_off) {
+bsmm_status bsmm_batch_set_args(bsmm_batch_t b, const double* alpha, const void* const* A,
+                                const int64_t* const* a_off, const void* const* B, const int64_t* const* b_off,
+                                const double* beta, void* const* C, const int64_t* const* c_off) {
   if (!b || !alpha || !beta || !A || !a_off || !B || !b_off || !C || !c_off)
     return set_error("NULL argument array"), BSMM_ERR_INVALID;
   const size_t n = b->plans.size();
   if (b->mode == BSMM_FP64) {
     b->fargs.assign(n, Fp64Args{});
     for (size_t i = 0; i < n; i++) {
-      fill_fp64_args(b->plans[i], b->fargs[i], alpha[i], A[i], a_off[i], B[i], b_off[i], beta[i], C[i], c_off[i]);
+      fill_fp64_args(b->plans[i], b->fargs[i], alpha[i], (const double*)A[i], a_off[i], (const double*)B[i], b_off[i],
+                     beta[i], (double*)C[i], c_off[i]);
       b->fargs[i].timings = nullptr;
       b->fargs[i].unit_cta = nullptr;
     }
@@ -259,7 +260,10 @@ bsmm_status bsmm_batch_set_args(bsmm_batch_t b, const double* alpha, const doubl
   } else {
     b->sargs.assign(n, SplitArgs{});
     for (size_t i = 0; i < n; i++) {
-      fill_split_args(b->plans[i], b->sargs[i], alpha[i], A[i], a_off[i], B[i], b_off[i], beta[i], C[i], c_off[i]);
+      // float32 elements take alpha and beta in float32, as bsmm_execute_f32 does
+      const bool f32 = b->plans[i]->opt.elem == BSMM_F32;
+      fill_split_args(b->plans[i], b->sargs[i], f32 ? (double)(float)alpha[i] : alpha[i], A[i], a_off[i], B[i],
+                      b_off[i], f32 ? (double)(float)beta[i] : beta[i], C[i], c_off[i]);
       b->sargs[i].timings = nullptr;
       b->sargs[i].unit_cta = nullptr;
     }
@@ -347,9 +351,9 @@ uint64_t g_one_clock = 0;
 
 extern "C" {
 
-bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const double* alpha, const double* const* A,
-                               const int64_t* const* a_off, const double* const* B, const int64_t* const* b_off,
-                               const double* beta, double* const* C, const int64_t* const* c_off, void* stream) {
+bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const double* alpha, const void* const* A,
+                               const int64_t* const* a_off, const void* const* B, const int64_t* const* b_off,
+                               const double* beta, void* const* C, const int64_t* const* c_off, void* stream) {
   if (count <= 0 || !plans || !alpha || !beta || !A || !a_off || !B || !b_off || !C || !c_off)
     return set_error("bsmm_execute_batch: NULL argument or count <= 0"), BSMM_ERR_INVALID;
   std::vector<uint64_t> uids(count);
@@ -427,7 +431,7 @@ bsmm_status bsmm_batch_set_costs(bsmm_batch_t b, const double* costs) {
   return repack(b);
 }
 
-bsmm_status BatchArgs::set(bsmm_batch_t b, const std::vector<double*>& Cs) const {
+bsmm_status BatchArgs::set(bsmm_batch_t b, const std::vector<void*>& Cs) const {
   return bsmm_batch_set_args(b, alpha.data(), A.data(), ao.data(), B.data(), bo.data(), beta.data(), Cs.data(),
                              co.data());
 }
@@ -468,7 +472,7 @@ bsmm_status bsmm_batch_autotune(bsmm_batch_t b, int32_t n, const bsmm_tune_point
   const size_t count = b->plans.size();
   // scratch C per product, as long as the caller's C extent
   std::vector<DevBuf> scratch(count);
-  std::vector<double*> scratch_c(count);
+  std::vector<void*> scratch_c(count);
   bsmm_status res = BSMM_OK;
   auto cleanup_scratch = [&]() {
     for (DevBuf& d : scratch)
@@ -481,15 +485,20 @@ bsmm_status bsmm_batch_autotune(bsmm_batch_t b, int32_t n, const bsmm_tune_point
       res = (set_error("reading c_off failed"), BSMM_ERR_CUDA);
       break;
     }
+    // the C extent in elements of the plan's type (a complex plan's column tiling counts
+    // both parts of each complex column)
+    const bool cplx = p->opt.elem == BSMM_C128;
+    const size_t es = p->opt.elem == BSMM_F32 ? sizeof(float) : cplx ? 2 * sizeof(double) : sizeof(double);
     int64_t extent = 1;
     for (int ii = 0; ii < p->M; ii++)
       for (int jj = 0; jj < p->N; jj++) {
         const size_t t = (size_t)ii * p->N + jj;
-        if (p->cs[t] && off[t] >= 0) extent = std::max<int64_t>(extent, off[t] + (int64_t)p->r[ii] * p->c[jj]);
+        const int64_t cols = cplx ? p->c[jj] / 2 : p->c[jj];
+        if (p->cs[t] && off[t] >= 0) extent = std::max<int64_t>(extent, off[t] + (int64_t)p->r[ii] * cols);
       }
-    if ((res = dalloc(scratch[i], sizeof(double) * extent)) != BSMM_OK) break;
-    if (cudaMemset(scratch[i].p, 0, sizeof(double) * extent) != cudaSuccess) res = (set_error("cudaMemset failed"), BSMM_ERR_CUDA);
-    scratch_c[i] = (double*)scratch[i].p;
+    if ((res = dalloc(scratch[i], es * extent)) != BSMM_OK) break;
+    if (cudaMemset(scratch[i].p, 0, es * extent) != cudaSuccess) res = (set_error("cudaMemset failed"), BSMM_ERR_CUDA);
+    scratch_c[i] = scratch[i].p;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (res == BSMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))

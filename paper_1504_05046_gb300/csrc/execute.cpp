@@ -220,18 +220,20 @@ bsmm_status bsmm_execute_f32(bsmm_plan_t p, float alpha, const float* A, const i
   return run(p, alpha, A, a_off, B, b_off, beta, C, c_off, (cudaStream_t)stream);
 }
 
-bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const double* A, int64_t a_elems,
-                              const int64_t* a_off, const double* B, int64_t b_elems, const int64_t* b_off,
-                              double beta, double* C, int64_t c_elems, const int64_t* c_off, void* stream) {
+bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const void* A, int64_t a_elems, const int64_t* a_off,
+                              const void* B, int64_t b_elems, const int64_t* b_off, double beta, void* C,
+                              int64_t c_elems, const int64_t* c_off, void* stream) {
   bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
   if (s != BSMM_OK) return s;
-  if (p->opt.elem != BSMM_F64) return set_error("bsmm_execute_host takes float64 elements"), BSMM_ERR_INVALID;
   if (a_elems < 0 || b_elems < 0 || c_elems < 0) return set_error("negative arena length"), BSMM_ERR_INVALID;
+  // bytes per element of the plan's element type
+  const size_t es = p->opt.elem == BSMM_F32 ? sizeof(float) : p->opt.elem == BSMM_C128 ? 2 * sizeof(double)
+                                                                                        : sizeof(double);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t na = (size_t)p->M * p->K, nb = (size_t)p->K * p->N, nc = (size_t)p->M * p->N;
-  if ((s = grow(p->h_A, sizeof(double) * a_elems)) != BSMM_OK) return s;
-  if ((s = grow(p->h_B, sizeof(double) * b_elems)) != BSMM_OK) return s;
-  if ((s = grow(p->h_C, sizeof(double) * c_elems)) != BSMM_OK) return s;
+  if ((s = grow(p->h_A, es * a_elems)) != BSMM_OK) return s;
+  if ((s = grow(p->h_B, es * b_elems)) != BSMM_OK) return s;
+  if ((s = grow(p->h_C, es * c_elems)) != BSMM_OK) return s;
   if ((s = grow(p->h_aoff, sizeof(int64_t) * na)) != BSMM_OK) return s;
   if ((s = grow(p->h_boff, sizeof(int64_t) * nb)) != BSMM_OK) return s;
   if ((s = grow(p->h_coff, sizeof(int64_t) * nc)) != BSMM_OK) return s;
@@ -243,15 +245,17 @@ bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const double* A, int6
   H2D(p->h_aoff.p, a_off, sizeof(int64_t) * na);
   H2D(p->h_boff.p, b_off, sizeof(int64_t) * nb);
   H2D(p->h_coff.p, c_off, sizeof(int64_t) * nc);
-  H2D(p->h_A.p, A, sizeof(double) * a_elems);
-  H2D(p->h_B.p, B, sizeof(double) * b_elems);
-  if (beta != 0.0) H2D(p->h_C.p, C, sizeof(double) * c_elems);
+  H2D(p->h_A.p, A, es * a_elems);
+  H2D(p->h_B.p, B, es * b_elems);
+  if (beta != 0.0) H2D(p->h_C.p, C, es * c_elems);
 #undef H2D
-  s = run(p, alpha, (const double*)p->h_A.p, (const int64_t*)p->h_aoff.p, (const double*)p->h_B.p,
-          (const int64_t*)p->h_boff.p, beta, (double*)p->h_C.p, (const int64_t*)p->h_coff.p, st);
+  const double al = p->opt.elem == BSMM_F32 ? (double)(float)alpha : alpha;
+  const double be = p->opt.elem == BSMM_F32 ? (double)(float)beta : beta;
+  s = run(p, al, p->h_A.p, (const int64_t*)p->h_aoff.p, p->h_B.p, (const int64_t*)p->h_boff.p, be, p->h_C.p,
+          (const int64_t*)p->h_coff.p, st);
   if (s != BSMM_OK) return s;
   if (c_elems > 0) {
-    cudaError_t e = cudaMemcpyAsync(C, p->h_C.p, sizeof(double) * c_elems, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(C, p->h_C.p, es * c_elems, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return set_error(std::string("D2H: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   }
   cudaError_t e = cudaStreamSynchronize(st);

@@ -644,8 +644,8 @@ bsmm_status validate_options(const bsmm_options& o) {
     return set_error("unknown element type"), BSMM_ERR_INVALID;
   if (o.elem != BSMM_F64 && o.mode == BSMM_FP64)
     return set_error("float32 and complex elements take a split mode"), BSMM_ERR_UNSUPPORTED;
-  if (o.elem == BSMM_C128 && (o.transa || o.transb || o.split_scale))
-    return set_error("complex elements are stored untransposed with one scale per tile"), BSMM_ERR_UNSUPPORTED;
+  if (o.elem == BSMM_C128 && o.split_scale)
+    return set_error("complex elements take one scale per tile"), BSMM_ERR_UNSUPPORTED;
   return BSMM_OK;
 }
 

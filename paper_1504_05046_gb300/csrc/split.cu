@@ -710,12 +710,15 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int64_t step = a.transa ? (m < a.Mtot ? a.r[i] : 0) : 1;
       const int k0 = kc * kSplitKC + ch * 8;
       if constexpr (CPLX) {
+        // complex element (lr, kc) of the tile at row + 2 kc cstep (cstep = 1, or the tile's
+        // row count when stored transposed); part 0 real, 1 imaginary
         const int qc = q >> 1;
-        const double* row = a.A + 2 * (off + lr * qc);
+        const int64_t cstep = a.transa ? step : 1;
+        const double* row = a.A + 2 * (off + (a.transa ? lr : lr * qc));
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const int kk = k0 + u, part = kk >= qc;
-          x[u] = (present && kk < q) ? neg_if(__ldg(row + 2 * (kk - part * qc) + part), part) : 0.0;
+          x[u] = (present && kk < q) ? neg_if(__ldg(row + 2 * (kk - part * qc) * cstep + part), part) : 0.0;
         }
       } else {
         const E* line = Ae + off + (a.transa ? lr : lr * q);
@@ -757,14 +760,17 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
       const int64_t step = a.transb ? 1 : cj;
       const int k0 = kc * kSplitKC + ch * 8;
       if constexpr (CPLX) {
+        // complex element (kc, c) of the tile at col + 2 kc kstep: kstep = the tile's complex
+        // column count, or 1 when stored transposed (then column c starts c * qc in)
         const int qc = q >> 1, cc = cj >> 1;
         const int cpart = lc >= cc;
-        const double* col = a.B + 2 * (off + (lc - cpart * cc));
+        const int64_t kstep = a.transb ? 1 : cc;
+        const double* col = a.B + 2 * (off + (lc - cpart * cc) * (a.transb ? qc : 1));
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const int kk = k0 + u, rpart = kk >= qc;
           x[u] = (present && kk < q)
-                     ? neg_if(__ldg(col + 2 * (int64_t)(kk - rpart * qc) * cc + (rpart ^ cpart)), rpart & cpart)
+                     ? neg_if(__ldg(col + 2 * (int64_t)(kk - rpart * qc) * kstep + (rpart ^ cpart)), rpart & cpart)
                      : 0.0;
         }
       } else {

@@ -145,3 +145,84 @@ def test_model_path_schedules_by_the_saved_model_with_the_same_bits(tmp_path):
     OS.bsmm_split(prob, cs, want, off, 6)
     assert np.array_equal(struct_elements(prob, cs, off, outs[0]), struct_elements(prob, cs, off, want))
     torch.cuda.synchronize()
+
+
+def _elem_problem(elem, seed):
+    """A small ragged product in the element type (float32 arenas re-laid on 16-byte tile
+    starts; complex arenas with imaginary parts of their own)."""
+    prob = G.make_problem("nonuniform_dense", seed, 420, lo=40, hi=160)
+    prob.alpha, prob.beta = 0.75, -0.5
+    if elem == P.BSMM_F32:
+        return G.as_float32(prob)
+    if elem == P.BSMM_C128:
+        return G.as_complex(prob, seed)
+    return prob
+
+
+def _c0(prob, cs, off, elem, seed):
+    _, C64 = c_arena(prob, cs, rng=np.random.default_rng(seed))
+    if elem == P.BSMM_F32:
+        return C64.astype(np.float32)
+    if elem == P.BSMM_C128:
+        return (C64 + 1j * np.random.default_rng(seed + 1).uniform(-1, 1, C64.size)).astype(np.complex128)
+    return C64
+
+
+@pytest.mark.parametrize("elem", [P.BSMM_F64, P.BSMM_F32, P.BSMM_C128])
+def test_execute_host_every_element_type(elem):
+    """bsmm_execute_host with host arenas of the plan's element type: the oracle's bits."""
+    prob = _elem_problem(elem, 31)
+    cs, _, _ = oracle.structure(prob)
+    off, _ = G.layout_arena(cs, prob.row_sizes, prob.col_sizes)
+    C0 = _c0(prob, cs, off, elem, 3)
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                       mode=P.BSMM_SPLIT_BF16, nslices=6, elem=elem, debug_checks=1)
+    C = C0.copy()
+    P.bsmm_execute_host(plan, prob.alpha, prob.A, prob.a_off, prob.B, prob.b_off, prob.beta, C, off)
+    P.bsmm_status_device(plan)
+    want = C0.copy()
+    OS.bsmm_split(prob, cs, want, off, 6)
+    assert np.array_equal(struct_elements(prob, cs, off, C), struct_elements(prob, cs, off, want))
+
+
+def test_batch_of_mixed_element_types():
+    """One batch holding float64, float32 and complex products (split mode): every product
+    gets the bits of its own oracle, in one launch and replayed from a CUDA graph."""
+    import torch
+    from gpu_helpers import to_dev
+    elems = [P.BSMM_F64, P.BSMM_F32, P.BSMM_C128, P.BSMM_F32, P.BSMM_F64]
+    items = []
+    for n, elem in enumerate(elems):
+        prob = _elem_problem(elem, 50 + n)
+        cs, _, _ = oracle.structure(prob)
+        off, _ = G.layout_arena(cs, prob.row_sizes, prob.col_sizes)
+        C0 = _c0(prob, cs, off, elem, n)
+        want = C0.copy()
+        OS.bsmm_split(prob, cs, want, off, 6)
+        plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                           mode=P.BSMM_SPLIT_BF16, nslices=6, elem=elem, debug_checks=1)
+        items.append(dict(prob=prob, cs=cs, off=off, C0=C0, want=want, plan=plan, A=to_dev(prob.A), B=to_dev(prob.B),
+                          ao=to_dev(prob.a_off), bo=to_dev(prob.b_off), co=to_dev(off), C=to_dev(C0)))
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                          [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                          [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+
+    def check():
+        torch.cuda.synchronize()
+        P.bsmm_batch_status_device(batch)
+        for it in items:
+            got = struct_elements(it["prob"], it["cs"], it["off"], it["C"].cpu().numpy())
+            assert np.array_equal(got, struct_elements(it["prob"], it["cs"], it["off"], it["want"]))
+
+    P.bsmm_batch_execute(batch)
+    check()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        P.bsmm_batch_execute(batch)
+    for it in items:
+        it["C"].copy_(torch.from_numpy(it["C0"]))
+    g.replay()
+    check()

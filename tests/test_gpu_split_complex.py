@@ -29,20 +29,28 @@ def _dense(arena, off, rows, cols):
     return out
 
 
-def run_c(prob, s=6, mode=P.BSMM_SPLIT_BF16, c_mask=None, **opt):
+def run_c(prob, s=6, mode=P.BSMM_SPLIT_BF16, c_mask=None, trans=(0, 0), **opt):
+    """Plan and run a complex product on the GPU (A and/or B supplied as the transposed
+    block matrix when trans says so); bit for bit against the split oracle, and the error
+    against numpy's complex product of the untransposed operands."""
     import torch
     from gpu_helpers import to_dev
-    cs, _, _ = oracle.structure(prob, c_mask)
+    base = prob
+    if any(trans):
+        prob = G.transposed_storage(base, bool(trans[0]), bool(trans[1]))
+        opt = dict(opt, transa=trans[0], transb=trans[1])
+    cs, _, _ = oracle.structure(base, c_mask)
     off, C64 = c_arena(prob, cs, rng=np.random.default_rng(0))
     C0 = (C64 + 1j * np.random.default_rng(1).uniform(-1, 1, C64.size)).astype(np.complex128)
     want = C0.copy()
-    OS.bsmm_split(prob, cs, want, off, s)
+    OS.bsmm_split(prob, cs, want, off, s)  # (the oracle reads the transposed storage)
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, c_mask,
                        mode=mode, nslices=s, elem=P.BSMM_C128, debug_checks=1, **opt)
+    prob, tprob = base, prob  # the reference below uses the untransposed operands
     dev = lambda x: to_dev(x if x.size else np.zeros(2, x.dtype))
     C = dev(C0)
-    P.bsmm_execute(plan, prob.alpha, dev(prob.A), dev(prob.a_off.astype(np.int64)), dev(prob.B),
-                   dev(prob.b_off.astype(np.int64)), prob.beta, C, dev(off.astype(np.int64)))
+    P.bsmm_execute(plan, prob.alpha, dev(tprob.A), dev(tprob.a_off.astype(np.int64)), dev(tprob.B),
+                   dev(tprob.b_off.astype(np.int64)), prob.beta, C, dev(off.astype(np.int64)))
     torch.cuda.synchronize()
     P.bsmm_status_device(plan)
     got = C.cpu().numpy()[:C0.size]
@@ -102,11 +110,24 @@ def test_thin_automatic_split_k():
     assert P.bsmm_plan_ksplit(plan)["n_regions"] > 0
 
 
+@pytest.mark.parametrize("trans", [(1, 0), (0, 1), (1, 1)])
+def test_transposed_storage(trans):
+    """Complex operands supplied as the transposed block matrix: the oracle's bits (those
+    of untransposed storage), ragged tiles, a C mask with beta, split k."""
+    prob = G.as_complex(G.random_small(21, max_blocks=6, max_size=60), 21)
+    _, err = run_c(prob, 6, trans=trans)
+    assert err <= 1e-11, err
+    prob = G.as_complex(G.make_problem("nonuniform_dense", 8, 600, lo=40, hi=200), 8)
+    prob.alpha, prob.beta = 0.5, -1.0
+    cm = (np.random.default_rng(3).random((prob.M, prob.N)) < 0.3).astype(np.uint8)
+    run_c(prob, 6, P.BSMM_SPLIT_FP16, c_mask=cm, trans=trans)
+    run_c(prob, 6, trans=trans, ksplit=2)
+
+
 def test_unsupported_combinations_are_rejected():
     prob = G.as_complex(G.random_small(1, max_blocks=3, max_size=30), 1)
     args = (prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask)
-    for bad in (dict(mode=P.BSMM_FP64), dict(mode=P.BSMM_SPLIT_BF16, transa=1),
-                dict(mode=P.BSMM_SPLIT_BF16, split_scale=1)):
+    for bad in (dict(mode=P.BSMM_FP64), dict(mode=P.BSMM_SPLIT_BF16, split_scale=1)):
         with pytest.raises(P.BsmmError):
             P.bsmm_plan(*args, elem=P.BSMM_C128, **bad)
     deep = np.array([300], np.int32)  # 2 x 300 real lines exceed the 6-slice exact depth

@@ -141,3 +141,33 @@ def test_exponent_is_shared_by_both_parts():
     assert C[0] == 1j * 2.0 ** 30
     OS.bsmm_split(prob, cs, C, np.zeros((1, 1), np.int64), 6)
     assert C[0] == 1.0 + 1j * 2.0 ** 30
+
+
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("seed", range(3))
+def test_transposed_storage(seed, ta, tb):
+    """A and/or B supplied as the transposed block matrix (tile (k,i) is q_k x r_i, complex
+    elements): the same bits as untransposed storage, and on integer inputs the exact
+    product of numpy's complex matmul of the untransposed operands."""
+    for values in ("uniform", "integers"):
+        base = G.as_complex(G.random_small(seed + 40, max_blocks=5, max_size=12, values=values), seed)
+        base.alpha, base.beta = 1.0, 0.0
+        tr = G.transposed_storage(base, bool(ta), bool(tb))
+        assert tr.A.dtype == np.complex128 and tr.B.dtype == np.complex128
+        cs, _, _ = oracle.structure(base)
+        off, C0 = _c_arena(base, cs, seed)
+        C1, C2 = C0.copy(), C0.copy()
+        OS.bsmm_split(base, cs, C1, off, 6)
+        OS.bsmm_split(tr, cs, C2, off, 6)
+        assert np.array_equal(C1, C2)
+        if values == "integers":
+            P = _dense(base, base.A, base.a_off, base.row_sizes, base.inner_sizes) @ \
+                _dense(base, base.B, base.b_off, base.inner_sizes, base.col_sizes)
+            ro = np.concatenate([[0], np.cumsum(base.row_sizes.astype(np.int64))])
+            co = np.concatenate([[0], np.cumsum(base.col_sizes.astype(np.int64))])
+            for i in range(base.M):
+                for j in range(base.N):
+                    if cs[i, j]:
+                        r, c = int(base.row_sizes[i]), int(base.col_sizes[j])
+                        o = off[i, j]
+                        assert np.array_equal(C2[o:o + r * c].reshape(r, c), P[ro[i]:ro[i + 1], co[j]:co[j + 1]])
