@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--cluster", type=int, default=0,
                     help="split modes: CTAs per column-block group (0 = library default)")
+    ap.add_argument("--store-warps", type=int, default=0, choices=[0, 1, 2],
+                    help="split modes: contraction kernel with C store warps (0 = library's choice, 1 = never, "
+                         "2 = always)")
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -383,7 +386,8 @@ def run_batch(args, rank, world):
                        "useful_flops_per_step": F, "seed": args.seed, "generation_s": t_gen},
             "batch_graph_autotuned": {"value": tf(ms_tuned), "ms_per_step": ms_tuned, "chosen": chosen,
                                       "tuning_s": t_tune,
-                                      "candidates_ms": {f"cluster={c['cluster']} stages={c['stages']}": m
+                                      "candidates_ms": {f"cluster={c['cluster']} stages={c['stages']} "
+                                                        f"store_warps={c['store_warps']}": m
                                                         for c, m in zip(space, tune_ms)}},
             "batch_graph_default": {"value": tf(ms_batch), "ms_per_step": ms_batch, "bins": default_bins},
             "separate_launches": {"value": tf(ms_sep), "ms_per_step": ms_sep, "launches_per_step":
@@ -490,6 +494,7 @@ def single_setup(args, w, dev):
         if mode != P.BSMM_FP64:
             opt.setdefault("split_scale", int(args.split_scale == "rows"))
             opt.setdefault("cluster", args.cluster)
+            opt.setdefault("store_warps", args.store_warps)
         opt.setdefault("ksplit", args.ksplit)
         prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,
@@ -689,7 +694,7 @@ def run_dense(args, rank, world, local):
     s = args.slices
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
                        mode=P.BSMM_SPLIT_BF16, nslices=s, profile=1, cluster=args.cluster, ksplit=args.ksplit, **tr,
-                       **sc)
+                       store_warps=args.store_warps, **sc)
     q = P.bsmm_plan_query(plan)
     F = q["useful_flops"]
     cs = q["c_mask"]

@@ -87,10 +87,11 @@ typedef struct {
   int32_t debug_checks;    /* 1 = kernels validate offsets against the plan */
   int32_t record_timings;  /* 1 = record per-unit start/end times (bsmm_plan_timings) */
   int32_t profile;         /* 1 = time each internal kernel with CUDA events (bsmm_plan_kernel_ms) */
-  int32_t cluster;         /* split modes: CTAs per column-block group, 1, 2 or 4 (0 = default):
+  int32_t cluster;         /* split modes: CTAs per column-block group, 1, 2 or 4 (0 = 1):
                               the group's CTAs take the same 128-row block at the same time,
                               one 32-column block each, and share its A panel through L2
-                              (each CTA loads its own operands) */
+                              (each CTA loads its own operands). Groups of one suit sparse
+                              masks best, where a neighbour's column block is often empty. */
   int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = 32) */
   int32_t stages;          /* split modes: depth of the shared-memory ring of 32-deep k chunks
                               (k panels in flight), 2..8 and within the 227 KB shared memory of
@@ -150,6 +151,11 @@ typedef struct {
                               equivalent real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]], so
                               an inner block may hold half the real depth (256 for 6 slices)
                               and the useful flop count is 8 r c q per nonzero triple. */
+  int32_t store_warps;     /* split modes: the contraction kernel's form. 0 = automatic: with
+                              four C store warps (the C store of a unit overlaps the next
+                              unit's accumulation) when the work units' mean inner depth is
+                              below 8192 elements, else without; 1 = never; 2 = always.
+                              Results do not depend on it. */
   const char* model_path;  /* NULL or "" = no model. Otherwise the path of a cost-model file
                               written by bsmm_mlp_save: bsmm_plan loads it, predicts every work
                               unit's time with it on the GPU and packs the units by those
@@ -342,12 +348,15 @@ bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const do
  * work-unit shape and pipeline depth.
  *
  * bsmm_tune_point: one candidate. Split modes: `cluster` CTAs per column-block group
- *   (a work unit is 128 rows x 32*cluster columns) and `stages`, the depth of the
- *   shared-memory ring (k panels in flight). FP64 mode: `fp64_tile`, the sub-tile edge
- *   of a work unit (32 or 64). Fields that do not apply to the mode must be 0.
+ *   (a work unit is 128 rows x 32*cluster columns), `stages`, the depth of the
+ *   shared-memory ring (k panels in flight), and `store_warps`, the contraction kernel's
+ *   form (as bsmm_options.store_warps: 0 = the planner's choice, 1 = without C store
+ *   warps, 2 = with them). FP64 mode: `fp64_tile`, the sub-tile edge of a work unit (32
+ *   or 64). Fields that do not apply to the mode must be 0.
  * bsmm_tune_space: the candidate list for a mode and slice count (split: cluster
- *   1, 2, 4 x every ring depth from 2 that fits one CTA's shared memory; FP64: 32 and
- *   64). Writes at most `cap` points to `out` (nullable) and their total to *count.
+ *   1, 2, 4 x every ring depth from 2 that fits one CTA's shared memory x both kernel
+ *   forms; FP64: 32 and 64). Writes at most `cap` points to `out` (nullable) and their
+ *   total to *count.
  * bsmm_batch_autotune: times the batch (bsmm_batch_set_args called before) under each
  *   candidate: every product is re-planned with that candidate's options (flop-count
  *   schedule; costs set earlier do not carry over), run once to warm up, then `reps`
@@ -366,7 +375,7 @@ typedef struct {
   int32_t cluster;    /* split modes: 1, 2 or 4 */
   int32_t stages;     /* split modes: 2..8 (0 = as many as fit) */
   int32_t fp64_tile;  /* FP64 mode: 32 or 64 */
-  int32_t reserved;   /* must be zero */
+  int32_t store_warps; /* split modes: 0, 1 or 2 (see bsmm_options.store_warps) */
 } bsmm_tune_point;
 bsmm_status bsmm_tune_space(int32_t mode, int32_t nslices, bsmm_tune_point* out, int32_t cap, int32_t* count);
 
@@ -393,6 +402,21 @@ bsmm_status bsmm_schedule_pieces(int64_t n, const double* cost, const int64_t* l
                                  double overhead, int32_t ksplit, int32_t* pieces);
 bsmm_status bsmm_batch_autotune(bsmm_batch_t batch, int32_t n, const bsmm_tune_point* candidates, int32_t reps,
                                 void* stream, int32_t* chosen, float* ms);
+
+/*
+ * bsmm_batch_autotune_cached: the tuning with a persistent cache. The cache is a JSON
+ * file at cache_path (format "bsmm-tune", version 1, one entry per line) keyed by the GPU's
+ * name, the mode and the slice count. When it holds an entry for this batch's key that is
+ * still one of bsmm_tune_space's candidates, the batch is re-planned under it without any
+ * timing (*from_cache = 1). Otherwise (no file, another format or version, no entry, a
+ * stale candidate) the batch is tuned over the whole bsmm_tune_space with `reps` timed runs
+ * per candidate (as bsmm_batch_autotune), and the fastest candidate and its time are
+ * written into the file, other keys kept (*from_cache = 0). *chosen (nullable) receives
+ * the candidate used. The file is replaced atomically; BSMM_ERR_INVALID when it cannot be
+ * written.
+ */
+bsmm_status bsmm_batch_autotune_cached(bsmm_batch_t batch, const char* cache_path, int32_t reps, void* stream,
+                                       bsmm_tune_point* chosen, int32_t* from_cache);
 
 /*
  * Learned task-cost model. The paper tolerates the load variation of nonuniform

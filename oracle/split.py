@@ -40,8 +40,9 @@ column has exponent 0 and zero slices. The contribution of a tile pair to elemen
 (ii, jj) is T[ii,jj] * 2^(e_A[ii] + e_B[jj] - beta*(s+1)); the exact sum and its single
 rounding are as above.
 
-Complex elements (complex128 arenas, tile mode, real alpha and beta): one exponent per
-tile over the real and imaginary parts together; both parts sliced with it; per tile pair
+Complex elements (complex128 arenas, real alpha and beta): one exponent per tile (per
+row of A and column of B with row/column scaling) over the real and imaginary parts
+together; both parts sliced with it; per tile pair
 the exact integers T_re = T(Ar,Br) - T(Ai,Bi) and T_im = T(Ar,Bi) + T(Ai,Br) (the complex
 product's definition), accumulated and rounded like a real element, each part on its own;
 the epilogue applies alpha and beta to each part.
@@ -90,12 +91,13 @@ def slice_tile(x: np.ndarray, s: int, beta: int = BETA_BITS, e=None):
     return e, slices, rho
 
 
-def slice_rows(x: np.ndarray, s: int, beta: int = BETA_BITS):
-    """Error-free slicing with one exponent per row. Returns (e per row, nonzero-row
-    flags, [N_1..N_s], rho_s residual in units of 2^e per row); an all-zero row has
-    e = 0 and zero slices."""
+def slice_rows(x: np.ndarray, s: int, beta: int = BETA_BITS, e=None):
+    """Error-free slicing with one exponent per row (its own, or the given ones). Returns
+    (e per row, nonzero-row flags, [N_1..N_s], rho_s residual in units of 2^e per row); an
+    all-zero row has e = 0 and zero slices."""
     x = np.asarray(x, np.float64)
-    e = np.array([tile_exponent(row) for row in x], np.int64) if x.shape[0] else np.zeros(0, np.int64)
+    if e is None:
+        e = np.array([tile_exponent(row) for row in x], np.int64) if x.shape[0] else np.zeros(0, np.int64)
     nz = np.array([bool(np.any(row != 0)) for row in x], bool) if x.shape[0] else np.zeros(0, bool)
     rho = np.ldexp(x, -e[:, None]) if x.size else x.copy()
     slices = []
@@ -266,8 +268,10 @@ def bsmm_split(prob_like, c_struct, C, c_off, s: int, beta: int = BETA_BITS, til
 
 
 def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
-    """bsmm_split with one exponent per row of A and per column of B."""
-    assert not np.iscomplexobj(prob_like.A), "complex elements take one exponent per tile"
+    """bsmm_split with one exponent per row of A and per column of B. Complex elements:
+    one exponent per row (column) over the real and imaginary parts together, both parts
+    sliced with it, the parts of the product as in tile mode."""
+    cplx = np.iscomplexobj(prob_like.A)
     r = np.asarray(prob_like.row_sizes, np.int64)
     c = np.asarray(prob_like.col_sizes, np.int64)
     q = np.asarray(prob_like.inner_sizes, np.int64)
@@ -279,13 +283,20 @@ def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
     b_off = prob_like.b_off.T if tb else prob_like.b_off
     cacheA, cacheB = {}, {}
 
+    def lines(x):  # per row of x: (e, nonzero, slices) or, complex, (e, nonzero, (re slices, im slices))
+        if not cplx:
+            e, nz, sl, _ = slice_rows(x, s, beta)
+            return e, nz, sl
+        both = np.concatenate([x.real, x.imag], axis=1)  # one exponent over both parts of a row
+        e, nz, _, _ = slice_rows(both, s, beta)
+        return e, nz, (slice_rows(x.real, s, beta, e)[2], slice_rows(x.imag, s, beta, e)[2])
+
     def a_sl(i, k):  # per row of A_ik: (e[r_i], nonzero[r_i], slices)
         if (i, k) not in cacheA:
             o = int(a_off[i, k])
             x = (prob_like.A[o:o + r[i] * q[k]].reshape(q[k], r[i]).T if ta
                  else prob_like.A[o:o + r[i] * q[k]].reshape(r[i], q[k]))
-            e, nz, sl, _ = slice_rows(x, s, beta)
-            cacheA[(i, k)] = (e, nz, sl)
+            cacheA[(i, k)] = lines(x)
         return cacheA[(i, k)]
 
     def b_sl(k, j):  # per column of B_kj: slicing of the transpose, slices turned back
@@ -293,30 +304,44 @@ def _bsmm_split_rows(prob_like, c_struct, C, c_off, s, beta, tiles):
             o = int(b_off[k, j])
             x = (prob_like.B[o:o + q[k] * c[j]].reshape(c[j], q[k]).T if tb
                  else prob_like.B[o:o + q[k] * c[j]].reshape(q[k], c[j]))
-            e, nz, sl, _ = slice_rows(x.T, s, beta)
-            cacheB[(k, j)] = (e, nz, [t.T for t in sl])
+            e, nz, sl = lines(x.T)
+            back = (lambda v: [t.T for t in v])
+            cacheB[(k, j)] = (e, nz, (back(sl[0]), back(sl[1])) if cplx else back(sl))
         return cacheB[(k, j)]
 
     todo = tiles if tiles is not None else [(i, j) for i in range(M) for j in range(N) if c_struct[i, j]]
     alpha, bet = float(prob_like.alpha), float(prob_like.beta)
     for (i, j) in todo:
-        terms = []  # (T, per-element binary position E_k[ii, jj])
+        terms = []  # (T per part, per-element binary position E_k[ii, jj])
         for k in range(K):
             if not (am[i, k] and bm[k, j]):
                 continue
             eA, _, na = a_sl(i, k)
             eB, _, nb = b_sl(k, j)
-            terms.append((pair_integer(na, nb, s, beta).astype(object),
-                          eA[:, None] + eB[None, :] - beta * (s + 1)))
+            if cplx:
+                (ar, ai), (br, bi) = na, nb
+                Ts = [pair_integer(ar, br, s, beta).astype(object) - pair_integer(ai, bi, s, beta).astype(object),
+                      pair_integer(ar, bi, s, beta).astype(object) + pair_integer(ai, br, s, beta).astype(object)]
+            else:
+                Ts = [pair_integer(na, nb, s, beta).astype(object)]
+            terms.append((Ts, eA[:, None] + eB[None, :] - beta * (s + 1)))
         # per element, the unit of the exact sum: the lowest position of its terms
         L = np.zeros((r[i], c[j]), np.int64)
         if terms:
             L = np.minimum.reduce([E for _, E in terms])
-        exact = np.zeros((r[i], c[j]), dtype=object)
-        exact[...] = 0
-        for T, E in terms:
-            if T.size:
-                exact = exact + T * np.left_shift(np.ones_like(E, dtype=object), (E - L).astype(object))
+        parts = [np.zeros((r[i], c[j]), dtype=object) for _ in range(2 if cplx else 1)]
+        for ex in parts:
+            ex[...] = 0
+        for Ts, E in terms:
+            sh = np.left_shift(np.ones_like(E, dtype=object), (E - L).astype(object))
+            for t, T in enumerate(Ts):
+                if T.size:
+                    parts[t] = parts[t] + T * sh
         o = int(c_off[i, j])
-        _finish(exact, L, C[o:o + r[i] * c[j]].reshape(r[i], c[j]), alpha, bet)
+        ct = C[o:o + r[i] * c[j]].reshape(r[i], c[j])
+        if cplx:
+            _finish(parts[0], L, ct.real, alpha, bet)
+            _finish(parts[1], L, ct.imag, alpha, bet)
+        else:
+            _finish(parts[0], L, ct, alpha, bet)
     return C

@@ -47,7 +47,7 @@ EXPORTED = [
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
     "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_selftest_wait", "bsmm_schedule_lpt",
     "bsmm_schedule_pieces", "bsmm_measure_rates", "bsmm_mlp_save", "bsmm_mlp_load", "bsmm_plan_cost_source",
-    "bsmm_execute_batch", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_execute_batch", "bsmm_batch_autotune_cached", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -63,7 +63,7 @@ class Options(ctypes.Structure):
                 ("record_timings", ctypes.c_int32), ("profile", ctypes.c_int32), ("cluster", ctypes.c_int32),
                 ("fp64_tile", ctypes.c_int32), ("stages", ctypes.c_int32), ("transa", ctypes.c_int32),
                 ("transb", ctypes.c_int32), ("split_scale", ctypes.c_int32), ("ksplit", ctypes.c_int32),
-                ("elem", ctypes.c_int32), ("model_path", ctypes.c_char_p)]
+                ("elem", ctypes.c_int32), ("store_warps", ctypes.c_int32), ("model_path", ctypes.c_char_p)]
 
 
 _lib = None
@@ -122,6 +122,7 @@ def lib():
         L.bsmm_plan_predict_costs.argtypes = [P, P, P]
         L.bsmm_mlp_save.argtypes = [P, ctypes.c_char_p]
         L.bsmm_execute_batch.argtypes = [i32, P, P, P, P, P, P, P, P, P, P]
+        L.bsmm_batch_autotune_cached.argtypes = [P, ctypes.c_char_p, i32, P, P, P]
         L.bsmm_mlp_load.argtypes = [ctypes.POINTER(P), ctypes.c_char_p]
         L.bsmm_plan_cost_source.argtypes = [P, P]
         L.bsmm_mlp_destroy.argtypes = [P]
@@ -202,7 +203,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
               nslices: int = 6, schedule: int = BSMM_SCHED_FLOPS, max_ctas: int = 0, debug_checks: int = 0,
               record_timings: int = 0, profile: int = 0, cluster: int = 0, fp64_tile: int = 0,
               stages: int = 0, transa: int = 0, transb: int = 0, split_scale: int = 0,
-              ksplit: int = 0, elem: int = BSMM_F64, model_path=None) -> Plan:
+              ksplit: int = 0, elem: int = BSMM_F64, model_path=None, store_warps: int = 0) -> Plan:
     r = _np(row_sizes, np.int32)
     c = _np(col_sizes, np.int32)
     q = _np(inner_sizes, np.int32)
@@ -219,6 +220,7 @@ def bsmm_plan(row_sizes, col_sizes, inner_sizes, a_mask, b_mask, c_mask=None, *,
     o.split_scale = split_scale
     o.ksplit = ksplit
     o.elem = elem
+    o.store_warps = store_warps
     path = None if model_path is None else os.fsencode(model_path)
     o.model_path = path  # read by bsmm_plan only; `path` keeps the bytes alive until it returns
     h = ctypes.c_void_p()
@@ -442,16 +444,18 @@ def bsmm_batch_destroy(batch: Batch):
 
 class TunePoint(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("stages", ctypes.c_int32), ("fp64_tile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("store_warps", ctypes.c_int32)]
 
 
 def bsmm_tune_space(mode: int, nslices: int = 6) -> list:
-    """The library's candidate list for a mode: dicts with cluster, stages, fp64_tile."""
+    """The library's candidate list for a mode: dicts with cluster, stages, fp64_tile,
+    store_warps."""
     n = ctypes.c_int32()
     _check(lib().bsmm_tune_space(mode, nslices, None, 0, ctypes.byref(n)))
     arr = (TunePoint * max(n.value, 1))()
     _check(lib().bsmm_tune_space(mode, nslices, arr, n.value, ctypes.byref(n)))
-    return [{"cluster": t.cluster, "stages": t.stages, "fp64_tile": t.fp64_tile} for t in arr[:n.value]]
+    return [{"cluster": t.cluster, "stages": t.stages, "fp64_tile": t.fp64_tile, "store_warps": t.store_warps}
+            for t in arr[:n.value]]
 
 
 def bsmm_batch_autotune(batch: Batch, candidates=None, reps: int = 3, stream=None):
@@ -461,12 +465,23 @@ def bsmm_batch_autotune(batch: Batch, candidates=None, reps: int = 3, stream=Non
         p0 = batch.plans[0]
         candidates = bsmm_tune_space(p0.mode, p0.nslices)
     n = len(candidates)
-    arr = (TunePoint * n)(*[TunePoint(c.get("cluster", 0), c.get("stages", 0), c.get("fp64_tile", 0), 0)
-                            for c in candidates])
+    arr = (TunePoint * n)(*[TunePoint(c.get("cluster", 0), c.get("stages", 0), c.get("fp64_tile", 0),
+                                      c.get("store_warps", 0)) for c in candidates])
     ms = (ctypes.c_float * n)()
     ch = ctypes.c_int32(-1)
     _check(lib().bsmm_batch_autotune(batch.handle, n, arr, reps, _stream(stream), ctypes.byref(ch), ms))
     return candidates[ch.value], list(ms)
+
+
+def bsmm_batch_autotune_cached(batch: Batch, cache_path, reps: int = 2, stream=None):
+    """Tune the batch with a persistent cache file (see include/bsmm.h); returns
+    (candidate dict, from_cache)."""
+    t = TunePoint()
+    fc = ctypes.c_int32()
+    _check(lib().bsmm_batch_autotune_cached(batch.handle, os.fsencode(cache_path), int(reps), _stream(stream),
+                                            ctypes.byref(t), ctypes.byref(fc)))
+    return {"cluster": t.cluster, "stages": t.stages, "fp64_tile": t.fp64_tile,
+            "store_warps": t.store_warps}, bool(fc.value)
 
 
 class Mlp:

@@ -17,7 +17,10 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
+#include <string>
 
 #include "bsmm_internal.h"
 
@@ -26,6 +29,7 @@ using namespace bsmm;
 struct bsmm_batch_s {
   std::vector<bsmm_plan_t> plans;
   int mode = 0, s = 0, cl = 1, stages = 0;
+  int sw = 0;  // split modes: the contraction launches use the kernel form with store warps
   int64_t n_units = 0;
   double useful_flops = 0.0;
   std::vector<int32_t> unit_prod, unit_local;
@@ -145,6 +149,7 @@ bsmm_status replan(const bsmm_batch_s* src, const bsmm_tune_point& t, std::vecto
     } else {
       o.cluster = t.cluster;
       o.stages = t.stages;
+      o.store_warps = t.store_warps;
     }
     bsmm_plan_t np = nullptr;
     const bsmm_status st = plan_build(&np, p->M, p->r.data(), p->N, p->c.data(), p->K, p->q.data(), p->am.data(),
@@ -157,6 +162,114 @@ bsmm_status replan(const bsmm_batch_s* src, const bsmm_tune_point& t, std::vecto
     out.push_back(np);
   }
   return BSMM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// The batch takes its products re-planned under candidate t, with the arguments already
+// set (the previous tables, and the plans of an earlier tuning, are released; the plans
+// given to bsmm_batch_create keep owning the slice workspace the new plans share).
+bsmm_status adopt(bsmm_batch_s* b, const bsmm_tune_point& t) {
+  const BatchArgs args(b);
+  std::vector<bsmm_plan_t> plans;
+  bsmm_status s = replan(b, t, plans);
+  bsmm_batch_t nb = nullptr;
+  if (s == BSMM_OK) s = bsmm_batch_create(&nb, (int32_t)plans.size(), plans.data());
+  if (s == BSMM_OK) s = args.set(nb, args.C);
+  if (s != BSMM_OK) {
+    if (nb) bsmm_batch_destroy(nb);
+    for (bsmm_plan_t q : plans) bsmm_destroy(q);
+    return s;
+  }
+  nb->owned = plans;
+  std::swap(*b, *nb);
+  free_batch(nb);
+  return BSMM_OK;
+}
+
+// The tuning cache: a JSON file, one entry per line, keyed by GPU, mode and slice count.
+//   {"format": "bsmm-tune", "version": 1, "entries": [
+//    {"key": "<gpu>|<mode>|s=<n>", "cluster": c, "stages": t, "fp64_tile": f, "store_warps": w,
+//     "ms_x1000": the candidate's median time in microseconds},
+//    ...
+//   ]}
+constexpr int kTuneCacheVersion = 1;
+
+struct TuneEntry {
+  std::string key;
+  bsmm_tune_point t{};
+  double ms = 0.0;
+};
+
+bool json_int(const std::string& line, const char* name, long long& v) {
+  const std::string pat = std::string("\"") + name + "\": ";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return false;
+  char* end = nullptr;
+  v = std::strtoll(line.c_str() + at + pat.size(), &end, 10);
+  return end != line.c_str() + at + pat.size();
+}
+
+// the entries of a cache file of this version (none for a missing, foreign or older file)
+std::vector<TuneEntry> read_tune_cache(const char* path) {
+  std::vector<TuneEntry> out;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return out;
+  std::string text;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (1u << 22)) text.append(buf, n);
+  std::fclose(f);
+  long long ver = 0;
+  if (text.find("\"format\": \"bsmm-tune\"") == std::string::npos || !json_int(text, "version", ver) ||
+      ver != kTuneCacheVersion)
+    return out;
+  size_t pos = 0;
+  while (pos < text.size()) {
+    size_t eol = text.find('\n', pos);
+    if (eol == std::string::npos) eol = text.size();
+    const std::string line = text.substr(pos, eol - pos);
+    pos = eol + 1;
+    const size_t k = line.find("\"key\": \"");
+    if (k == std::string::npos) continue;
+    const size_t k0 = k + 8, k1 = line.find('"', k0);
+    if (k1 == std::string::npos) continue;
+    TuneEntry e;
+    e.key = line.substr(k0, k1 - k0);
+    long long cl = 0, st = 0, ft = 0, sw = 0, ms = 0;
+    if (!json_int(line, "cluster", cl) || !json_int(line, "stages", st) || !json_int(line, "fp64_tile", ft) ||
+        !json_int(line, "store_warps", sw))
+      continue;
+    json_int(line, "ms_x1000", ms);
+    e.t = {(int32_t)cl, (int32_t)st, (int32_t)ft, (int32_t)sw};
+    e.ms = ms / 1000.0;
+    out.push_back(e);
+  }
+  return out;
+}
+
+bool write_tune_cache(const char* path, const std::vector<TuneEntry>& entries) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  std::fprintf(f, "{\"format\": \"bsmm-tune\", \"version\": %d, \"entries\": [\n", kTuneCacheVersion);
+  for (size_t i = 0; i < entries.size(); i++) {
+    const TuneEntry& e = entries[i];
+    std::fprintf(f,
+                 " {\"key\": \"%s\", \"cluster\": %d, \"stages\": %d, \"fp64_tile\": %d, \"store_warps\": %d, "
+                 "\"ms_x1000\": %lld}%s\n",
+                 e.key.c_str(), e.t.cluster, e.t.stages, e.t.fp64_tile, e.t.store_warps,
+                 (long long)std::llround(e.ms * 1000.0), i + 1 < entries.size() ? "," : "");
+  }
+  std::fprintf(f, "]}\n");
+  const bool ok = std::fclose(f) == 0;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return false;
+  }
+  return true;
 }
 
 }  // namespace
@@ -198,6 +311,18 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   }
   b->n_units = (int64_t)b->unit_prod.size();
   b->prod_begin.push_back(b->n_units);
+  // the kernel form of the batch's contraction launches: the one all plans ask for, else
+  // by the units' mean inner depth over the whole batch
+  {
+    double depth = 0.0;
+    bool same = true;
+    for (int32_t i = 0; i < count; i++) {
+      depth += plans[i]->unit_depth * (double)plans[i]->n_units;
+      same = same && plans[i]->opt.store_warps == p0->opt.store_warps;
+    }
+    const int32_t sw = same ? p0->opt.store_warps : 0;
+    b->sw = sw == 2 ? 1 : sw == 1 ? 0 : (depth < kStoreWarpDepth * (double)std::max<int64_t>(1, b->n_units) ? 1 : 0);
+  }
   // one product's default bin count describes the machine (CTAs or clusters)
   bsmm_plan_s tmp_view = bsmm_plan_s();
   tmp_view.opt = p0->opt;
@@ -206,6 +331,7 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   tmp_view.s = p0->s;
   tmp_view.cl = p0->cl;
   tmp_view.stages = p0->stages;
+  tmp_view.sw = b->sw;
   tmp_view.n_units = std::max<int64_t>(1, b->n_units);
   b->bins = default_bins(&tmp_view);
   // waves (see bsmm_batch_s)
@@ -308,6 +434,7 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
       }
       if (e != cudaSuccess) break;
       SplitArgs a = b->sargs[0];
+      a.sw = b->sw;
       a.sched_ptr = sp;
       a.sched_units = (const int32_t*)b->d_sched_units.p;
       a.prods = (const SplitArgs*)b->d_prods.p;
@@ -446,7 +573,8 @@ bsmm_status bsmm_tune_space(int32_t mode, int32_t nslices, bsmm_tune_point* out,
     if (nslices < 1 || nslices > kSplitMaxS) return set_error("nslices must be in 1..6"), BSMM_ERR_INVALID;
     for (int cl : {1, 2, 4})
       for (int st = 2; st <= 8; st++)
-        if (split_smem_bytes(nslices, split_tile_n(nslices), st) <= kMaxSmemPerCta) v.push_back({cl, st, 0, 0});
+        for (int sw : {1, 2})
+          if (split_smem_bytes(nslices, split_tile_n(nslices), st) <= kMaxSmemPerCta) v.push_back({cl, st, 0, sw});
   } else {
     return set_error("unknown mode"), BSMM_ERR_INVALID;
   }
@@ -462,10 +590,11 @@ bsmm_status bsmm_batch_autotune(bsmm_batch_t b, int32_t n, const bsmm_tune_point
   if (!b->args_set) return set_error("bsmm_batch_set_args has not been called"), BSMM_ERR_INVALID;
   for (int32_t c = 0; c < n; c++) {
     const bsmm_tune_point& t = cand[c];
-    const bool ok = b->mode == BSMM_FP64 ? (t.cluster == 0 && t.stages == 0 && (t.fp64_tile == 32 || t.fp64_tile == 64))
-                                         : (t.fp64_tile == 0 && (t.cluster == 1 || t.cluster == 2 || t.cluster == 4) &&
-                                            (t.stages == 0 || (t.stages >= 2 && t.stages <= 8)));
-    if (!ok || t.reserved) return set_error("candidate " + std::to_string(c) + " does not fit the batch's mode"), BSMM_ERR_INVALID;
+    const bool ok = b->mode == BSMM_FP64
+                        ? (t.cluster == 0 && t.stages == 0 && t.store_warps == 0 && (t.fp64_tile == 32 || t.fp64_tile == 64))
+                        : (t.fp64_tile == 0 && (t.cluster == 1 || t.cluster == 2 || t.cluster == 4) &&
+                           (t.stages == 0 || (t.stages >= 2 && t.stages <= 8)) && t.store_warps >= 0 && t.store_warps <= 2);
+    if (!ok) return set_error("candidate " + std::to_string(c) + " does not fit the batch's mode"), BSMM_ERR_INVALID;
   }
   cudaStream_t st = (cudaStream_t)stream;
   const BatchArgs args(b);
@@ -551,24 +680,56 @@ bsmm_status bsmm_batch_autotune(bsmm_batch_t b, int32_t n, const bsmm_tune_point
   cleanup_scratch();
   if (res != BSMM_OK) return res;
   if (best < 0) return set_error("no candidate fits"), BSMM_ERR_UNSUPPORTED;
-  // the batch takes its products re-planned under the fastest candidate
-  std::vector<bsmm_plan_t> plans;
-  bsmm_status s = replan(b, cand[best], plans);
-  bsmm_batch_t nb = nullptr;
-  if (s == BSMM_OK) s = bsmm_batch_create(&nb, (int32_t)count, plans.data());
-  if (s == BSMM_OK) s = args.set(nb, args.C);
-  if (s != BSMM_OK) {
-    if (nb) bsmm_batch_destroy(nb);
-    for (bsmm_plan_t q : plans) bsmm_destroy(q);
-    return s;
-  }
-  nb->owned = plans;
-  std::swap(*b, *nb);
-  // nb now holds the batch's previous tables (and the plans of an earlier autotune),
-  // which are released; the plans given to bsmm_batch_create keep owning the slice
-  // workspace the new plans share
-  free_batch(nb);
+  const bsmm_status s = adopt(b, cand[best]);
+  if (s != BSMM_OK) return s;
   if (chosen) *chosen = best;
+  return BSMM_OK;
+}
+
+bsmm_status bsmm_batch_autotune_cached(bsmm_batch_t b, const char* cache_path, int32_t reps, void* stream,
+                                       bsmm_tune_point* chosen, int32_t* from_cache) {
+  if (!b || !cache_path || !*cache_path || reps < 1)
+    return set_error("batch, cache path and reps >= 1 are required"), BSMM_ERR_INVALID;
+  if (!b->args_set) return set_error("bsmm_batch_set_args has not been called"), BSMM_ERR_INVALID;
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, b->plans[0]->device) != cudaSuccess)
+    return set_error("cudaGetDeviceProperties failed"), BSMM_ERR_CUDA;
+  std::string gpu = prop.name;
+  for (char& ch : gpu)
+    if (ch == '"' || ch == '\\' || ch == '|' || ch == '\n') ch = '_';
+  const char* mode = b->mode == BSMM_FP64 ? "fp64" : b->mode == BSMM_SPLIT_FP16 ? "split_fp16" : "split_bf16";
+  const std::string key = gpu + "|" + mode + "|s=" + std::to_string(b->mode == BSMM_FP64 ? 0 : b->s);
+  std::vector<TuneEntry> entries = read_tune_cache(cache_path);
+  int32_t n = 0;
+  bsmm_status s = bsmm_tune_space(b->mode, b->mode == BSMM_FP64 ? 6 : b->s, nullptr, 0, &n);
+  if (s != BSMM_OK) return s;
+  std::vector<bsmm_tune_point> space(n);
+  bsmm_tune_space(b->mode, b->mode == BSMM_FP64 ? 6 : b->s, space.data(), n, &n);
+  for (const TuneEntry& e : entries) {
+    if (e.key != key) continue;
+    // a cached choice is used only while it is still one of the library's candidates
+    const bool valid = std::any_of(space.begin(), space.end(), [&](const bsmm_tune_point& t) {
+      return t.cluster == e.t.cluster && t.stages == e.t.stages && t.fp64_tile == e.t.fp64_tile &&
+             t.store_warps == e.t.store_warps;
+    });
+    if (!valid) break;
+    s = adopt(b, e.t);
+    if (s != BSMM_OK) return s;
+    if (chosen) *chosen = e.t;
+    if (from_cache) *from_cache = 1;
+    return BSMM_OK;
+  }
+  std::vector<float> ms(n);
+  int32_t best = -1;
+  s = bsmm_batch_autotune(b, n, space.data(), reps, stream, &best, ms.data());
+  if (s != BSMM_OK) return s;
+  entries.erase(std::remove_if(entries.begin(), entries.end(), [&](const TuneEntry& e) { return e.key == key; }),
+                entries.end());
+  entries.push_back({key, space[best], ms[best]});
+  if (!write_tune_cache(cache_path, entries))
+    return set_error(std::string("cannot write the tuning cache ") + cache_path), BSMM_ERR_INVALID;
+  if (chosen) *chosen = space[best];
+  if (from_cache) *from_cache = 0;
   return BSMM_OK;
 }
 

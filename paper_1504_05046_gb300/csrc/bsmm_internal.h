@@ -41,9 +41,13 @@ constexpr size_t kSplitBarBytes = 512;          // mbarriers, TMEM slot, flags a
 constexpr int16_t kNonUniform = 0x7FFF;         // scale-class sentinel (offsets are <= 0)
 constexpr int32_t kZeroLine = -(1 << 20);       // exponent of an all-zero row or column
 int split_max_depth(int s);
-constexpr int kSplitDefaultCluster = 2;
-// Largest number of groups of `cl` contraction CTAs that can be resident at once.
-int split_max_clusters(int s, int cl, int stages);
+constexpr int kSplitDefaultCluster = 1;  // groups of one: no CTA idles on a neighbour's empty column block
+// Largest number of groups of `cl` contraction CTAs that can be resident at once (the
+// kernel form with store warps when sw is set).
+int split_max_clusters(int s, int cl, int stages, bool sw);
+// The planner's choice of the contraction kernel's form: store warps when a unit's mean
+// inner depth (its own k blocks' sizes summed) is below this many elements.
+constexpr double kStoreWarpDepth = 8192.0;
 
 // Device arrays owned by a plan.
 struct DevBuf {
@@ -118,7 +122,8 @@ struct Fp64Args {
 // Arguments of the split-mode kernels.
 struct SplitArgs {
   int32_t M, N, K, s, tn, stages, fp16;
-  int32_t cl, CBG;          // CTAs per cluster; column-block groups (units are (rb, group))
+  int32_t cl, CBG;          // CTAs per column-block group; groups (units are (rb, group))
+  int32_t sw;               // the contraction kernel's form: 1 = with C store warps
   int64_t Mtot, Ntot;
   int32_t RB, CB, kwords;
   const int32_t* r;
@@ -291,6 +296,8 @@ struct bsmm_plan_s {
 
   // split geometry
   int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0, cl = 1, CBG = 0;
+  int sw = 0;                // contraction kernel with C store warps
+  double unit_depth = 0.0;   // mean inner depth of the work units (split modes)
   int64_t Mtot = 0, Ntot = 0, colexp_ld = 0;
   int64_t apk_bytes = 0, bpk_bytes = 0;
 

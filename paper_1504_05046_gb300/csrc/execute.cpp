@@ -111,6 +111,7 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const void* A, 
   a.sched_units = (const int32_t*)p->d_sched_units.p;
   a.alpha = alpha;
   a.beta = beta;
+  a.sw = p->sw;
   a.f32 = p->opt.elem == BSMM_F32;
   a.cplx = p->opt.elem == BSMM_C128;
   a.A = a.f32 ? nullptr : (const double*)A;

@@ -26,6 +26,8 @@
 // reduction kernel adds the partials in piece order and applies the epilogue.
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bsmm_internal.h"
 
 namespace bsmm {
@@ -446,10 +448,12 @@ int fp64_ctas_per_sm(int tile) {
 // One product's launch (a batch launches its products' reductions itself).
 cudaError_t launch_fp64(const Fp64Args& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
   if (ev) cudaEventRecord(ev[0], st);
+  nvtxRangePushA("bsmm fp64: tile tasks");  // (a timeline tool's name for the phase)
   if (a.tile == 32)
     fp64_tile_kernel<32><<<ctas, 64, 0, st>>>(a);
   else
     fp64_tile_kernel<64><<<ctas, 256, 0, st>>>(a);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[1], st);
   int k = 1;
   cudaError_t e = cudaGetLastError();

@@ -185,6 +185,7 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
   a.presB = t->presB;
   a.presBg = t->presB;  // clusters of one CTA: a column-block group is one column block
   a.cl = 1;
+  a.sw = 0;  // the kernel form without store warps
   a.CBG = CB;
   a.apk_off = t->apk_off;
   a.bpk_off = t->bpk_off;

@@ -117,7 +117,7 @@ int machine_bins(const bsmm_plan_s* p) {
   if (p->opt.mode == BSMM_FP64)
     c = (int64_t)p->sms * std::max(1, fp64_ctas_per_sm(p->f64_tile));
   else
-    c = std::max(1, split_max_clusters(p->s, p->cl, p->stages));
+    c = std::max(1, split_max_clusters(p->s, p->cl, p->stages, p->sw != 0));
   if (p->opt.max_ctas > 0) c = std::min<int64_t>(c, p->opt.max_ctas);
   return (int)std::max<int64_t>(1, c);
 }
@@ -497,6 +497,16 @@ bsmm_status plan_split(bsmm_plan_s* p) {
     int nrt, nct;
     bcost[u] = std::max(region_flops(base[u].rb, base[u].cb, 0, K, nrt, nct), 1.0);
   }
+  // the contraction kernel's form: C store warps when units are short (the unit end's
+  // rounding and store then weigh on the epilogue), decided by the units' mean inner depth
+  {
+    double depth = 0.0;
+    for (size_t u = 0; u < base.size(); u++)
+      for (int64_t x = bk_ptr[u]; x < bk_ptr[u + 1]; x++) depth += p->q[bk[x]];
+    p->unit_depth = base.empty() ? 0.0 : depth / (double)base.size();
+    const int32_t sw = p->opt.store_warps;
+    p->sw = sw == 2 ? 1 : sw == 1 ? 0 : (p->unit_depth < kStoreWarpDepth ? 1 : 0);
+  }
   const std::vector<int32_t> np =
       choose_pieces(bcost, blen, machine_bins(p), kSplitPieceOverhead, p->opt.ksplit == -1 ? 0 : p->opt.ksplit);
   std::vector<int32_t> slot0(base.size(), -1);
@@ -640,12 +650,11 @@ bsmm_status validate_options(const bsmm_options& o) {
     return set_error("transa and transb must be 0 or 1"), BSMM_ERR_INVALID;
   if (o.split_scale != 0 && o.split_scale != 1) return set_error("split_scale must be 0 or 1"), BSMM_ERR_INVALID;
   if (o.ksplit < -1 || o.ksplit > 65536) return set_error("ksplit must be in -1..65536"), BSMM_ERR_INVALID;
+  if (o.store_warps < 0 || o.store_warps > 2) return set_error("store_warps must be 0, 1 or 2"), BSMM_ERR_INVALID;
   if (o.elem != BSMM_F64 && o.elem != BSMM_F32 && o.elem != BSMM_C128)
     return set_error("unknown element type"), BSMM_ERR_INVALID;
   if (o.elem != BSMM_F64 && o.mode == BSMM_FP64)
     return set_error("float32 and complex elements take a split mode"), BSMM_ERR_UNSUPPORTED;
-  if (o.elem == BSMM_C128 && o.split_scale)
-    return set_error("complex elements take one scale per tile"), BSMM_ERR_UNSUPPORTED;
   return BSMM_OK;
 }
 

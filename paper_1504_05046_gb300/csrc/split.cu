@@ -45,6 +45,8 @@
 #include <cuda_fp16.h>
 #include <math_constants.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <climits>
 #include <cstdint>
 #include <type_traits>
@@ -61,18 +63,26 @@ constexpr int kEpiThreads = kSplitEpiWarps * 32;
 // their N, so the slice products of a step are spread over kMmaWarps issuing warps.
 constexpr int kMmaWarps = 3;
 constexpr int kEpiWarp0 = 1 + kMmaWarps;                 // first epilogue warp (warpgroups 1 and 2)
-constexpr int kStoreWarps = 4;                           // C store warps (warpgroup 3)
+constexpr int kStoreWarps = 4;                           // C store warps (warpgroup 3), when present
 constexpr int kStoreWarp0 = kEpiWarp0 + kSplitEpiWarps;  // first store warp
-constexpr int kThreads = 32 * (kStoreWarp0 + kStoreWarps);
-// Register split with setmaxnreg: the CTA is launched with kThreads x kRegsLaunch registers
-// (the whole register file); the producer and MMA warps (warpgroup 0) and the store warps
-// (warpgroup 3) give registers back and the epilogue warps take them. The shares add up to
-// the launch's total exactly, so every setmaxnreg.inc is satisfiable.
-constexpr int kRegsLaunch = 65536 / kThreads;  // 128
+// Two forms of the contraction kernel: without store warps (the epilogue warps store each
+// unit's C themselves) and with them (the C store of a unit runs while the epilogue drains
+// the next one; it pays off when units are short).
+template <bool SW>
+constexpr int threads_of() {
+  return 32 * (kStoreWarp0 + (SW ? kStoreWarps : 0));
+}
+// Register split with setmaxnreg (form with store warps): the CTA is launched with
+// kThreadsSW x kRegsLaunch registers (the whole register file); the producer and MMA warps
+// (warpgroup 0) and the store warps (warpgroup 3) give registers back and the epilogue warps
+// take them. The shares add up to the launch's total exactly, so every setmaxnreg.inc is
+// satisfiable.
+constexpr int kThreadsSW = threads_of<true>();  // 512
+constexpr int kRegsLaunch = 65536 / kThreadsSW;  // 128
 constexpr int kRegsCtl = 80, kRegsEpi = 168, kRegsStore = 96;
 static_assert(kEpiWarp0 % 4 == 0 && kStoreWarp0 % 4 == 0, "roles start on warpgroup boundaries");
 static_assert(4 * 32 * kRegsCtl + kSplitEpiWarps * 32 * kRegsEpi + kStoreWarps * 32 * kRegsStore ==
-                  kThreads * kRegsLaunch,
+                  kThreadsSW * kRegsLaunch,
               "the warpgroups' register shares must add up to the launch's registers");
 constexpr uint32_t kTmemCols = 512;
 constexpr int kAChunk = kSplitBM * kSplitKC * 2;  // bytes of one slice of a 128x32 A chunk
@@ -370,6 +380,33 @@ __global__ void __launch_bounds__(256) split_exp_lines_kernel(SplitArgs a) {
   // element u of line l: A row l is (l, u), B column l is (u, l); stored transposed or not
   const int64_t lstep = isA ? (tr ? 1 : cols) : (tr ? rows : 1);
   const int64_t ustep = isA ? (tr ? rows : 1) : (tr ? 1 : cols);
+  if (a.cplx) {
+    // complex elements: the plan's inner and column tilings count both parts, so an A tile
+    // is rows x (2 qc) and a B tile (2 qc) x (2 cc) of the real product; a line's exponent
+    // is that of the complex row (column) over both parts, and the B column cl and its
+    // partner cl + cc (the same complex column's other part) share it
+    const int qc = (isA ? cols : rows) >> 1;
+    const int nlc = isA ? rows : cols >> 1;  // complex lines
+    const int64_t cl_step = isA ? (tr ? 1 : qc) : (tr ? qc : 1);           // between lines
+    const int64_t cu_step = isA ? (tr ? rows : 1) : (tr ? 1 : (cols >> 1));  // along a line
+    const double* xc = (isA ? a.A : a.B) + 2 * off;
+    for (int l = threadIdx.x; l < nlc; l += blockDim.x) {
+      unsigned long long lm = 0;
+      const double* line = xc + 2 * (l * cl_step);
+      for (int u = 0; u < qc; u++) {
+        lm = max(lm, mag_bits(__ldg(line + 2 * u * cu_step)));
+        lm = max(lm, mag_bits(__ldg(line + 2 * u * cu_step + 1)));
+      }
+      const int e = (lm > 0 && lm < kInfBits) ? exponent_above(lm) : kZeroLine;
+      if (isA) {
+        a.eArow[(int64_t)k_or_j * a.Mtot + a.ro[i_or_k] + l] = e;
+      } else {
+        a.eBcol[(int64_t)i_or_k * a.Ntot + a.co[k_or_j] + l] = e;
+        a.eBcol[(int64_t)i_or_k * a.Ntot + a.co[k_or_j] + nlc + l] = e;
+      }
+    }
+    return;
+  }
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     int e = kZeroLine;
     if (a.f32) {
@@ -1207,12 +1244,12 @@ struct ChunkCursor {
   }
 };
 
-// CL consecutive CTAs form a column-block group: they take the same units (a 128-row
-// block times CL column blocks), each its own column block, at about the same time, so
+// a.cl consecutive CTAs form a column-block group: they take the same units (a 128-row
+// block times cl column blocks), each its own column block, at about the same time, so
 // the A panel they all read is served from L2. Every CTA loads its own operands; no CTA
 // reads or signals another's shared memory.
-template <int S, int TN, int CL>
-__global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_constant__ SplitArgs a) {
+template <int S, int TN, bool SW>
+__global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __grid_constant__ SplitArgs a) {
   constexpr int TH = TN / 2;                    // columns per epilogue thread
   constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
   constexpr int B_STAGE = S * TN * kSplitKC * 2;
@@ -1244,6 +1281,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   double* cstage = (double*)(smem + (size_t)stages * STAGE + kSplitBarBytes);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int CL = a.cl;
   const int cta = blockIdx.x / CL;   // the group: schedules are per group
   const int rank = blockIdx.x % CL;  // this CTA's column block within the group's units
   const int ubeg = a.sched_ptr[cta], uend = a.sched_ptr[cta + 1];
@@ -1273,10 +1311,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  // Roles by warpgroup; each warpgroup first takes its register share (every warp of the
-  // warpgroup executes the setmaxnreg, and it dominates the role's code).
+  // Roles by warpgroup; with store warps each warpgroup first takes its register share
+  // (every warp of the warpgroup executes the setmaxnreg, and it dominates the role's code).
   if (warp < kEpiWarp0) {
-    regs_dec<kRegsCtl>();
+    if constexpr (SW) regs_dec<kRegsCtl>();
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
@@ -1430,7 +1468,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
     }
   }
   } else if (warp < kStoreWarp0) {
-    regs_inc<kRegsEpi>();
+    if constexpr (SW) regs_inc<kRegsEpi>();
     // ------------------------------------------------------------ epilogue warps
     const int ew = warp - kEpiWarp0;   // 0..7
     const int quad = warp & 3;         // TMEM lane quadrant this warp may access
@@ -1551,10 +1589,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
       // so all eight leave the unit loop together)
       if (un.slot < 0) {
         // C = alpha*fl(sum) + beta*C on the unit's elements that lie in S_C tiles: each
-        // thread rounds its row's sums to doubles into the staging buffer once the store
-        // warps are done with the previous unit's, and hands it to them; the C store then
-        // runs while this warp drains the next unit.
-        if (ok && !wait_warp(cfree, (ncs & 1) ^ 1, abort_flag, a.err)) ok = false;
+        // thread rounds its row's sums to doubles into the staging buffer (with store warps,
+        // once they are done with the previous unit's); then whole rows are stored, lane =
+        // column, so a store instruction writes one or two contiguous row segments. With
+        // store warps the store runs while this warp drains the next unit.
+        if constexpr (SW)
+          if (ok && !wait_warp(cfree, (ncs & 1) ^ 1, abort_flag, a.err)) ok = false;
         if (ok) {
           // the accumulator's unit 2^L: per row block and column block of tiles, or per row
           // and column with row/column scaling
@@ -1565,8 +1605,20 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
           else
             round_row<TH, false>(acc, srow, P, row_ok, n0, Lrow);
         }
-        mbar_arrive(cready);  // every thread: its row is in cstage (release)
-        ncs++;
+        if constexpr (SW) {
+          mbar_arrive(cready);  // every thread: its row is in cstage (release)
+          ncs++;
+        } else {
+          asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+          if (ok && !*abort_flag) {
+            if (P.f32)
+              store_region<TN, kSplitEpiWarps, 1>(P, cstage, un.rb, cb, ew, lane, a.err);
+            else if (P.cplx)
+              store_region<TN, kSplitEpiWarps, 2>(P, cstage, un.rb, cb, ew, lane, a.err);
+            else
+              store_region<TN, kSplitEpiWarps, 0>(P, cstage, un.rb, cb, ew, lane, a.err);
+          }
+        }
       } else if (ok) {
         // a piece of a split k-list: its exact partial sums go to the workspace (column-
         // major, so the 32 rows of a warp write 512 contiguous bytes per column)
@@ -1574,7 +1626,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
 #pragma unroll
         for (int c = 0; c < TH; c++) dst[(size_t)c * kSplitBM] = make_uint4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
       }
-      ok = epi_all(ok);  // every epilogue warp has the same outcome
+      ok = epi_all(ok);  // every epilogue warp has the same outcome (and, without store warps,
+                         // cstage is free again)
       if (!ok) break;
       if (a.timings && rank == 0) {
         if (ew == 0 && lane == 0) {
@@ -1583,7 +1636,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_mma_kernel(const __grid_con
         }
       }
     }
-  } else {
+  } else if constexpr (SW) {
     regs_dec<kRegsStore>();
     // ------------------------------------------------------------ C store warps
     // The units' rounded results from the staging buffer to C, in the epilogue's unit
@@ -1683,57 +1736,50 @@ __global__ void __launch_bounds__(96) wait_selftest_kernel(int32_t* err, int64_t
   __syncthreads();
 }
 
-template <int S, int TN, int CL>
+template <int S, int TN, bool SW>
 cudaError_t launch_mma(const SplitArgs& a, int groups, cudaStream_t st) {
   const size_t smem = split_smem_bytes(S, TN, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  // the register split assumes exactly kRegsLaunch registers per thread at launch (a
-  // smaller allocation could not satisfy the epilogue's setmaxnreg.inc): refuse otherwise
-  cudaFuncAttributes fa{};
-  e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, CL>);
-  if (e != cudaSuccess) return e;
-  if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
-  split_mma_kernel<S, TN, CL><<<(unsigned)(groups * CL), kThreads, smem, st>>>(a);
+  if constexpr (SW) {
+    // the register split assumes exactly kRegsLaunch registers per thread at launch (a
+    // smaller allocation could not satisfy the epilogue's setmaxnreg.inc): refuse otherwise
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, SW>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
+  }
+  split_mma_kernel<S, TN, SW><<<(unsigned)(groups * a.cl), threads_of<SW>(), smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t launch_mma_cl(const SplitArgs& a, int clusters, cudaStream_t st) {
-  switch (a.cl) {
-    case 1: return launch_mma<S, 32, 1>(a, clusters, st);
-    case 2: return launch_mma<S, 32, 2>(a, clusters, st);
-    case 4: return launch_mma<S, 32, 4>(a, clusters, st);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_mma_sw(const SplitArgs& a, int groups, cudaStream_t st) {
+  if (a.cl != 1 && a.cl != 2 && a.cl != 4) return cudaErrorInvalidValue;
+  return a.sw ? launch_mma<S, 32, true>(a, groups, st) : launch_mma<S, 32, false>(a, groups, st);
 }
 
-// Groups of CL CTAs that are resident at once: the persistent grid (one CTA per SM at
+// Groups of cl CTAs that are resident at once: the persistent grid (one CTA per SM at
 // this shared-memory size) divided into groups.
-template <int S, int CL>
-int max_clusters_for(int stages) {
+template <int S, bool SW>
+int max_groups_for(int cl, int stages) {
   const size_t smem = split_smem_bytes(S, 32, stages);
-  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, CL>, kThreads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, SW>, threads_of<SW>(), smem) !=
       cudaSuccess)
     return 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
-  return per_sm * sms / CL;
+  return cl > 0 ? per_sm * sms / cl : 0;
 }
 
 template <int S>
-int max_clusters_s(int cl, int stages) {
-  switch (cl) {
-    case 1: return max_clusters_for<S, 1>(stages);
-    case 2: return max_clusters_for<S, 2>(stages);
-    case 4: return max_clusters_for<S, 4>(stages);
-    default: return 0;
-  }
+int max_groups_s(int cl, int stages, bool sw) {
+  return sw ? max_groups_for<S, true>(cl, stages) : max_groups_for<S, false>(cl, stages);
 }
 
 }  // namespace
@@ -1796,15 +1842,22 @@ cudaError_t launch_split_prep(const SplitArgs& a, cudaStream_t st, cudaEvent_t* 
   return cudaGetLastError();
 }
 
+// NVTX ranges name the phases of a product for a timeline tool (host-side enqueue spans).
 cudaError_t launch_split(const SplitArgs& a, int ctas, cudaStream_t st, cudaEvent_t* ev, int* nk) {
   int k = 0;
   if (ev) cudaEventRecord(ev[0], st);
+  nvtxRangePushA("bsmm split: exponents, scales, slices");
   cudaError_t e = launch_split_prep(a, st, ev, &k);
+  nvtxRangePop();
   if (e != cudaSuccess) return e;
+  nvtxRangePushA("bsmm split: contraction");
   e = launch_split_mma(a, ctas, st);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[++k], st);
   if (e == cudaSuccess && !a.prods && a.n_red > 0) {  // a batch launches its products' reductions
+    nvtxRangePushA("bsmm split: split-k reduction");
     e = launch_split_reduce(a, st);
+    nvtxRangePop();
     if (ev) cudaEventRecord(ev[++k], st);
   }
   if (nk) *nk = k;
@@ -1824,26 +1877,26 @@ cudaError_t launch_split_reduce(const SplitArgs& a, cudaStream_t st) {
 
 cudaError_t launch_split_mma(const SplitArgs& a, int ctas, cudaStream_t st) {
   cudaError_t e;
-  switch (a.s) {  // `ctas` counts clusters of a.cl CTAs
-    case 1: e = launch_mma_cl<1>(a, ctas, st); break;
-    case 2: e = launch_mma_cl<2>(a, ctas, st); break;
-    case 3: e = launch_mma_cl<3>(a, ctas, st); break;
-    case 4: e = launch_mma_cl<4>(a, ctas, st); break;
-    case 5: e = launch_mma_cl<5>(a, ctas, st); break;
-    case 6: e = launch_mma_cl<6>(a, ctas, st); break;
+  switch (a.s) {  // `ctas` counts groups of a.cl CTAs
+    case 1: e = launch_mma_sw<1>(a, ctas, st); break;
+    case 2: e = launch_mma_sw<2>(a, ctas, st); break;
+    case 3: e = launch_mma_sw<3>(a, ctas, st); break;
+    case 4: e = launch_mma_sw<4>(a, ctas, st); break;
+    case 5: e = launch_mma_sw<5>(a, ctas, st); break;
+    case 6: e = launch_mma_sw<6>(a, ctas, st); break;
     default: e = cudaErrorInvalidValue;
   }
   return e;
 }
 
-int split_max_clusters(int s, int cl, int stages) {
+int split_max_clusters(int s, int cl, int stages, bool sw) {
   switch (s) {
-    case 1: return max_clusters_s<1>(cl, stages);
-    case 2: return max_clusters_s<2>(cl, stages);
-    case 3: return max_clusters_s<3>(cl, stages);
-    case 4: return max_clusters_s<4>(cl, stages);
-    case 5: return max_clusters_s<5>(cl, stages);
-    case 6: return max_clusters_s<6>(cl, stages);
+    case 1: return max_groups_s<1>(cl, stages, sw);
+    case 2: return max_groups_s<2>(cl, stages, sw);
+    case 3: return max_groups_s<3>(cl, stages, sw);
+    case 4: return max_groups_s<4>(cl, stages, sw);
+    case 5: return max_groups_s<5>(cl, stages, sw);
+    case 6: return max_groups_s<6>(cl, stages, sw);
     default: return 0;
   }
 }

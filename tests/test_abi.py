@@ -78,14 +78,16 @@ def test_plan_without_gpu_reports_cuda_error():
 def test_tune_space_lists_fitting_candidates():
     """The autotuner's candidate list is host logic: FP64 tries both sub-tile edges;
     the split modes try every cluster size with every ring depth that fits 227 KB next to
-    the C staging buffer."""
+    the C staging buffer, each in both kernel forms (without and with C store warps)."""
     import paper_1504_05046_gb300 as P
-    assert P.bsmm_tune_space(P.BSMM_FP64) == [{"cluster": 0, "stages": 0, "fp64_tile": 32},
-                                               {"cluster": 0, "stages": 0, "fp64_tile": 64}]
+    assert P.bsmm_tune_space(P.BSMM_FP64) == [{"cluster": 0, "stages": 0, "fp64_tile": 32, "store_warps": 0},
+                                               {"cluster": 0, "stages": 0, "fp64_tile": 64, "store_warps": 0}]
     s6 = P.bsmm_tune_space(P.BSMM_SPLIT_BF16, 6)
-    assert [(c["cluster"], c["stages"]) for c in s6] == [(cl, st) for cl in (1, 2, 4) for st in (2, 3)]
+    assert [(c["cluster"], c["stages"], c["store_warps"]) for c in s6] == \
+        [(cl, st, sw) for cl in (1, 2, 4) for st in (2, 3) for sw in (1, 2)]
     s3 = P.bsmm_tune_space(P.BSMM_SPLIT_FP16, 3)
-    assert [(c["cluster"], c["stages"]) for c in s3] == [(cl, st) for cl in (1, 2, 4) for st in range(2, 7)]
+    assert [(c["cluster"], c["stages"], c["store_warps"]) for c in s3] == \
+        [(cl, st, sw) for cl in (1, 2, 4) for st in range(2, 7) for sw in (1, 2)]
     with pytest.raises(P.BsmmError):
         P.bsmm_tune_space(P.BSMM_SPLIT_BF16, 7)
 

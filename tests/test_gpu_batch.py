@@ -147,3 +147,52 @@ def test_autotune_keeps_caller_c_and_bits(mode):
     alone, _ = run_lib(it["prob"], it["cs"], it["C0"], it["off"], mode=mode, plan=it["plan"])
     assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], alone),
                           struct_elements(it["prob"], it["cs"], it["off"], _reference(it, mode)))
+
+
+@pytest.mark.parametrize("mode", [P.BSMM_FP64, P.BSMM_SPLIT_BF16])
+def test_autotune_cache_file(mode, tmp_path):
+    """The tuning cache: the first call tunes and writes the file (keyed by GPU, mode and
+    slice count); a second batch takes the cached choice without timing; a file of
+    another format is tuned over and replaced; results keep the oracles' bits."""
+    import json
+    import torch
+    path = tmp_path / "tune.json"
+
+    def make():
+        items = _setup(mode, count=4, seed=14, fp64_tile=32)
+        batch = P.bsmm_batch_create([it["plan"] for it in items])
+        P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                              [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                              [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+        return items, batch
+
+    def check(items, batch):
+        for it in items:
+            it["C"].copy_(torch.from_numpy(it["C0"] if it["C0"].size else np.zeros(2)))
+        P.bsmm_batch_execute(batch)
+        torch.cuda.synchronize()
+        P.bsmm_batch_status_device(batch)
+        for it in items:
+            got = it["C"].cpu().numpy()
+            assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
+                                  struct_elements(it["prob"], it["cs"], it["off"], _reference(it, mode)))
+
+    items, batch = make()
+    chosen, cached = P.bsmm_batch_autotune_cached(batch, path, reps=1)
+    assert not cached and chosen in P.bsmm_tune_space(mode, 6)
+    doc = json.loads(path.read_text())
+    assert doc["format"] == "bsmm-tune" and doc["version"] == 1 and len(doc["entries"]) == 1
+    entry = doc["entries"][0]
+    assert entry["key"].endswith("|fp64|s=0" if mode == P.BSMM_FP64 else "|split_bf16|s=6")
+    assert (entry["cluster"], entry["stages"], entry["fp64_tile"]) == (chosen["cluster"], chosen["stages"],
+                                                                      chosen["fp64_tile"])
+    check(items, batch)
+    items2, batch2 = make()
+    chosen2, cached2 = P.bsmm_batch_autotune_cached(batch2, path, reps=1)
+    assert cached2 and chosen2 == chosen
+    check(items2, batch2)
+    path.write_text('{"format": "something-else", "version": 1}\n')
+    items3, batch3 = make()
+    _, cached3 = P.bsmm_batch_autotune_cached(batch3, path, reps=1)
+    assert not cached3 and json.loads(path.read_text())["format"] == "bsmm-tune"
+    check(items3, batch3)

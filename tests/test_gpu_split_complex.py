@@ -43,7 +43,8 @@ def run_c(prob, s=6, mode=P.BSMM_SPLIT_BF16, c_mask=None, trans=(0, 0), **opt):
     off, C64 = c_arena(prob, cs, rng=np.random.default_rng(0))
     C0 = (C64 + 1j * np.random.default_rng(1).uniform(-1, 1, C64.size)).astype(np.complex128)
     want = C0.copy()
-    OS.bsmm_split(prob, cs, want, off, s)  # (the oracle reads the transposed storage)
+    # (the oracle reads the transposed storage; row/column scaling when asked)
+    OS.bsmm_split(prob, cs, want, off, s, scaling="rows" if opt.get("split_scale") else "tile")
     plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, c_mask,
                        mode=mode, nslices=s, elem=P.BSMM_C128, debug_checks=1, **opt)
     prob, tprob = base, prob  # the reference below uses the untransposed operands
@@ -124,10 +125,35 @@ def test_transposed_storage(trans):
     run_c(prob, 6, trans=trans, ksplit=2)
 
 
+@pytest.mark.parametrize("trans", [(0, 0), (1, 1)])
+def test_row_column_scaling(trans):
+    """One exponent per complex row of A and column of B (over both parts): the row-scaled
+    oracle's bits on ragged tiles and on rows and columns scaled up to 40 binades apart,
+    where one exponent per tile loses the small lines; with split k as well."""
+    prob = G.as_complex(G.random_small(23, max_blocks=6, max_size=60), 23)
+    run_c(prob, 6, trans=trans, split_scale=1)
+    # complex integers (both parts), then every row of A scaled by its own power of two: each
+    # C element is one scale times an exact complex integer sum, so the product is exact
+    base = G.as_complex(G.make_problem("nonuniform_dense", 9, 500, lo=40, hi=160, values="integers"), 9)
+    rng = np.random.default_rng(9)
+    ra = np.ldexp(1.0, -10 * rng.integers(0, 5, int(base.row_sizes.sum())))
+    ro = np.concatenate([[0], np.cumsum(base.row_sizes)])
+    A = base.A.copy()
+    for i in range(base.M):
+        for k in range(base.K):
+            o = base.a_off[i, k]
+            A[o:o + base.row_sizes[i] * base.inner_sizes[k]].reshape(base.row_sizes[i], base.inner_sizes[k])[...] *= \
+                ra[ro[i]:ro[i + 1], None]
+    prob = dataclasses.replace(base, A=A)
+    _, err = run_c(prob, 6, trans=trans, split_scale=1)
+    assert err == 0.0, err
+    run_c(prob, 6, trans=trans, split_scale=1, ksplit=2)
+
+
 def test_unsupported_combinations_are_rejected():
     prob = G.as_complex(G.random_small(1, max_blocks=3, max_size=30), 1)
     args = (prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask)
-    for bad in (dict(mode=P.BSMM_FP64), dict(mode=P.BSMM_SPLIT_BF16, split_scale=1)):
+    for bad in (dict(mode=P.BSMM_FP64),):
         with pytest.raises(P.BsmmError):
             P.bsmm_plan(*args, elem=P.BSMM_C128, **bad)
     deep = np.array([300], np.int32)  # 2 x 300 real lines exceed the 6-slice exact depth

@@ -171,3 +171,64 @@ def test_transposed_storage(seed, ta, tb):
                         r, c = int(base.row_sizes[i]), int(base.col_sizes[j])
                         o = off[i, j]
                         assert np.array_equal(C2[o:o + r * c].reshape(r, c), P[ro[i]:ro[i + 1], co[j]:co[j + 1]])
+
+
+def _row_scaled_complex(seed):
+    """Complex integers with every row of A and every column of B scaled by its own power
+    of two, up to 40 binades apart: each C element is 2^(a_row + b_col) times an exact
+    complex integer sum, so numpy's complex product of the dense operands is exact."""
+    base = G.random_small(seed + 60, max_blocks=4, max_size=10, allow_zero=False, values="integers")
+    base.alpha, base.beta = 1.0, 0.0
+    prob = G.as_complex(base, seed)
+    rng = np.random.default_rng(seed)
+    ra = np.ldexp(1.0, -10 * rng.integers(0, 5, int(prob.row_sizes.sum())))
+    cb = np.ldexp(1.0, -10 * rng.integers(0, 5, int(prob.col_sizes.sum())))
+    ro = np.concatenate([[0], np.cumsum(prob.row_sizes)])
+    co = np.concatenate([[0], np.cumsum(prob.col_sizes)])
+    A, B = prob.A.copy(), prob.B.copy()
+    for i in range(prob.M):
+        for k in range(prob.K):
+            if prob.a_mask[i, k]:
+                o = prob.a_off[i, k]
+                A[o:o + prob.row_sizes[i] * prob.inner_sizes[k]].reshape(prob.row_sizes[i], prob.inner_sizes[k])[...] *= \
+                    ra[ro[i]:ro[i + 1], None]
+    for k in range(prob.K):
+        for j in range(prob.N):
+            if prob.b_mask[k, j]:
+                o = prob.b_off[k, j]
+                B[o:o + prob.inner_sizes[k] * prob.col_sizes[j]].reshape(prob.inner_sizes[k], prob.col_sizes[j])[...] *= \
+                    cb[None, co[j]:co[j + 1]]
+    return dataclasses.replace(prob, A=A, B=B)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_row_scaling_exact_on_scaled_complex_integers(seed):
+    prob = _row_scaled_complex(seed)
+    cs, _, _ = oracle.structure(prob)
+    off, C0 = _c_arena(prob, cs, seed)
+    C = np.zeros_like(C0)
+    OS.bsmm_split(prob, cs, C, off, 6, scaling="rows")
+    P = _dense(prob, prob.A, prob.a_off, prob.row_sizes, prob.inner_sizes) @ \
+        _dense(prob, prob.B, prob.b_off, prob.inner_sizes, prob.col_sizes)
+    ro = np.concatenate([[0], np.cumsum(prob.row_sizes.astype(np.int64))])
+    co = np.concatenate([[0], np.cumsum(prob.col_sizes.astype(np.int64))])
+    for i in range(prob.M):
+        for j in range(prob.N):
+            if cs[i, j]:
+                r, c = int(prob.row_sizes[i]), int(prob.col_sizes[j])
+                o = off[i, j]
+                assert np.array_equal(C[o:o + r * c].reshape(r, c), P[ro[i]:ro[i + 1], co[j]:co[j + 1]])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_row_scaling_zero_imaginary_parts_equal_the_real_oracle(seed):
+    base = G.random_small(seed + 70, max_blocks=5, max_size=12)
+    prob = dataclasses.replace(base, A=base.A.astype(np.complex128), B=base.B.astype(np.complex128))
+    cs, _, _ = oracle.structure(base)
+    off, C0 = c_arena(base, cs, rng=np.random.default_rng(seed))
+    real = C0.copy()
+    OS.bsmm_split(base, cs, real, off, 6, scaling="rows")
+    cpx = C0.astype(np.complex128)
+    OS.bsmm_split(prob, cs, cpx, off, 6, scaling="rows")
+    assert np.array_equal(cpx.real, real)
+    assert np.array_equal(cpx.imag, np.zeros_like(real))  # beta times a zero imaginary part
