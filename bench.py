@@ -417,6 +417,21 @@ SINGLE = {
 CONTRACTION_INDEX = {"split": 2, "fp64": 0}
 
 
+def fp64_roofline(P, pk, achieved):
+    """The FP64 path against its unit count x clock (152 SMs x 2 FP64 FMA per clock x 2 flops
+    x the maximum SM clock) and against the rates measured in this run on every SM (DFMA
+    chains, the FP64 mma.sync, and for reference the INT8 mma.sync)."""
+    rates = P.bsmm_measure_rates()
+    peak = 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_def": "152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+            "measured_dfma_tflops": rates["dfma"], "frac_of_measured_dfma": achieved / rates["dfma"],
+            "measured_dmma_tflops": rates["dmma"], "frac_of_measured_dmma": achieved / rates["dmma"],
+            "measured_int8_mma_sync_tops": rates["imma"],
+            "measured_def": "bsmm_measure_rates in this run: DFMA chains, FP64 mma.sync m8n8k4, INT8 mma.sync "
+                            "m16n8k32, each on every SM"}
+
+
 def timed_steps(plan, run, steps, warmup):
     """Mean step time (ms, CUDA events on the current stream) of `steps` runs after
     `warmup` untimed ones, and each kernel's mean device time over the timed runs (read
@@ -580,11 +595,7 @@ def run_single(args, rank, world):
                 "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"}
     else:
-        rates = P.bsmm_measure_rates()
-        roof = {"bound": "alu", "kernel": "fp64_tile_kernel", "achieved": F / (k64[cif] * 1e-3) / 1e12,
-                "peak": rates["dfma"], "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "measured in this run (bsmm_measure_rates): DFMA on every SM",
-                "dmma_tflops": rates["dmma"], "frac_of_dmma": F / (k64[cif] * 1e-3) / 1e12 / rates["dmma"]}
+        roof = dict(fp64_roofline(P, pk, F / (k64[cif] * 1e-3) / 1e12), kernel="fp64_tile_kernel", traffic=None)
     roof["frac"] = roof["achieved"] / roof["peak"]
     head = split if head_split else fp64
     line = {"metric": METRIC, "value": head["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -778,15 +789,9 @@ def run_dense(args, rank, world, local):
         c64 = C64.cpu().numpy()
         d = Csplit - c64
         err = float(np.linalg.norm(d) / np.linalg.norm(c64))
-        rates = P.bsmm_measure_rates()  # this GPU's FP64 rates, measured now (DFMA; FP64 mma.sync)
         v64 = F / (ms64 * 1e-3) / 1e12
         extra["fp64_path"] = {"value": v64, "unit": "TFLOP/s", "ms_per_step": ms64,
-                              "roofline": {"bound": "alu", "peak": rates["dfma"], "unit": "TFLOP/s",
-                                           "frac": v64 / rates["dfma"], "dmma_tflops": rates["dmma"],
-                                           "frac_of_dmma": v64 / rates["dmma"],
-                                           "int8_mma_sync_tops": rates["imma"],
-                                           "peak_def": "measured in this run (bsmm_measure_rates): DFMA chains on "
-                                                       "every SM; dmma = FP64 mma.sync m8n8k4 on every SM"}}
+                              "roofline": fp64_roofline(P, pk, v64)}
         extra["split_rel_err_vs_fp64"] = err
         extra["split_speedup_vs_fp64"] = ms64 / ms_max
         # the other slice counts on the same inputs: throughput and error against the FP64 result

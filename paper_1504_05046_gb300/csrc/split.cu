@@ -134,6 +134,8 @@ __device__ bool wait1(uint64_t* bar, uint32_t parity, volatile int* abort_flag, 
   }
 }
 
+constexpr uint32_t kGroupPollNs = 128;  // the epilogue's sleep between polls for the next group
+
 // Warp-uniform bounded wait (every lane polls; the decision is taken by the warp). A warp
 // whose wait is not on the critical path passes sleep_ns > 0: it sleeps between polls,
 // leaving the issue slots to the warps that are.
@@ -1511,7 +1513,9 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
       bool more = (un.own >> rank) & 1;
       while (more) {
         const uint32_t buf = tcount & 1, use = tcount >> 1;
-        if (!wait_warp(&gready[buf], use & 1, abort_flag, a.err)) {
+        // (the epilogue warps sleep between polls here: while the MMA warps fill a group
+        // they would otherwise take issue slots from the producer and MMA threads)
+        if (!wait_warp(&gready[buf], use & 1, abort_flag, a.err, kWaitNs, kGroupPollNs)) {
           ok = false;
           break;
         }
