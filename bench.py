@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=16384, help="matrix order")
+    ap.add_argument("--single-n", type=int, default=0,
+                    help="banded / clustered / uniform / thin workloads: another order (small cases for profiling; "
+                         "0 = the workload's own)")
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--cluster", type=int, default=0,
                     help="split modes: CTAs per column-block group (0 = library default)")
@@ -511,7 +514,7 @@ def single_setup(args, w, dev):
             opt.setdefault("cluster", args.cluster)
             opt.setdefault("store_warps", args.store_warps)
         opt.setdefault("ksplit", args.ksplit)
-        prob = G.make_problem(w["recipe"], seed, w["n"], **w["kw"])
+        prob = G.make_problem(w["recipe"], seed, args.single_n or w["n"], **w["kw"])
         plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask, mode=mode,
                            nslices=args.slices, profile=1, **opt)
         q = P.bsmm_plan_query(plan)
@@ -602,7 +605,8 @@ def run_single(args, rank, world):
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if head_split and "BF16" in w["mode"] else
             ("f16" if head_split else "f64"), "data": "synthetic",
-            "config": {"workload": w["desc"], "useful_flops_per_step": F, "seed": seed,
+            "config": {"workload": w["desc"] + (f" (order {args.single_n} instead)" if args.single_n else ""),
+                       "useful_flops_per_step": F, "seed": seed,
                        "headline_path": "split" if head_split else "fp64"},
             "split_path": split, "fp64_path": fp64, "roofline": roof, "gpu_launches":
                 (kernels_per_execute(P, plan, mode, args.split_scale == "rows") if head_split
