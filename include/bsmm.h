@@ -91,7 +91,11 @@ typedef struct {
                               the group's CTAs take the same 128-row block at the same time,
                               one 32-column block each, and share its A panel through L2
                               (each CTA loads its own operands). Groups of one suit sparse
-                              masks best, where a neighbour's column block is often empty. */
+                              masks best, where a neighbour's column block is often empty.
+                              -1 = the planner's choice: 4, else 2, when the column blocks of
+                              every group carry the same tensor-core work to within 0.5% (a
+                              dense block pattern), else 1. Plans of one batch need equal
+                              sizes, so a plan meant for a batch should fix it. */
   int32_t fp64_tile;       /* FP64 mode: sub-tile edge of a work unit, 32 or 64 (0 = 32) */
   int32_t stages;          /* split modes: depth of the shared-memory ring of 32-deep k chunks
                               (k panels in flight), 2..8 and within the 227 KB shared memory of
@@ -151,11 +155,10 @@ typedef struct {
                               equivalent real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]], so
                               an inner block may hold half the real depth (256 for 6 slices)
                               and the useful flop count is 8 r c q per nonzero triple. */
-  int32_t store_warps;     /* split modes: the contraction kernel's form. 0 = automatic: with
-                              four C store warps (the C store of a unit overlaps the next
-                              unit's accumulation) when the work units' mean inner depth is
-                              below 8192 elements, else without; 1 = never; 2 = always.
-                              Results do not depend on it. */
+  int32_t store_warps;     /* split modes: the contraction kernel's form. 0 = automatic (with
+                              store warps); 2 = with four C store warps (the C store of a
+                              unit overlaps the next unit's accumulation); 1 = without (the
+                              epilogue warps store). Results do not depend on it. */
   const char* model_path;  /* NULL or "" = no model. Otherwise the path of a cost-model file
                               written by bsmm_mlp_save: bsmm_plan loads it, predicts every work
                               unit's time with it on the GPU and packs the units by those
@@ -269,16 +272,42 @@ bsmm_status bsmm_execute_f32(bsmm_plan_t plan, float alpha, const float* A, cons
 /*
  * Same as bsmm_execute (bsmm_execute_f32 for float32 elements) with HOST buffers:
  * copies A, B (and C when beta != 0) and the offset tables to device buffers the plan
- * keeps, runs, copies C back and synchronises `stream` before returning. The arenas
- * hold the plan's element type (bsmm_options.elem): float64, float32, or interleaved
- * complex doubles; a_elems, b_elems, c_elems = arena lengths in those elements.
- * alpha and beta are real (converted to float32 for float32 elements). Pinned host
- * memory makes the copies asynchronous.
+ * keeps, runs the product's kernels on `stream`, copies C back, and returns once C is
+ * on the host (bsmm_execute_host_async followed by bsmm_host_wait). The arenas hold the
+ * plan's element type (bsmm_options.elem): float64, float32, or interleaved complex
+ * doubles; a_elems, b_elems, c_elems = arena lengths in those elements. alpha and beta
+ * are real (converted to float32 for float32 elements). Pinned host memory makes the
+ * copies asynchronous.
  */
 bsmm_status bsmm_execute_host(bsmm_plan_t plan, double alpha, const void* A, int64_t a_elems,
                               const int64_t* a_off, const void* B, int64_t b_elems,
                               const int64_t* b_off, double beta, void* C, int64_t c_elems,
                               const int64_t* c_off, void* stream);
+
+/*
+ * Host-buffer products in flight (Sec. 3.2: several iterations issued at once, further
+ * ones as earlier ones retire, so that data movement of one overlaps the computation of
+ * another). bsmm_execute_host_async enqueues one product with the arguments of
+ * bsmm_execute_host and returns without waiting: the host-to-device copies run on a
+ * copy stream of the plan, the kernels on `stream` (after the copies and after the plan's
+ * previous host product), the copy of C back on a second copy stream. Product i uses
+ * staging slot i % 2 of the plan (device buffers grown on demand), so the copies of
+ * product i + 1 and the copy back of product i - 1 overlap product i's contraction; a
+ * product whose slot must grow first waits for that slot's previous product.
+ * Ownership: A, B, C and the offset tables stay the caller's and must stay valid and
+ * unchanged (C unread) until bsmm_host_wait returns; with pinned memory the copies are
+ * asynchronous, with pageable memory they may block the call. Errors: as
+ * bsmm_execute_host for the arguments; a failed copy or launch returns BSMM_ERR_CUDA
+ * after the plan's streams have been synchronised.
+ * bsmm_host_wait: blocks until every host product enqueued on the plan has its C on
+ * the host. BSMM_ERR_INVALID for a NULL plan, BSMM_ERR_CUDA if a copy or kernel failed.
+ * Device-side error words are read by bsmm_status_device as for bsmm_execute.
+ */
+bsmm_status bsmm_execute_host_async(bsmm_plan_t plan, double alpha, const void* A, int64_t a_elems,
+                                    const int64_t* a_off, const void* B, int64_t b_elems,
+                                    const int64_t* b_off, double beta, void* C, int64_t c_elems,
+                                    const int64_t* c_off, void* stream);
+bsmm_status bsmm_host_wait(bsmm_plan_t plan);
 
 /*
  * Batches: many independent products in one persistent launch. The task set of the

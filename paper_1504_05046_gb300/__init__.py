@@ -23,7 +23,7 @@ __all__ = [
     "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features",
     "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
-    "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
+    "bsmm_execute_host_async", "bsmm_host_wait", "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
     "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_selftest_wait", "bsmm_last_error",
     "bsmm_measure_rates",
     "bsmm_destroy", "EXPORTED",
@@ -39,8 +39,8 @@ STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_
 # every symbol include/bsmm.h declares
 EXPORTED = [
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features", "bsmm_plan_set_costs",
-    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host", "bsmm_status_device",
-    "bsmm_plan_timings",
+    "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host", "bsmm_execute_host_async",
+    "bsmm_host_wait", "bsmm_status_device", "bsmm_plan_timings",
     "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_batch_create", "bsmm_batch_set_args",
     "bsmm_batch_execute", "bsmm_batch_query", "bsmm_batch_kernels", "bsmm_batch_set_costs", "bsmm_batch_status_device",
     "bsmm_batch_destroy", "bsmm_tune_space", "bsmm_batch_autotune", "bsmm_mlp_create", "bsmm_mlp_num_params", "bsmm_mlp_set_params", "bsmm_mlp_get_params",
@@ -91,6 +91,8 @@ def lib():
         L.bsmm_execute.argtypes = [P, f64, P, P, P, P, f64, P, P, P]
         L.bsmm_execute_f32.argtypes = [P, ctypes.c_float, P, P, P, P, ctypes.c_float, P, P, P]
         L.bsmm_execute_host.argtypes = [P, f64, P, i64, P, P, i64, P, f64, P, i64, P, P]
+        L.bsmm_execute_host_async.argtypes = [P, f64, P, i64, P, P, i64, P, f64, P, i64, P, P]
+        L.bsmm_host_wait.argtypes = [P]
         L.bsmm_status_device.argtypes = [P, P]
         L.bsmm_plan_timings.argtypes = [P, P, P, P]
         L.bsmm_plan_kernel_ms.argtypes = [P, P, i32, P]
@@ -286,6 +288,28 @@ def bsmm_execute_host(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, str
         return int(x.size if isinstance(x, np.ndarray) else x.numel())
     _check(lib().bsmm_execute_host(plan.handle, float(alpha), _ptr(A), n(A), _ptr(a_off), _ptr(B), n(B),
                                    _ptr(b_off), float(beta), _ptr(C), n(C), _ptr(c_off), _stream(stream)))
+
+
+# host arrays of the products in flight per plan handle, kept alive until bsmm_host_wait
+_in_flight = {}
+
+
+def bsmm_execute_host_async(plan: Plan, alpha, A, a_off, B, b_off, beta, C, c_off, stream=None):
+    """Enqueues one host-buffer product and returns; C holds its result after bsmm_host_wait.
+    The arrays are kept referenced until then (and must not be changed meanwhile)."""
+    def n(x):
+        return int(x.size if isinstance(x, np.ndarray) else x.numel())
+    _check(lib().bsmm_execute_host_async(plan.handle, float(alpha), _ptr(A), n(A), _ptr(a_off), _ptr(B), n(B),
+                                         _ptr(b_off), float(beta), _ptr(C), n(C), _ptr(c_off), _stream(stream)))
+    _in_flight.setdefault(plan.handle, []).append((A, a_off, B, b_off, C, c_off))
+
+
+def bsmm_host_wait(plan: Plan):
+    """Waits until every host product enqueued on the plan has its C on the host."""
+    try:
+        _check(lib().bsmm_host_wait(plan.handle))
+    finally:
+        _in_flight.pop(plan.handle, None)
 
 
 def bsmm_status_device(plan: Plan, stream=None):
@@ -586,5 +610,6 @@ def bsmm_mlp_destroy(mlp: Mlp):
 
 def bsmm_destroy(plan: Plan):
     if plan is not None and plan.handle:
-        lib().bsmm_destroy(plan.handle)
+        lib().bsmm_destroy(plan.handle)  # waits for the plan's host products first
+        _in_flight.pop(plan.handle, None)
         plan.handle = None

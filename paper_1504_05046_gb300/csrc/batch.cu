@@ -311,17 +311,12 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
   }
   b->n_units = (int64_t)b->unit_prod.size();
   b->prod_begin.push_back(b->n_units);
-  // the kernel form of the batch's contraction launches: the one all plans ask for, else
-  // by the units' mean inner depth over the whole batch
+  // the kernel form of the batch's contraction launches: without store warps only when
+  // every plan asks for that
   {
-    double depth = 0.0;
-    bool same = true;
-    for (int32_t i = 0; i < count; i++) {
-      depth += plans[i]->unit_depth * (double)plans[i]->n_units;
-      same = same && plans[i]->opt.store_warps == p0->opt.store_warps;
-    }
-    const int32_t sw = same ? p0->opt.store_warps : 0;
-    b->sw = sw == 2 ? 1 : sw == 1 ? 0 : (depth < kStoreWarpDepth * (double)std::max<int64_t>(1, b->n_units) ? 1 : 0);
+    bool none = true;
+    for (int32_t i = 0; i < count; i++) none = none && plans[i]->opt.store_warps == 1;
+    b->sw = none ? 0 : 1;
   }
   // one product's default bin count describes the machine (CTAs or clusters)
   bsmm_plan_s tmp_view = bsmm_plan_s();

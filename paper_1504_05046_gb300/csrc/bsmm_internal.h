@@ -45,9 +45,6 @@ constexpr int kSplitDefaultCluster = 1;  // groups of one: no CTA idles on a nei
 // Largest number of groups of `cl` contraction CTAs that can be resident at once (the
 // kernel form with store warps when sw is set).
 int split_max_clusters(int s, int cl, int stages, bool sw);
-// The planner's choice of the contraction kernel's form: store warps when a unit's mean
-// inner depth (its own k blocks' sizes summed) is below this many elements.
-constexpr double kStoreWarpDepth = 8192.0;
 
 // Device arrays owned by a plan.
 struct DevBuf {
@@ -256,6 +253,8 @@ int fp64_ctas_per_sm(int tile);
 cudaError_t unit_rates(double* rates, cudaStream_t st);
 
 void set_error(const std::string& msg);
+// waits for the plan's host-buffer products and frees their staging slots, streams, events
+void host_release(bsmm_plan_s* p);
 
 // bsmm_plan with an optional donor: a split plan of the same structure and slice count
 // whose slice workspace the new plan shares instead of allocating its own (the packed
@@ -297,7 +296,6 @@ struct bsmm_plan_s {
   // split geometry
   int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0, cl = 1, CBG = 0;
   int sw = 0;                // contraction kernel with C store warps
-  double unit_depth = 0.0;   // mean inner depth of the work units (split modes)
   int64_t Mtot = 0, Ntot = 0, colexp_ld = 0;
   int64_t apk_bytes = 0, bpk_bytes = 0;
 
@@ -323,6 +321,16 @@ struct bsmm_plan_s {
   int32_t cost_source = BSMM_COSTS_FLOPS;  // where `cost` came from (bsmm_cost_source)
   uint64_t uid = 0;  // unique over the process's plans (never reused, unlike an address)
 
-  // host-buffer execute staging (grown on demand)
-  bsmm::DevBuf h_A, h_B, h_C, h_aoff, h_boff, h_coff;
+  // Host-buffer executes: two device staging slots (grown on demand), so that the copies
+  // of one product run while the product before it computes (several iterations in
+  // flight, Sec. 3.2). Slot i % 2 takes the i-th product; its events mark where that
+  // product's copies in, contraction and copy out end.
+  struct HostSlot {
+    bsmm::DevBuf A, B, C, aoff, boff, coff;
+    cudaEvent_t in = nullptr, run = nullptr, out = nullptr;
+    bool used = false;
+  } hs[2];
+  cudaStream_t h2d = nullptr, d2h = nullptr;  // copy streams (created on first use)
+  cudaEvent_t last_run = nullptr;             // the last host product's kernels (workspace order)
+  int64_t host_count = 0;                     // host-buffer products enqueued so far
 };

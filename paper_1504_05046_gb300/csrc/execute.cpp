@@ -201,6 +201,99 @@ bsmm_status grow(DevBuf& b, size_t bytes) {
   return BSMM_OK;
 }
 
+
+// The host-buffer path (bsmm_execute_host_async): product i uses staging slot i % 2.
+//   copy stream in:  [slot's previous contraction done] offsets, A, B; [its copy out done] C
+//                    (when beta != 0)                                        -> event in
+//   stream:          [in] [slot's previous copy out done] [previous host product's kernels]
+//                    the product's kernels                                  -> event run
+//   copy stream out: [run] C back to the host                                -> event out
+// so the copies of product i + 1 (and the copy out of product i - 1) overlap the
+// contraction of product i, and at most two products hold staging memory.
+bsmm_status host_setup(bsmm_plan_s* p) {
+  if (p->h2d) return BSMM_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->last_run, cudaEventDisableTiming);
+  for (auto& h : p->hs) {
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.run, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.out, cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    host_release(p);
+    return set_error(std::string("host streams: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  }
+  return BSMM_OK;
+}
+
+bsmm_status enqueue_host(bsmm_plan_s* p, double alpha, const void* A, int64_t a_elems, const int64_t* a_off,
+                         const void* B, int64_t b_elems, const int64_t* b_off, double beta, void* C, int64_t c_elems,
+                         const int64_t* c_off, cudaStream_t st) {
+  bsmm_status s = host_setup(p);
+  if (s != BSMM_OK) return s;
+  // bytes per element of the plan's element type
+  const size_t es = p->opt.elem == BSMM_F32 ? sizeof(float) : p->opt.elem == BSMM_C128 ? 2 * sizeof(double)
+                                                                                        : sizeof(double);
+  const size_t na = (size_t)p->M * p->K, nb = (size_t)p->K * p->N, nc = (size_t)p->M * p->N;
+  bsmm_plan_s::HostSlot& h = p->hs[p->host_count & 1];
+  const bool fits = h.A.bytes >= es * a_elems && h.B.bytes >= es * b_elems && h.C.bytes >= es * c_elems &&
+                    h.aoff.bytes >= sizeof(int64_t) * na && h.boff.bytes >= sizeof(int64_t) * nb &&
+                    h.coff.bytes >= sizeof(int64_t) * nc;
+  cudaError_t e = cudaSuccess;
+  if (!fits && h.used) e = cudaEventSynchronize(h.out);  // the slot's buffers are about to be replaced
+  if (e != cudaSuccess) return set_error(std::string("host slot: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  if ((s = grow(h.A, es * a_elems)) != BSMM_OK) return s;
+  if ((s = grow(h.B, es * b_elems)) != BSMM_OK) return s;
+  if ((s = grow(h.C, es * c_elems)) != BSMM_OK) return s;
+  if ((s = grow(h.aoff, sizeof(int64_t) * na)) != BSMM_OK) return s;
+  if ((s = grow(h.boff, sizeof(int64_t) * nb)) != BSMM_OK) return s;
+  if ((s = grow(h.coff, sizeof(int64_t) * nc)) != BSMM_OK) return s;
+  auto h2d = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes > 0) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, p->h2d);
+  };
+  if (h.used) e = cudaStreamWaitEvent(p->h2d, h.run, 0);  // the slot's inputs are no longer read
+  h2d(h.aoff.p, a_off, sizeof(int64_t) * na);
+  h2d(h.boff.p, b_off, sizeof(int64_t) * nb);
+  h2d(h.coff.p, c_off, sizeof(int64_t) * nc);
+  h2d(h.A.p, A, es * a_elems);
+  h2d(h.B.p, B, es * b_elems);
+  if (beta != 0.0) {
+    if (h.used && e == cudaSuccess) e = cudaStreamWaitEvent(p->h2d, h.out, 0);  // its C went back
+    h2d(h.C.p, C, es * c_elems);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h.in, p->h2d);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h.in, 0);
+  if (e == cudaSuccess && h.used) e = cudaStreamWaitEvent(st, h.out, 0);  // C is written by this product
+  if (e == cudaSuccess && p->host_count > 0) e = cudaStreamWaitEvent(st, p->last_run, 0);  // shared workspaces
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(p->h2d);
+    return set_error(std::string("H2D: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  }
+  const double al = p->opt.elem == BSMM_F32 ? (double)(float)alpha : alpha;
+  const double be = p->opt.elem == BSMM_F32 ? (double)(float)beta : beta;
+  s = run(p, al, h.A.p, (const int64_t*)h.aoff.p, h.B.p, (const int64_t*)h.boff.p, be, h.C.p,
+          (const int64_t*)h.coff.p, st);
+  if (s != BSMM_OK) {
+    cudaStreamSynchronize(p->h2d);
+    cudaStreamSynchronize(st);
+    return s;
+  }
+  e = cudaEventRecord(h.run, st);
+  if (e == cudaSuccess) e = cudaEventRecord(p->last_run, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, h.run, 0);
+  if (e == cudaSuccess && c_elems > 0) e = cudaMemcpyAsync(C, h.C.p, es * c_elems, cudaMemcpyDeviceToHost, p->d2h);
+  if (e == cudaSuccess) e = cudaEventRecord(h.out, p->d2h);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(p->d2h);
+    return set_error(std::string("D2H: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  }
+  h.used = true;
+  p->host_count++;
+  return BSMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -221,47 +314,32 @@ bsmm_status bsmm_execute_f32(bsmm_plan_t p, float alpha, const float* A, const i
   return run(p, alpha, A, a_off, B, b_off, beta, C, c_off, (cudaStream_t)stream);
 }
 
-bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const void* A, int64_t a_elems, const int64_t* a_off,
-                              const void* B, int64_t b_elems, const int64_t* b_off, double beta, void* C,
-                              int64_t c_elems, const int64_t* c_off, void* stream) {
+bsmm_status bsmm_execute_host_async(bsmm_plan_t p, double alpha, const void* A, int64_t a_elems,
+                                    const int64_t* a_off, const void* B, int64_t b_elems, const int64_t* b_off,
+                                    double beta, void* C, int64_t c_elems, const int64_t* c_off, void* stream) {
   bsmm_status s = check_ptrs(p, A, a_off, B, b_off, C, c_off);
   if (s != BSMM_OK) return s;
   if (a_elems < 0 || b_elems < 0 || c_elems < 0) return set_error("negative arena length"), BSMM_ERR_INVALID;
-  // bytes per element of the plan's element type
-  const size_t es = p->opt.elem == BSMM_F32 ? sizeof(float) : p->opt.elem == BSMM_C128 ? 2 * sizeof(double)
-                                                                                        : sizeof(double);
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t na = (size_t)p->M * p->K, nb = (size_t)p->K * p->N, nc = (size_t)p->M * p->N;
-  if ((s = grow(p->h_A, es * a_elems)) != BSMM_OK) return s;
-  if ((s = grow(p->h_B, es * b_elems)) != BSMM_OK) return s;
-  if ((s = grow(p->h_C, es * c_elems)) != BSMM_OK) return s;
-  if ((s = grow(p->h_aoff, sizeof(int64_t) * na)) != BSMM_OK) return s;
-  if ((s = grow(p->h_boff, sizeof(int64_t) * nb)) != BSMM_OK) return s;
-  if ((s = grow(p->h_coff, sizeof(int64_t) * nc)) != BSMM_OK) return s;
-#define H2D(dst, src, bytes)                                                                      \
-  if ((bytes) > 0) {                                                                              \
-    cudaError_t e_ = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st);          \
-    if (e_ != cudaSuccess) return set_error(std::string("H2D: ") + cudaGetErrorString(e_)), BSMM_ERR_CUDA; \
+  return enqueue_host(p, alpha, A, a_elems, a_off, B, b_elems, b_off, beta, C, c_elems, c_off, (cudaStream_t)stream);
+}
+
+bsmm_status bsmm_host_wait(bsmm_plan_t p) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  for (const auto& h : p->hs) {
+    if (!h.used) continue;
+    const cudaError_t e = cudaEventSynchronize(h.out);
+    if (e != cudaSuccess) return set_error(std::string("host wait: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   }
-  H2D(p->h_aoff.p, a_off, sizeof(int64_t) * na);
-  H2D(p->h_boff.p, b_off, sizeof(int64_t) * nb);
-  H2D(p->h_coff.p, c_off, sizeof(int64_t) * nc);
-  H2D(p->h_A.p, A, es * a_elems);
-  H2D(p->h_B.p, B, es * b_elems);
-  if (beta != 0.0) H2D(p->h_C.p, C, es * c_elems);
-#undef H2D
-  const double al = p->opt.elem == BSMM_F32 ? (double)(float)alpha : alpha;
-  const double be = p->opt.elem == BSMM_F32 ? (double)(float)beta : beta;
-  s = run(p, al, p->h_A.p, (const int64_t*)p->h_aoff.p, p->h_B.p, (const int64_t*)p->h_boff.p, be, p->h_C.p,
-          (const int64_t*)p->h_coff.p, st);
-  if (s != BSMM_OK) return s;
-  if (c_elems > 0) {
-    cudaError_t e = cudaMemcpyAsync(C, p->h_C.p, es * c_elems, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return set_error(std::string("D2H: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
-  }
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return set_error(std::string("sync: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   return BSMM_OK;
+}
+
+bsmm_status bsmm_execute_host(bsmm_plan_t p, double alpha, const void* A, int64_t a_elems, const int64_t* a_off,
+                              const void* B, int64_t b_elems, const int64_t* b_off, double beta, void* C,
+                              int64_t c_elems, const int64_t* c_off, void* stream) {
+  bsmm_status s = bsmm_execute_host_async(p, alpha, A, a_elems, a_off, B, b_elems, b_off, beta, C, c_elems, c_off,
+                                          stream);
+  if (s != BSMM_OK) return s;
+  return bsmm_host_wait(p);
 }
 
 bsmm_status bsmm_status_device(bsmm_plan_t p, void* stream) {

@@ -350,6 +350,65 @@ bsmm_status plan_fp64(bsmm_plan_s* p) {
 // one cluster (pipeline start and drain, the 128-bit partial's store and its reduction).
 constexpr double kSplitPieceOverhead = 4.0e6;
 
+// The column-block group size for bsmm_options.cluster = -1. The CTAs of a group take the
+// same row block at the same time, one column block each, and read its A panel once from
+// DRAM between them; a CTA whose column block carries less tensor-core work waits for its
+// partners. So: the largest of 4 and 2 for which, summed over the groups that hold a C
+// tile, the CTAs' work (32-deep chunks of the k blocks where both the row block's A panel
+// and the CTA's own B column block are present, on column blocks that hold a C tile) is
+// at least 99.5% of the group count times its slowest CTA's; else 1.
+int choose_cluster(const bsmm_plan_s* p, const std::vector<uint64_t>& presA, const std::vector<uint64_t>& presB,
+                   const std::vector<int32_t>& row_tile) {
+  const int RB = p->RB, CB = p->CB, KW = p->kwords, tn = p->tn, N = p->N;
+  if (RB == 0 || CB < 2) return 1;
+  // C tile present in (row block, column block), and the pair's chunk count
+  std::vector<uint8_t> has((size_t)RB * CB, 0);
+  for (int rb = 0; rb < RB; rb++) {
+    const int64_t m0 = (int64_t)rb * kSplitBM, m1 = std::min<int64_t>(p->Mtot, m0 + kSplitBM);
+    for (int i = row_tile[m0]; i < p->M && p->ro[i] < m1; i++) {
+      if (p->ro[i + 1] <= m0) continue;
+      for (int j = 0; j < N; j++) {
+        if (!p->cs[(int64_t)i * N + j] || p->c[j] == 0) continue;
+        for (int64_t cb = p->co[j] / tn; cb <= (p->co[j + 1] - 1) / tn; cb++) has[(size_t)rb * CB + cb] = 1;
+      }
+    }
+  }
+  std::vector<double> w((size_t)RB * CB, 0.0);
+  for (int rb = 0; rb < RB; rb++)
+    for (int cb = 0; cb < CB; cb++) {
+      if (!has[(size_t)rb * CB + cb]) continue;
+      double chunks = 0.0;
+      for (int wd = 0; wd < KW; wd++) {
+        uint64_t bits = presA[(size_t)rb * KW + wd] & presB[(size_t)cb * KW + wd];
+        while (bits) {
+          chunks += (double)((p->q[wd * 64 + __builtin_ctzll(bits)] + kSplitKC - 1) / kSplitKC);
+          bits &= bits - 1;
+        }
+      }
+      w[(size_t)rb * CB + cb] = chunks;
+    }
+  for (int cl : {4, 2}) {
+    double sum = 0.0, worst = 0.0;
+    for (int rb = 0; rb < RB; rb++)
+      for (int g = 0; g * cl < CB; g++) {
+        double s = 0.0, mx = 0.0;
+        bool any = false;
+        for (int r = 0; r < cl; r++) {
+          const int cb = g * cl + r;
+          if (cb >= CB) continue;  // a CTA past the last column block idles
+          any = any || has[(size_t)rb * CB + cb];
+          s += w[(size_t)rb * CB + cb];
+          mx = std::max(mx, w[(size_t)rb * CB + cb]);
+        }
+        if (!any) continue;
+        sum += s;
+        worst += cl * mx;
+      }
+    if (worst > 0.0 && sum >= 0.995 * worst) return cl;
+  }
+  return 1;
+}
+
 bsmm_status plan_split(bsmm_plan_s* p) {
   const int M = p->M, N = p->N, K = p->K;
   const int s = p->s, tn = p->tn;
@@ -420,6 +479,8 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   std::vector<double> w((size_t)M * N, 0.0);
   for (int64_t t = 0; t < (int64_t)M * N; t++)
     for (int64_t e = p->kptr[t]; e < p->kptr[t + 1]; e++) w[t] += 2.0 * p->q[p->klist[e]];
+
+  if (p->opt.cluster == -1) p->cl = choose_cluster(p, presA, presB, row_tile);
 
   // A work unit is one group's task: a 128-row block times CL consecutive column blocks
   // (CL * tn columns), one column block per CTA of the group; the CL CTAs read the same
@@ -497,16 +558,8 @@ bsmm_status plan_split(bsmm_plan_s* p) {
     int nrt, nct;
     bcost[u] = std::max(region_flops(base[u].rb, base[u].cb, 0, K, nrt, nct), 1.0);
   }
-  // the contraction kernel's form: C store warps when units are short (the unit end's
-  // rounding and store then weigh on the epilogue), decided by the units' mean inner depth
-  {
-    double depth = 0.0;
-    for (size_t u = 0; u < base.size(); u++)
-      for (int64_t x = bk_ptr[u]; x < bk_ptr[u + 1]; x++) depth += p->q[bk[x]];
-    p->unit_depth = base.empty() ? 0.0 : depth / (double)base.size();
-    const int32_t sw = p->opt.store_warps;
-    p->sw = sw == 2 ? 1 : sw == 1 ? 0 : (p->unit_depth < kStoreWarpDepth ? 1 : 0);
-  }
+  // the contraction kernel's form: with C store warps unless the options say otherwise
+  p->sw = p->opt.store_warps == 1 ? 0 : 1;
   const std::vector<int32_t> np =
       choose_pieces(bcost, blen, machine_bins(p), kSplitPieceOverhead, p->opt.ksplit == -1 ? 0 : p->opt.ksplit);
   std::vector<int32_t> slot0(base.size(), -1);
@@ -639,8 +692,8 @@ bsmm_status validate_options(const bsmm_options& o) {
   if (o.schedule < 0 || o.schedule > 2) return set_error("unknown schedule"), BSMM_ERR_INVALID;
   if (o.max_ctas < 0) return set_error("max_ctas < 0"), BSMM_ERR_INVALID;
   if (o.profile < 0 || o.profile > 1) return set_error("profile must be 0 or 1"), BSMM_ERR_INVALID;
-  if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4)
-    return set_error("cluster must be 0, 1, 2 or 4"), BSMM_ERR_INVALID;
+  if (o.cluster != -1 && o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4)
+    return set_error("cluster must be -1, 0, 1, 2 or 4"), BSMM_ERR_INVALID;
   if (o.fp64_tile != 0 && o.fp64_tile != 32 && o.fp64_tile != 64)
     return set_error("fp64_tile must be 0, 32 or 64"), BSMM_ERR_INVALID;
   if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) return set_error("stages must be 0 or 2..8"), BSMM_ERR_INVALID;
@@ -663,6 +716,28 @@ bsmm_status validate_options(const bsmm_options& o) {
 // ======================================================================================
 // C ABI
 // ======================================================================================
+namespace bsmm {
+
+void host_release(bsmm_plan_s* p) {
+  for (auto& h : p->hs) {
+    if (h.used && h.out) cudaEventSynchronize(h.out);
+    for (DevBuf* b : {&h.A, &h.B, &h.C, &h.aoff, &h.boff, &h.coff}) dev_free(*b);
+    for (cudaEvent_t* ev : {&h.in, &h.run, &h.out})
+      if (*ev) {
+        cudaEventDestroy(*ev);
+        *ev = nullptr;
+      }
+    h.used = false;
+  }
+  if (p->last_run) cudaEventDestroy(p->last_run);
+  if (p->h2d) cudaStreamDestroy(p->h2d);
+  if (p->d2h) cudaStreamDestroy(p->d2h);
+  p->last_run = nullptr;
+  p->h2d = p->d2h = nullptr;
+}
+
+}  // namespace bsmm
+
 extern "C" {
 
 void bsmm_options_default(bsmm_options* opt) {
@@ -682,8 +757,8 @@ void bsmm_destroy(bsmm_plan_t p) {
                     &p->d_presA, &p->d_presB, &p->d_presBg, &p->d_apk_off, &p->d_bpk_off, &p->d_apk, &p->d_bpk,
                     &p->d_eArow, &p->d_eBcol, &p->d_eAmaxr, &p->d_eBmaxc,
                     &p->d_am, &p->d_bm, &p->d_rowexp, &p->d_colexp, &p->d_urow, &p->d_ucol, &p->d_rowadj, &p->d_coladj, &p->d_emaxr, &p->d_emaxc, &p->d_eA, &p->d_eB, &p->d_eAmax, &p->d_eBmax, &p->d_a_tiles, &p->d_b_tiles,
-                    &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta, &p->d_part, &p->d_red,
-                    &p->h_A, &p->h_B, &p->h_C, &p->h_aoff, &p->h_boff, &p->h_coff};
+                    &p->d_a_blocks, &p->d_b_blocks, &p->d_err, &p->d_timings, &p->d_unit_cta, &p->d_part, &p->d_red};
+  host_release(p);
   for (DevBuf* b : bufs) dev_free(*b);
   for (auto& set : p->ev)
     for (cudaEvent_t& e : set)
@@ -805,7 +880,7 @@ bsmm_status plan_build(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, in
     st = plan_fp64(p);
   } else {
     p->s = o.nslices;
-    p->cl = o.cluster ? o.cluster : kSplitDefaultCluster;
+    p->cl = o.cluster > 0 ? o.cluster : kSplitDefaultCluster;  // -1: chosen in plan_split
     p->tn = split_tile_n(p->s);
     p->stages = o.stages ? o.stages : split_stages(p->s, p->tn);
     st = plan_split(p);

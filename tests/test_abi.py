@@ -142,3 +142,10 @@ def test_execute_batch_rejects_null_arguments():
     d = (ctypes.c_double * 1)(1.0)
     assert L.bsmm_execute_batch(1, one, d, one, one, one, one, d, one, one, None) == 1
     assert L.bsmm_measure_rates(None, None) == 1
+
+
+def test_host_products_reject_null_arguments():
+    L = P.lib()
+    assert L.bsmm_execute_host_async(None, 1.0, None, 0, None, None, 0, None, 0.0, None, 0, None, None) == 1
+    assert L.bsmm_host_wait(None) == 1
+    assert "NULL" in P.bsmm_last_error()

@@ -1,6 +1,9 @@
-"""The boundary's one-call batch (bsmm_execute_batch) and the learned schedule's
-checkpoint (bsmm_mlp_save / bsmm_mlp_load, bsmm_options.model_path), through the C ABI.
-Neither may change a single bit of any result: only the order of the work units does."""
+"""The boundary's one-call batch (bsmm_execute_batch), the learned schedule's checkpoint
+(bsmm_mlp_save / bsmm_mlp_load, bsmm_options.model_path) and host-buffer products in
+flight (bsmm_execute_host_async / bsmm_host_wait), through the C ABI. None may change a
+single bit of any result: only the order of the work units, or of the copies, does."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -226,3 +229,47 @@ def test_batch_of_mixed_element_types():
         it["C"].copy_(torch.from_numpy(it["C0"]))
     g.replay()
     check()
+
+
+def test_host_products_in_flight_match_the_oracle():
+    """Five host-buffer products enqueued on one plan before a single wait: staging slots
+    alternate, the copies of one overlap the kernels of another, beta = 0 and beta != 0 mix,
+    pinned and pageable host arrays mix, and one product's longer A arena makes its slot
+    grow while the slot's previous product may still be in flight. Each C gets exactly the
+    oracle's bits for its own inputs."""
+    import torch
+    prob = _elem_problem(P.BSMM_F64, 37)
+    cs, _, _ = oracle.structure(prob)
+    off, _ = G.layout_arena(cs, prob.row_sizes, prob.col_sizes)
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                       mode=P.BSMM_SPLIT_BF16, nslices=6, debug_checks=1)
+    rng = np.random.default_rng(5)
+    runs = []
+    for i in range(5):
+        pi = copy.copy(prob)
+        pi.A = rng.uniform(-1, 1, prob.A.size)
+        pi.B = rng.uniform(-1, 1, prob.B.size) * 2.0 ** (i - 2)
+        pi.alpha, pi.beta = [1.0, -0.5, 3.0, 0.25, 1.0][i], [0.0, 1.0, 0.0, -2.0, 0.5][i]
+        _, C0 = c_arena(pi, cs, rng=np.random.default_rng(100 + i))
+        A = np.concatenate([pi.A, np.zeros(4096)]) if i == 3 else pi.A
+        if i % 2 == 0:  # pinned host memory
+            A, B, C = (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (A, pi.B, C0))
+        else:
+            B, C = pi.B.copy(), C0.copy()
+        runs.append((pi, C0, A, B, C))
+    for pi, _, A, B, C in runs:
+        P.bsmm_execute_host_async(plan, pi.alpha, A, prob.a_off, B, prob.b_off, pi.beta, C, off)
+    P.bsmm_host_wait(plan)
+    P.bsmm_status_device(plan)
+    for pi, C0, _, _, C in runs:
+        got = C.numpy() if hasattr(C, "numpy") else C
+        want = C0.copy()
+        OS.bsmm_split(pi, cs, want, off, 6)
+        assert np.array_equal(struct_elements(pi, cs, off, got), struct_elements(pi, cs, off, want))
+    # the synchronous form after them, on the same slots
+    pi, C0, _, _, _ = runs[1]
+    C = C0.copy()
+    P.bsmm_execute_host(plan, pi.alpha, pi.A, prob.a_off, pi.B, prob.b_off, pi.beta, C, off)
+    want = C0.copy()
+    OS.bsmm_split(pi, cs, want, off, 6)
+    assert np.array_equal(struct_elements(pi, cs, off, C), struct_elements(pi, cs, off, want))

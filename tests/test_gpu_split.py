@@ -274,10 +274,10 @@ def test_too_deep_inner_block_is_rejected():
     assert ei.value.status == 5
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("cluster", [1, 2, 4, -1])
 @pytest.mark.parametrize("recipe", ["nonuniform_dense", "clustered", "ragged"])
 def test_column_block_group_sizes(cluster, recipe):
-    """Units of 1, 2 or 4 column blocks, one per CTA of a group: same bits, including
+    """Units of 1, 2 or 4 column blocks (or the planner's choice, -1), one per CTA of a group: same bits, including
     groups whose last members fall beyond the matrix and CTAs whose own column block has
     no B tile at some k block of the group's list."""
     if recipe == "nonuniform_dense":
