@@ -11,8 +11,14 @@
 // still in L2 (a product larger than that is a wave of its own). FP64 is one wave.
 // Products whose plans split a k-list (bsmm_options.ksplit) get their reduction kernels
 // after the contraction launch of their wave.
-// bsmm_batch_execute issues kernels only, so a stream capture of it records a CUDA
-// graph that replays the whole batch with one graph launch.
+// Consecutive waves of a split batch go to two streams in turn (the caller's and one of
+// the batch's, forked from and joined back into the caller's), as the paper lets the
+// stages of independent products overlap (Sec. 1: no global synchronisation between
+// multiplications): a wave's slicing kernels and contraction start on the SMs that the
+// previous wave's contraction frees during its last units, instead of after its last
+// CTA. Waves share no buffer, so nothing orders them but the stream they run on.
+// bsmm_batch_execute issues kernels and stream events only, so a stream capture of it
+// records a CUDA graph that replays the whole batch with one graph launch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -51,6 +57,8 @@ struct bsmm_batch_s {
   int32_t launches = 0;  // kernels the last bsmm_batch_execute launched
   DevBuf d_prods, d_unit_prod, d_unit_local, d_sched_ptr, d_sched_units, d_err;
   std::vector<bsmm_plan_t> owned;  // plans made by bsmm_batch_autotune, destroyed with the batch
+  cudaStream_t side = nullptr;     // split modes with two or more waves: the second stream
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -103,8 +111,12 @@ bsmm_status repack(bsmm_batch_s* b) {
 }
 
 void free_batch(bsmm_batch_s* b) {
+  if (b->side) cudaStreamSynchronize(b->side);
   for (DevBuf* d : {&b->d_prods, &b->d_unit_prod, &b->d_unit_local, &b->d_sched_ptr, &b->d_sched_units, &b->d_err})
     if (d->p) cudaFree(d->p);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
   for (bsmm_plan_t p : b->owned) bsmm_destroy(p);
   delete b;
 }
@@ -358,6 +370,15 @@ bsmm_status bsmm_batch_create(bsmm_batch_t* out, int32_t count, const bsmm_plan_
     free_batch(b);
     return set_error("cudaMemset failed"), BSMM_ERR_CUDA;
   }
+  if (b->mode != BSMM_FP64 && b->wave_bins.size() >= 2) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return set_error(std::string("batch stream: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+    }
+  }
   *out = b;
   return BSMM_OK;
 }
@@ -402,8 +423,14 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   int32_t n = 0;
+  if (b->side) {  // the second stream starts after everything the caller enqueued before
+    e = cudaEventRecord(b->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+  }
+  int32_t nw = 0;  // waves with units so far
   for (size_t w = 0; w + 1 < b->wave_prod.size() && e == cudaSuccess; w++) {
     if (b->prod_begin[b->wave_prod[w + 1]] == b->prod_begin[b->wave_prod[w]]) continue;  // no units
+    const cudaStream_t ws = b->side && (nw++ & 1) ? b->side : st;
     const int32_t* sp = (const int32_t*)b->d_sched_ptr.p + b->wave_ptr[w];
     if (b->mode == BSMM_FP64) {
       Fp64Args a = b->fargs[0];
@@ -424,7 +451,7 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
     } else {
       for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1] && e == cudaSuccess; i++) {
         int k = 0;
-        e = launch_split_prep(b->sargs[i], st, nullptr, &k);
+        e = launch_split_prep(b->sargs[i], ws, nullptr, &k);
         n += split_prep_kernels(b->sargs[i]);
       }
       if (e != cudaSuccess) break;
@@ -436,14 +463,19 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
       a.unit_prod = (const int32_t*)b->d_unit_prod.p;
       a.unit_local = (const int32_t*)b->d_unit_local.p;
       a.err = (int32_t*)b->d_err.p;
-      e = launch_split_mma(a, b->wave_bins[w], st);
+      e = launch_split_mma(a, b->wave_bins[w], ws);
       n++;
       for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1] && e == cudaSuccess; i++)
         if (b->sargs[i].n_red > 0) {
-          e = launch_split_reduce(b->sargs[i], st);
+          e = launch_split_reduce(b->sargs[i], ws);
           n++;
         }
     }
+  }
+  if (b->side) {  // join: the caller's stream continues after both streams' waves
+    const cudaError_t j = cudaEventRecord(b->join, b->side);
+    const cudaError_t k = j == cudaSuccess ? cudaStreamWaitEvent(st, b->join, 0) : j;
+    if (e == cudaSuccess) e = k;
   }
   if (e != cudaSuccess) return set_error(std::string("batch launch: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
   b->launches = n;

@@ -196,3 +196,52 @@ def test_autotune_cache_file(mode, tmp_path):
     _, cached3 = P.bsmm_batch_autotune_cached(batch3, path, reps=1)
     assert not cached3 and json.loads(path.read_text())["format"] == "bsmm-tune"
     check(items3, batch3)
+
+
+def test_batch_waves_on_two_streams_same_bits_as_separate():
+    """Products whose slice workspaces (about 61 MB each) make every one a wave of its own,
+    with small products between them: the waves alternate between the caller's stream and
+    the batch's second one. Eager and graph-replayed, every C has the bits of the product
+    run on its own."""
+    import torch
+    probs = [G.make_problem("nonuniform_dense", 40 + i, 1600, lo=64, hi=256) if i % 2 == 0 else
+             G.make_problem("clustered", 40 + i, 500, lo=16, hi=120, nclusters=4, cluster_density=0.3)
+             for i in range(6)]
+    items = []
+    for i, prob in enumerate(probs):
+        prob.alpha, prob.beta = [1.0, -0.5, 2.0][i % 3], [0.0, 1.0, 0.5][i % 3]
+        cs, _, _ = oracle.structure(prob)
+        off, C0 = c_arena(prob, cs, rng=np.random.default_rng(i))
+        plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                           mode=P.BSMM_SPLIT_BF16, nslices=6)
+        d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        items.append(dict(prob=prob, C0=C0, plan=plan, A=d(prob.A), B=d(prob.B), ao=d(prob.a_off),
+                          bo=d(prob.b_off), co=d(off), C=d(C0)))
+    wants = []
+    for it in items:
+        C = torch.from_numpy(it["C0"].copy()).cuda()
+        P.bsmm_execute(it["plan"], it["prob"].alpha, it["A"], it["ao"], it["B"], it["bo"], it["prob"].beta, C,
+                       it["co"])
+        wants.append(C.cpu().numpy())
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                          [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                          [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    P.bsmm_batch_status_device(batch)
+    for it, want in zip(items, wants):
+        assert np.array_equal(it["C"].cpu().numpy(), want)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        P.bsmm_batch_execute(batch)
+    for _ in range(2):
+        for it in items:
+            it["C"].copy_(torch.from_numpy(it["C0"]))
+        g.replay()
+        torch.cuda.synchronize()
+        for it, want in zip(items, wants):
+            assert np.array_equal(it["C"].cpu().numpy(), want)
+    P.bsmm_batch_status_device(batch)
