@@ -525,8 +525,10 @@ bsmm_status bsmm_selftest_wait(int64_t limit_ns, void* stream);
 /*
  * Per-unit timing records of the last execute with record_timings set:
  * start_ns[n_units], end_ns[n_units] (device %globaltimer, host outputs, either
- * may be NULL) and the CTA each unit ran on (cta[n_units], may be NULL).
- * Synchronises the device.
+ * may be NULL) and the CTA each unit ran on (cta[n_units], may be NULL). A split-mode
+ * unit of a column-block group of several CTAs (bsmm_options.cluster) starts when the
+ * group's first CTA starts it, and end_ns - start_ns is the longest time any CTA of the
+ * group spent on it (the group's cost in the packing). Synchronises the device.
  */
 bsmm_status bsmm_plan_timings(bsmm_plan_t plan, int64_t* start_ns, int64_t* end_ns, int32_t* cta);
 

@@ -163,6 +163,11 @@ bsmm_status run(bsmm_plan_s* p, double alpha, const void* A, const int64_t* a_of
     ev = p->ev[set];
   }
   int nk = 0;
+  // the split kernels take the longest of a group's CTA times with atomicMax
+  if (p->opt.record_timings && p->d_timings.p) {
+    e = cudaMemsetAsync(p->d_timings.p, 0, p->d_timings.bytes, st);
+    if (e != cudaSuccess) return set_error(std::string("timing records: ") + cudaGetErrorString(e)), BSMM_ERR_CUDA;
+  }
   if (p->opt.mode == BSMM_FP64) {
     Fp64Args a{};
     fill_fp64_args(p, a, alpha, (const double*)A, a_off, (const double*)B, b_off, beta, (double*)C, c_off);
@@ -420,9 +425,10 @@ bsmm_status bsmm_plan_timings(bsmm_plan_t p, int64_t* start_ns, int64_t* end_ns,
     if (cta && cudaMemcpy(cta, p->d_unit_cta.p, sizeof(int32_t) * p->n_units, cudaMemcpyDeviceToHost) != cudaSuccess)
       return set_error("timing copy failed"), BSMM_ERR_CUDA;
   }
+  // the device records each unit's start and the longest time a CTA spent on it
   for (int64_t u = 0; u < p->n_units; u++) {
     if (start_ns) start_ns[u] = t[2 * u];
-    if (end_ns) end_ns[u] = t[2 * u + 1];
+    if (end_ns) end_ns[u] = t[2 * u] + t[2 * u + 1];
   }
   return BSMM_OK;
 }

@@ -109,7 +109,8 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
     const Fp64Args& P = a.prods ? a.prods[a.unit_prod[u]] : a;
     if (a.prods) u = a.unit_local[u];
     const Fp64Unit un = P.units[u];
-    if (a.timings && tid == 0) a.timings[2 * (int64_t)u] = gtimer();
+    const int64_t t_unit = a.timings && tid == 0 ? gtimer() : 0;
+    if (a.timings && tid == 0) a.timings[2 * (int64_t)u] = t_unit;
     const int i = un.i, j = un.j;
     const int ri = P.r[i], cj = P.c[j];
     const int rows = min(BM, ri - un.r0), cols = min(BN, cj - un.c0);
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__((T / 4) * (T / 4), 4096 / (T * T) * 2 > 8 ? 8 
     if (a.timings) {
       __syncthreads();
       if (tid == 0) {
-        a.timings[2 * (int64_t)u + 1] = gtimer();
+        a.timings[2 * (int64_t)u + 1] = gtimer() - t_unit;  // the unit's time
         a.unit_cta[u] = cta;
       }
     }

@@ -1501,7 +1501,10 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
       const SplitUnit un = P.units[u];
       const int cb = un.cb * CL + rank;
       if (cb >= P.CB) continue;  // a group's CTA past the last column block has no work
-      if (a.timings && rank == 0 && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = gtimer();
+      // timing record: the unit's start (the group's first CTA) and the longest time any CTA
+      // of the group spends on it
+      const int64_t t_unit = a.timings && ew == 0 && lane == 0 ? gtimer() : 0;
+      if (a.timings && rank == 0 && ew == 0 && lane == 0) a.timings[2 * (int64_t)u] = t_unit;
       const int64_t m = (int64_t)un.rb * kSplitBM + row;
       const bool row_ok = m < P.Mtot;
       const int64_t n0 = (int64_t)cb * TN + half * TH;
@@ -1633,11 +1636,10 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
       ok = epi_all(ok);  // every epilogue warp has the same outcome (and, without store warps,
                          // cstage is free again)
       if (!ok) break;
-      if (a.timings && rank == 0) {
-        if (ew == 0 && lane == 0) {
-          a.timings[2 * (int64_t)u + 1] = gtimer();
-          a.unit_cta[u] = cta;
-        }
+      if (a.timings && ew == 0 && lane == 0) {
+        atomicMax(reinterpret_cast<unsigned long long*>(&a.timings[2 * (int64_t)u + 1]),
+                  (unsigned long long)(gtimer() - t_unit));
+        if (rank == 0) a.unit_cta[u] = cta;
       }
     }
   } else if constexpr (SW) {

@@ -69,3 +69,31 @@ def test_learned_schedule_vs_flop_count():
     print(record)
     assert err_mlp < err_flops
     assert t_mlp <= t_flops
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+def test_unit_records_of_column_block_groups(cluster):
+    """Timing records of groups of 1, 2 or 4 CTAs: every unit that ran has a start and a
+    positive time (the longest of its group's CTAs), no longer than the whole contraction,
+    and the records are rewritten, not accumulated, by the next execute."""
+    import torch
+    prob = G.make_problem("clustered", 3, 2000, lo=16, hi=160, nclusters=5, cluster_density=0.3)
+    plan = P.bsmm_plan(prob.row_sizes, prob.col_sizes, prob.inner_sizes, prob.a_mask, prob.b_mask,
+                       mode=P.BSMM_SPLIT_BF16, nslices=6, record_timings=1, profile=1, cluster=cluster)
+    q = P.bsmm_plan_query(plan)
+    off, tot = G.layout_arena(q["c_mask"], prob.row_sizes, prob.col_sizes)
+    d = lambda x: torch.from_numpy(x).cuda()
+    A, B, ao, bo, co = d(prob.A), d(prob.B), d(prob.a_off), d(prob.b_off), d(off)
+    C = torch.zeros(max(tot, 2), dtype=torch.float64, device="cuda")
+    spans = []
+    for _ in range(2):
+        P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
+        torch.cuda.synchronize()
+        s, e, cta = P.bsmm_plan_timings(plan)
+        ms = P.bsmm_plan_kernel_ms(plan)[2]
+        ran = s > 0
+        assert ran.all()
+        assert (e[ran] > s[ran]).all()
+        assert ((e[ran] - s[ran]) <= ms * 1e6 * 1.05 + 1e4).all()
+        spans.append((e - s)[ran].sum())
+    assert spans[1] < 1.5 * spans[0]
