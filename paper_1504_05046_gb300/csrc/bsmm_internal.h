@@ -25,6 +25,7 @@ constexpr int kSplitBeta = 7;      // bits per slice
 constexpr int kSplitMaxS = 6;      // slices per operand
 constexpr int kSplitEpiWarps = 8;  // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kSplitGuard = 55;    // guard bits of the 128-bit accumulator below the largest scale
+constexpr double kEpiWalkBlocks = 32.0;  // mean k blocks per unit from which the epilogue walks
 constexpr int kSplitMaxK = 8192;   // inner blocks per product (keeps the 128-bit sum from overflowing)
 
 // FP64-mode geometry.
@@ -121,6 +122,8 @@ struct SplitArgs {
   int32_t M, N, K, s, tn, stages, fp16;
   int32_t cl, CBG;          // CTAs per column-block group; groups (units are (rb, group))
   int32_t sw;               // the contraction kernel's form: 1 = with C store warps
+  int32_t epi_walk;         // 1: the epilogue finds the accumulation groups on its own k list
+                            // (long lists); 0: it takes them from the MMA warps' descriptors
   int64_t Mtot, Ntot;
   int32_t RB, CB, kwords;
   const int32_t* r;
@@ -296,6 +299,7 @@ struct bsmm_plan_s {
   // split geometry
   int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0, cl = 1, CBG = 0;
   int sw = 0;                // contraction kernel with C store warps
+  int epi_walk = 0;          // the epilogue walks the k lists itself (SplitArgs::epi_walk)
   int64_t Mtot = 0, Ntot = 0, colexp_ld = 0;
   int64_t apk_bytes = 0, bpk_bytes = 0;
 

@@ -186,6 +186,7 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
   a.presBg = t->presB;  // clusters of one CTA: a column-block group is one column block
   a.cl = 1;
   a.sw = 0;  // the kernel form without store warps
+  a.epi_walk = 0;  // one short k list: the MMA warps' descriptors
   a.CBG = CB;
   a.apk_off = t->apk_off;
   a.bpk_off = t->bpk_off;

@@ -1250,7 +1250,10 @@ struct ChunkCursor {
 // block times cl column blocks), each its own column block, at about the same time, so
 // the A panel they all read is served from L2. Every CTA loads its own operands; no CTA
 // reads or signals another's shared memory.
-template <int S, int TN, bool SW>
+// WALK: the epilogue finds the accumulation groups on its own k list (products of long
+// k lists) instead of taking the MMA warps' descriptors; the two ways share no code path,
+// so each form keeps its own register allocation.
+template <int S, int TN, bool SW, bool WALK>
 __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __grid_constant__ SplitArgs a) {
   constexpr int TH = TN / 2;                    // columns per epilogue thread
   constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
@@ -1511,32 +1514,66 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
       uint32_t acc[TH][4];  // exact 128-bit two's-complement sums, unit 2^L per column
 #pragma unroll
       for (int c = 0; c < TH; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0u;
-      // The unit's accumulation groups as the MMA warps close them (none when this CTA's
-      // column block has no B tile in the unit's inner range: the planner's own mask).
-      bool more = (un.own >> rank) & 1;
+      // The unit's accumulation groups, in the order the MMA warps fill them. With WALK the
+      // epilogue walks the CTA's own k list with the MMA warps' rule, ahead of them;
+      // otherwise it takes each group's descriptor when the first MMA warp closes it (none
+      // when this CTA's column block has no B tile in the unit's inner range: the planner's
+      // own mask). Either way the groups are the same, in the same order.
+      UnitIter it;
+      int kt = -1;
+      if constexpr (WALK) {
+        it.init(P, un, cb);
+        kt = it.next_own();
+      }
+      bool more = WALK ? kt >= 0 : ((un.own >> rank) & 1) != 0;
       while (more) {
         const uint32_t buf = tcount & 1, use = tcount >> 1;
-        // (the epilogue warps sleep between polls here: while the MMA warps fill a group
-        // they would otherwise take issue slots from the producer and MMA threads)
-        if (!wait_warp(&gready[buf], use & 1, abort_flag, a.err, kWaitNs, kGroupPollNs)) {
-          ok = false;
-          break;
+        int gk0, gsig;  // the group's first k block and, for a uniform group, its class
+        bool guni;
+        if constexpr (WALK) {
+          GroupRule grp;
+          {
+            int sg = 0;
+            const bool uni = scale_class(P, kt, un.rb, cb, sg);
+            grp.start(uni, sg, P.q[kt], P.kdepth);
+          }
+          int kn = it.next_own();
+          for (; kn >= 0; kn = it.next_own()) {
+            int sg = 0;
+            const bool uni = scale_class(P, kn, un.rb, cb, sg);
+            if (!grp.joins(uni, sg, P.q[kn])) break;
+          }
+          gk0 = kt;
+          guni = grp.uni;
+          gsig = grp.sig;
+          kt = kn;
+          more = kt >= 0;
+        } else {
+          // (the epilogue warps sleep between polls here: while the MMA warps fill a group
+          // they would otherwise take issue slots from the producer and MMA threads)
+          if (!wait_warp(&gready[buf], use & 1, abort_flag, a.err, kWaitNs, kGroupPollNs)) {
+            ok = false;
+            break;
+          }
+          const int4 gd = gdesc[buf];
+          more = (gd.z & 2) == 0;
+          gk0 = gd.x;
+          guni = (gd.z & 1) != 0;
+          gsig = gd.y;
         }
-        const int4 gd = gdesc[buf];
-        more = (gd.z & 2) == 0;
         // the binary position of the group's integers: one shift for a uniform group (its
         // common class plus the row's and the columns' parts), per-row and per-column
         // offsets for a lone k block; loaded while the tensor core finishes the group
         int shr = kSplitGuard;
         uint4 cx[TH / 8];
-        if (gd.z & 1) {
-          shr += gd.y + (row_ok ? (int)P.rowadj[m] : 0);
+        if (guni) {
+          shr += gsig + (row_ok ? (int)P.rowadj[m] : 0);
           const uint4* src = reinterpret_cast<const uint4*>(P.coladj + n0);
 #pragma unroll
           for (int w = 0; w < TH / 8; w++) cx[w] = __ldg(src + w);
         } else {
-          shr += row_ok ? (int)P.rowexp[(int64_t)gd.x * P.Mtot + m] : 0;
-          const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)gd.x * P.colexp_ld + n0);
+          shr += row_ok ? (int)P.rowexp[(int64_t)gk0 * P.Mtot + m] : 0;
+          const uint4* src = reinterpret_cast<const uint4*>(P.colexp + (int64_t)gk0 * P.colexp_ld + n0);
 #pragma unroll
           for (int w = 0; w < TH / 8; w++) cx[w] = __ldg(src + w);
         }
@@ -1742,28 +1779,32 @@ __global__ void __launch_bounds__(96) wait_selftest_kernel(int32_t* err, int64_t
   __syncthreads();
 }
 
-template <int S, int TN, bool SW>
+template <int S, int TN, bool SW, bool WALK>
 cudaError_t launch_mma(const SplitArgs& a, int groups, cudaStream_t st) {
   const size_t smem = split_smem_bytes(S, TN, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, SW, WALK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (SW) {
     // the register split assumes exactly kRegsLaunch registers per thread at launch (a
     // smaller allocation could not satisfy the epilogue's setmaxnreg.inc): refuse otherwise
     cudaFuncAttributes fa{};
-    e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, SW>);
+    e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, SW, WALK>);
     if (e != cudaSuccess) return e;
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
   }
-  split_mma_kernel<S, TN, SW><<<(unsigned)(groups * a.cl), threads_of<SW>(), smem, st>>>(a);
+  split_mma_kernel<S, TN, SW, WALK><<<(unsigned)(groups * a.cl), threads_of<SW>(), smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int S>
 cudaError_t launch_mma_sw(const SplitArgs& a, int groups, cudaStream_t st) {
   if (a.cl != 1 && a.cl != 2 && a.cl != 4) return cudaErrorInvalidValue;
-  return a.sw ? launch_mma<S, 32, true>(a, groups, st) : launch_mma<S, 32, false>(a, groups, st);
+  // the walking epilogue is built for the 6-slice form with store warps (the dense
+  // products' default); other forms take the descriptors whatever epi_walk says
+  if constexpr (S == 6)
+    if (a.sw && a.epi_walk) return launch_mma<S, 32, true, true>(a, groups, st);
+  return a.sw ? launch_mma<S, 32, true, false>(a, groups, st) : launch_mma<S, 32, false, false>(a, groups, st);
 }
 
 // Groups of cl CTAs that are resident at once: the persistent grid (one CTA per SM at
@@ -1771,11 +1812,11 @@ cudaError_t launch_mma_sw(const SplitArgs& a, int groups, cudaStream_t st) {
 template <int S, bool SW>
 int max_groups_for(int cl, int stages) {
   const size_t smem = split_smem_bytes(S, 32, stages);
-  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, SW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, SW>, threads_of<SW>(), smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, SW, false>, threads_of<SW>(), smem) !=
       cudaSuccess)
     return 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

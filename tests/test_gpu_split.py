@@ -453,3 +453,23 @@ def test_subnormal_inputs(split_scale):
     OS.bsmm_split(prob, cs, want, off, 6, scaling="rows" if split_scale else "tile")
     Cg, _ = run_lib(prob, cs, C0, off, mode=P.BSMM_SPLIT_BF16, nslices=6, split_scale=split_scale)
     assert np.array_equal(struct_elements(prob, cs, off, Cg), struct_elements(prob, cs, off, want))
+
+
+@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("case", ["uniform", "mixed_scales"])
+def test_long_k_lists_epilogue_walks(cluster, case):
+    """Units of about 70 k blocks (inner blocks of 8..24): the planner lets the epilogue
+    find the accumulation groups on its own k list instead of taking the MMA warps'
+    descriptors. The groups, and so the bits, are the split oracle's: merged groups on
+    uniform scales, and lone or shifting groups when tiles are scaled by k."""
+    rng = np.random.default_rng(77)
+    r = rng.integers(90, 200, 4).astype(np.int32)
+    c = rng.integers(20, 90, 5).astype(np.int32)
+    q = rng.integers(8, 25, 72).astype(np.int32)
+    if case == "uniform":
+        fa, fb = (lambda i, k: 0), (lambda k, j: 0)
+    else:
+        fa, fb = (lambda i, k: (k // 5) % 3 - i % 2), (lambda k, j: (k % 4 == 0) * 2 - j % 2)
+    prob = _scaled_problem(78 + cluster, r, q, c, fa, fb)
+    prob.alpha, prob.beta = 0.5, -1.5
+    check(prob, 6, cluster=cluster)
