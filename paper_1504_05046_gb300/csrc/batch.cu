@@ -457,6 +457,14 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
       if (e != cudaSuccess) break;
       SplitArgs a = b->sargs[0];
       a.sw = b->sw;
+      // the epilogue's way of learning the groups (one kernel form per launch): the one
+      // most of the wave's units ask for; either gives the same bits
+      {
+        int64_t walk = 0;
+        for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1]; i++)
+          if (b->sargs[i].epi_walk) walk += b->prod_begin[i + 1] - b->prod_begin[i];
+        a.epi_walk = 2 * walk >= b->prod_begin[b->wave_prod[w + 1]] - b->prod_begin[b->wave_prod[w]] ? 1 : 0;
+      }
       a.sched_ptr = sp;
       a.sched_units = (const int32_t*)b->d_sched_units.p;
       a.prods = (const SplitArgs*)b->d_prods.p;
