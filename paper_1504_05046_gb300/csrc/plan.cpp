@@ -560,10 +560,10 @@ bsmm_status plan_split(bsmm_plan_s* p) {
   }
   // the contraction kernel's form: with C store warps unless the options say otherwise
   p->sw = p->opt.store_warps == 1 ? 0 : 1;
-  // how the epilogue learns the accumulation groups (6-slice form with store warps): on
-  // units of long k lists it walks the list itself, ahead of the MMA warps (the dense
-  // product: 4% faster); on short ones it takes the MMA warps' descriptors, which spares
-  // the walk's table loads on its critical path (banded: 8% faster)
+  // how the epilogue learns the accumulation groups (forms with store warps, 3 to 6
+  // slices): on units of long k lists it walks the list itself, ahead of the MMA warps
+  // (the dense product: 3.5% faster); on short ones it takes the MMA warps' descriptors,
+  // which spares the walk's table loads on its critical path (banded: 8% faster)
   {
     double blocks = 0.0;
     for (size_t u = 0; u < base.size(); u++) blocks += (double)blen[u];

@@ -1800,9 +1800,9 @@ cudaError_t launch_mma(const SplitArgs& a, int groups, cudaStream_t st) {
 template <int S>
 cudaError_t launch_mma_sw(const SplitArgs& a, int groups, cudaStream_t st) {
   if (a.cl != 1 && a.cl != 2 && a.cl != 4) return cudaErrorInvalidValue;
-  // the walking epilogue is built for the 6-slice form with store warps (the dense
-  // products' default); other forms take the descriptors whatever epi_walk says
-  if constexpr (S == 6)
+  // the walking epilogue is built for the forms with store warps and 3 to 6 slices (the
+  // dense products' default); other forms take the descriptors whatever epi_walk says
+  if constexpr (S >= 3)
     if (a.sw && a.epi_walk) return launch_mma<S, 32, true, true>(a, groups, st);
   return a.sw ? launch_mma<S, 32, true, false>(a, groups, st) : launch_mma<S, 32, false, false>(a, groups, st);
 }

@@ -455,9 +455,9 @@ def test_subnormal_inputs(split_scale):
     assert np.array_equal(struct_elements(prob, cs, off, Cg), struct_elements(prob, cs, off, want))
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("cluster,s", [(1, 6), (2, 6), (1, 4), (4, 3)])
 @pytest.mark.parametrize("case", ["uniform", "mixed_scales"])
-def test_long_k_lists_epilogue_walks(cluster, case):
+def test_long_k_lists_epilogue_walks(cluster, s, case):
     """Units of about 70 k blocks (inner blocks of 8..24): the planner lets the epilogue
     find the accumulation groups on its own k list instead of taking the MMA warps'
     descriptors. The groups, and so the bits, are the split oracle's: merged groups on
@@ -472,4 +472,4 @@ def test_long_k_lists_epilogue_walks(cluster, case):
         fa, fb = (lambda i, k: (k // 5) % 3 - i % 2), (lambda k, j: (k % 4 == 0) * 2 - j % 2)
     prob = _scaled_problem(78 + cluster, r, q, c, fa, fb)
     prob.alpha, prob.beta = 0.5, -1.5
-    check(prob, 6, cluster=cluster)
+    check(prob, s, cluster=cluster)
