@@ -230,7 +230,10 @@ bsmm_status bsmm_plan_ksplit(bsmm_plan_t plan, int64_t* n_regions, int64_t* n_pi
  * lg(columns), lg(inner blocks in its k-list), lg(inner depth), lg(16-deep steps),
  * lg(useful flops), useful / padded flops, then for the split modes 1, s/6,
  * lg(row tiles), lg(column tiles), lg(32-deep chunks); for FP64 0, 0, 0, 0,
- * lg(16-deep steps). A piece of a cut k-list has the features of its own range.
+ * lg(16-deep steps). A piece of a cut k-list has the features of its own range. In the
+ * split modes the k-list terms are those of the group's slowest CTA (the one with the
+ * most 16-deep steps on its own column block's list; with groups of one CTA, the unit's
+ * list), since a group costs what its slowest CTA does.
  */
 #define BSMM_NFEATURES 12
 bsmm_status bsmm_plan_features(bsmm_plan_t plan, float* features, double* flop_costs);
@@ -491,13 +494,14 @@ bsmm_status bsmm_plan_predict_costs(bsmm_plan_t plan, bsmm_mlp_t mlp, void* stre
  * parameters and the standardisation of `mlp` to `path` (created or replaced); the
  * file is binary, little-endian: the 8 bytes "BSMMMLP\0", uint32 format version (1),
  * uint32 feature version (BSMM_FEATURE_VERSION: the order and meaning of the
- * bsmm_plan_features columns), uint32 F, uint32 hidden width, uint32 parameter count,
+ * bsmm_plan_features columns; 2 since the split modes' k-list terms are the slowest
+ * CTA's of a group), uint32 F, uint32 hidden width, uint32 parameter count,
  * the float32 parameters, x means[F], x deviations[F], y mean, y deviation, then a
  * uint64 FNV-1a checksum of every byte before it. bsmm_mlp_load creates a model from
  * such a file (BSMM_ERR_INVALID for a missing or unreadable file, a bad checksum, or
  * another format, feature version or shape). Adam state is not saved.
  */
-#define BSMM_FEATURE_VERSION 1
+#define BSMM_FEATURE_VERSION 2
 bsmm_status bsmm_mlp_save(bsmm_mlp_t mlp, const char* path);
 bsmm_status bsmm_mlp_load(bsmm_mlp_t* out, const char* path);
 /* Where the plan's current unit costs came from (bsmm_cost_source). */

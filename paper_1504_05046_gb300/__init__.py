@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "BsmmError", "lib", "library_path", "BSMM_FP64", "BSMM_SPLIT_BF16", "BSMM_SPLIT_FP16",
-    "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "Plan",
+    "BSMM_SCHED_FLOPS", "BSMM_SCHED_COSTS", "BSMM_SCHED_NATURAL", "BSMM_NFEATURES", "BSMM_FEATURE_VERSION", "Plan",
     "bsmm_options_default", "bsmm_plan", "bsmm_plan_query", "bsmm_plan_ksplit", "bsmm_plan_features",
     "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
     "bsmm_execute_host_async", "bsmm_host_wait", "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
@@ -33,6 +33,7 @@ BSMM_FP64, BSMM_SPLIT_BF16, BSMM_SPLIT_FP16 = 0, 1, 2
 BSMM_SCHED_FLOPS, BSMM_SCHED_COSTS, BSMM_SCHED_NATURAL = 0, 1, 2
 BSMM_F64, BSMM_F32, BSMM_C128 = 0, 1, 2
 BSMM_NFEATURES = 12
+BSMM_FEATURE_VERSION = 2  # include/bsmm.h: the meaning of the bsmm_plan_features columns
 STATUS = {0: "BSMM_OK", 1: "BSMM_ERR_INVALID", 2: "BSMM_ERR_CUDA", 3: "BSMM_ERR_NOMEM",
           4: "BSMM_ERR_TIMEOUT", 5: "BSMM_ERR_UNSUPPORTED", 6: "BSMM_ERR_DEVICE"}
 

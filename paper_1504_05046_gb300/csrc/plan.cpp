@@ -615,14 +615,24 @@ bsmm_status plan_split(bsmm_plan_s* p) {
       const int64_t n0 = (int64_t)cb * CL * tn, n1 = std::min<int64_t>(Ntot, n0 + (int64_t)CL * tn);
       int nrt, nct;
       const double fl = region_flops(rb, cb, un.k0, un.k1, nrt, nct);
-      int64_t kq = 0, kg = 0, kc = 0;
-      for (int64_t x = lo; x < hi; x++) {
-        const int k = ks[x];
-        kq += p->q[k];
-        kg += log2i_ceil_div(p->q[k], 16);
-        kc += log2i_ceil_div(p->q[k], kSplitKC);
+      // the k-list terms of the group's slowest CTA: each CTA of a group takes the k blocks
+      // where its own column block has a B tile, and the group costs what its slowest CTA
+      // does (with groups of one: the unit's whole list)
+      int64_t kq = 0, kg = 0, kc = 0, nk = 0;
+      for (int r = 0; r < CL; r++) {
+        const int64_t cbr = (int64_t)cb * CL + r;
+        if (cbr >= CB) break;
+        int64_t q_r = 0, g_r = 0, c_r = 0, n_r = 0;
+        for (int64_t x = lo; x < hi; x++) {
+          const int k = ks[x];
+          if (!(presB[(size_t)cbr * KW + k / 64] >> (k % 64) & 1)) continue;
+          q_r += p->q[k];
+          g_r += log2i_ceil_div(p->q[k], 16);
+          c_r += log2i_ceil_div(p->q[k], kSplitKC);
+          n_r++;
+        }
+        if (g_r > kg || (g_r == kg && q_r > kq)) kq = q_r, kg = g_r, kc = c_r, nk = n_r;
       }
-      const int64_t nk = hi - lo;
       p->flop_cost.push_back(std::max(fl, 1.0));
       const double padded = 2.0 * kSplitBM * tn * CL * 16.0 * (double)kg;
       float f[BSMM_NFEATURES] = {lg((double)(m1 - m0)), lg((double)(n1 - n0)), lg((double)nk), lg((double)kq),

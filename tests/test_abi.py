@@ -92,7 +92,7 @@ def test_tune_space_lists_fitting_candidates():
         P.bsmm_tune_space(P.BSMM_SPLIT_BF16, 7)
 
 
-def _model_file(path, version=1, feature_version=1, F=12, H=32, corrupt=False):
+def _model_file(path, version=1, feature_version=P.BSMM_FEATURE_VERSION, F=12, H=32, corrupt=False):
     """A cost-model file laid out as include/bsmm.h states (written here byte by byte)."""
     import struct
     NP = H * F + H + H * H + H + H + 1
@@ -117,7 +117,7 @@ def test_cost_model_file_checks_before_any_device_work(tmp_path):
     with pytest.raises(P.BsmmError) as ei:
         P.bsmm_mlp_load(tmp_path / "missing.bin")
     assert ei.value.status == 1
-    for kw in (dict(corrupt=True), dict(version=2), dict(feature_version=9), dict(H=16)):
+    for kw in (dict(corrupt=True), dict(version=2), dict(feature_version=9), dict(feature_version=1), dict(H=16)):
         _model_file(tmp_path / "m.bin", **kw)
         with pytest.raises(P.BsmmError) as ei:
             P.bsmm_mlp_load(tmp_path / "m.bin")
