@@ -597,7 +597,8 @@ def run_single(args, rank, world):
     if head_split:
         roof = {"bound": "tensor", "kernel": "split_mma_kernel", "achieved": pair / (k_split[cis] * 1e-3) / 1e12,
                 "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s", "traffic": None,
-                "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"}
+                "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
+                "launch": P.bsmm_plan_form(plan)}
     else:
         roof = dict(fp64_roofline(P, pk, F / (k64[cif] * 1e-3) / 1e12), kernel="fp64_tile_kernel", traffic=None)
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -770,7 +771,7 @@ def run_dense(args, rank, world, local):
                 "unit": "TFLOP/s", "frac": mma_tflops / peak_tc, "traffic": traffic,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (MEASURED_PEAKS.json)",
                 "achieved_def": f"{s * (s + 1) // 2} slice-pair products x useful flops per launch / mean launch time",
-                "kernel_ms": k_avg}
+                "kernel_ms": k_avg, "launch": P.bsmm_plan_form(plan)}
     if traffic:  # the recorded DRAM bytes per launch over this run's launch time, against the copy peak
         roofline["dram_gbs"] = traffic / t_mma / 1e9
         roofline["dram_frac_of_measured_copy_peak"] = roofline["dram_gbs"] / pk["hbm_gbs"]

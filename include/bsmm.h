@@ -506,6 +506,19 @@ bsmm_status bsmm_mlp_save(bsmm_mlp_t mlp, const char* path);
 bsmm_status bsmm_mlp_load(bsmm_mlp_t* out, const char* path);
 /* Where the plan's current unit costs came from (bsmm_cost_source). */
 bsmm_status bsmm_plan_cost_source(bsmm_plan_t plan, int32_t* source);
+
+/*
+ * The contraction launch the planner chose for a plan (host outputs; any may be NULL):
+ * cluster = CTAs per column-block group (1, 2 or 4; bsmm_options.cluster = -1 resolved),
+ * store_warps = 1 when the kernel form has C store warps, epi_walk = 1 when the epilogue
+ * walks its own k lists for the accumulation groups (long k lists, 3 to 6 slices with
+ * store warps) rather than taking the MMA warps' descriptors, stages = depth of the
+ * shared-memory ring, ctas = persistent CTAs (FP64) or groups (split modes) of a launch.
+ * FP64 plans report cluster 1, store_warps 0, epi_walk 0, stages 0. BSMM_ERR_INVALID for
+ * a NULL plan.
+ */
+bsmm_status bsmm_plan_form(bsmm_plan_t plan, int32_t* cluster, int32_t* store_warps, int32_t* epi_walk,
+                           int32_t* stages, int32_t* ctas);
 void bsmm_mlp_destroy(bsmm_mlp_t mlp);
 
 /*

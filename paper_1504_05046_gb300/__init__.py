@@ -25,7 +25,7 @@ __all__ = [
     "bsmm_plan_set_costs", "bsmm_plan_set_ctas", "bsmm_execute", "bsmm_execute_f32", "bsmm_execute_host",
     "bsmm_execute_host_async", "bsmm_host_wait", "bsmm_status_device", "BSMM_F64", "BSMM_F32", "BSMM_C128",
     "bsmm_plan_timings", "bsmm_plan_kernel_ms", "bsmm_split_tile_noalloc", "bsmm_selftest_wait", "bsmm_last_error",
-    "bsmm_measure_rates",
+    "bsmm_measure_rates", "bsmm_plan_form",
     "bsmm_destroy", "EXPORTED",
 ]
 
@@ -48,7 +48,7 @@ EXPORTED = [
     "bsmm_mlp_set_norm", "bsmm_mlp_get_norm", "bsmm_mlp_loss_grad", "bsmm_mlp_fit", "bsmm_mlp_predict",
     "bsmm_plan_predict_costs", "bsmm_mlp_destroy", "bsmm_selftest_wait", "bsmm_schedule_lpt",
     "bsmm_schedule_pieces", "bsmm_measure_rates", "bsmm_mlp_save", "bsmm_mlp_load", "bsmm_plan_cost_source",
-    "bsmm_execute_batch", "bsmm_batch_autotune_cached", "bsmm_last_error", "bsmm_destroy",
+    "bsmm_execute_batch", "bsmm_batch_autotune_cached", "bsmm_plan_form", "bsmm_last_error", "bsmm_destroy",
 ]
 
 
@@ -128,6 +128,7 @@ def lib():
         L.bsmm_batch_autotune_cached.argtypes = [P, ctypes.c_char_p, i32, P, P, P]
         L.bsmm_mlp_load.argtypes = [ctypes.POINTER(P), ctypes.c_char_p]
         L.bsmm_plan_cost_source.argtypes = [P, P]
+        L.bsmm_plan_form.argtypes = [P, P, P, P, P, P]
         L.bsmm_mlp_destroy.argtypes = [P]
         L.bsmm_mlp_destroy.restype = None
         L.bsmm_last_error.argtypes = []
@@ -590,6 +591,13 @@ def bsmm_mlp_load(path) -> Mlp:
 
 
 BSMM_COSTS_FLOPS, BSMM_COSTS_MODEL, BSMM_COSTS_GIVEN = 0, 1, 2
+
+
+def bsmm_plan_form(plan: Plan) -> dict:
+    """The planner's launch choices: cluster, store_warps, epi_walk, stages, ctas."""
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check(lib().bsmm_plan_form(plan.handle, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("cluster", "store_warps", "epi_walk", "stages", "ctas"), (x.value for x in v)))
 
 
 def bsmm_plan_cost_source(plan: Plan) -> int:

@@ -1066,6 +1066,18 @@ bsmm_status bsmm_plan_cost_source(bsmm_plan_t p, int32_t* source) {
   return BSMM_OK;
 }
 
+bsmm_status bsmm_plan_form(bsmm_plan_t p, int32_t* cluster, int32_t* store_warps, int32_t* epi_walk,
+                           int32_t* stages, int32_t* ctas) {
+  if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
+  const bool split = p->opt.mode != BSMM_FP64;
+  if (cluster) *cluster = split ? p->cl : 1;
+  if (store_warps) *store_warps = split ? p->sw : 0;
+  if (epi_walk) *epi_walk = split && p->sw && p->s >= 3 ? p->epi_walk : 0;
+  if (stages) *stages = split ? p->stages : 0;
+  if (ctas) *ctas = p->ctas;
+  return BSMM_OK;
+}
+
 bsmm_status bsmm_plan_set_ctas(bsmm_plan_t p, int32_t ctas) {
   if (!p) return set_error("plan is NULL"), BSMM_ERR_INVALID;
   if (ctas < 0 || ctas > 65535) return set_error("ctas out of range"), BSMM_ERR_INVALID;

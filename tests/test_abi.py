@@ -146,6 +146,7 @@ def test_execute_batch_rejects_null_arguments():
 
 def test_host_products_reject_null_arguments():
     L = P.lib()
+    assert L.bsmm_plan_form(None, None, None, None, None, None) == 1
     assert L.bsmm_execute_host_async(None, 1.0, None, 0, None, None, 0, None, 0.0, None, 0, None, None) == 1
     assert L.bsmm_host_wait(None) == 1
     assert "NULL" in P.bsmm_last_error()

@@ -273,3 +273,30 @@ def test_host_products_in_flight_match_the_oracle():
     want = C0.copy()
     OS.bsmm_split(pi, cs, want, off, 6)
     assert np.array_equal(struct_elements(pi, cs, off, C), struct_elements(pi, cs, off, want))
+
+
+def test_plan_form_reports_the_planners_choices():
+    """bsmm_plan_form: a dense pattern whose column blocks fill groups of 4 exactly gets
+    groups of 4 from cluster = -1, a sparse clustered one groups of 1; long k lists (72
+    inner blocks) get the walking epilogue with 3 to 6 slices and store warps, and not with
+    2 slices, without store warps or with short lists; FP64 plans report the neutral form."""
+    dense = G.make_problem("nonuniform_dense", 5, 1024, lo=64, hi=200)
+    f = P.bsmm_plan_form(P.bsmm_plan(dense.row_sizes, dense.col_sizes, dense.inner_sizes, dense.a_mask,
+                                     dense.b_mask, mode=P.BSMM_SPLIT_BF16, nslices=6, cluster=-1))
+    assert f["cluster"] == 4 and f["store_warps"] == 1 and f["epi_walk"] == 0 and f["stages"] >= 2
+    f = P.bsmm_plan_form(P.bsmm_plan(dense.row_sizes, dense.col_sizes, dense.inner_sizes, dense.a_mask,
+                                     dense.b_mask, mode=P.BSMM_SPLIT_BF16, nslices=6))
+    assert f["cluster"] == 1
+    sparse = G.make_problem("clustered", 6, 3000, lo=16, hi=160, nclusters=5, cluster_density=0.2)
+    f = P.bsmm_plan_form(P.bsmm_plan(sparse.row_sizes, sparse.col_sizes, sparse.inner_sizes, sparse.a_mask,
+                                     sparse.b_mask, mode=P.BSMM_SPLIT_BF16, nslices=6, cluster=-1))
+    assert f["cluster"] == 1 and f["epi_walk"] == 0
+    rng = np.random.default_rng(8)
+    r, c = rng.integers(90, 200, 3).astype(np.int32), rng.integers(20, 90, 4).astype(np.int32)
+    q = rng.integers(8, 25, 72).astype(np.int32)
+    am, bm = np.ones((3, 72), np.uint8), np.ones((72, 4), np.uint8)
+    walk = lambda **o: P.bsmm_plan_form(P.bsmm_plan(r, c, q, am, bm, mode=P.BSMM_SPLIT_BF16, **o))["epi_walk"]
+    assert walk(nslices=6) == 1 and walk(nslices=3) == 1
+    assert walk(nslices=2) == 0 and walk(nslices=6, store_warps=1) == 0
+    f = P.bsmm_plan_form(P.bsmm_plan(r, c, q, am, bm, mode=P.BSMM_FP64))
+    assert (f["cluster"], f["store_warps"], f["epi_walk"], f["stages"]) == (1, 0, 0, 0) and f["ctas"] >= 1
