@@ -36,13 +36,13 @@ def test_tile_exponent_definition():
         assert not (Fraction(mu) < Fraction(2) ** (e - 1))
 
 
+@pytest.mark.parametrize("beta", [7, 8])
 @pytest.mark.parametrize("s", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("seed", range(4))
-def test_slicing_exact_reconstruction_and_bounds(s, seed):
+def test_slicing_exact_reconstruction_and_bounds(s, seed, beta):
     rng = np.random.default_rng(seed * 10 + s)
     x = _wide_tile(rng, 5, 7, spread=60)
-    beta = S.BETA_BITS
-    e, sl, rho = S.slice_tile(x, s)
+    e, sl, rho = S.slice_tile(x, s, beta)
     assert len(sl) == s
     for t, n in enumerate(sl, start=1):
         assert np.array_equal(n, np.rint(n))                 # integers
@@ -69,26 +69,30 @@ def test_slicing_narrow_range_is_error_free(s):
         assert np.array_equal(back, x)
 
 
-def test_slices_representable_in_bf16_and_fp16():
+@pytest.mark.parametrize("s,beta", [(6, 7), (5, 8)])
+def test_slices_representable_in_bf16_and_fp16(s, beta):
+    """|N_1| <= 2^beta and |N_t| <= 2^(beta-1): at most 8 significant bits, exact in bf16
+    (8-bit significand) and fp16 for beta = 7 and 8 alike."""
     rng = np.random.default_rng(1)
     x = _wide_tile(rng, 32, 32, spread=40)
-    _, sl, _ = S.slice_tile(x, 6)
+    x[0, 0] = 1.0 - 2.0 ** -30  # rounds up to the first slice's largest value, 2^beta
+    _, sl, _ = S.slice_tile(x, s, beta)
+    assert np.max(np.abs(sl[0])) == 2 ** beta
     for n in sl:
         t = torch.from_numpy(n.astype(np.float32))
         assert torch.equal(t.to(torch.bfloat16).to(torch.float32), t)
         assert torch.equal(t.to(torch.float16).to(torch.float32), t)
 
 
-@pytest.mark.parametrize("s", [1, 3, 6])
-def test_pair_integer_brute_force(s):
+@pytest.mark.parametrize("s,beta", [(1, 7), (3, 7), (6, 7), (3, 8), (5, 8)])
+def test_pair_integer_brute_force(s, beta):
     """T = sum_{p+q<=s+1} N^A_p N^B_q 2^(beta(s+1-p-q)) by explicit Python-integer loops."""
     rng = np.random.default_rng(s)
     a = _wide_tile(rng, 4, 5, 20)
     b = _wide_tile(rng, 5, 3, 20)
-    _, na, _ = S.slice_tile(a, s)
-    _, nb, _ = S.slice_tile(b, s)
-    T = S.pair_integer(na, nb, s)
-    beta = S.BETA_BITS
+    _, na, _ = S.slice_tile(a, s, beta)
+    _, nb, _ = S.slice_tile(b, s, beta)
+    T = S.pair_integer(na, nb, s, beta)
     for i in range(4):
         for j in range(3):
             tot = 0
@@ -117,21 +121,20 @@ def _span_tiles(prob, seed, binades):
 
 
 @pytest.mark.parametrize("span", [0, 120])
-@pytest.mark.parametrize("s", [2, 3, 6])
+@pytest.mark.parametrize("s,beta", [(2, 7), (3, 7), (6, 7), (3, 8), (5, 8)])
 @pytest.mark.parametrize("seed", range(3))
-def test_split_result_is_exact_sum_rounded_once(s, seed, span):
+def test_split_result_is_exact_sum_rounded_once(s, beta, seed, span):
     """Independent route: the exact rational sum over k blocks, kept slice pairs and
-    inner indices of N^A_p N^B_q 2^(eA+eB-7(p+q)), rounded once (Fraction -> float is
+    inner indices of N^A_p N^B_q 2^(eA+eB-beta(p+q)), rounded once (Fraction -> float is
     correctly rounded). The oracle's value must equal it bit for bit, also when the k
-    blocks' products lie up to 120 binades apart."""
+    blocks' products lie up to 120 binades apart; for 7- and 8-bit slices."""
     prob = G.random_small(seed + 500, max_blocks=4, max_size=9)
     prob.alpha, prob.beta = 1.0, 0.0
     if span:
         prob = _span_tiles(prob, seed, span)
     cs, _, _ = oracle.structure(prob)
     off, C = c_arena(prob, cs, fill=0.0)
-    S.bsmm_split(prob, cs, C, off, s)
-    beta = S.BETA_BITS
+    S.bsmm_split(prob, cs, C, off, s, beta=beta)
     for i in range(prob.M):
         for j in range(prob.N):
             if not cs[i, j]:
@@ -143,8 +146,8 @@ def test_split_result_is_exact_sum_rounded_once(s, seed, span):
                     continue
                 At = G.tile_view(prob.A, prob.a_off, prob.row_sizes, prob.inner_sizes, i, k)
                 Bt = G.tile_view(prob.B, prob.b_off, prob.inner_sizes, prob.col_sizes, k, j)
-                eA, na, _ = S.slice_tile(At, s)
-                eB, nb, _ = S.slice_tile(Bt, s)
+                eA, na, _ = S.slice_tile(At, s, beta)
+                eB, nb, _ = S.slice_tile(Bt, s, beta)
                 for p in range(1, s + 1):
                     for qq in range(1, s + 2 - p):
                         w = Fraction(2) ** (eA + eB - beta * (p + qq))
@@ -159,17 +162,16 @@ def test_split_result_is_exact_sum_rounded_once(s, seed, span):
                     assert got[ii, jj] == float(exact[ii][jj])
 
 
-@pytest.mark.parametrize("s", [2, 3, 4, 6])
+@pytest.mark.parametrize("s,beta", [(2, 7), (3, 7), (4, 7), (6, 7), (3, 8), (5, 8)])
 @pytest.mark.parametrize("seed", range(3))
-def test_split_within_truncation_bound(s, seed):
+def test_split_within_truncation_bound(s, beta, seed):
     """|C_split - C_exact| <= sum_k q_k (s+3) 2^(-beta s) 2^(eA+eB) |alpha| + rounding, where the
     first term bounds the dropped slice pairs (p+q > s+1) and the slicing residuals."""
     prob = G.random_small(seed + 300, max_blocks=4, max_size=8)
     prob.beta = 0.0
     cs, _, _ = oracle.structure(prob)
     off, C = c_arena(prob, cs, fill=0.0)
-    S.bsmm_split(prob, cs, C, off, s)
-    beta = S.BETA_BITS
+    S.bsmm_split(prob, cs, C, off, s, beta=beta)
     u = 2.0 ** -53
     for i in range(prob.M):
         for j in range(prob.N):
