@@ -152,13 +152,17 @@ typedef struct {
                               real and imaginary parts of the product are exact sums (of
                               Ar Br - Ai Bi and Ar Bi + Ai Br) rounded once each; alpha and
                               beta are real and scale each part. The tensor cores run the
-                              equivalent real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]], so
-                              an inner block may hold half the real depth (256 for 6 slices)
-                              and the useful flop count is 8 r c q per nonzero triple. */
+                              equivalent real product [Ar, -Ai] x [[Br, Bi], [Bi, -Br]] (an
+                              inner block of q complex elements is 2q real ones deep) and the
+                              useful flop count is 8 r c q per nonzero triple. */
   int32_t store_warps;     /* split modes: the contraction kernel's form. 0 = automatic (with
                               store warps); 2 = with four C store warps (the C store of a
                               unit overlaps the next unit's accumulation); 1 = without (the
-                              epilogue warps store). Results do not depend on it. */
+                              epilogue warps store). Results do not depend on it. An inner
+                              block deeper than the exact FP32 accumulation depth (512 for 6
+                              slices, more for fewer) is accumulated in several groups by a
+                              form with store warps; with 1 such a plan is BSMM_ERR_UNSUPPORTED.
+                              The whole inner dimension may hold up to 2^22 elements. */
   const char* model_path;  /* NULL or "" = no model. Otherwise the path of a cost-model file
                               written by bsmm_mlp_save: bsmm_plan loads it, predicts every work
                               unit's time with it on the GPU and packs the units by those

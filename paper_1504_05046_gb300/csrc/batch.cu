@@ -457,6 +457,8 @@ bsmm_status bsmm_batch_execute(bsmm_batch_t b, void* stream) {
       if (e != cudaSuccess) break;
       SplitArgs a = b->sargs[0];
       a.sw = b->sw;
+      a.deep = 0;  // the DEEP form when any product of the wave has a deep inner block
+      for (int32_t i = b->wave_prod[w]; i < b->wave_prod[w + 1]; i++) a.deep |= b->sargs[i].deep;
       // the epilogue's way of learning the groups (one kernel form per launch): the one
       // most of the wave's units ask for; either gives the same bits
       {

@@ -26,13 +26,15 @@ constexpr int kSplitMaxS = 6;      // slices per operand
 constexpr int kSplitEpiWarps = 8;  // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kSplitGuard = 55;    // guard bits of the 128-bit accumulator below the largest scale
 constexpr double kEpiWalkBlocks = 32.0;  // mean k blocks per unit from which the epilogue walks
-constexpr int kSplitMaxK = 8192;   // inner blocks per product (keeps the 128-bit sum from overflowing)
+constexpr int kSplitMaxK = 8192;   // inner blocks per product
+constexpr int64_t kSplitMaxInner = int64_t(1) << 22;  // inner elements per product (128-bit sums' headroom)
 
 // FP64-mode geometry.
 constexpr int kF64BK = 16;  // inner depth of one staged chunk (FP64 path)
 
-// Largest inner block for which every diagonal sum of slice products stays an
-// integer of magnitude <= 2^24 (exact in the FP32 tensor-core accumulator).
+// Deepest inner range (elements) over which every diagonal sum of slice products stays an
+// integer of magnitude <= 2^24 (exact in the FP32 tensor-core accumulator); a deeper inner
+// block is accumulated in several groups.
 int split_max_depth(int s);
 int split_tile_n(int s);          // work-unit width (32 or 64)
 int split_stages(int s, int tn);  // smem ring depth
@@ -122,6 +124,7 @@ struct SplitArgs {
   int32_t M, N, K, s, tn, stages, fp16;
   int32_t cl, CBG;          // CTAs per column-block group; groups (units are (rb, group))
   int32_t sw;               // the contraction kernel's form: 1 = with C store warps
+  int32_t deep;             // 1: some inner block is deeper than kdepth (the kernel's DEEP form)
   int32_t epi_walk;         // 1: the epilogue finds the accumulation groups on its own k list
                             // (long lists); 0: it takes them from the MMA warps' descriptors
   int64_t Mtot, Ntot;
@@ -300,6 +303,7 @@ struct bsmm_plan_s {
   int s = 0, tn = 0, stages = 0, RB = 0, CB = 0, kwords = 0, cl = 1, CBG = 0;
   int sw = 0;                // contraction kernel with C store warps
   int epi_walk = 0;          // the epilogue walks the k lists itself (SplitArgs::epi_walk)
+  int deep = 0;              // some inner block is deeper than the exact FP32 depth
   int64_t Mtot = 0, Ntot = 0, colexp_ld = 0;
   int64_t apk_bytes = 0, bpk_bytes = 0;
 

@@ -113,6 +113,7 @@ void fill_split_args(bsmm_plan_s* p, SplitArgs& a, double alpha, const void* A, 
   a.beta = beta;
   a.sw = p->sw;
   a.epi_walk = p->epi_walk;
+  a.deep = p->deep;
   a.f32 = p->opt.elem == BSMM_F32;
   a.cplx = p->opt.elem == BSMM_C128;
   a.A = a.f32 ? nullptr : (const double*)A;

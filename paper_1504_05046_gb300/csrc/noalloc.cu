@@ -187,6 +187,8 @@ extern "C" bsmm_status bsmm_split_tile_noalloc(int32_t m, int32_t n, int32_t k, 
   a.cl = 1;
   a.sw = 0;  // the kernel form without store warps
   a.epi_walk = 0;  // one short k list: the MMA warps' descriptors
+  a.deep = 0;      // k <= 512: within the exact depth of every slice count
+  a.kdepth = split_max_depth(nslices);
   a.CBG = CB;
   a.apk_off = t->apk_off;
   a.bpk_off = t->bpk_off;

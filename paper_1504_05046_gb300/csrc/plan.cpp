@@ -422,13 +422,27 @@ bsmm_status plan_split(bsmm_plan_s* p) {
     set_error("split modes take at most " + std::to_string(kSplitMaxK) + " inner blocks");
     return BSMM_ERR_UNSUPPORTED;
   }
-  for (int k = 0; k < K; k++)
-    if (p->q[k] > maxd) {
-      set_error("inner block " + std::to_string(k) + " has " + std::to_string(p->q[k]) +
-                " > " + std::to_string(maxd) + " elements, the exact FP32 accumulation depth for " +
-                std::to_string(s) + " slices");
+  // an inner block deeper than the exact FP32 depth is accumulated in several groups (the
+  // kernel's DEEP form, with store warps); the 128-bit sums stay below 2^127 while the
+  // whole inner dimension is at most 2^22 elements (every slice-pair term of one inner
+  // element is below 2^(7(s+1)+56) units of 2^L)
+  {
+    int64_t depth = 0;
+    p->deep = 0;
+    for (int k = 0; k < K; k++) {
+      depth += p->q[k];
+      if (p->q[k] > maxd) p->deep = 1;
+    }
+    if (depth > kSplitMaxInner) {
+      set_error("split modes take an inner dimension of at most " + std::to_string(kSplitMaxInner) + " elements");
       return BSMM_ERR_UNSUPPORTED;
     }
+    if (p->deep && p->opt.store_warps == 1) {
+      set_error("an inner block deeper than " + std::to_string(maxd) +
+                " elements needs the kernel form with store warps (store_warps 0 or 2)");
+      return BSMM_ERR_UNSUPPORTED;
+    }
+  }
 
   std::vector<int32_t> row_tile(std::max<int64_t>(Mtot, 1), 0), col_tile(std::max<int64_t>(Ntot, 1), 0);
   for (int i = 0; i < M; i++)

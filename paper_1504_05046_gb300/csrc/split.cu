@@ -1253,7 +1253,11 @@ struct ChunkCursor {
 // WALK: the epilogue finds the accumulation groups on its own k list (products of long
 // k lists) instead of taking the MMA warps' descriptors; the two ways share no code path,
 // so each form keeps its own register allocation.
-template <int S, int TN, bool SW, bool WALK>
+// DEEP: some inner block is deeper than the exact FP32 depth; such a block (it always
+// starts a group of its own) is cut into groups of kdepth / 32 whole 32-deep chunks, the
+// last of which may take the following blocks. A form of its own, because any extra work
+// in the MMA-issuing loop slows every product.
+template <int S, int TN, bool SW, bool WALK, bool DEEP>
 __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __grid_constant__ SplitArgs a) {
   constexpr int TH = TN / 2;                    // columns per epilogue thread
   constexpr int A_STAGE = S * kAChunk;          // bytes of A per stage
@@ -1427,8 +1431,22 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
             gk0 = kt;
             in_group = true;
           }
-          const uint32_t dbase = tmem_base + buf * BUF_COLS;
+          uint32_t dbase = tmem_base + buf * BUF_COLS;
           for (int kc = 0; kc < nkc; kc++) {
+            if constexpr (DEEP) {
+              const int cpg = P.kdepth >= kSplitKC ? P.kdepth / kSplitKC : 1;
+              if (kc > 0 && q > P.kdepth && kc % cpg == 0) {  // the block's next group
+                close_group(mw == 0, gdesc, gready, tfull, buf, gk0, grp, false);
+                tcount++;
+                buf = tcount & 1;
+                if (!wait1(&tempty[buf], (tcount >> 1) & 1, abort_flag, a.err)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                dbase = tmem_base + buf * BUF_COLS;
+              }
+            }
             if (!wait1(&full[stage], phase, abort_flag, a.err)) {
               ok = false;
               break;
@@ -1451,6 +1469,10 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
               stage = 0;
               phase ^= 1;
             }
+          }
+          if constexpr (DEEP) {
+            const int cpg = P.kdepth >= kSplitKC ? P.kdepth / kSplitKC : 1;
+            if (q > P.kdepth) grp.depth = q - kSplitKC * cpg * ((nkc - 1) / cpg);  // its last group's depth
           }
           cur = nxt;
         }
@@ -1521,6 +1543,7 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
       // own mask). Either way the groups are the same, in the same order.
       UnitIter it;
       int kt = -1;
+      [[maybe_unused]] int sub = 0;  // DEEP: groups already taken from k block kt
       if constexpr (WALK) {
         it.init(P, un, cb);
         kt = it.next_own();
@@ -1537,16 +1560,32 @@ __global__ void __launch_bounds__(threads_of<SW>(), 1) split_mma_kernel(const __
             const bool uni = scale_class(P, kt, un.rb, cb, sg);
             grp.start(uni, sg, P.q[kt], P.kdepth);
           }
-          int kn = it.next_own();
-          for (; kn >= 0; kn = it.next_own()) {
-            int sg = 0;
-            const bool uni = scale_class(P, kn, un.rb, cb, sg);
-            if (!grp.joins(uni, sg, P.q[kn])) break;
-          }
           gk0 = kt;
           guni = grp.uni;
           gsig = grp.sig;
-          kt = kn;
+          bool whole = true;  // DEEP: a deep block's groups but its last take no other block
+          if constexpr (DEEP) {
+            const int qk = P.q[kt];
+            if (qk > P.kdepth) {
+              const int cpg = P.kdepth >= kSplitKC ? P.kdepth / kSplitKC : 1;
+              const int nsub = ((qk + kSplitKC - 1) / kSplitKC + cpg - 1) / cpg;
+              if (++sub < nsub) {
+                whole = false;
+              } else {
+                grp.depth = qk - kSplitKC * cpg * (nsub - 1);
+                sub = 0;
+              }
+            }
+          }
+          if (whole) {
+            int kn = it.next_own();
+            for (; kn >= 0; kn = it.next_own()) {
+              int sg = 0;
+              const bool uni = scale_class(P, kn, un.rb, cb, sg);
+              if (!grp.joins(uni, sg, P.q[kn])) break;
+            }
+            kt = kn;
+          }
           more = kt >= 0;
         } else {
           // (the epilogue warps sleep between polls here: while the MMA warps fill a group
@@ -1779,21 +1818,21 @@ __global__ void __launch_bounds__(96) wait_selftest_kernel(int32_t* err, int64_t
   __syncthreads();
 }
 
-template <int S, int TN, bool SW, bool WALK>
+template <int S, int TN, bool SW, bool WALK, bool DEEP = false>
 cudaError_t launch_mma(const SplitArgs& a, int groups, cudaStream_t st) {
   const size_t smem = split_smem_bytes(S, TN, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, SW, WALK>,
+  cudaError_t e = cudaFuncSetAttribute(split_mma_kernel<S, TN, SW, WALK, DEEP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (SW) {
     // the register split assumes exactly kRegsLaunch registers per thread at launch (a
     // smaller allocation could not satisfy the epilogue's setmaxnreg.inc): refuse otherwise
     cudaFuncAttributes fa{};
-    e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, SW, WALK>);
+    e = cudaFuncGetAttributes(&fa, split_mma_kernel<S, TN, SW, WALK, DEEP>);
     if (e != cudaSuccess) return e;
     if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
   }
-  split_mma_kernel<S, TN, SW, WALK><<<(unsigned)(groups * a.cl), threads_of<SW>(), smem, st>>>(a);
+  split_mma_kernel<S, TN, SW, WALK, DEEP><<<(unsigned)(groups * a.cl), threads_of<SW>(), smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1802,6 +1841,12 @@ cudaError_t launch_mma_sw(const SplitArgs& a, int groups, cudaStream_t st) {
   if (a.cl != 1 && a.cl != 2 && a.cl != 4) return cudaErrorInvalidValue;
   // the walking epilogue is built for the forms with store warps and 3 to 6 slices (the
   // dense products' default); other forms take the descriptors whatever epi_walk says
+  if (a.deep) {  // products with inner blocks deeper than the exact depth: store-warp forms
+    if (!a.sw) return cudaErrorInvalidConfiguration;
+    if constexpr (S >= 3)
+      if (a.epi_walk) return launch_mma<S, 32, true, true, true>(a, groups, st);
+    return launch_mma<S, 32, true, false, true>(a, groups, st);
+  }
   if constexpr (S >= 3)
     if (a.sw && a.epi_walk) return launch_mma<S, 32, true, true>(a, groups, st);
   return a.sw ? launch_mma<S, 32, true, false>(a, groups, st) : launch_mma<S, 32, false, false>(a, groups, st);
@@ -1812,11 +1857,11 @@ cudaError_t launch_mma_sw(const SplitArgs& a, int groups, cudaStream_t st) {
 template <int S, bool SW>
 int max_groups_for(int cl, int stages) {
   const size_t smem = split_smem_bytes(S, 32, stages);
-  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, SW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(split_mma_kernel<S, 32, SW, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, SW, false>, threads_of<SW>(), smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_mma_kernel<S, 32, SW, false, false>, threads_of<SW>(), smem) !=
       cudaSuccess)
     return 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -16,7 +16,7 @@ def to_dev(x, dtype=None):
 
 def run_lib(prob, c_struct, C0, c_off, *, mode=P.BSMM_FP64, nslices=6, c_mask=None, schedule=P.BSMM_SCHED_FLOPS,
             max_ctas=0, ctas=None, costs=None, debug=1, plan=None, record_timings=0, cluster=0, stages=0,
-            split_scale=0, ksplit=0):
+            split_scale=0, ksplit=0, store_warps=0):
     """Plan (unless given) and execute on the GPU; returns (C result numpy, plan)."""
     import torch
     if plan is None:
@@ -24,7 +24,7 @@ def run_lib(prob, c_struct, C0, c_off, *, mode=P.BSMM_FP64, nslices=6, c_mask=No
                            mode=mode, nslices=nslices, schedule=schedule, max_ctas=max_ctas, debug_checks=debug,
                            record_timings=record_timings, cluster=cluster, stages=stages,
                            transa=int(getattr(prob, "transa", False)), transb=int(getattr(prob, "transb", False)),
-                           split_scale=split_scale, ksplit=ksplit)
+                           split_scale=split_scale, ksplit=ksplit, store_warps=store_warps)
     if ctas is not None:
         P.bsmm_plan_set_ctas(plan, ctas)
     if costs is not None:

@@ -268,9 +268,18 @@ def test_deep_uniform_classes_are_not_merged():
         assert check_window(prob, s) == 1
 
 
-def test_too_deep_inner_block_is_rejected():
+def test_deep_inner_block_limits():
+    """Inner blocks deeper than the exact FP32 depth are accepted with store warps (the
+    default) and refused without them; an inner dimension of more than 2^22 elements is
+    refused (the 128-bit sums' headroom), all with BSMM_ERR_UNSUPPORTED."""
+    P.bsmm_plan([8], [8], [513], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6)
     with pytest.raises(P.BsmmError) as ei:
-        P.bsmm_plan([8], [8], [513], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6)
+        P.bsmm_plan([8], [8], [513], [[1]], [[1]], mode=P.BSMM_SPLIT_BF16, nslices=6, store_warps=1)
+    assert ei.value.status == 5
+    q = [8192] * 512 + [1]
+    with pytest.raises(P.BsmmError) as ei:
+        P.bsmm_plan([8], [8], q, np.ones((1, len(q)), np.uint8), np.ones((len(q), 1), np.uint8),
+                    mode=P.BSMM_SPLIT_BF16, nslices=6)
     assert ei.value.status == 5
 
 
@@ -473,3 +482,27 @@ def test_long_k_lists_epilogue_walks(cluster, s, case):
     prob = _scaled_problem(78 + cluster, r, q, c, fa, fb)
     prob.alpha, prob.beta = 0.5, -1.5
     check(prob, s, cluster=cluster)
+
+
+@pytest.mark.parametrize("s", [3, 6])
+@pytest.mark.parametrize("layout", ["deep_blocks", "deep_long_lists"])
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_inner_blocks_deeper_than_the_exact_depth(s, layout, cluster):
+    """Inner blocks deeper than the exact FP32 depth (512 for 6 slices, 819 for 3) are
+    accumulated in several groups of 32-deep chunks, by the MMA warps and by the walking
+    epilogue alike (long k lists), and through the descriptors otherwise; the last group
+    of such a block takes the following blocks when they fit. Every bit is the split
+    oracle's; blocks up to 1700 deep, tile exponents varying with k."""
+    rng = np.random.default_rng(90 + s * 10)
+    r = rng.integers(60, 200, 3).astype(np.int32)
+    c = rng.integers(20, 90, 4).astype(np.int32)
+    if layout == "deep_blocks":
+        q = np.array([150, 1700, 33, 290, 512, 513, 900, 64], np.int32)
+    else:
+        q = np.concatenate([rng.integers(8, 40, 40), [1100], rng.integers(8, 40, 30)]).astype(np.int32)
+    fa, fb = (lambda i, k: (k // 3) % 2 - i % 2), (lambda k, j: (k % 5 == 0) - j % 2)
+    prob = _scaled_problem(91 + s, r, q, c, fa, fb)
+    prob.alpha, prob.beta = 1.25, -0.5
+    _, plan, _ = check(prob, s, cluster=cluster)
+    f = P.bsmm_plan_form(plan)
+    assert f["store_warps"] == 1 and f["epi_walk"] == (1 if layout == "deep_long_lists" else 0)

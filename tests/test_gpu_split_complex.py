@@ -156,7 +156,18 @@ def test_unsupported_combinations_are_rejected():
     for bad in (dict(mode=P.BSMM_FP64),):
         with pytest.raises(P.BsmmError):
             P.bsmm_plan(*args, elem=P.BSMM_C128, **bad)
-    deep = np.array([300], np.int32)  # 2 x 300 real lines exceed the 6-slice exact depth
-    with pytest.raises(P.BsmmError):
-        P.bsmm_plan(np.array([10], np.int32), np.array([10], np.int32), deep, np.ones((1, 1), np.uint8),
-                    np.ones((1, 1), np.uint8), mode=P.BSMM_SPLIT_BF16, elem=P.BSMM_C128)
+
+
+
+def test_deep_complex_inner_block_runs_in_groups():
+    """2 x 300 real inner lines exceed the 6-slice exact FP32 depth (512): the block is
+    accumulated in several groups, with the complex oracle's bits."""
+    rng = np.random.default_rng(3)
+    r, c, q = np.array([40, 70], np.int32), np.array([30, 50], np.int32), np.array([300, 20], np.int32)
+    am, bm = np.ones((2, 2), np.uint8), np.ones((2, 2), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    real = G.Problem("deep_complex", r, c, q, am, bm, a_off, b_off, rng.uniform(-1, 1, at),
+                     rng.uniform(-1, 1, bt), 1.0, 0.0)
+    _, err = run_c(G.as_complex(real, 4), 6)
+    assert err <= 1e-11, err
