@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cublas", action="store_true",
+                    help="dense workload: skip the cuBLAS DGEMM reference point (torch.matmul float64)")
     ap.add_argument("--no-learned", action="store_true",
                     help="dense workload: skip the learned-schedule comparison on the clustered workload")
     ap.add_argument("--workload", default="dense", choices=["dense", "batch", "uniform", "banded", "banded_wide",
@@ -644,6 +646,48 @@ def main():
         dist.destroy_process_group()
 
 
+def densify(torch, arena_t, offs, rows, cols, dev):
+    """Gather a tile-by-tile arena into the dense matrix (a library reference point's input,
+    not part of the measured path); tiles absent from offs (-1) stay zero."""
+    ro = np.concatenate([[0], np.cumsum(rows.astype(np.int64))])
+    cc = np.concatenate([[0], np.cumsum(cols.astype(np.int64))])
+    out = torch.zeros((int(ro[-1]), int(cc[-1])), dtype=arena_t.dtype, device=dev)
+    for u in range(len(rows)):
+        for v in range(len(cols)):
+            if offs[u, v] < 0:
+                continue
+            nn = int(rows[u]) * int(cols[v])
+            out[ro[u]:ro[u + 1], cc[v]:cc[v + 1]] = arena_t[offs[u, v]:offs[u, v] + nn].view(int(rows[u]), int(cols[v]))
+    return out
+
+
+def cublas_dgemm_line(P, torch, prob, A, B, C64, c_off, dev, stream):
+    """cuBLAS DGEMM (torch.matmul float64) of the densified operands of the dense product: a
+    library reference point for the FP64 path, with its error against that path's result
+    and cuBLAS's FP64 emulation setting as the environment gives it."""
+    Ad = densify(torch, A, prob.a_off, prob.row_sizes, prob.inner_sizes, dev)
+    Bd = densify(torch, B, prob.b_off, prob.inner_sizes, prob.col_sizes, dev)
+    Cd = torch.matmul(Ad, Bd)  # warm-up
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    torch.matmul(Ad, Bd, out=Cd)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms = g0.elapsed_time(g1)
+    del Ad, Bd
+    ref = densify(torch, C64, c_off, prob.row_sizes, prob.col_sizes, dev)
+    err = float(torch.linalg.norm(Cd - ref) / torch.linalg.norm(ref))
+    del Cd, ref
+    n = int(prob.row_sizes.sum()), int(prob.inner_sizes.sum()), int(prob.col_sizes.sum())
+    flops = 2.0 * n[0] * n[1] * n[2]
+    return {"value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms": ms,
+            "rel_err_vs_fp64_path": err,
+            "emulation": os.environ.get("CUBLAS_EMULATION_STRATEGY", "unset (cuBLAS default)"),
+            "what": "torch.matmul float64 of the densified dense operands, one timed call after one "
+                    "warm-up; a library reference point, not part of the measured path"}
+
+
 def complex_line(args, P, G, torch, dev, stream):
     """Complex elements on the N/2 nonuniform dense product: split-mode throughput in
     useful flops (8 r c q per triple) and the error against cuBLAS ZGEMM of the dense
@@ -656,15 +700,7 @@ def complex_line(args, P, G, torch, dev, stream):
     off, tot = G.layout_arena(cs, pc.row_sizes, pc.col_sizes)
     co = d(off)
     # dense reference: the arenas are tile by tile; gather them into dense matrices
-    def dense(arena_t, offs, rows, cols):
-        ro = np.concatenate([[0], np.cumsum(rows.astype(np.int64))])
-        cc = np.concatenate([[0], np.cumsum(cols.astype(np.int64))])
-        out = torch.zeros((int(ro[-1]), int(cc[-1])), dtype=torch.complex128, device=dev)
-        for u in range(len(rows)):
-            for v in range(len(cols)):
-                nn = int(rows[u]) * int(cols[v])
-                out[ro[u]:ro[u + 1], cc[v]:cc[v + 1]] = arena_t[offs[u, v]:offs[u, v] + nn].view(int(rows[u]), int(cols[v]))
-        return out
+    dense = lambda arena_t, offs, rows, cols: densify(torch, arena_t, offs, rows, cols, dev)
     ref = dense(Ac, pc.a_off, pc.row_sizes, pc.inner_sizes) @ dense(Bc, pc.b_off, pc.inner_sizes, pc.col_sizes)
     out = {"workload": f"nonuniform_dense N={n2} blocks U-int[64,256], complex128 entries (re and im U[-1,1])"}
     for s2 in args.c128_slices:
@@ -800,6 +836,8 @@ def run_dense(args, rank, world, local):
                               "roofline": fp64_roofline(P, pk, v64)}
         extra["split_rel_err_vs_fp64"] = err
         extra["split_speedup_vs_fp64"] = ms64 / ms_max
+        if not args.no_cublas and not (ta or tb):
+            extra["cublas_dgemm"] = cublas_dgemm_line(P, torch, prob, A, B, C64, c_off, dev, stream)
         # the other slice counts on the same inputs: throughput and error against the FP64 result
         modes = {}
         for s2 in args.other_slices:
