@@ -109,10 +109,19 @@ def slice_rows(x: np.ndarray, s: int, beta: int = BETA_BITS, e=None):
 
 
 def pair_integer(na, nb, s: int, beta: int = BETA_BITS) -> np.ndarray:
-    """T = sum_d S_d 2^(beta(s+1-d)) for one tile pair, as an int64 matrix."""
+    """T = sum_d S_d 2^(beta(s+1-d)) for one tile pair: an int64 matrix, or a matrix of
+    Python integers when the tile pair's inner depth n could take |T| beyond int64.
+
+    |N_p N_q| <= 2^(2 beta), so |S_d| <= (d-1) n 2^(2 beta): each S_d is exact in the
+    float64 matmul while s n 2^(2 beta) < 2^53 (checked), and |T| < 2 s n 2^(2 beta)
+    2^(beta(s-1))."""
     r = na[0].shape[0]
     c = nb[0].shape[1]
-    T = np.zeros((r, c), np.int64)
+    n = na[0].shape[1]
+    if s * n * 2.0 ** (2 * beta) >= 2.0 ** 53:
+        raise ValueError(f"pair_integer: inner depth {n} is beyond exact float64 slice sums")
+    big = 2 * s * n * 2 ** (2 * beta + beta * (s - 1)) >= 2 ** 63
+    T = np.zeros((r, c), object if big else np.int64)
     if r == 0 or c == 0:
         return T
     for d in range(2, s + 2):
@@ -122,7 +131,10 @@ def pair_integer(na, nb, s: int, beta: int = BETA_BITS) -> np.ndarray:
             if p > s or q > s:
                 continue
             Sd += na[p - 1] @ nb[q - 1]
-        T += Sd.astype(np.int64) << np.int64(beta * (s + 1 - d))
+        if big:
+            T += Sd.astype(np.int64).astype(object) * (1 << (beta * (s + 1 - d)))
+        else:
+            T += Sd.astype(np.int64) << np.int64(beta * (s + 1 - d))
     return T
 
 

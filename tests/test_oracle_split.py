@@ -107,6 +107,29 @@ def test_pair_integer_brute_force(s, beta):
             assert int(T[i, j]) == tot
 
 
+def test_pair_integer_beyond_int64():
+    """A 20000-deep tile pair of same-sign entries near the top of their binade: every first
+    slice is 2^7, |T| passes 2^63, and T must still be the exact integer (formed here by
+    int64 slice-pair products, exact at this depth, combined in Python integers)."""
+    s, beta, n = 6, 7, 20000
+    rng = np.random.default_rng(11)
+    a = rng.uniform(0.997, 0.9999, (2, n))
+    b = rng.uniform(0.997, 0.9999, (n, 2))
+    ea, na, _ = S.slice_tile(a, s, beta)
+    eb, nb, _ = S.slice_tile(b, s, beta)
+    assert ea == eb == 0 and np.all(na[0] == 2 ** beta) and np.all(nb[0] == 2 ** beta)
+    T = S.pair_integer(na, nb, s, beta)
+    ia = [x.astype(np.int64) for x in na]
+    ib = [x.astype(np.int64) for x in nb]
+    for i in range(2):
+        for j in range(2):
+            tot = 0
+            for p in range(1, s + 1):
+                for q in range(1, s + 2 - p):
+                    tot += int(ia[p - 1][i] @ ib[q - 1][:, j]) << (beta * (s + 1 - p - q))
+            assert tot > 2 ** 63 and int(T[i, j]) == tot
+
+
 def _span_tiles(prob, seed, binades):
     """Scale every A tile of inner block k by 2^(-binades * k / K): the k blocks of one C
     element then contribute at positions up to ``binades`` binades apart."""
