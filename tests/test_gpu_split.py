@@ -506,3 +506,33 @@ def test_inner_blocks_deeper_than_the_exact_depth(s, layout, cluster):
     _, plan, _ = check(prob, s, cluster=cluster)
     f = P.bsmm_plan_form(plan)
     assert f["store_warps"] == 1 and f["epi_walk"] == (1 if layout == "deep_long_lists" else 0)
+
+
+def _same_sign_problem(seed, r, q, c):
+    """Dense problem with entries in [0.997, 0.9999): every first slice is 2^7 and every
+    slice-pair product has the same sign, the largest sums the exact accumulation sees."""
+    rng = np.random.default_rng(seed)
+    r, q, c = (np.asarray(x, np.int32) for x in (r, q, c))
+    am = np.ones((len(r), len(q)), np.uint8)
+    bm = np.ones((len(q), len(c)), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    return G.Problem("same_sign", r, c, q, am, bm, a_off, b_off, rng.uniform(0.997, 0.9999, at),
+                     rng.uniform(0.997, 0.9999, bt), 1.0, 0.0)
+
+
+@pytest.mark.parametrize("ksplit", [0, 1])
+def test_maximum_inner_dimension_at_full_magnitude(ksplit):
+    """The largest inner dimension a split plan takes (2^22 elements in 8192 blocks of 512),
+    with same-sign entries at the top of their binade: the 128-bit sums reach about 2^126
+    units and must not overflow; bits equal the split oracle's, with k uncut and cut."""
+    prob = _same_sign_problem(5, [16], [512] * 8192, [8])
+    check(prob, 6, ksplit=ksplit)
+
+
+@pytest.mark.parametrize("ksplit", [0, 1])
+def test_deep_block_beyond_int64_pair_sums(ksplit):
+    """A 20000-deep inner block of same-sign entries (its tile pair's integer passes 2^63;
+    40 accumulation groups) followed by a shallow block that joins the last group."""
+    prob = _same_sign_problem(6, [40, 100], [20000, 100], [30, 40])
+    check(prob, 6, ksplit=ksplit)
