@@ -773,14 +773,16 @@ def run_dense(args, rank, world, local):
     torch.cuda.synchronize()
     P.bsmm_plan_kernel_ms(plan)  # start the per-kernel means at the first timed step
     per_step = kernels_per_execute(P, plan, P.BSMM_SPLIT_BF16, sc["split_scale"])
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # an event between consecutive steps as well (recording one adds no wait), for the
+    # median and spread of the step times beside the mean over the whole timed region
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = ev[0], ev[-1]
     launches = 0
     e0.record(stream)
-    for _ in range(args.steps):
+    for i in range(args.steps):
         P.bsmm_execute(plan, 1.0, A, ao, B, bo, 0.0, C, co)
         launches += per_step
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
@@ -788,6 +790,7 @@ def run_dense(args, rank, world, local):
     # recorded around its launches on this stream (read once, after the timed region)
     kms = [P.bsmm_plan_kernel_ms(plan)]
     ms = e0.elapsed_time(e1) / args.steps
+    steps_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     ms_max, F_all = aggregate(ms, F, dev)
     value = F_all / (ms_max * 1e-3) / 1e12
     P.bsmm_status_device(plan)
@@ -957,7 +960,9 @@ def run_dense(args, rank, world, local):
                            "useful_flops_per_step": F,
                            "l2": "inputs larger than L2 (A and B 2.1 GB each), no flush",
                            "parallelism": f"replicas x{world}", "seed": args.seed},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "step_ms": {"mean": ms, "median": statistics.median(steps_ms), "min": min(steps_ms),
+                            "max": max(steps_ms), "rank": "this rank's (0) timed steps"}}
         line.update(extra)
         print(json.dumps(line))
 
