@@ -824,7 +824,8 @@ __global__ void __launch_bounds__(256) split_pack_kernel(SplitArgs a) {
 
 // ---------------------------------------------------------------- exact accumulation
 // w (four 32-bit words, two's complement) += T * 2^sh, with floor(T / 2^-sh) for sh < 0.
-// |T| < 2^59 and sh <= kSplitGuard for every stored tile pair; an absent pair has T = 0.
+// |T| < 2^59 and sh <= kSplitGuard for every accumulation group (its depth keeps each FP32
+// partial sum below 2^24); an absent tile pair has T = 0.
 __device__ __forceinline__ void acc_add(uint32_t (&w)[4], long long T, int sh) {
   const int sl = min(max(sh, 0), 63);
   long long lo = T << sl;
