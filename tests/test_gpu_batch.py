@@ -12,9 +12,10 @@ from helpers import c_arena, struct_elements
 pytestmark = pytest.mark.gpu
 
 
-def _setup(mode, count=7, seed=5, fp64_tile=0):
+def _setup(mode, count=7, seed=5, fp64_tile=0, probs=None):
     import torch
-    probs = G.make_batch(count, seed, n_lo=150, n_hi=900, b_lo=24, b_hi=140)
+    if probs is None:
+        probs = G.make_batch(count, seed, n_lo=150, n_hi=900, b_lo=24, b_hi=140)
     items = []
     for i, prob in enumerate(probs):
         prob.alpha, prob.beta = [1.0, -0.5, 2.0][i % 3], [0.0, 1.0, 0.5][i % 3]
@@ -245,3 +246,36 @@ def test_batch_waves_on_two_streams_same_bits_as_separate():
         for it, want in zip(items, wants):
             assert np.array_equal(it["C"].cpu().numpy(), want)
     P.bsmm_batch_status_device(batch)
+
+
+def test_batch_with_deep_inner_blocks():
+    """Products with inner blocks deeper than the exact FP32 depth (700, 900, 1300 at 6
+    slices) batched with ordinary ones: the wave runs the deep kernel form, and every
+    product gets the split oracle's bits."""
+    import torch
+    rng = np.random.default_rng(12)
+    probs = G.make_batch(3, 8, n_lo=150, n_hi=500, b_lo=24, b_hi=140)
+    for t, q in enumerate(([700, 40, 1300], [64, 900])):
+        q = np.array(q, np.int32)
+        r = rng.integers(30, 150, 2).astype(np.int32)
+        c = rng.integers(20, 90, 3).astype(np.int32)
+        am = np.ones((2, len(q)), np.uint8)
+        bm = (rng.random((len(q), 3)) < 0.7).astype(np.uint8)
+        bm[:, 0] = 1
+        a_off, at = G.layout_arena(am, r, q)
+        b_off, bt = G.layout_arena(bm, q, c)
+        probs.insert(2 * t, G.Problem(f"deep{t}", r, c, q, am, bm, a_off, b_off, rng.uniform(-1, 1, at),
+                                      rng.uniform(-1, 1, bt), 1.0, 0.0))
+    items = _setup(P.BSMM_SPLIT_BF16, probs=probs)
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                          [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                          [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    P.bsmm_batch_status_device(batch)
+    for it in items:
+        want = _reference(it, P.BSMM_SPLIT_BF16)
+        got = it["C"].cpu().numpy()
+        assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
+                              struct_elements(it["prob"], it["cs"], it["off"], want)), it["prob"].name

@@ -84,3 +84,25 @@ def test_batch_mixed_scaling_modes():
         got = it["C"].cpu().numpy()
         assert np.array_equal(struct_elements(it["p"], it["cs"], it["off"], got),
                               struct_elements(it["p"], it["cs"], it["off"], want))
+
+
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_rows_deep_inner_blocks(cluster):
+    """Inner blocks deeper than the exact FP32 depth (700 and 1100 at 6 slices) with one
+    scale per row of A and column of B, rows and columns up to 30 binades apart."""
+    rng = np.random.default_rng(96)
+    r, q, c = np.array([60, 120], np.int32), np.array([700, 64, 1100], np.int32), np.array([40, 70], np.int32)
+    am, bm = np.ones((2, 3), np.uint8), np.ones((3, 2), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    A, B = rng.uniform(-1, 1, at), rng.uniform(-1, 1, bt)
+    for i in range(2):
+        for k in range(3):
+            t = A[a_off[i, k]:a_off[i, k] + r[i] * q[k]].reshape(r[i], q[k])
+            t *= 2.0 ** rng.integers(-15, 16, (r[i], 1))
+    for k in range(3):
+        for j in range(2):
+            t = B[b_off[k, j]:b_off[k, j] + q[k] * c[j]].reshape(q[k], c[j])
+            t *= 2.0 ** rng.integers(-15, 16, (1, c[j]))
+    prob = G.Problem("rows_deep", r, c, q, am, bm, a_off, b_off, A, B, 0.5, -1.0)
+    check_rows(prob, 6, cluster=cluster)
