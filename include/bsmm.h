@@ -195,11 +195,13 @@ void bsmm_options_default(bsmm_options* opt);
  *   c_mask[M*N]      NULL, or extra C tiles to keep in S_C
  *   opt              NULL = defaults
  * Allocates device memory (task tables; slice arenas for the split modes).
- * Returns BSMM_ERR_INVALID for negative sizes or an unknown option value,
- * BSMM_ERR_UNSUPPORTED for a split mode whose inner block exceeds the exact
- * accumulation depth of the tensor-core path (512 for 6 slices, half that for complex
- * elements), and for an element type the mode or storage does not take (float32 or
- * complex elements in FP64 mode; complex elements transposed or with split_scale).
+ * Returns BSMM_ERR_INVALID for negative sizes or an unknown option value, and
+ * BSMM_ERR_UNSUPPORTED for a split mode with more than 8192 inner blocks or more than
+ * 2^22 inner elements in all (the 128-bit sums' headroom; a complex inner block of q
+ * elements counts 2q), for a split mode with an inner block deeper than the exact FP32
+ * accumulation depth (512 real lines for 6 slices) and store_warps = 1, and for an
+ * element type the mode or storage does not take (float32 or complex elements in FP64
+ * mode; complex elements transposed or with split_scale).
  */
 bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
                       const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,
