@@ -248,11 +248,9 @@ def test_batch_waves_on_two_streams_same_bits_as_separate():
     P.bsmm_batch_status_device(batch)
 
 
-def test_batch_with_deep_inner_blocks():
-    """Products with inner blocks deeper than the exact FP32 depth (700, 900, 1300 at 6
-    slices) batched with ordinary ones: the wave runs the deep kernel form, and every
-    product gets the split oracle's bits."""
-    import torch
+def _deep_probs():
+    """Three ordinary products and two with inner blocks deeper than the exact FP32 depth
+    (700, 900, 1300 at 6 slices)."""
     rng = np.random.default_rng(12)
     probs = G.make_batch(3, 8, n_lo=150, n_hi=500, b_lo=24, b_hi=140)
     for t, q in enumerate(([700, 40, 1300], [64, 900])):
@@ -266,7 +264,22 @@ def test_batch_with_deep_inner_blocks():
         b_off, bt = G.layout_arena(bm, q, c)
         probs.insert(2 * t, G.Problem(f"deep{t}", r, c, q, am, bm, a_off, b_off, rng.uniform(-1, 1, at),
                                       rng.uniform(-1, 1, bt), 1.0, 0.0))
-    items = _setup(P.BSMM_SPLIT_BF16, probs=probs)
+    return probs
+
+
+def _check_batch_bits(items):
+    for it in items:
+        want = _reference(it, P.BSMM_SPLIT_BF16)
+        got = it["C"].cpu().numpy()
+        assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
+                              struct_elements(it["prob"], it["cs"], it["off"], want)), it["prob"].name
+
+
+def test_batch_with_deep_inner_blocks():
+    """Deep inner blocks batched with ordinary products: the wave runs the deep kernel
+    form, and every product gets the split oracle's bits."""
+    import torch
+    items = _setup(P.BSMM_SPLIT_BF16, probs=_deep_probs())
     batch = P.bsmm_batch_create([it["plan"] for it in items])
     P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
                           [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
@@ -274,8 +287,25 @@ def test_batch_with_deep_inner_blocks():
     P.bsmm_batch_execute(batch)
     torch.cuda.synchronize()
     P.bsmm_batch_status_device(batch)
-    for it in items:
-        want = _reference(it, P.BSMM_SPLIT_BF16)
-        got = it["C"].cpu().numpy()
-        assert np.array_equal(struct_elements(it["prob"], it["cs"], it["off"], got),
-                              struct_elements(it["prob"], it["cs"], it["off"], want)), it["prob"].name
+    _check_batch_bits(items)
+
+
+def test_autotune_skips_forms_without_deep_blocks():
+    """Autotuning a batch with deep inner blocks: the 12-warp candidates cannot take them
+    (their plans are refused) and are skipped with an infinite time; the batch keeps a
+    store-warp form and the oracle's bits."""
+    import torch
+    items = _setup(P.BSMM_SPLIT_BF16, probs=_deep_probs())
+    batch = P.bsmm_batch_create([it["plan"] for it in items])
+    P.bsmm_batch_set_args(batch, [it["prob"].alpha for it in items], [it["A"] for it in items],
+                          [it["ao"] for it in items], [it["B"] for it in items], [it["bo"] for it in items],
+                          [it["prob"].beta for it in items], [it["C"] for it in items], [it["co"] for it in items])
+    cands = [dict(cluster=1, stages=3, fp64_tile=0, store_warps=sw) for sw in (1, 2)] + \
+            [dict(cluster=2, stages=3, fp64_tile=0, store_warps=sw) for sw in (1, 2)]
+    chosen, ms = P.bsmm_batch_autotune(batch, candidates=cands, reps=1)
+    assert ms[0] == np.inf and ms[2] == np.inf and np.isfinite(ms[1]) and np.isfinite(ms[3])
+    assert chosen["store_warps"] == 2
+    P.bsmm_batch_execute(batch)
+    torch.cuda.synchronize()
+    P.bsmm_batch_status_device(batch)
+    _check_batch_bits(items)
