@@ -57,7 +57,7 @@ typedef enum {
   BSMM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
   BSMM_ERR_NOMEM = 3,        /* host or device allocation failed */
   BSMM_ERR_TIMEOUT = 4,      /* a kernel's bounded wait ran out (device error word) */
-  BSMM_ERR_UNSUPPORTED = 5,  /* a mode or size this build does not handle */
+  BSMM_ERR_UNSUPPORTED = 5,  /* a mode or size the library does not handle */
   BSMM_ERR_DEVICE = 6        /* a kernel check failed (device error word) */
 } bsmm_status;
 
