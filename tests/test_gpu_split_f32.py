@@ -147,3 +147,17 @@ def test_errors_are_reported():
     with pytest.raises(P.BsmmError):
         P.bsmm_status_device(plan)
     del first
+
+
+def test_deep_inner_blocks():
+    """Float32 elements with inner blocks deeper than the exact FP32 depth (700 and 1100
+    at 6 slices): the deep kernel form gives the float32 split oracle's bits."""
+    rng = np.random.default_rng(41)
+    r, q, c = np.array([50, 90], np.int32), np.array([700, 48, 1100], np.int32), np.array([30, 60], np.int32)
+    am, bm = np.ones((2, 3), np.uint8), np.ones((3, 2), np.uint8)
+    a_off, at = G.layout_arena(am, r, q)
+    b_off, bt = G.layout_arena(bm, q, c)
+    prob = G.as_float32(G.Problem("f32_deep", r, c, q, am, bm, a_off, b_off, rng.uniform(-1, 1, at),
+                                  rng.uniform(-1, 1, bt), 1.5, -0.25))
+    _, err = run_f32(prob, 6)
+    assert err <= 1.2e-7, err
