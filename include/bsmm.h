@@ -145,7 +145,8 @@ typedef struct {
                               even) and the epilogue runs in float32,
                               C = fl32(fl32(alpha*acc) + fl32(beta*C)). Execute with
                               bsmm_execute_f32, bsmm_execute_host or in a batch.
-                              BSMM_C128 (split modes, untransposed, one scale per tile): A, B
+                              BSMM_C128 (split modes; transposed storage and split_scale
+                              are taken as for float64): A, B
                               and C are complex double arenas passed to bsmm_execute as double
                               arrays of interleaved (re, im) pairs; offsets count complex
                               elements. Each tile takes one exponent over both parts; the
@@ -199,9 +200,8 @@ void bsmm_options_default(bsmm_options* opt);
  * BSMM_ERR_UNSUPPORTED for a split mode with more than 8192 inner blocks or more than
  * 2^22 inner elements in all (the 128-bit sums' headroom; a complex inner block of q
  * elements counts 2q), for a split mode with an inner block deeper than the exact FP32
- * accumulation depth (512 real lines for 6 slices) and store_warps = 1, and for an
- * element type the mode or storage does not take (float32 or complex elements in FP64
- * mode; complex elements transposed or with split_scale).
+ * accumulation depth (512 real lines for 6 slices) and store_warps = 1, and for
+ * float32 or complex elements in FP64 mode.
  */
 bsmm_status bsmm_plan(bsmm_plan_t* out, int32_t M, const int32_t* row_sizes, int32_t N,
                       const int32_t* col_sizes, int32_t K, const int32_t* inner_sizes,

@@ -158,7 +158,6 @@ def test_unsupported_combinations_are_rejected():
             P.bsmm_plan(*args, elem=P.BSMM_C128, **bad)
 
 
-
 def test_deep_complex_inner_block_runs_in_groups():
     """2 x 300 real inner lines exceed the 6-slice exact FP32 depth (512): the block is
     accumulated in several groups, with the complex oracle's bits."""
