@@ -336,7 +336,11 @@ bsmm_status bsmm_host_wait(bsmm_plan_t plan);
  * bsmm_batch_execute: issues the kernels of the whole batch on `stream`. FP64: one
  *   contraction launch. Split modes: the products are taken in waves whose slice
  *   workspaces fit in half of L2 (a larger product is a wave of its own); each wave
- *   issues its products' exponent and slicing kernels, then one contraction launch. It
+ *   issues its products' exponent and slicing kernels, then one contraction launch.
+ *   Consecutive waves go to `stream` and to a second stream of the batch in turn (the
+ *   second forked from `stream` before the first wave and joined back into it after the
+ *   last, with events), so a wave's slicing overlaps the end of the previous wave's
+ *   contraction; everything enqueued later on `stream` runs after the whole batch. It
  *   allocates, copies and synchronises nothing, so it can be captured into a CUDA
  *   graph and replayed. Products must not overlap in C.
  * bsmm_batch_query: units over the batch, summed useful flops, persistent bins (CTAs
@@ -406,7 +410,9 @@ bsmm_status bsmm_execute_batch(int32_t count, const bsmm_plan_t* plans, const do
  *   new plans share the slice workspace of the plans given to bsmm_batch_create, which
  *   must therefore still outlive the batch and must not run while the batch runs.
  *   chosen (nullable) receives the fastest candidate's index; ms (nullable, n entries)
- *   the median times in milliseconds, +infinity for a candidate that does not fit.
+ *   the median times in milliseconds, +infinity for a candidate that does not fit or
+ *   whose plans are refused (e.g. the form without store warps for a batch with inner
+ *   blocks deeper than the exact accumulation depth).
  *   Synchronises `stream`. Fails with BSMM_ERR_UNSUPPORTED when no candidate fits.
  */
 typedef struct {
